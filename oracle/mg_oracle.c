@@ -1,0 +1,420 @@
+/*
+ * CPU oracle for the mixed-precision multigrid-preconditioned iterative
+ * refinement of Oo & Vogel, "Accelerating Geometric Multigrid Preconditioning
+ * with Half-Precision Arithmetic on GPUs" (arXiv 2007.07539).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain FP64 statement of
+ * what the GPU library computes.  Only the test-suite, the package's smoke
+ * check and the benchmark's CPU-baseline leg may load it.  It shares no code,
+ * header, table or constant with the CUDA path, and imports nothing from it.
+ *
+ * Every routine is written directly from the paper's text, in FP64 (double),
+ * with no blocking, fusion or reordering beyond what the cited definition says:
+ *
+ *   or_apply_A        Poisson's equation (Sec. 5, Eq. 1) discretised by the
+ *                     finite-difference 5-point (2D) / 7-point (3D) stencil on
+ *                     the unit square/cube, zero Dirichlet boundary, h = 1/(n+1)
+ *   or_residual       IR step 1, r = b - A u (Sec. 4.1)
+ *   or_jacobi         damped Jacobi smoothing step (Sec. 4.2, smoother paragraph)
+ *   or_restrict       restriction of a residual to the next coarser grid
+ *                     (Alg. 1 step 2): full weighting
+ *   or_prolong_add    transfer of the coarse correction to the fine grid and
+ *                     update (Alg. 1 step 4): bi/trilinear interpolation
+ *   or_coarse_solve   exact solve on the base level (Sec. 4.2: "an exact solve
+ *                     is applied at the coarsest level")
+ *   or_cycle          Alg. 1 applied recursively (V-cycle; gamma = 2 gives the
+ *                     W-cycle)
+ *   or_ir_solve       Alg. 2, mixed-precision IR with residuum scaling; here all
+ *                     in FP64
+ *
+ * Grid vectors are interior-only, contiguous, x fastest:
+ *   index(i, j[, k]) = i + n*j [+ n*n*k], point ((i+1)h, (j+1)h[, (k+1)h]).
+ * Levels: level 0 is the coarsest, level L the finest; n_{l-1} = (n_l - 1)/2;
+ * fine 0-based index 2I+1 coincides with coarse 0-based index I.
+ *
+ * Parallelism: the stencil loops may run under OpenMP (each output point is
+ * computed independently, so results do not depend on the thread count);
+ * every reduction (norms, dot products) runs serially in index order.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAX_LEVELS 24
+
+typedef struct {
+    int dim;              /* 2 or 3 */
+    int n;                /* interior points per dimension on the finest level */
+    int levels;           /* 0 = as many as the coarsening rule allows */
+    int nu1, nu2;         /* pre- and post-smoothing steps */
+    int gamma;            /* 1 = V-cycle, 2 = W-cycle */
+    double omega;         /* Jacobi damping */
+    int scaling;          /* 0: alpha = 1; 1: alpha = ||r||_inf; 2: alpha = ||r||_2 */
+    int tol_mode;         /* 0: ||r||_2 <= tol*||b||_2; 1: ||r||_2 < tol */
+    double tol;
+    int max_iter;
+    int true_residual_guard; /* 1: confirm convergence with b - A u */
+    int nthreads;         /* OpenMP threads for stencil loops (<= 0: 1) */
+} or_params;
+
+typedef struct {
+    int iters;            /* IR iterations performed */
+    int converged;        /* 1 if the stopping test held for b - A u */
+    int levels;           /* levels used */
+    double bnorm;         /* ||b||_2 */
+    double rel_res;       /* last recursive ||r||_2 / ||b||_2 */
+    double rel_res_true;  /* ||b - A u||_2 / ||b||_2 at exit */
+    int guard_restarts;   /* times the true residual replaced the recursive one */
+} or_result;
+
+static int g_threads = 1;
+
+static size_t npts(int d, int n) { return d == 2 ? (size_t)n * n : (size_t)n * n * n; }
+
+/* Value of v at (i, j, k); zero outside the interior (Dirichlet boundary). */
+static double at(const double *v, int d, int n, int i, int j, int k) {
+    if (i < 0 || i >= n || j < 0 || j >= n) return 0.0;
+    if (d == 2) return v[(size_t)j * n + i];
+    if (k < 0 || k >= n) return 0.0;
+    return v[((size_t)k * n + j) * n + i];
+}
+
+/*
+ * (A v)_p = h^-2 * (2d v_p - sum of the 2d axis neighbours of p), the standard
+ * second-order finite-difference approximation of -Laplace(v) (Sec. 5, Eq. 1).
+ * With absmode != 0 the neighbour coefficients are taken as +1: this gives
+ * |A| |v|, the magnitude used to scale rounding tolerances.
+ */
+void or_apply_A_mode(int d, int n, const double *v, double *out, int absmode) {
+    const double h = 1.0 / (n + 1);
+    const double ih2 = 1.0 / (h * h);
+    const double sgn = absmode ? 1.0 : -1.0;
+    const int nk = d == 3 ? n : 1;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double nb = at(v, d, n, i - 1, j, k) + at(v, d, n, i + 1, j, k)
+                          + at(v, d, n, i, j - 1, k) + at(v, d, n, i, j + 1, k);
+                if (d == 3) nb += at(v, d, n, i, j, k - 1) + at(v, d, n, i, j, k + 1);
+                double c = at(v, d, n, i, j, k);
+                if (absmode) c = fabs(c), nb = 0.0
+                    + fabs(at(v, d, n, i - 1, j, k)) + fabs(at(v, d, n, i + 1, j, k))
+                    + fabs(at(v, d, n, i, j - 1, k)) + fabs(at(v, d, n, i, j + 1, k))
+                    + (d == 3 ? fabs(at(v, d, n, i, j, k - 1)) + fabs(at(v, d, n, i, j, k + 1)) : 0.0);
+                size_t p = d == 2 ? (size_t)j * n + i : ((size_t)k * n + j) * n + i;
+                out[p] = ih2 * (2.0 * d * c + sgn * nb);
+            }
+}
+
+void or_apply_A(int d, int n, const double *v, double *out) { or_apply_A_mode(d, n, v, out, 0); }
+
+/* IR step 1 (Sec. 4.1): r = b - A u. */
+void or_residual(int d, int n, const double *b, const double *u, double *r) {
+    size_t N = npts(d, n);
+    double *au = (double *)malloc(N * sizeof(double));
+    or_apply_A(d, n, u, au);
+    for (size_t p = 0; p < N; ++p) r[p] = b[p] - au[p];
+    free(au);
+}
+
+/*
+ * One damped Jacobi step (Sec. 4.2): out = v + omega D^-1 (g - A v), with
+ * D = diag(A) = 2d/h^2.  The update is simultaneous: out must not alias v.
+ */
+void or_jacobi(int d, int n, double omega, const double *g, const double *v, double *out) {
+    const double h = 1.0 / (n + 1);
+    const double dinv = h * h / (2.0 * d);
+    size_t N = npts(d, n);
+    double *av = (double *)malloc(N * sizeof(double));
+    or_apply_A(d, n, v, av);
+    for (size_t p = 0; p < N; ++p) out[p] = v[p] + omega * dinv * (g[p] - av[p]);
+    free(av);
+}
+
+/* 1-D full-weighting weight of fine offset o in {-1, 0, 1}: [1/4, 1/2, 1/4]. */
+static double fw(int o) { return o == 0 ? 0.5 : 0.25; }
+
+/*
+ * Restriction (Alg. 1 step 2): full weighting, the tensor product of the 1-D
+ * stencil [1/4, 1/2, 1/4] centred on the fine point 2I+1 that coincides with
+ * coarse point I.  nf = 2 nc + 1.
+ */
+void or_restrict(int d, int nf, const double *rf, double *gc) {
+    const int nc = (nf - 1) / 2;
+    const int nk = d == 3 ? nc : 1;
+    const int ok0 = d == 3 ? -1 : 0, ok1 = d == 3 ? 1 : 0;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int K = 0; K < nk; ++K)
+        for (int J = 0; J < nc; ++J)
+            for (int I = 0; I < nc; ++I) {
+                double s = 0.0;
+                for (int ok = ok0; ok <= ok1; ++ok)
+                    for (int oj = -1; oj <= 1; ++oj)
+                        for (int oi = -1; oi <= 1; ++oi) {
+                            double w = fw(oi) * fw(oj) * (d == 3 ? fw(ok) : 1.0);
+                            s += w * at(rf, d, nf, 2 * I + 1 + oi, 2 * J + 1 + oj, 2 * K + 1 + ok);
+                        }
+                size_t p = d == 2 ? (size_t)J * nc + I : ((size_t)K * nc + J) * nc + I;
+                gc[p] = s;
+            }
+}
+
+/*
+ * 1-D linear interpolation from coarse to fine at fine 0-based index i:
+ * an odd index 2I+1 takes coarse I; an even index 2I lies between coarse I-1
+ * and I and takes their mean (coarse values outside the grid are zero).
+ * Returns the number of contributing coarse indices (1 or 2) in *cnt and
+ * fills idx/wt.
+ */
+static void lin1d(int i, int *cnt, int idx[2], double wt[2]) {
+    if (i % 2 == 1) { *cnt = 1; idx[0] = (i - 1) / 2; wt[0] = 1.0; }
+    else { *cnt = 2; idx[0] = i / 2 - 1; idx[1] = i / 2; wt[0] = wt[1] = 0.5; }
+}
+
+/*
+ * Prolongation and correction (Alg. 1 step 4): cf += P cc, with P the
+ * tensor-product (bi/trilinear) interpolation.  nf = 2 nc + 1.
+ */
+void or_prolong_add(int d, int nc, const double *cc, double *cf) {
+    const int nf = 2 * nc + 1;
+    const int nk = d == 3 ? nf : 1;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < nf; ++j)
+            for (int i = 0; i < nf; ++i) {
+                int ci, cj, ck = 1, ii[2], jj[2], kk[2] = {0, 0};
+                double wi[2], wj[2], wk[2] = {1.0, 1.0};
+                lin1d(i, &ci, ii, wi);
+                lin1d(j, &cj, jj, wj);
+                if (d == 3) lin1d(k, &ck, kk, wk);
+                double s = 0.0;
+                for (int c = 0; c < ck; ++c)
+                    for (int b = 0; b < cj; ++b)
+                        for (int a = 0; a < ci; ++a)
+                            s += wi[a] * wj[b] * wk[c] * at(cc, d, nc, ii[a], jj[b], kk[c]);
+                size_t p = d == 2 ? (size_t)j * nf + i : ((size_t)k * nf + j) * nf + i;
+                cf[p] += s;
+            }
+}
+
+/*
+ * Exact base-level solve (Sec. 4.2): assemble the dense matrix of A on the
+ * n^d grid column by column (A applied to unit vectors), factor it by
+ * Cholesky (A is symmetric positive definite) and solve.  Returns 0 on
+ * success, -1 if the factorisation breaks down or n^d is too large.
+ */
+int or_coarse_solve(int d, int n, const double *g, double *c) {
+    size_t m = npts(d, n);
+    if (m > 4096) return -1;
+    double *A = (double *)calloc(m * m, sizeof(double));
+    double *e = (double *)calloc(m, sizeof(double));
+    double *col = (double *)malloc(m * sizeof(double));
+    double *y = (double *)malloc(m * sizeof(double));
+    int saved = g_threads;
+    g_threads = 1;
+    for (size_t q = 0; q < m; ++q) {
+        e[q] = 1.0;
+        or_apply_A(d, n, e, col);
+        for (size_t p = 0; p < m; ++p) A[p * m + q] = col[p];
+        e[q] = 0.0;
+    }
+    g_threads = saved;
+    int rc = 0;
+    /* Cholesky A = L L^T, L stored in the lower triangle of A. */
+    for (size_t j = 0; j < m && rc == 0; ++j) {
+        double s = A[j * m + j];
+        for (size_t k = 0; k < j; ++k) s -= A[j * m + k] * A[j * m + k];
+        if (!(s > 0.0)) { rc = -1; break; }
+        double ljj = sqrt(s);
+        A[j * m + j] = ljj;
+        for (size_t i = j + 1; i < m; ++i) {
+            double t = A[i * m + j];
+            for (size_t k = 0; k < j; ++k) t -= A[i * m + k] * A[j * m + k];
+            A[i * m + j] = t / ljj;
+        }
+    }
+    if (rc == 0) {
+        for (size_t i = 0; i < m; ++i) {           /* L y = g */
+            double t = g[i];
+            for (size_t k = 0; k < i; ++k) t -= A[i * m + k] * y[k];
+            y[i] = t / A[i * m + i];
+        }
+        for (size_t ii = m; ii-- > 0;) {           /* L^T c = y */
+            double t = y[ii];
+            for (size_t k = ii + 1; k < m; ++k) t -= A[k * m + ii] * c[k];
+            c[ii] = t / A[ii * m + ii];
+        }
+    }
+    free(A); free(e); free(col); free(y);
+    return rc;
+}
+
+/* Coarsening rule: n_{l-1} = (n_l - 1)/2 while n_l is odd and > 3.
+ * Fills sizes[0..L] with sizes[L] = n (finest) and returns the level count. */
+int or_level_sizes(int n, int levels_req, int *sizes) {
+    int tmp[OR_MAX_LEVELS], cnt = 0, m = n;
+    tmp[cnt++] = m;
+    while (m % 2 == 1 && m > 3 && cnt < OR_MAX_LEVELS && (levels_req <= 0 || cnt < levels_req)) {
+        m = (m - 1) / 2;
+        tmp[cnt++] = m;
+    }
+    for (int l = 0; l < cnt; ++l) sizes[l] = tmp[cnt - 1 - l];
+    return cnt;
+}
+
+typedef struct {
+    int d, L;
+    int n[OR_MAX_LEVELS];
+    double *c[OR_MAX_LEVELS], *g[OR_MAX_LEVELS], *t[OR_MAX_LEVELS];
+} or_hier;
+
+/*
+ * Alg. 1 applied recursively on level l, with c the initial guess on entry
+ * (zero at the first visit) and the approximate solution of A_l c = g on exit.
+ *   step 1: nu1 damped Jacobi sweeps
+ *   step 2: residual g - A_l c, restricted to level l-1
+ *   step 3: coarse correction by gamma visits of the same cycle on level l-1
+ *           (gamma = 1: V-cycle); the base level is solved exactly
+ *   step 4: prolongation of the coarse correction and update of c
+ *   step 5: nu2 damped Jacobi sweeps
+ */
+static int cycle(or_hier *H, const or_params *P, int l) {
+    int d = H->d, n = H->n[l];
+    size_t N = npts(d, n);
+    double *c = H->c[l], *g = H->g[l], *t = H->t[l];
+    if (l == 0) return or_coarse_solve(d, n, g, c);
+    for (int s = 0; s < P->nu1; ++s) { or_jacobi(d, n, P->omega, g, c, t); memcpy(c, t, N * sizeof(double)); }
+    or_residual(d, n, g, c, t);
+    or_restrict(d, n, t, H->g[l - 1]);
+    memset(H->c[l - 1], 0, npts(d, H->n[l - 1]) * sizeof(double));
+    for (int k = 0; k < P->gamma; ++k) { int rc = cycle(H, P, l - 1); if (rc) return rc; }
+    or_prolong_add(d, H->n[l - 1], H->c[l - 1], c);
+    for (int s = 0; s < P->nu2; ++s) { or_jacobi(d, n, P->omega, g, c, t); memcpy(c, t, N * sizeof(double)); }
+    return 0;
+}
+
+static int hier_alloc(or_hier *H, const or_params *P) {
+    memset(H, 0, sizeof(*H));
+    H->d = P->dim;
+    int cnt = or_level_sizes(P->n, P->levels, H->n);
+    H->L = cnt - 1;
+    for (int l = 0; l < cnt; ++l) {
+        size_t N = npts(H->d, H->n[l]);
+        H->c[l] = (double *)calloc(N, sizeof(double));
+        H->g[l] = (double *)calloc(N, sizeof(double));
+        H->t[l] = (double *)calloc(N, sizeof(double));
+        if (!H->c[l] || !H->g[l] || !H->t[l]) return -1;
+    }
+    return 0;
+}
+
+static void hier_free(or_hier *H) {
+    for (int l = 0; l <= H->L; ++l) { free(H->c[l]); free(H->g[l]); free(H->t[l]); }
+}
+
+/*
+ * One multigrid cycle as a preconditioner: c = MG(g) with zero initial guess
+ * on the finest level.  Exposed for the contraction-factor pin and for
+ * per-cycle parity checks.  Returns the level count, or -1 on failure.
+ */
+int or_mg_cycle(const or_params *P, const double *g, double *c) {
+    or_hier H;
+    g_threads = P->nthreads > 0 ? P->nthreads : 1;
+    if (hier_alloc(&H, P)) { hier_free(&H); return -1; }
+    size_t N = npts(P->dim, P->n);
+    memcpy(H.g[H.L], g, N * sizeof(double));
+    memcpy(H.c[H.L], c, N * sizeof(double));
+    int rc = cycle(&H, P, H.L);
+    memcpy(c, H.c[H.L], N * sizeof(double));
+    int L = H.L;
+    hier_free(&H);
+    return rc ? -1 : L + 1;
+}
+
+double or_norm2(size_t N, const double *v) {
+    double s = 0.0;
+    for (size_t p = 0; p < N; ++p) s += v[p] * v[p];
+    return sqrt(s);
+}
+
+double or_norminf(size_t N, const double *v) {
+    double m = 0.0;
+    for (size_t p = 0; p < N; ++p) { double a = fabs(v[p]); if (a > m) m = a; }
+    return m;
+}
+
+/*
+ * Alg. 2: iterative refinement with residuum scaling and one multigrid cycle
+ * per step, all in FP64.
+ *   r = b - A u
+ *   while the stopping test fails:
+ *     alpha = ||r|| (inf-norm, 2-norm, or 1 without scaling)
+ *     g = (1/alpha) r                       (Alg. 2 line 4)
+ *     c = one multigrid cycle for A c = g   (line 5)
+ *     u = u + alpha c                       (line 6)
+ *     r = r - alpha A c                     (line 7)
+ * When the recursive residual passes the test, b - A u is recomputed; if it
+ * fails the test the loop continues from that true residual.
+ * history (optional, max_iter+1 entries) receives ||r||_2/||b||_2 before each
+ * step and after the last.  Returns 0 on convergence, 1 if max_iter was hit,
+ * -1 on failure (allocation, base solve, non-finite residual).
+ */
+int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, double *history) {
+    or_hier H;
+    g_threads = P->nthreads > 0 ? P->nthreads : 1;
+    memset(res, 0, sizeof(*res));
+    if (hier_alloc(&H, P)) { hier_free(&H); return -1; }
+    res->levels = H.L + 1;
+    const int d = P->dim, n = P->n;
+    size_t N = npts(d, n);
+    double *r = (double *)malloc(N * sizeof(double));
+    double *ac = (double *)malloc(N * sizeof(double));
+    int status = 1;
+    or_residual(d, n, b, u, r);
+    double bnorm = or_norm2(N, b);
+    res->bnorm = bnorm;
+    double scale = P->tol_mode == 0 ? bnorm : 1.0;
+    int it = 0;
+    for (;;) {
+        double rn = or_norm2(N, r);
+        if (!isfinite(rn)) { status = -1; break; }
+        if (history) history[it] = bnorm > 0 ? rn / bnorm : rn;
+        res->rel_res = bnorm > 0 ? rn / bnorm : rn;
+        if (rn <= P->tol * scale) {
+            if (!P->true_residual_guard) { status = 0; break; }
+            or_residual(d, n, b, u, ac);
+            double tn = or_norm2(N, ac);
+            if (tn <= P->tol * scale) { status = 0; break; }
+            memcpy(r, ac, N * sizeof(double));
+            res->guard_restarts++;
+            rn = tn;
+            res->rel_res = bnorm > 0 ? rn / bnorm : rn;
+            if (history) history[it] = res->rel_res;
+        }
+        if (it >= P->max_iter) { status = 1; break; }
+        double alpha = 1.0;
+        if (P->scaling == 1) alpha = or_norminf(N, r);
+        else if (P->scaling == 2) alpha = rn;
+        if (!(alpha > 0.0)) { status = -1; break; }
+        double inv = 1.0 / alpha;
+        double *g = H.g[H.L], *c = H.c[H.L];
+        for (size_t p = 0; p < N; ++p) g[p] = inv * r[p];
+        memset(c, 0, N * sizeof(double));
+        if (cycle(&H, P, H.L)) { status = -1; break; }
+        for (size_t p = 0; p < N; ++p) u[p] = u[p] + alpha * c[p];
+        or_apply_A(d, n, c, ac);
+        for (size_t p = 0; p < N; ++p) r[p] = r[p] - alpha * ac[p];
+        ++it;
+    }
+    res->iters = it;
+    res->converged = status == 0;
+    or_residual(d, n, b, u, ac);
+    res->rel_res_true = bnorm > 0 ? or_norm2(N, ac) / bnorm : or_norm2(N, ac);
+    free(r); free(ac);
+    hier_free(&H);
+    return status;
+}
