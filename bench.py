@@ -1,0 +1,300 @@
+#!/usr/bin/env python3
+"""Benchmark of the mixed-precision multigrid-preconditioned iterative refinement.
+
+Workload (one "step" = one complete solve to relative FP64 residual 1e-10):
+3D Poisson, 7-point finite differences, zero Dirichlet boundary, 255^3
+interior points (16,581,375 DOF), f ~ U[-1, 1) from SplitMix64 seed 2 (seed
+2 + rank on other ranks), u0 = 0.  Preconditioner: one V(2,2) cycle per IR
+step, damped Jacobi omega = 0.8, full weighting / trilinear transfers, exact
+3^3 base solve, every level stored in FP16 with FP32 sweep arithmetic (H_MG),
+residual scaled by 2^14/||r||_inf before the cast; FP64 refinement.  The same
+solve with all levels in FP64 (D_MG, no scaling) is timed beside it.
+
+Metric: DOF/s to relative residual 1e-10 (whole job: DOF solved by all ranks
+per second of the slowest rank).  Each step flushes L2 (256 MiB write) before
+it starts; the inputs (b, u: 133 MB each in FP64) are also larger than L2.
+
+JSON line keys follow the benchmark contract: value / ms_per_step from the
+library's CUDA events around each solve (device time, inputs resident in
+HBM), e2e through the same C-ABI call with pinned host buffers (H2D of b and
+D2H of u inside the timed region), roofline of the dominant kernel from CUDA
+events around every kernel of a profiled solve, cpu_baseline from the FP64
+oracle on the host cores, clocks sampled with nvidia-smi during the timed
+region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIM, N, SEED, TOL = 3, 255, 2, 1e-10
+METRIC = "DOF/s to rel. residual 1e-10: mixed-FP16 MG-IR vs FP64 MG; stencil HBM % peak"
+WORKLOAD = ("3D Poisson 7-point FDM, zero Dirichlet, 255^3 interior (16,581,375 DOF), f~U[-1,1) seed 2; "
+            "H_MG: V(2,2) damped-Jacobi (omega 0.8) MG preconditioner with all 7 levels in FP16 "
+            "(FP32 in-sweep accumulation), residual scaled by 2^14/||r||_inf before the FP16 cast, "
+            "FP64 iterative refinement to rel. residual 1e-10; compared with all-FP64 MG (D_MG)")
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.rows, self.proc = [], None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def oracle_iters(name: str) -> int:
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_solves.json")) as f:
+        return int(json.load(f)[name]["iters"])
+
+
+def cpu_oracle_sample(b, steps: int = 1):
+    """The FP64 oracle on the same 255^3 workload, bounded: solves with max_iter = 0
+    (initial and final residual) and max_iter = 1 are timed; the per-step cost is their
+    difference and DOF/s to 1e-10 is extrapolated with the oracle's own iteration count
+    for this workload (tests/golden/oracle_solves.json, written by the oracle)."""
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    iters = oracle_iters("3d_n255_random_seed2")
+    t0s, t1s = [], []
+    for _ in range(steps):
+        t = time.perf_counter()
+        O.ir_solve(b, max_iter=0, nthreads=cores)
+        t0s.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        O.ir_solve(b, max_iter=1, nthreads=cores)
+        t1s.append(time.perf_counter() - t)
+    t0, t1 = min(t0s), min(t1s)
+    t_solve = t0 + iters * max(t1 - t0, 0.0)
+    dofs = b.size / t_solve
+    sample = (f"oracle FP64 IR on the 255^3 workload, {cores} threads: solves with 0 and 1 IR steps timed "
+              f"({t0:.2f} s, {t1:.2f} s), extrapolated to the oracle's {iters} steps ({t_solve:.1f} s per solve)")
+    return dofs, cores, sample, t0 + t1
+
+
+def reference_arm(args):
+    """--impl reference: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
+    import numpy as np  # noqa: F401
+    from paper_2007_07539_gb300 import inputs as I
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    b = I.random_rhs(DIM, N, SEED)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(b, 1)
+    vals, walls = [], []
+    sample = cores = None
+    for _ in range(args.steps):
+        v, cores, sample, wall = cpu_oracle_sample(b, 1)
+        vals.append(v)
+        walls.append(wall)
+    value = statistics.median(vals)
+    line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(walls), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD.replace("H_MG", "reference: FP64 CPU oracle of the same method; H_MG")},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2007_07539_gb300 import inputs as I
+    from paper_2007_07539_gb300 import mg
+
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def allmax(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ndof = N**DIM
+    b = I.random_rhs(DIM, N, SEED + rank)
+    bd = torch.from_numpy(b).cuda()
+    ud = torch.zeros_like(bd)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    hH = mg.Hierarchy(mg.make_params(DIM, N, "H", zero_guess=1))
+    hD = mg.Hierarchy(mg.make_params(DIM, N, "D", zero_guess=1, scaling=0))
+
+    def run(h, bb, uu, k):
+        secs, res = [], None
+        for _ in range(k):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            res = h.solve(bb, uu)
+            if res["status"] != 0:
+                raise RuntimeError(f"solve failed: {res}")
+            secs.append(res["seconds"])
+        return secs, res
+
+    run(hH, bd, ud, args.warmup)
+    run(hD, bd, ud, max(1, min(args.warmup, 2)))
+
+    # timed region: H_MG solves, device time from the library's CUDA events
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    t_wall = time.perf_counter()
+    secs, resH = run(hH, bd, ud, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clocks = clk.stop()
+    launches = resH["launches"] * args.steps
+    t_dev = allmax(sum(secs))
+    value = world * ndof * args.steps / t_dev
+    uH = ud.cpu().numpy().copy()
+
+    # all-FP64 MG on the same grid
+    secsD, resD = run(hD, bd, ud, max(1, min(args.steps, 3)))
+    tD = allmax(sum(secsD) / len(secsD))
+    valueD = world * ndof / tD
+    uD = ud.cpu().numpy()
+    rel_diff = float(np.linalg.norm(uH - uD) / np.linalg.norm(uD))
+
+    # end to end: the same C-ABI call on pinned host buffers (H2D of b, D2H of u timed)
+    bh = torch.from_numpy(b).pin_memory()
+    uh = torch.zeros_like(bh).pin_memory()
+    run(hH, bh, uh, 1)
+    secsE, _ = run(hH, bh, uh, args.steps)
+    e2e = world * ndof * args.steps / allmax(sum(secsE))
+
+    # per-kernel device times of one profiled solve (events around every kernel)
+    resP, ktimes = hH.profile_solve(bd, ud)
+    top = max(ktimes, key=lambda k: k["total_ms"])
+    tot_ms = sum(k["total_ms"] for k in ktimes)
+    peak, peak_kind = measured_peaks()
+    ach = top["bytes"] * top["launches"] / (top["total_ms"] * 1e-3) / 1e9
+    finest = max(k["level"] for k in ktimes)
+    sweeps = [k for k in ktimes if k["kind"] == 0 and k["level"] == finest and k["mode"] in (0, 1, 3)]
+    sweep_bytes = sum(k["bytes"] * k["launches"] for k in sweeps)
+    sweep_ms = sum(k["total_ms"] for k in sweeps)
+    byshare = sorted(ktimes, key=lambda k: -k["total_ms"])[:8]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16 storage / f32 sweeps / f64 refinement",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dof": ndof, "iters_fp16": resH["iters"], "iters_fp64": resD["iters"],
+                   "oracle_iters": oracle_iters("3d_n255_random_seed2"),
+                   "rel_res_true_fp16": resH["rel_res_true"], "rel_res_true_fp64": resD["rel_res_true"],
+                   "fp64_mg_dofs": valueD, "fp64_mg_ms": 1e3 * tD, "speedup_fp16_vs_fp64": value / valueD,
+                   "rel_diff_u_fp16_vs_fp64": rel_diff, "l2": "256 MiB L2 flush before every step; "
+                   "b and u (133 MB each) exceed the 129 MB L2", "wall_s_timed_region": wall,
+                   "parallelism": f"{world} independent instance(s), one per GPU, no collective on the data path",
+                   "finest_sweeps_gbs": sweep_bytes / (sweep_ms * 1e-3) / 1e9 if sweep_ms else None,
+                   "kernel_shares": [{"kernel": f"{k['name']}@L{k['level']}", "ms": round(k["total_ms"], 4),
+                                      "share": round(k["total_ms"] / tot_ms, 4),
+                                      "gbs": round(k["bytes"] * k["launches"] / max(k["total_ms"], 1e-9) / 1e6, 1)}
+                                     for k in byshare]},
+        "roofline": {"bound": "hbm", "kernel": f"{top['name']} level {top['level']}", "achieved": ach,
+                     "peak": peak, "peak_source": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None, "bytes_per_launch": top["bytes"],
+                     "avg_launch_ms": top["total_ms"] / max(top["launches"], 1)},
+        "e2e": {"value": e2e, "unit": "DOF/s", "h2d_bytes_per_step": ndof * 8, "d2h_bytes_per_step": ndof * 8},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample, _ = cpu_oracle_sample(b, 1)
+        line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    hH.close()
+    hD.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,252 @@
+/*
+ * mg.h - C ABI of libmgfp, a GB300 (sm_103a) solver for finite-difference
+ * Poisson problems by mixed-precision iterative refinement preconditioned with
+ * one geometric-multigrid cycle per step.
+ *
+ * Method: K. L. Oo and A. Vogel, "Accelerating Geometric Multigrid
+ * Preconditioning with Half-Precision Arithmetic on GPUs", arXiv 2007.07539.
+ *   - Iterative refinement (IR), Sec. 4.1: r = b - A u; solve A c = r
+ *     approximately; u = u + c.
+ *   - Multigrid cycle, Sec. 4.2 and Alg. 1: damped-Jacobi pre-smoothing,
+ *     residual, restriction with a precision change, coarse correction,
+ *     prolongation with a precision change, post-smoothing; exact solve on the
+ *     coarsest (base) level; recursion gives the V-cycle (gamma = 2: W-cycle).
+ *   - Per-level precisions, Table 2 and Fig. 1 (D_MG, H_MG, HSD_MG, DSH_MG).
+ *   - Mixed-precision IR with residuum scaling, Sec. 4.3 and Alg. 2:
+ *     alpha = ||r||; r_low = (1/alpha) r_high; one cycle gives c_low;
+ *     u += alpha c_low; r -= alpha A c_low, with r, u and the stopping test in FP64.
+ *   - Model problem, Sec. 5 (Eq. 1): -Laplace(u) = f on the unit square/cube,
+ *     u = 0 on the boundary.  Here discretised by the 5-point (2D) / 7-point
+ *     (3D) finite-difference stencil on n interior points per dimension,
+ *     h = 1/(n+1):  (A u)_p = h^-2 (2d u_p - sum of the 2d axis neighbours).
+ *
+ * Conventions for every entry point:
+ *   - Grid vectors passed by the caller (b, u) are interior-only, contiguous,
+ *     FP64, x fastest: element (i, j[, k]) at i + n*j [+ n*n*k], i.e. the
+ *     C-order layout of an array of shape (n, n[, n]) indexed [k][j][i].
+ *   - Pointers may be device pointers (cudaMalloc / torch CUDA tensors) or
+ *     host pointers (pinned or pageable); the library detects which with
+ *     cudaPointerGetAttributes and copies host data through its own device
+ *     staging buffers on the hierarchy's stream.  The caller keeps ownership.
+ *   - Every call returns an mg_status; nothing throws across the ABI.  On an
+ *     error mg_last_error() returns a message for the calling thread.
+ *   - A hierarchy is bound to the device that was current at creation and to
+ *     the CUDA stream given there.  Calls on one hierarchy must not run
+ *     concurrently from several host threads.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_ABI_VERSION 1
+#define MG_MAX_LEVELS 16
+
+/* Storage precision of one multigrid level (Table 2, Fig. 1).  Arithmetic
+ * inside a sweep is FP32 for FP16/BF16/FP32 levels and FP64 for FP64 levels. */
+typedef enum { MG_FP64 = 0, MG_FP32 = 1, MG_FP16 = 2, MG_BF16 = 3 } mg_prec;
+
+typedef enum {
+    MG_OK = 0,
+    MG_BUSY = 1,               /* mg_poll: request still running */
+    MG_ERR_INVALID = 2,        /* bad argument or parameter */
+    MG_ERR_OOM = 3,            /* device allocation failed */
+    MG_ERR_CUDA = 4,           /* a CUDA call failed */
+    MG_ERR_NOT_CONVERGED = 5,  /* max_iter reached, or the residual stagnated */
+    MG_ERR_NUMERIC = 6,        /* non-finite residual */
+    MG_ERR_TIMEOUT = 7,        /* a bounded device wait expired */
+    MG_ERR_ADMISSION = 8       /* request can never fit the memory budget */
+} mg_status;
+
+/* Solver parameters.  Fill with mg_params_init() and then override fields. */
+typedef struct mg_params {
+    int32_t dim;        /* 2 or 3 */
+    int32_t n;          /* interior points per dimension on the finest level (>= 1) */
+    int32_t levels;     /* number of levels; 0 = as many as the coarsening rule allows.
+                           Rule: n_{l-1} = (n_l - 1)/2 while n_l is odd and > 3; the
+                           coarsest level must have at most 4096 unknowns */
+    int32_t prec[MG_MAX_LEVELS]; /* mg_prec per level, prec[0] = coarsest (base level),
+                           prec[levels-1] = finest; default all MG_FP64 (D_MG) */
+    int32_t nu1, nu2;   /* pre-/post-smoothing sweeps (Alg. 1 steps 1 and 5); default 2, 2 */
+    double omega;       /* Jacobi damping; default 0.8 (the paper uses 2/3, Sec. 4.2) */
+    int32_t gamma;      /* coarse visits per level: 1 = V-cycle (default), 2 = W-cycle */
+    int32_t scaling;    /* Alg. 2 line 4 scale alpha: 0 = none (alpha = 1, the paper's
+                           choice for D_MG, Sec. 6), 1 = ||r||_inf (default), 2 = ||r||_2 */
+    int32_t sigma_log2; /* the scaled residual is r * 2^sigma_log2 / alpha, so its inf-norm
+                           is 2^sigma_log2 (scaling = 1); -1 = automatic: 14 when any
+                           level is FP16, else 0.  Ignored when scaling = 0 */
+    int32_t tol_mode;   /* 0: stop when ||r||_2 <= tol ||b||_2 (default);
+                           1: stop when ||r||_2 < tol (the paper's absolute test, Sec. 6) */
+    double tol;         /* default 1e-10 */
+    int32_t max_iter;   /* IR step limit; default 100, at most 1000 */
+    int32_t zero_guess; /* 1: ignore u on entry and start from u0 = 0 (default 0) */
+    int32_t guard;      /* 1 (default): when the recursively updated residual passes the
+                           test, recompute b - A u in FP64 and continue from it if it fails */
+    int32_t graph;      /* 1 (default): run each IR step as one CUDA graph launch */
+    int32_t reserved[8];
+} mg_params;
+
+/* Outcome of one solve. */
+typedef struct mg_result {
+    int32_t iters;          /* IR steps performed */
+    int32_t status;         /* mg_status of the solve */
+    int32_t levels;         /* levels used */
+    int32_t guard_restarts; /* times the true residual replaced the recursive one */
+    int32_t launches;       /* kernels of this library launched by the solve */
+    int32_t reserved;
+    double rel_res;         /* recursive ||r||_2 / ||b||_2 at exit */
+    double rel_res_true;    /* ||b - A u||_2 / ||b||_2 at exit, computed in FP64 */
+    double bnorm;           /* ||b||_2 */
+    double seconds;         /* device time of the solve (CUDA events) */
+} mg_result;
+
+typedef struct mg_hierarchy mg_hierarchy; /* opaque; owns all device state of a solver */
+
+/* Describes one level of a hierarchy (for tests and diagnostics). */
+typedef struct mg_level_info {
+    int32_t n;        /* interior points per dimension */
+    int32_t prec;     /* mg_prec */
+    int32_t pitch;    /* row pitch of the padded device layout, in elements */
+    int32_t reserved;
+    size_t bytes;     /* device bytes held for this level */
+} mg_level_info;
+
+/* ---------------------------------------------------------------- basics */
+
+/* Fills *p with the defaults listed above for the given dim and n. */
+void mg_params_init(mg_params* p, int32_t dim, int32_t n);
+
+/* Number of levels the coarsening rule gives for n (levels_req = 0) or the
+ * smaller of that and levels_req; fills sizes[0..count-1] (coarsest first)
+ * when sizes is not NULL.  Returns 0 for invalid n. */
+int32_t mg_level_count(int32_t n, int32_t levels_req, int32_t* sizes);
+
+/* Message describing the last error on this host thread ("" if none). */
+const char* mg_last_error(void);
+
+/* Device bytes a hierarchy with these parameters will hold (0 if invalid). */
+size_t mg_footprint_bytes(const mg_params* p);
+
+/* ---------------------------------------------------------------- the five calls */
+
+/* Creates a hierarchy: level geometry, per-level precision ladder, padded
+ * device buffers, the dense FP64 inverse of the base-level operator and the
+ * launch schedule of one IR step.  `cuda_stream` is a cudaStream_t (NULL =
+ * the legacy default stream) on which every later call of this hierarchy
+ * runs.  Host-side setup only: nothing here is part of a solve's time.
+ * Errors: MG_ERR_INVALID (parameters), MG_ERR_OOM, MG_ERR_CUDA. */
+mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, mg_hierarchy** out);
+
+/* Solves A u = b (Alg. 2).  b: n^d FP64 values, read only.  u: n^d FP64
+ * values, in: initial guess (ignored when zero_guess = 1), out: solution.
+ * Blocks until the solve has finished.  Returns the solve status (also in
+ * res->status): MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_NUMERIC, or a CUDA error.
+ * On a failed solve u holds the last iterate.  res may be NULL. */
+mg_status mg_solve(mg_hierarchy* h, const double* b, double* u, mg_result* res);
+
+/* Queues a solve of A u = b on hierarchy h and returns at once with a ticket.
+ * Requests are admitted to the device by a memory budget (see
+ * mg_serve_configure); admitted requests run concurrently with other
+ * requests of other hierarchies and with new arrivals.  b and u must stay
+ * valid until mg_poll reports completion.  Errors: MG_ERR_INVALID,
+ * MG_ERR_ADMISSION (the request's footprint exceeds the whole budget). */
+mg_status mg_submit(mg_hierarchy* h, const double* b, double* u, uint64_t* ticket);
+
+/* Completion test for a ticket of mg_submit: MG_BUSY while queued or running;
+ * otherwise the solve's status, with the result in *res (may be NULL).  A
+ * completed ticket may be polled again until mg_destroy. */
+mg_status mg_poll(mg_hierarchy* h, uint64_t ticket, mg_result* res);
+
+/* Waits for outstanding requests of h, then frees all its device and host
+ * state.  NULL is accepted. */
+mg_status mg_destroy(mg_hierarchy* h);
+
+/* ---------------------------------------------------------------- serving and batching */
+
+/* Sets the serving engine's device-memory budget for request working sets
+ * (bytes; 0 = 80% of the free device memory at the first submit) and the
+ * maximum number of requests in flight (0 = 16).  Call before the first
+ * mg_submit of the process. */
+mg_status mg_serve_configure(size_t budget_bytes, int32_t max_inflight);
+
+/* Solves `count` independent problems together, one per hierarchy, with
+ * level-synchronous launches: each launch of a given kernel covers that
+ * level of every instance that still iterates.  b[i], u[i], res[i] as for
+ * mg_solve.  All hierarchies must share dim and the per-level precision of
+ * the finest levels, and were created on the same stream.  Instances stop
+ * independently when they converge.  Returns MG_OK if every instance
+ * converged, else the first failing status. */
+mg_status mg_solve_batch(int32_t count, mg_hierarchy* const* hs, const double* const* b,
+                         double* const* u, mg_result* res);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Device time of one kernel of the IR step, summed over the steps of a solve. */
+typedef struct mg_kernel_time {
+    int32_t kind;        /* 0 stencil march, 1 base solve, 2 prolongation, 3 zero fill, 4 norm finalise */
+    int32_t level;       /* level index (0 = coarsest) */
+    int32_t mode;        /* march mode: 0 sweep, 1 two sweeps from zero, 2 one sweep from zero,
+                            3 residual + restriction, 4 FP64 IR update */
+    int32_t loader;      /* march input: 0 stored vector, 1 scaled FP64 residual, 2 with prolongation */
+    int32_t prec;        /* mg_prec of the level */
+    int32_t prec_coarse; /* mg_prec of the next coarser level */
+    int32_t launches;    /* number of launches timed */
+    int32_t threads;     /* threads per CTA */
+    int32_t grid[3];     /* CTA grid */
+    int32_t reserved;
+    double total_ms;     /* summed device time (CUDA events around each launch) */
+    double bytes;        /* algorithmic bytes per launch: each array touched once */
+} mg_kernel_time;
+
+/* Runs mg_solve with one launch per kernel (no CUDA graph) and CUDA events
+ * around every kernel of every IR step; fills out[0..min(count, max_out)-1]
+ * with one record per kernel of the step schedule (in launch order) and sets
+ * *count to the schedule length.  Same arguments and result as mg_solve. */
+mg_status mg_profile_solve(mg_hierarchy* h, const double* b, double* u, mg_result* res,
+                           mg_kernel_time* out, int32_t max_out, int32_t* count);
+
+/* ---------------------------------------------------------------- stages (tests, diagnostics) */
+
+/* Level vectors addressable by mg_level_write / mg_level_read.  C, G, T are
+ * stored in the level's precision; U, R are FP64 and exist on the finest
+ * level only. */
+typedef enum { MG_VEC_C = 0, MG_VEC_G = 1, MG_VEC_T = 2, MG_VEC_U = 3, MG_VEC_R = 4 } mg_vec;
+
+/* Copies n_l^d interior values (contiguous, x fastest, element type = the
+ * vector's storage type: double/float/half/bfloat16) into or out of a level
+ * vector.  src/dst may be host or device pointers. */
+mg_status mg_level_write(mg_hierarchy* h, int32_t level, int32_t vec, const void* src);
+mg_status mg_level_read(mg_hierarchy* h, int32_t level, int32_t vec, void* dst);
+mg_status mg_level_info_get(const mg_hierarchy* h, int32_t level, mg_level_info* out);
+
+/* One step of the method on one level, run on the hierarchy's stream:
+ *   MG_STAGE_JACOBI        C <- C + omega D^-1 (G - A C)          (Sec. 4.2)
+ *   MG_STAGE_JACOBI_ZERO2  C <- two damped Jacobi sweeps from C = 0 on G
+ *   MG_STAGE_RESTRICT      G_{l-1} <- cast(R (G_l - A_l C_l))     (Alg. 1 step 2)
+ *   MG_STAGE_PROLONG       C_l <- C_l + cast(P C_{l-1})           (Alg. 1 step 4)
+ *   MG_STAGE_JACOBI_PROLONG  C_l <- one sweep applied to C_l + P C_{l-1}
+ *   MG_STAGE_COARSE        C_0 <- A_0^-1 G_0 (level 0 only)
+ *   MG_STAGE_SCALE_ZERO2   G_L <- cast(R * s), then JACOBI_ZERO2 on level L;
+ *                          s = arg[0]
+ *   MG_STAGE_IR_UPDATE     U <- U + a C_L;  R <- R - a A C_L;  a = arg[0]  (Alg. 2 l. 6-7)
+ *   MG_STAGE_RESIDUAL      R <- B - A U with B = arg pointer (n^d FP64, device)
+ *   MG_STAGE_CYCLE         C_L <- one full cycle on G_L (Alg. 1, recursive)
+ * out (may be NULL) receives, where the stage computes them, ||R||_2 and
+ * ||R||_inf (IR_UPDATE, RESIDUAL).  Synchronous. */
+typedef enum {
+    MG_STAGE_JACOBI = 0, MG_STAGE_JACOBI_ZERO2 = 1, MG_STAGE_RESTRICT = 2, MG_STAGE_PROLONG = 3,
+    MG_STAGE_JACOBI_PROLONG = 4, MG_STAGE_COARSE = 5, MG_STAGE_SCALE_ZERO2 = 6,
+    MG_STAGE_IR_UPDATE = 7, MG_STAGE_RESIDUAL = 8, MG_STAGE_CYCLE = 9
+} mg_stage;
+mg_status mg_run_stage(mg_hierarchy* h, int32_t stage, int32_t level, const double* arg,
+                       const void* ptr_arg, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

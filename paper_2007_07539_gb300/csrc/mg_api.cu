@@ -1,0 +1,262 @@
+// Stage-level entry points of libmgfp (mg_level_write / mg_level_read /
+// mg_level_info_get / mg_run_stage): run one production kernel of the method
+// on one level so that tests can compare it with the CPU oracle.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mg_host.h"
+
+using namespace mgi;
+
+#define SFAIL(code, msg)      \
+    do {                      \
+        mgi_set_error(msg);   \
+        return code;          \
+    } while (0)
+#define SCK(call)                                                                                    \
+    do {                                                                                             \
+        cudaError_t e_ = (cudaError_t)(call);                                                        \
+        if (e_ != cudaSuccess) SFAIL(MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void* vec_ptr(mgi_hier& h, int level, int vec, int& prec, Geom& geo, void** alloc, size_t* bytes) {
+    if (level < 0 || level >= h.nlev) return nullptr;
+    Level& L = h.lv[level];
+    geo = L.geo;
+    if (vec >= MG_VEC_C && vec <= MG_VEC_T) {
+        prec = L.prec;
+        if (alloc) *alloc = L.alloc[vec];
+        if (bytes) *bytes = (size_t)geo.total * L.esz;
+        return vec == MG_VEC_C ? L.c : (vec == MG_VEC_G ? L.g : L.t);
+    }
+    if ((vec == MG_VEC_U || vec == MG_VEC_R) && level == h.nlev - 1) {
+        prec = MG_FP64;
+        if (alloc) *alloc = vec == MG_VEC_U ? (void*)h.u_alloc : (void*)h.r_alloc;
+        if (bytes) *bytes = (size_t)geo.total * 8;
+        return vec == MG_VEC_U ? (void*)h.u : (void*)h.r;
+    }
+    return nullptr;
+}
+
+static size_t count_pts(const Geom& g) {
+    return g.dim == 3 ? (size_t)g.n * g.n * g.n : (size_t)g.n * g.n;
+}
+
+static mg_status order_after_user(mgi_hier& h) {
+    SCK(cudaEventRecord(h.ev_in, h.user_stream));
+    SCK(cudaStreamWaitEvent(h.stream, h.ev_in, 0));
+    return MG_OK;
+}
+
+extern "C" mg_status mg_level_write(mg_hierarchy* hh, int32_t level, int32_t vec, const void* src) {
+    mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
+    if (!h || !src) SFAIL(MG_ERR_INVALID, "NULL argument");
+    int prec = 0;
+    Geom geo;
+    void* dst = vec_ptr(*h, level, vec, prec, geo, nullptr, nullptr);
+    if (!dst) SFAIL(MG_ERR_INVALID, "no such level vector");
+    SCK(cudaSetDevice(h->device));
+    mg_status st = order_after_user(*h);
+    if (st) return st;
+    const size_t bytes = count_pts(geo) * elem_size(prec);
+    const void* dsrc = src;
+    void* tmp = nullptr;
+    if (!mgi_is_device_ptr(src)) {
+        SCK(cudaMalloc(&tmp, bytes));
+        SCK(cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, h->stream));
+        dsrc = tmp;
+    }
+    int rc = launch_pack(h->dim, prec, geo, dsrc, dst, h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (tmp) cudaFree(tmp);
+    if (rc) SFAIL(MG_ERR_CUDA, std::string("pack: ") + cudaGetErrorString((cudaError_t)rc));
+    SCK(e);
+    return MG_OK;
+}
+
+extern "C" mg_status mg_level_read(mg_hierarchy* hh, int32_t level, int32_t vec, void* dst) {
+    mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
+    if (!h || !dst) SFAIL(MG_ERR_INVALID, "NULL argument");
+    int prec = 0;
+    Geom geo;
+    void* src = vec_ptr(*h, level, vec, prec, geo, nullptr, nullptr);
+    if (!src) SFAIL(MG_ERR_INVALID, "no such level vector");
+    SCK(cudaSetDevice(h->device));
+    mg_status st = order_after_user(*h);
+    if (st) return st;
+    const size_t bytes = count_pts(geo) * elem_size(prec);
+    void* ddst = dst;
+    void* tmp = nullptr;
+    const bool host = !mgi_is_device_ptr(dst);
+    if (host) {
+        SCK(cudaMalloc(&tmp, bytes));
+        ddst = tmp;
+    }
+    int rc = launch_unpack(h->dim, prec, geo, src, ddst, h->stream);
+    if (!rc && host) rc = (int)cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (tmp) cudaFree(tmp);
+    if (rc) SFAIL(MG_ERR_CUDA, std::string("unpack: ") + cudaGetErrorString((cudaError_t)rc));
+    SCK(e);
+    return MG_OK;
+}
+
+extern "C" mg_status mg_level_info_get(const mg_hierarchy* hh, int32_t level, mg_level_info* out) {
+    const mgi_hier* h = reinterpret_cast<const mgi_hier*>(hh);
+    if (!h || !out) SFAIL(MG_ERR_INVALID, "NULL argument");
+    if (level < 0 || level >= h->nlev) SFAIL(MG_ERR_INVALID, "no such level");
+    const Level& L = h->lv[level];
+    out->n = L.geo.n;
+    out->prec = L.prec;
+    out->pitch = L.geo.P;
+    out->reserved = h->nlev;
+    out->bytes = 3 * (size_t)L.geo.total * L.esz;
+    return MG_OK;
+}
+
+// Reduces per-CTA norm partials on the host: out[0] = ||r||_2, out[1] = ||r||_inf.
+static mg_status host_norms(mgi_hier& h, int nblocks, int stride, double* out) {
+    std::vector<double> p((size_t)nblocks * stride);
+    SCK(cudaMemcpy(p.data(), h.partials, p.size() * 8, cudaMemcpyDeviceToHost));
+    double s = 0.0;
+    unsigned long long m = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        s += p[(size_t)b * stride];
+        unsigned long long k;
+        std::memcpy(&k, &p[(size_t)b * stride + 1], 8);
+        if (k > m) m = k;
+    }
+    double mx;
+    std::memcpy(&mx, &m, 8);
+    if (out) { out[0] = std::sqrt(s); out[1] = mx; }
+    return MG_OK;
+}
+
+static mg_status copy_back(mgi_hier& h, int level, void* from_base) {
+    // The result of a sweep lands in T; copy T's allocation over C's.
+    Level& L = h.lv[level];
+    (void)from_base;
+    SCK(cudaMemcpyAsync(L.alloc[0], L.alloc[2], (size_t)L.geo.total * L.esz, cudaMemcpyDeviceToDevice, h.stream));
+    return MG_OK;
+}
+
+extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level, const double* arg,
+                                  const void* ptr_arg, double* out) {
+    mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
+    if (!h) SFAIL(MG_ERR_INVALID, "NULL hierarchy");
+    if (level < 0 || level >= h->nlev) SFAIL(MG_ERR_INVALID, "no such level");
+    SCK(cudaSetDevice(h->device));
+    mg_status st0 = order_after_user(*h);
+    if (st0) return st0;
+    const int L = h->nlev - 1;
+    Level& lv = h->lv[level];
+    cudaStream_t s = h->stream;
+    int rc = 0;
+    switch (stage) {
+        case MG_STAGE_JACOBI: {
+            if (level == 0 && L == 0 && false) break;
+            Op op = mgi_march_op(*h, level, M_JACOBI, L_PLAIN, lv.c, lv.t, lv.g, 0, nullptr);
+            rc = mgi_run_op(*h, op, s);
+            if (!rc) { mg_status e = copy_back(*h, level, nullptr); if (e) return e; }
+            break;
+        }
+        case MG_STAGE_JACOBI_ZERO2: {
+            Op op = mgi_march_op(*h, level, M_ZERO2, L_PLAIN, lv.g, lv.c, nullptr, 0, nullptr);
+            rc = mgi_run_op(*h, op, s);
+            break;
+        }
+        case MG_STAGE_RESTRICT: {
+            if (level < 1) SFAIL(MG_ERR_INVALID, "restriction needs level >= 1");
+            Op op = mgi_march_op(*h, level, M_RESTRICT, L_PLAIN, lv.c, h->lv[level - 1].g, lv.g, 0, nullptr);
+            rc = mgi_run_op(*h, op, s);
+            break;
+        }
+        case MG_STAGE_PROLONG: {
+            if (level < 1) SFAIL(MG_ERR_INVALID, "prolongation needs level >= 1");
+            Op op{};
+            op.kind = OP_PROLONG;
+            op.level = level;
+            op.prec = lv.prec;
+            op.prec_c = h->lv[level - 1].prec;
+            op.fine = lv.c;
+            op.coarse = h->lv[level - 1].c;
+            rc = mgi_run_op(*h, op, s);
+            break;
+        }
+        case MG_STAGE_JACOBI_PROLONG: {
+            if (level < 1) SFAIL(MG_ERR_INVALID, "prolongation needs level >= 1");
+            Op op = mgi_march_op(*h, level, M_JACOBI, L_PROLONG, lv.c, lv.t, lv.g, 0, nullptr);
+            op.a.coarse = h->lv[level - 1].c;
+            rc = mgi_run_op(*h, op, s);
+            if (!rc) { mg_status e = copy_back(*h, level, nullptr); if (e) return e; }
+            break;
+        }
+        case MG_STAGE_COARSE: {
+            if (level != 0) SFAIL(MG_ERR_INVALID, "base solve runs on level 0");
+            Op op{};
+            op.kind = OP_COARSE;
+            op.prec = lv.prec;
+            op.g = lv.g;
+            op.c = lv.c;
+            rc = mgi_run_op(*h, op, s);
+            break;
+        }
+        case MG_STAGE_SCALE_ZERO2: {
+            if (level != L) SFAIL(MG_ERR_INVALID, "scale-cast runs on the finest level");
+            if (!arg) SFAIL(MG_ERR_INVALID, "arg[0] (scale) required");
+            Op op = mgi_march_op(*h, level, L > 0 ? M_ZERO2 : M_ZERO1, L_SCALED, nullptr, lv.c, nullptr, 0, nullptr);
+            op.a.inv_explicit = arg[0];
+            rc = mgi_run_op(*h, op, s);
+            break;
+        }
+        case MG_STAGE_IR_UPDATE: {
+            if (level != L) SFAIL(MG_ERR_INVALID, "update runs on the finest level");
+            if (!arg) SFAIL(MG_ERR_INVALID, "arg[0] (alpha) required");
+            Op op = mgi_update_op(*h, lv.c, 0, nullptr);
+            op.a.a_step = arg[0];
+            rc = mgi_run_op(*h, op, s);
+            if (!rc) {
+                SCK(cudaStreamSynchronize(s));
+                return host_norms(*h, op.sh.nblocks(), 2, out);
+            }
+            break;
+        }
+        case MG_STAGE_RESIDUAL: {
+            if (level != L) SFAIL(MG_ERR_INVALID, "residual runs on the finest level");
+            if (!ptr_arg || !mgi_is_device_ptr(ptr_arg)) SFAIL(MG_ERR_INVALID, "ptr_arg must be a device pointer to b");
+            const Geom& g = lv.geo;
+            RArgs a{};
+            a.n = g.n; a.P = g.P; a.S = g.S;
+            a.u = h->u; a.b = (const double*)ptr_arg; a.r = h->r; a.partials = h->partials;
+            a.h2inv = (double)(g.n + 1) * (double)(g.n + 1);
+            int nb = 0;
+            rc = launch_residual64(h->dim, a, &nb, s);
+            if (!rc) {
+                SCK(cudaStreamSynchronize(s));
+                return host_norms(*h, nb, 4, out);
+            }
+            break;
+        }
+        case MG_STAGE_CYCLE: {
+            if (level != L) SFAIL(MG_ERR_INVALID, "a cycle starts on the finest level");
+            std::vector<Op> ops;
+            void* cL = mgi_build_cycle(*h, ops, false, 0, nullptr);
+            for (const Op& op : ops) {
+                rc = mgi_run_op(*h, op, s);
+                if (rc) break;
+            }
+            if (!rc && cL != lv.c) { mg_status e = copy_back(*h, level, nullptr); if (e) return e; }
+            break;
+        }
+        default:
+            SFAIL(MG_ERR_INVALID, "unknown stage");
+    }
+    if (rc) SFAIL(MG_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString((cudaError_t)rc));
+    SCK(cudaStreamSynchronize(s));
+    if (out) out[0] = out[1] = 0.0;
+    return MG_OK;
+}

@@ -1,0 +1,797 @@
+// Host side of libmgfp: hierarchy construction, the launch schedule of one
+// iterative-refinement step, the IR control loop and the C ABI of mg.h.
+//
+// The IR loop (Alg. 2) runs as a small state machine per solve: every action
+// (initial residual, one IR step, the true-residual check, the final report)
+// is a launch sequence on the hierarchy's stream followed by an asynchronous
+// copy of the device control state to pinned host memory and an event.  A
+// blocking solve waits on that event; the batch and serving paths poll the
+// events of many solves and advance whichever is ready, so their kernels
+// overlap on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mg_host.h"
+
+using namespace mgi;
+
+namespace mgi {
+int residual64_blocks(int dim, int n);
+}
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+void mgi_set_error(const std::string& s) { g_err = s; }
+#define FAIL(code, msg)              \
+    do {                             \
+        mgi_set_error(msg);          \
+        return code;                 \
+    } while (0)
+#define CUCHK(call)                                                                                \
+    do {                                                                                           \
+        cudaError_t e_ = (cudaError_t)(call);                                                      \
+        if (e_ != cudaSuccess) FAIL(MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" const char* mg_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------- parameters
+extern "C" void mg_params_init(mg_params* p, int32_t dim, int32_t n) {
+    std::memset(p, 0, sizeof(*p));
+    p->dim = dim;
+    p->n = n;
+    p->levels = 0;
+    for (int i = 0; i < MG_MAX_LEVELS; ++i) p->prec[i] = MG_FP64;
+    p->nu1 = 2;
+    p->nu2 = 2;
+    p->omega = 0.8;
+    p->gamma = 1;
+    p->scaling = 1;
+    p->sigma_log2 = -1;
+    p->tol_mode = 0;
+    p->tol = 1e-10;
+    p->max_iter = 100;
+    p->zero_guess = 0;
+    p->guard = 1;
+    p->graph = 1;
+}
+
+extern "C" int32_t mg_level_count(int32_t n, int32_t levels_req, int32_t* sizes) {
+    if (n < 1) return 0;
+    int tmp[64], cnt = 0, m = n;
+    tmp[cnt++] = m;
+    while (m % 2 == 1 && m > 3 && cnt < MG_MAX_LEVELS && (levels_req <= 0 || cnt < levels_req)) {
+        m = (m - 1) / 2;
+        tmp[cnt++] = m;
+    }
+    if (sizes)
+        for (int l = 0; l < cnt; ++l) sizes[l] = tmp[cnt - 1 - l];
+    return cnt;
+}
+
+static bool prec_ok(int p) { return p >= MG_FP64 && p <= MG_BF16; }
+
+int mgi_validate(const mg_params* p, std::string& why) {
+    if (!p) { why = "params is NULL"; return 0; }
+    if (p->dim != 2 && p->dim != 3) { why = "dim must be 2 or 3"; return 0; }
+    if (p->n < 1 || p->n > (p->dim == 3 ? 2047 : 65535)) { why = "n out of range"; return 0; }
+    if (p->levels < 0 || p->levels > MG_MAX_LEVELS) { why = "levels out of range"; return 0; }
+    int sizes[MG_MAX_LEVELS];
+    int L = mg_level_count(p->n, p->levels, sizes);
+    if (p->levels > 0 && L != p->levels) { why = "levels exceeds what the coarsening rule allows for n"; return 0; }
+    long long m0 = 1;
+    for (int a = 0; a < p->dim; ++a) m0 *= sizes[0];
+    if (m0 > 4096) { why = "coarsest level has more than 4096 unknowns; use more levels"; return 0; }
+    for (int l = 0; l < L; ++l)
+        if (!prec_ok(p->prec[l])) { why = "invalid precision in prec[]"; return 0; }
+    if (p->nu1 < 0 || p->nu1 > 16 || p->nu2 < 0 || p->nu2 > 16) { why = "nu1/nu2 out of range"; return 0; }
+    if (!(p->omega > 0.0 && p->omega < 2.0)) { why = "omega must be in (0, 2)"; return 0; }
+    if (p->gamma != 1 && p->gamma != 2) { why = "gamma must be 1 or 2"; return 0; }
+    if (p->scaling < 0 || p->scaling > 2) { why = "scaling must be 0, 1 or 2"; return 0; }
+    if (p->sigma_log2 < -1 || p->sigma_log2 > 60) { why = "sigma_log2 out of range"; return 0; }
+    if (p->tol_mode != 0 && p->tol_mode != 1) { why = "tol_mode must be 0 or 1"; return 0; }
+    if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) { why = "tol must be finite and >= 0"; return 0; }
+    if (p->max_iter < 0 || p->max_iter > kMaxIter) { why = "max_iter out of range"; return 0; }
+    return L;
+}
+
+// ---------------------------------------------------------------- footprint
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    size_t level_off[MG_MAX_LEVELS][3];
+    size_t u_off, r_off, part_off, st_off, minv_off, total;
+    size_t part_cap;
+};
+
+static size_t update_blocks_max(const mgi_hier& h);
+
+static void compute_layout(mgi_hier& h, Layout& lay) {
+    size_t off = 0;
+    for (int l = 0; l < h.nlev; ++l) {
+        size_t b = align_up((size_t)h.lv[l].geo.total * h.lv[l].esz, 256);
+        for (int v = 0; v < 3; ++v) { lay.level_off[l][v] = off; off += b; }
+    }
+    const Geom& gf = h.lv[h.nlev - 1].geo;
+    size_t b64 = align_up((size_t)gf.total * 8, 256);
+    lay.u_off = off; off += b64;
+    lay.r_off = off; off += b64;
+    size_t nb = std::max<size_t>((size_t)residual64_blocks(h.dim, gf.n) * 4, update_blocks_max(h) * 2);
+    lay.part_cap = nb;
+    lay.part_off = off; off += align_up(nb * 8, 256);
+    lay.st_off = off; off += align_up(sizeof(DevState), 256);
+    lay.minv_off = off; off += align_up((size_t)h.m0 * h.m0 * 8, 256);
+    lay.total = off;
+}
+
+// ---------------------------------------------------------------- base-level operator inverse
+// Dense A0 of the 5/7-point operator on the coarsest grid, inverted by
+// Gauss-Jordan elimination with partial pivoting in FP64 (host, at setup).
+static bool coarse_inverse(int dim, int n, std::vector<double>& inv) {
+    int m = 1;
+    for (int a = 0; a < dim; ++a) m *= n;
+    const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+    std::vector<double> A((size_t)m * m, 0.0);
+    for (int p = 0; p < m; ++p) {
+        int i = p % n, j = (p / n) % n, k = p / (n * n);
+        A[(size_t)p * m + p] = 2.0 * dim * ih2;
+        int c[3] = {i, j, k};
+        int stride[3] = {1, n, n * n};
+        for (int a = 0; a < dim; ++a)
+            for (int s = -1; s <= 1; s += 2) {
+                int v = c[a] + s;
+                if (v >= 0 && v < n) A[(size_t)p * m + p + s * stride[a]] = -ih2;
+            }
+    }
+    inv.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) inv[(size_t)i * m + i] = 1.0;
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r)
+            if (std::fabs(A[(size_t)r * m + col]) > std::fabs(A[(size_t)piv * m + col])) piv = r;
+        if (A[(size_t)piv * m + col] == 0.0) return false;
+        if (piv != col)
+            for (int c2 = 0; c2 < m; ++c2) {
+                std::swap(A[(size_t)piv * m + c2], A[(size_t)col * m + c2]);
+                std::swap(inv[(size_t)piv * m + c2], inv[(size_t)col * m + c2]);
+            }
+        double d = 1.0 / A[(size_t)col * m + col];
+        for (int c2 = 0; c2 < m; ++c2) { A[(size_t)col * m + c2] *= d; inv[(size_t)col * m + c2] *= d; }
+        for (int r = 0; r < m; ++r) {
+            if (r == col) continue;
+            double f = A[(size_t)r * m + col];
+            if (f == 0.0) continue;
+            for (int c2 = 0; c2 < m; ++c2) {
+                A[(size_t)r * m + c2] -= f * A[(size_t)col * m + c2];
+                inv[(size_t)r * m + c2] -= f * inv[(size_t)col * m + c2];
+            }
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- schedule of one IR step
+namespace {
+struct Gen {
+    mgi_hier* h;
+    int cur[MG_MAX_LEVELS];
+    int gate;
+    const DevState* st;
+    bool top_from_r;  // finest g comes from the FP64 residual (solve) or is given (stage)
+    std::vector<Op>* out;
+
+    void* cbuf(int l) { return cur[l] ? h->lv[l].t : h->lv[l].c; }
+    void* obuf(int l) { return cur[l] ? h->lv[l].c : h->lv[l].t; }
+    const void* gbuf(int l) {
+        if (l == h->nlev - 1 && top_from_r && h->g_alias_r) return h->r;
+        return h->lv[l].g;
+    }
+
+    Op march(int l, int mode, int loader, const void* src, void* dst, const void* g) {
+        Op op{};
+        op.kind = OP_MARCH;
+        op.level = l;
+        op.mode = mode;
+        op.loader = loader;
+        op.prec = h->lv[l].prec;
+        op.prec_c = l > 0 ? h->lv[l - 1].prec : op.prec;
+        const Geom& f = h->lv[l].geo;
+        KArgs& a = op.a;
+        a.n = f.n; a.P = f.P; a.S = f.S;
+        if (l > 0) { const Geom& c = h->lv[l - 1].geo; a.nc = c.n; a.Pc = c.P; a.Sc = c.S; }
+        a.src = src; a.dst = dst; a.g = g;
+        a.r64 = h->r;
+        a.gside = h->lv[l].g;
+        a.u64 = h->u; a.rw64 = h->r; a.partials = h->partials;
+        a.st = st; a.gate = gate;
+        a.omega = h->p.omega;
+        a.h2inv = (double)(f.n + 1) * (double)(f.n + 1);
+        op.sh = march_shape(h->dim, mode, op.prec, f.n, f.P, 0);
+        a.xstep = op.sh.xstep; a.ystep = op.sh.ystep; a.zstep = op.sh.zstep; a.zlen = op.sh.zlen;
+        return op;
+    }
+
+    void sweep(int l) {  // one Jacobi sweep on level l, ping-pong
+        out->push_back(march(l, M_JACOBI, L_PLAIN, cbuf(l), obuf(l), gbuf(l)));
+        cur[l] ^= 1;
+    }
+
+    void cycle(int l, bool first) {
+        const int L = h->nlev - 1;
+        const bool top = (l == L) && top_from_r && !h->g_alias_r;
+        if (l == 0) {
+            if (top) {  // single-level hierarchy: cast the scaled residual into g_0 first
+                Op op = march(0, M_ZERO1, L_SCALED, nullptr, obuf(0), nullptr);
+                out->push_back(op);
+            }
+            Op op{};
+            op.kind = OP_COARSE;
+            op.level = 0;
+            op.prec = h->lv[0].prec;
+            op.g = gbuf(0);
+            op.c = cbuf(0);
+            op.a.gate = gate;
+            op.a.st = st;
+            out->push_back(op);
+            return;
+        }
+        if (first) {
+            const int ld = top ? L_SCALED : L_PLAIN;
+            const void* src = top ? nullptr : gbuf(l);
+            if (h->p.nu1 >= 2) {
+                out->push_back(march(l, M_ZERO2, ld, src, cbuf(l), nullptr));
+                for (int s = 2; s < h->p.nu1; ++s) sweep(l);
+            } else if (h->p.nu1 == 1) {
+                out->push_back(march(l, M_ZERO1, ld, src, cbuf(l), nullptr));
+            } else {
+                if (top) out->push_back(march(l, M_ZERO1, L_SCALED, nullptr, obuf(l), nullptr));
+                Op z{};
+                z.kind = OP_ZERO;
+                z.ptr = cbuf(l);
+                z.bytes = (size_t)h->lv[l].geo.total * h->lv[l].esz;
+                z.zero_base = h->lv[l].geo.base * h->lv[l].esz;
+                out->push_back(z);
+            }
+        } else {
+            for (int s = 0; s < h->p.nu1; ++s) sweep(l);
+        }
+        out->push_back(march(l, M_RESTRICT, L_PLAIN, cbuf(l), h->lv[l - 1].g, gbuf(l)));
+        cur[l - 1] = 0;
+        for (int k = 0; k < h->p.gamma; ++k) cycle(l - 1, k == 0);
+        if (h->p.nu2 >= 1) {
+            Op op = march(l, M_JACOBI, L_PROLONG, cbuf(l), obuf(l), gbuf(l));
+            op.a.coarse = cbuf(l - 1);
+            out->push_back(op);
+            cur[l] ^= 1;
+            for (int s = 1; s < h->p.nu2; ++s) sweep(l);
+        } else {
+            Op op{};
+            op.kind = OP_PROLONG;
+            op.level = l;
+            op.prec = h->lv[l].prec;
+            op.prec_c = h->lv[l - 1].prec;
+            op.fine = cbuf(l);
+            op.coarse = cbuf(l - 1);
+            op.a.gate = gate;
+            op.a.st = st;
+            out->push_back(op);
+        }
+    }
+};
+}  // namespace
+
+// Builds the ops of one MG cycle on the finest level (c_L from g_L) and
+// returns where c_L ends up.
+void* mgi_build_cycle(mgi_hier& h, std::vector<Op>& ops, bool top_from_r, int gate, const DevState* st) {
+    Gen gen{};
+    gen.h = &h;
+    gen.gate = gate;
+    gen.st = st;
+    gen.top_from_r = top_from_r;
+    gen.out = &ops;
+    for (int l = 0; l < MG_MAX_LEVELS; ++l) gen.cur[l] = 0;
+    gen.cycle(h.nlev - 1, true);
+    return gen.cbuf(h.nlev - 1);
+}
+
+Op mgi_march_op(mgi_hier& h, int level, int mode, int loader, const void* src, void* dst, const void* g,
+                int gate, const DevState* st) {
+    Gen gen{};
+    gen.h = &h;
+    gen.gate = gate;
+    gen.st = st;
+    gen.top_from_r = false;
+    return gen.march(level, mode, loader, src, dst, g);
+}
+
+Op mgi_update_op(mgi_hier& h, const void* cL, int gate, const DevState* st) {
+    const int L = h.nlev - 1;
+    Gen gen{};
+    gen.h = &h;
+    gen.gate = gate;
+    gen.st = st;
+    gen.top_from_r = true;
+    return gen.march(L, M_UPDATE, L_PLAIN, cL, nullptr, nullptr);
+}
+
+static size_t update_blocks_max(const mgi_hier& h) {
+    const Geom& f = h.lv[h.nlev - 1].geo;
+    MarchShape s = march_shape(h.dim, M_UPDATE, h.lv[h.nlev - 1].prec, f.n, f.P, 0);
+    return (size_t)s.nblocks();
+}
+
+static void build_step(mgi_hier& h) {
+    h.step.clear();
+    void* cL = mgi_build_cycle(h, h.step, true, 1, h.st);
+    Op up = mgi_update_op(h, cL, 1, h.st);
+    h.step.push_back(up);
+    Op fin{};
+    fin.kind = OP_FINALIZE;
+    fin.fin_kind = FIN_STEP;
+    fin.nblocks = up.sh.nblocks();
+    h.step.push_back(fin);
+    h.step_kernels = 0;
+    for (const Op& op : h.step) h.step_kernels += op.kind != OP_ZERO;
+}
+
+int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
+    switch (op.kind) {
+        case OP_MARCH:
+            return launch_march(h.dim, op.mode, op.loader, op.prec, op.prec_c, op.a, op.sh.gx, op.sh.gy,
+                                op.sh.gz, op.sh.ty, op.sh.smem, s);
+        case OP_COARSE:
+            return launch_coarse_solve(op.prec, h.minv, h.m0, op.g, op.c, h.lv[0].geo, op.a.st, op.a.gate, s);
+        case OP_PROLONG:
+            return launch_prolong_add(h.dim, op.prec, op.prec_c, h.lv[op.level].geo, h.lv[op.level - 1].geo,
+                                      op.fine, op.coarse, op.a.st, op.a.gate, s);
+        case OP_ZERO:
+            return (int)cudaMemsetAsync((char*)op.ptr - op.zero_base, 0, op.bytes, s);
+        case OP_FINALIZE:
+            return launch_finalize(op.fin_kind, h.st, h.partials, op.nblocks, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- creation
+static void free_hier(mgi_hier* h) {
+    if (!h) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(h->device);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->arena) cudaFree(h->arena);
+    if (h->bstage) cudaFree(h->bstage);
+    if (h->ustage) cudaFree(h->ustage);
+    if (h->st_host) cudaFreeHost(h->st_host);
+    if (h->e0) cudaEventDestroy(h->e0);
+    if (h->e1) cudaEventDestroy(h->e1);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_state) cudaEventDestroy(h->ev_state);
+    for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    cudaSetDevice(dev);
+    delete h;
+}
+
+static mg_status plan_hier(const mg_params* p, mgi_hier& h) {
+    std::string why;
+    int L = mgi_validate(p, why);
+    if (!L) FAIL(MG_ERR_INVALID, why);
+    h.p = *p;
+    h.dim = p->dim;
+    h.nlev = L;
+    int sizes[MG_MAX_LEVELS];
+    mg_level_count(p->n, p->levels, sizes);
+    bool any16 = false;
+    for (int l = 0; l < L; ++l) {
+        h.lv[l].geo = make_geom(p->dim, sizes[l]);
+        h.lv[l].prec = p->prec[l];
+        h.lv[l].esz = elem_size(p->prec[l]);
+        any16 = any16 || p->prec[l] == MG_FP16;
+    }
+    int sl = p->sigma_log2 >= 0 ? p->sigma_log2 : (any16 ? 14 : 0);
+    h.sigma = p->scaling == 0 ? 1.0 : std::ldexp(1.0, sl);
+    h.g_alias_r = (p->prec[L - 1] == MG_FP64 && p->scaling == 0);
+    h.m0 = 1;
+    for (int a = 0; a < p->dim; ++a) h.m0 *= sizes[0];
+    Layout lay;
+    compute_layout(h, lay);
+    h.footprint = lay.total;
+    h.part_cap = lay.part_cap;
+    return MG_OK;
+}
+
+extern "C" size_t mg_footprint_bytes(const mg_params* p) {
+    mgi_hier h;
+    if (plan_hier(p, h) != MG_OK) return 0;
+    return h.footprint;
+}
+
+extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, mg_hierarchy** out) {
+    if (!out) FAIL(MG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    mgi_hier* h = new mgi_hier();
+    mg_status st = plan_hier(p, *h);
+    if (st != MG_OK) { delete h; return st; }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { delete h; FAIL(MG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)); }
+    h->user_stream = (cudaStream_t)cuda_stream;
+    Layout lay;
+    compute_layout(*h, lay);
+    e = cudaMalloc(&h->arena, lay.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->arena = nullptr;
+        free_hier(h);
+        FAIL(MG_ERR_OOM, "device allocation of " + std::to_string(lay.total) + " bytes failed");
+    }
+    h->arena_bytes = lay.total;
+    char* base = (char*)h->arena;
+    for (int l = 0; l < h->nlev; ++l) {
+        const size_t bo = (size_t)h->lv[l].geo.base * h->lv[l].esz;
+        h->lv[l].c = base + lay.level_off[l][0] + bo;
+        h->lv[l].g = base + lay.level_off[l][1] + bo;
+        h->lv[l].t = base + lay.level_off[l][2] + bo;
+        h->lv[l].alloc[0] = base + lay.level_off[l][0];
+        h->lv[l].alloc[1] = base + lay.level_off[l][1];
+        h->lv[l].alloc[2] = base + lay.level_off[l][2];
+    }
+    const Geom& gf = h->lv[h->nlev - 1].geo;
+    h->u_alloc = (double*)(base + lay.u_off);
+    h->r_alloc = (double*)(base + lay.r_off);
+    h->u = h->u_alloc + gf.base;
+    h->r = h->r_alloc + gf.base;
+    h->partials = (double*)(base + lay.part_off);
+    h->st = (DevState*)(base + lay.st_off);
+    h->minv = (double*)(base + lay.minv_off);
+    std::vector<double> inv;
+    if (!coarse_inverse(h->dim, h->lv[0].geo.n, inv)) { free_hier(h); FAIL(MG_ERR_INVALID, "singular base-level operator"); }
+#define CK_CREATE(call)                                                                       \
+    do {                                                                                      \
+        cudaError_t e2 = (call);                                                              \
+        if (e2 != cudaSuccess) {                                                              \
+            free_hier(h);                                                                     \
+            FAIL(MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e2));            \
+        }                                                                                     \
+    } while (0)
+    CK_CREATE(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK_CREATE(cudaEventCreate(&h->e0));
+    CK_CREATE(cudaEventCreate(&h->e1));
+    CK_CREATE(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK_CREATE(cudaEventCreateWithFlags(&h->ev_state, cudaEventDisableTiming));
+    CK_CREATE(cudaMallocHost((void**)&h->st_host, sizeof(DevState)));
+    std::memset(h->st_host, 0, sizeof(DevState));
+    CK_CREATE(cudaMemsetAsync(h->arena, 0, lay.total, h->stream));
+    CK_CREATE(cudaMemcpyAsync(h->minv, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    CK_CREATE(cudaStreamSynchronize(h->stream));
+#undef CK_CREATE
+    build_step(*h);
+    *out = reinterpret_cast<mg_hierarchy*>(h);
+    return MG_OK;
+}
+
+extern "C" mg_status mg_destroy(mg_hierarchy* hh) {
+    mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
+    if (!h) return MG_OK;
+    mgi_serve_forget(h);
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_hier(h);
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- the IR state machine
+bool mgi_is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static size_t npoints(const mgi_hier& h) {
+    size_t n = (size_t)h.lv[h.nlev - 1].geo.n;
+    return h.dim == 3 ? n * n * n : n * n;
+}
+
+static int ensure_staging(mgi_hier& h) {
+    if (h.bstage) return 0;
+    size_t bytes = npoints(h) * 8;
+    if (cudaMalloc(&h.bstage, bytes) != cudaSuccess) { cudaGetLastError(); h.bstage = nullptr; return 1; }
+    if (cudaMalloc(&h.ustage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h.bstage);
+        h.bstage = h.ustage = nullptr;
+        return 1;
+    }
+    return 0;
+}
+
+static int launch_step(mgi_hier& h) {
+    cudaStream_t s = h.stream;
+    h.ctx.launches += h.step_kernels;
+    if (h.prof) {
+        for (size_t i = 0; i < h.step.size(); ++i) {
+            cudaError_t e = cudaEventRecord(h.prof_ev[2 * i], s);
+            if (e != cudaSuccess) return (int)e;
+            int rc = mgi_run_op(h, h.step[i], s);
+            if (rc) return rc;
+            e = cudaEventRecord(h.prof_ev[2 * i + 1], s);
+            if (e != cudaSuccess) return (int)e;
+        }
+        h.prof_pending = true;
+        return 0;
+    }
+    if (h.p.graph) {
+        if (!h.graph_exec) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return (int)e;
+            int rc = 0;
+            for (const Op& op : h.step) {
+                rc = mgi_run_op(h, op, s);
+                if (rc) break;
+            }
+            e = cudaStreamEndCapture(s, &g);
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return (int)e;
+            e = cudaGraphInstantiate(&h.graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { h.graph_exec = nullptr; return (int)e; }
+        }
+        return (int)cudaGraphLaunch(h.graph_exec, s);
+    }
+    for (const Op& op : h.step) {
+        int rc = mgi_run_op(h, op, s);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+static int launch_residual(mgi_hier& h, const double* b, double* r, double* uout, int fin_kind) {
+    const Geom& g = h.lv[h.nlev - 1].geo;
+    RArgs a{};
+    a.n = g.n; a.P = g.P; a.S = g.S;
+    a.u = h.u; a.b = b; a.r = r; a.uout = uout; a.partials = h.partials;
+    a.h2inv = (double)(g.n + 1) * (double)(g.n + 1);
+    int nb = 0;
+    int rc = launch_residual64(h.dim, a, &nb, h.stream);
+    if (rc) return rc;
+    h.ctx.launches += 2;
+    return launch_finalize(fin_kind, h.st, h.partials, nb, h.stream);
+}
+
+static int push_state(mgi_hier& h) {
+    cudaError_t e = cudaMemcpyAsync(h.st_host, h.st, offsetof(DevState, hist), cudaMemcpyDeviceToHost, h.stream);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaEventRecord(h.ev_state, h.stream);
+}
+
+// Starts a solve: resolves host/device pointers, writes the control state,
+// launches r = b - A u0 (or r = b) and the first state copy.
+mg_status mgi_solve_begin(mgi_hier& h, const double* b, double* u) {
+    SolveCtx& c = h.ctx;
+    c = SolveCtx{};
+    c.b_user = b;
+    c.u_user = u;
+    c.b_host = !mgi_is_device_ptr(b);
+    c.u_host = !mgi_is_device_ptr(u);
+    cudaStream_t s = h.stream;
+    const size_t N = npoints(h);
+    CUCHK(cudaEventRecord(h.ev_in, h.user_stream));
+    CUCHK(cudaStreamWaitEvent(s, h.ev_in, 0));
+    CUCHK(cudaEventRecord(h.e0, s));
+    c.bd = b;
+    c.ud = u;
+    if (c.b_host || c.u_host) {
+        if (ensure_staging(h)) FAIL(MG_ERR_OOM, "staging allocation failed");
+    }
+    if (c.b_host) {
+        CUCHK(cudaMemcpyAsync(h.bstage, b, N * 8, cudaMemcpyHostToDevice, s));
+        c.bd = h.bstage;
+    }
+    if (c.u_host) {
+        if (!h.p.zero_guess) CUCHK(cudaMemcpyAsync(h.ustage, u, N * 8, cudaMemcpyHostToDevice, s));
+        c.ud = h.ustage;
+    }
+    DevState& sh = *h.st_host;
+    std::memset(&sh, 0, offsetof(DevState, hist));
+    sh.alpha = 1.0;
+    sh.inv = 1.0;
+    sh.sigma = h.sigma;
+    sh.tol = h.p.tol;
+    sh.max_iter = h.p.max_iter;
+    sh.scaling = h.p.scaling;
+    sh.tol_mode = h.p.tol_mode;
+    sh.guard = h.p.guard;
+    sh.phase = 0;
+    CUCHK(cudaMemcpyAsync(h.st, &sh, offsetof(DevState, hist), cudaMemcpyHostToDevice, s));
+    const Geom& g = h.lv[h.nlev - 1].geo;
+    if (h.p.zero_guess) {
+        CUCHK(cudaMemsetAsync(h.u_alloc, 0, (size_t)g.total * 8, s));
+        int nb = 0;
+        CUCHK(launch_init_rb(h.dim, g, c.bd, h.r, h.partials, &nb, s));
+        CUCHK(launch_finalize(FIN_INIT, h.st, h.partials, nb, s));
+        c.launches += 2;
+    } else {
+        CUCHK(launch_pack(h.dim, MG_FP64, g, c.ud, h.u, s));
+        c.launches += 1;
+        CUCHK(launch_residual(h, c.bd, h.r, nullptr, FIN_INIT));
+    }
+    c.dirty = true;
+    CUCHK(push_state(h));
+    c.active = true;
+    return MG_OK;
+}
+
+// Advances a started solve by one action; call once its state event has
+// completed.  Returns 1 when the solve has finished (result in h.ctx), 0 when
+// a new action was launched, or a negative mg_status on a launch error.
+int mgi_solve_advance(mgi_hier& h) {
+    SolveCtx& c = h.ctx;
+    const DevState& s = *h.st_host;
+    int rc = 0;
+    if (h.prof_pending) {  // the previous step has completed: collect its kernel times
+        for (size_t i = 0; i < h.step.size(); ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, h.prof_ev[2 * i], h.prof_ev[2 * i + 1]) == cudaSuccess) {
+                h.prof_ms[i] += ms;
+                h.prof_cnt[i] += 1;
+            }
+        }
+        h.prof_pending = false;
+    }
+    if (!c.finishing) {
+        if (s.phase == 0) {
+            rc = launch_step(h);
+            c.dirty = true;
+        } else if (s.phase == 1) {
+            rc = launch_residual(h, c.bd, h.r, c.ud, FIN_GUARD);
+            c.dirty = false;
+        } else {
+            c.finishing = true;
+        }
+        if (!c.finishing) {
+            if (rc || (rc = push_state(h))) { mgi_set_error(std::string("launch: ") + cudaGetErrorString((cudaError_t)rc)); c.active = false; return -MG_ERR_CUDA; }
+            return 0;
+        }
+    }
+    if (c.dirty) {  // final report: b - A u in FP64 and the unpacked solution
+        rc = launch_residual(h, c.bd, nullptr, c.ud, 3);
+        c.dirty = false;
+        if (!rc) rc = push_state(h);
+        if (rc) { mgi_set_error(std::string("launch: ") + cudaGetErrorString((cudaError_t)rc)); c.active = false; return -MG_ERR_CUDA; }
+        return 0;
+    }
+    if (c.u_host && !c.copied_back) {
+        rc = (int)cudaMemcpyAsync(c.u_user, c.ud, npoints(h) * 8, cudaMemcpyDeviceToHost, h.stream);
+        c.copied_back = true;
+        if (!rc) rc = (int)cudaEventRecord(h.ev_state, h.stream);
+        if (rc) { mgi_set_error(std::string("copy: ") + cudaGetErrorString((cudaError_t)rc)); c.active = false; return -MG_ERR_CUDA; }
+        return 0;
+    }
+    cudaEventRecord(h.e1, h.stream);
+    cudaEventSynchronize(h.e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h.e0, h.e1);
+    mg_result& r = c.res;
+    r.iters = s.iter;
+    r.status = s.status;
+    r.levels = h.nlev;
+    r.guard_restarts = s.guard_restarts;
+    r.bnorm = s.bnorm2;
+    r.rel_res = s.bnorm2 > 0 ? s.rnorm2 / s.bnorm2 : s.rnorm2;
+    r.rel_res_true = s.rel_true;
+    r.seconds = ms * 1e-3;
+    r.launches = c.launches;
+    c.active = false;
+    return 1;
+}
+
+extern "C" mg_status mg_solve(mg_hierarchy* hh, const double* b, double* u, mg_result* res) {
+    mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
+    if (!h || !b || !u) FAIL(MG_ERR_INVALID, "NULL argument");
+    if (mgi_serve_busy(h)) FAIL(MG_ERR_INVALID, "hierarchy has serving requests in flight");
+    CUCHK(cudaSetDevice(h->device));
+    mg_status st = mgi_solve_begin(*h, b, u);
+    if (st != MG_OK) return st;
+    for (;;) {
+        cudaError_t e = cudaEventSynchronize(h->ev_state);
+        if (e != cudaSuccess) FAIL(MG_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(e));
+        int rc = mgi_solve_advance(*h);
+        if (rc < 0) return (mg_status)(-rc);
+        if (rc == 1) break;
+    }
+    if (res) *res = h->ctx.res;
+    return (mg_status)h->ctx.res.status;
+}
+
+// ---------------------------------------------------------------- batch (concurrent instances)
+extern "C" mg_status mg_solve_batch(int32_t count, mg_hierarchy* const* hs, const double* const* b,
+                                    double* const* u, mg_result* res) {
+    if (count < 0 || (count > 0 && (!hs || !b || !u))) FAIL(MG_ERR_INVALID, "bad batch arguments");
+    std::vector<mgi_hier*> H(count);
+    for (int i = 0; i < count; ++i) {
+        H[i] = reinterpret_cast<mgi_hier*>(hs[i]);
+        if (!H[i] || !b[i] || !u[i]) FAIL(MG_ERR_INVALID, "NULL entry in batch");
+        for (int j = 0; j < i; ++j)
+            if (H[j] == H[i]) FAIL(MG_ERR_INVALID, "a hierarchy appears twice in the batch");
+    }
+    return mgi_batch_run(H, b, u, res);
+}
+
+// ---------------------------------------------------------------- profiling
+static double op_bytes(const mgi_hier& h, const Op& op) {
+    auto pts = [&](int l) {
+        double n = h.lv[l].geo.n;
+        return h.dim == 3 ? n * n * n : n * n;
+    };
+    const double s = (double)elem_size(op.prec);
+    const double sc = (double)elem_size(op.prec_c);
+    const double N = pts(op.level);
+    const double Nc = op.level > 0 ? pts(op.level - 1) : 0.0;
+    switch (op.kind) {
+        case OP_MARCH:
+            switch (op.mode) {
+                case M_JACOBI: return 3 * s * N + (op.loader == L_PROLONG ? sc * Nc : 0.0);
+                case M_ZERO2:
+                case M_ZERO1: return op.loader == L_SCALED ? (8 + 2 * s) * N : 2 * s * N;
+                case M_RESTRICT: return 2 * s * N + sc * Nc;
+                case M_UPDATE: return (32 + s) * N;
+            }
+            return 0.0;
+        case OP_COARSE: return 2 * s * N + 8.0 * h.m0 * h.m0;
+        case OP_PROLONG: return 2 * s * N + sc * Nc;
+        case OP_ZERO: return (double)op.bytes;
+        case OP_FINALIZE: return 16.0 * op.nblocks;
+    }
+    return 0.0;
+}
+
+extern "C" mg_status mg_profile_solve(mg_hierarchy* hh, const double* b, double* u, mg_result* res,
+                                      mg_kernel_time* out, int32_t max_out, int32_t* count) {
+    mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
+    if (!h) FAIL(MG_ERR_INVALID, "NULL hierarchy");
+    CUCHK(cudaSetDevice(h->device));
+    const size_t nops = h->step.size();
+    if (h->prof_ev.size() != 2 * nops) {
+        for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+        h->prof_ev.assign(2 * nops, nullptr);
+        for (auto& e : h->prof_ev) CUCHK(cudaEventCreate(&e));
+    }
+    h->prof_ms.assign(nops, 0.0);
+    h->prof_cnt.assign(nops, 0);
+    h->prof = true;
+    mg_result r{};
+    mg_status st = mg_solve(hh, b, u, &r);
+    h->prof = false;
+    h->prof_pending = false;
+    if (res) *res = r;
+    if (count) *count = (int32_t)nops;
+    for (size_t i = 0; i < nops && (int32_t)i < max_out && out; ++i) {
+        const Op& op = h->step[i];
+        mg_kernel_time& k = out[i];
+        std::memset(&k, 0, sizeof(k));
+        k.kind = op.kind;
+        k.level = op.level;
+        k.mode = op.mode;
+        k.loader = op.loader;
+        k.prec = op.prec;
+        k.prec_coarse = op.prec_c;
+        k.launches = h->prof_cnt[i];
+        if (op.kind == OP_MARCH) {
+            k.threads = 32 * op.sh.ty;
+            k.grid[0] = op.sh.gx; k.grid[1] = op.sh.gy; k.grid[2] = op.sh.gz;
+        }
+        k.total_ms = h->prof_ms[i];
+        k.bytes = op_bytes(*h, op);
+    }
+    return st;
+}

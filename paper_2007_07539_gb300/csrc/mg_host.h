@@ -1,0 +1,108 @@
+// Host-side structures of libmgfp shared by the hierarchy/solve code, the
+// stage API and the serving engine.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "mg_internal.h"
+
+namespace mgi {
+
+struct Level {
+    Geom geo;
+    int prec = MG_FP64;
+    size_t esz = 8;
+    void* c = nullptr;  // correction (points at (0,0,0) of the padded layout)
+    void* g = nullptr;  // right-hand side / restricted residual
+    void* t = nullptr;  // ping-pong partner of c
+    void* alloc[3] = {nullptr, nullptr, nullptr};  // allocation starts of c, g, t
+};
+
+enum OpKind : int { OP_MARCH = 0, OP_COARSE = 1, OP_PROLONG = 2, OP_ZERO = 3, OP_FINALIZE = 4 };
+
+struct Op {
+    int kind = 0, level = 0;
+    int mode = 0, loader = 0, prec = 0, prec_c = 0;
+    KArgs a{};
+    MarchShape sh{};
+    const void* g = nullptr;  // OP_COARSE
+    void* c = nullptr;
+    void* fine = nullptr;     // OP_PROLONG
+    const void* coarse = nullptr;
+    void* ptr = nullptr;      // OP_ZERO: padded base pointer
+    size_t bytes = 0;
+    size_t zero_base = 0;     // bytes between allocation start and ptr
+    int fin_kind = 0, nblocks = 0;
+};
+
+struct SolveCtx {
+    const double* b_user = nullptr;
+    double* u_user = nullptr;
+    const double* bd = nullptr;  // device b (caller's or staging)
+    double* ud = nullptr;        // device u (caller's or staging)
+    bool b_host = false, u_host = false;
+    bool dirty = false;          // u changed since it was last unpacked
+    bool finishing = false;
+    bool copied_back = false;
+    bool active = false;
+    int launches = 0;
+    mg_result res{};
+};
+
+struct mgi_hier {
+    mg_params p{};
+    int dim = 0, nlev = 0;
+    Level lv[MG_MAX_LEVELS];
+    double* u = nullptr;  // FP64 solution, padded finest layout
+    double* r = nullptr;  // FP64 residual, padded finest layout
+    double* u_alloc = nullptr;
+    double* r_alloc = nullptr;
+    double* partials = nullptr;
+    size_t part_cap = 0;
+    DevState* st = nullptr;
+    DevState* st_host = nullptr;  // pinned mirror
+    double* minv = nullptr;       // dense inverse of the base-level operator
+    int m0 = 0;
+    double sigma = 1.0;
+    bool g_alias_r = false;       // finest g is r itself (FP64 finest level, no scaling)
+    double* bstage = nullptr;
+    double* ustage = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t user_stream = nullptr;
+    int device = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, ev_in = nullptr, ev_state = nullptr;
+    std::vector<Op> step;
+    cudaGraphExec_t graph_exec = nullptr;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    size_t footprint = 0;
+    SolveCtx ctx;
+    // launch accounting and per-kernel profiling of the IR step
+    int step_kernels = 0;            // kernels per IR step (memsets excluded)
+    bool prof = false;
+    bool prof_pending = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<double> prof_ms;
+    std::vector<int> prof_cnt;
+};
+
+}  // namespace mgi
+
+void mgi_set_error(const std::string& s);
+int mgi_validate(const mg_params* p, std::string& why);
+int mgi_run_op(mgi::mgi_hier& h, const mgi::Op& op, cudaStream_t s);
+void* mgi_build_cycle(mgi::mgi_hier& h, std::vector<mgi::Op>& ops, bool top_from_r, int gate,
+                      const mgi::DevState* st);
+mgi::Op mgi_march_op(mgi::mgi_hier& h, int level, int mode, int loader, const void* src, void* dst,
+                     const void* g, int gate, const mgi::DevState* st);
+bool mgi_is_device_ptr(const void* p);
+mgi::Op mgi_update_op(mgi::mgi_hier& h, const void* cL, int gate, const mgi::DevState* st);
+mg_status mgi_solve_begin(mgi::mgi_hier& h, const double* b, double* u);
+int mgi_solve_advance(mgi::mgi_hier& h);
+mg_status mgi_batch_run(std::vector<mgi::mgi_hier*>& hs, const double* const* b, double* const* u,
+                        mg_result* res);
+// serving engine hooks
+void mgi_serve_forget(mgi::mgi_hier* h);
+bool mgi_serve_busy(mgi::mgi_hier* h);

@@ -1,0 +1,158 @@
+// Internal declarations shared by the host code and the CUDA kernels of libmgfp.
+//
+// Padded level layout (every level vector, every storage type):
+//   row pitch P = round_up(n + 1, 16) elements; rows y = 0..n per plane, row n
+//   all zero; planes z = -1..n (3D), planes -1 and n all zero; a zero guard of
+//   2P + 32 elements before plane -1 and after plane n.  Element (x, y, z) sits
+//   at base + z*S + y*P + x with S = P*(n+1) (3D; 2D has no z term).
+// Only interior points (x, y, z < n) are ever written with non-zero values, so
+// every read at x = -1 or x = n (the previous/this row's pad column), y = -1
+// or y = n (a pad row) and z = -1 or z = n (a pad plane) returns the zero
+// Dirichlet boundary value without a branch.  P is a multiple of 16 elements,
+// so x = 0 of every row is 16-byte aligned for all types.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/mg.h"
+
+namespace mgi {
+
+constexpr int kMaxHist = 1024;
+constexpr int kMaxIter = 1000;
+
+struct Geom {
+    int dim = 0;
+    int n = 0;          // interior points per dimension
+    int P = 0;          // row pitch (elements)
+    long long S = 0;    // plane stride (elements): P*(n+1)
+    long long base = 0; // element offset of (0,0,0) in the allocation
+    long long total = 0;// allocated elements
+};
+
+inline Geom make_geom(int dim, int n) {
+    Geom g;
+    g.dim = dim;
+    g.n = n;
+    g.P = ((n + 1 + 15) / 16) * 16;
+    g.S = (long long)g.P * (n + 1);
+    long long guard = 2LL * g.P + 32;
+    if (dim == 3) {
+        g.base = guard + g.S;                         // plane -1 precedes (0,0,0)
+        g.total = g.base + (long long)(n + 1) * g.S + guard;
+    } else {
+        g.base = guard + g.P;                         // row -1 precedes (0,0)
+        g.total = g.base + (long long)(n + 1) * g.P + guard;
+    }
+    g.total = ((g.total + 127) / 128) * 128;
+    return g;
+}
+
+// Device-side solver state of one solve (one per hierarchy / solve slot).
+struct DevState {
+    double alpha;     // scale of the current correction: u += alpha c, r -= alpha A c
+    double inv;       // sigma/alpha: the scaled residual is r * inv
+    double rnorm2;    // ||r||_2 of the current recursive residual
+    double rnorminf;  // ||r||_inf
+    double bnorm2;    // ||b||_2
+    double tol_abs;   // threshold on ||r||_2
+    double sigma;     // 2^sigma_log2
+    double rel_true;  // last ||b - A u||_2 / ||b||_2
+    double tol;
+    int iter;         // completed IR steps
+    int phase;        // 0 iterate, 1 recursive test passed (guard pending), 2 converged, 3 stopped
+    int status;       // mg_status
+    int guard_restarts;
+    int max_iter;
+    int scaling;
+    int tol_mode;
+    int guard;
+    int stag;         // consecutive steps without decrease
+    int pad_;
+    double hist[kMaxHist + 2];
+};
+
+enum Mode : int {
+    M_JACOBI = 0,   // dst = c + w D^-1 (g - A c), c from the loader
+    M_ZERO2 = 1,    // dst = two sweeps from zero; the marched values are g
+    M_ZERO1 = 2,    // dst = w D^-1 g
+    M_RESTRICT = 3, // coarse dst = R (g - A c)
+    M_UPDATE = 4,   // u += alpha c; r -= alpha A c; norms
+};
+
+enum Loader : int {
+    L_PLAIN = 0,    // values of src (type T)
+    L_SCALED = 1,   // round_T(r64 * inv): the scaled, cast residual (Alg. 2 line 4)
+    L_PROLONG = 2,  // src + P coarse (coarse type TC)
+};
+
+// Arguments of the stencil march kernels (passed by value).
+struct KArgs {
+    int n, P;            // this level
+    long long S;
+    int nc, Pc;          // coarser level (restrict target / prolong source)
+    long long Sc;
+    const void* src;     // marched vector (T)
+    const void* g;       // right-hand side (T)
+    void* dst;           // output (T, or TC for M_RESTRICT)
+    const void* coarse;  // coarse correction (TC) for L_PROLONG
+    const double* r64;   // FP64 residual for L_SCALED (padded, finest geometry)
+    void* gside;         // L_SCALED: where the cast g is stored (T)
+    double* u64;         // M_UPDATE: FP64 solution (padded)
+    double* rw64;        // M_UPDATE: FP64 residual (padded)
+    double* partials;    // per-CTA norm partials (M_UPDATE): 2 doubles each
+    const DevState* st;  // alpha / inv, phase (early exit)
+    double a_step;       // M_UPDATE explicit alpha when st == nullptr
+    double inv_explicit; // L_SCALED explicit scale when st == nullptr
+    double omega;
+    double h2inv;        // 1/h^2 of this level
+    int xstep, ystep, zstep, zlen;  // tile strides / march length
+    int gate;            // 1: return at once unless st->phase == 0
+};
+
+// Arguments of the FP64 residual kernel r = b - A u.
+struct RArgs {
+    int n, P;
+    long long S;
+    const double* u;      // padded
+    const double* b;      // contiguous interior (n^d)
+    double* r;            // padded output (may be null)
+    double* uout;         // contiguous interior copy of u (may be null)
+    double* partials;     // 4 doubles per CTA: sum r^2, max |r|, sum b^2, unused
+    double h2inv;
+    int zstep, zlen, ystep;
+};
+
+// Launchers (one translation unit per fine storage type).
+// prec codes follow mg_prec.
+int launch_march(int dim, int mode, int loader, int prec, int prec_c, const KArgs& a,
+                 int grid_x, int grid_y, int grid_z, int ty, size_t smem, void* stream);
+
+struct MarchShape {
+    int gx, gy, gz, ty;
+    size_t smem;
+    int xstep, ystep, zstep, zlen;
+    int nblocks() const { return gx * gy * gz; }
+};
+// Launch geometry for a stencil march over a level of size n (pitch P).
+MarchShape march_shape(int dim, int mode, int prec, int n, int P, int tz_hint);
+
+// Misc kernels (mg_misc.cu).
+int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void* c, const Geom& geo,
+                        const DevState* st, int gate, void* stream);
+int launch_prolong_add(int dim, int prec, int prec_c, const Geom& f, const Geom& c, void* fine,
+                       const void* coarse, const DevState* st, int gate, void* stream);
+int launch_residual64(int dim, const RArgs& a, int* nblocks, void* stream);
+int launch_init_rb(int dim, const Geom& geo, const double* b, double* r, double* partials,
+                   int* nblocks, void* stream);
+int launch_finalize(int kind, DevState* st, const double* partials, int nblocks, void* stream);
+int launch_pack(int dim, int prec, const Geom& geo, const void* src_contig, void* dst_padded,
+                void* stream);
+int launch_unpack(int dim, int prec, const Geom& geo, const void* src_padded, void* dst_contig,
+                  void* stream);
+
+enum FinalizeKind : int { FIN_INIT = 0, FIN_STEP = 1, FIN_GUARD = 2 };
+
+size_t elem_size(int prec);
+
+}  // namespace mgi

@@ -1,0 +1,409 @@
+// Small kernels of libmgfp: base-level solve, stand-alone prolongation,
+// FP64 residual b - A u with norms, norm finalisation and the IR control
+// state, and packing between the caller's contiguous layout and the padded
+// device layout.  Also the launch-geometry rule of the stencil march.
+#include <cmath>
+
+#include "mg_march.cuh"
+
+namespace mgi {
+
+int launch_march_f64(int, int, int, int, const KArgs&, int, int, int, int, size_t, void*);
+int launch_march_f32(int, int, int, int, const KArgs&, int, int, int, int, size_t, void*);
+int launch_march_f16(int, int, int, int, const KArgs&, int, int, int, int, size_t, void*);
+int launch_march_bf16(int, int, int, int, const KArgs&, int, int, int, int, size_t, void*);
+
+size_t elem_size(int prec) {
+    switch (prec) {
+        case MG_FP64: return 8;
+        case MG_FP32: return 4;
+        default: return 2;
+    }
+}
+
+int launch_march(int dim, int mode, int loader, int prec, int prec_c, const KArgs& a, int gx, int gy,
+                 int gz, int ty, size_t smem, void* stream) {
+    switch (prec) {
+        case MG_FP64: return launch_march_f64(dim, mode, loader, prec_c, a, gx, gy, gz, ty, smem, stream);
+        case MG_FP32: return launch_march_f32(dim, mode, loader, prec_c, a, gx, gy, gz, ty, smem, stream);
+        case MG_FP16: return launch_march_f16(dim, mode, loader, prec_c, a, gx, gy, gz, ty, smem, stream);
+        case MG_BF16: return launch_march_bf16(dim, mode, loader, prec_c, a, gx, gy, gz, ty, smem, stream);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+static int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Grid shape of a stencil march.  Non-restricting passes: 3D CTAs of 8 warps
+// (8 rows of one 32V-wide x-chunk) marching over z-ranges sized so that the
+// grid has >= ~4 CTAs per SM (152 SMs); 2D: 4 warps per CTA, one x-chunk per
+// warp, marching over row ranges.  Restriction: 2TJ+1 fine rows (TJ coarse
+// rows) per CTA and 2TK+1 fine planes per z-range, with one shared fine row /
+// plane between neighbouring tiles and x-chunks overlapping by one vector.
+MarchShape march_shape(int dim, int mode, int prec, int n, int P, int tz_hint) {
+    const int V = (int)(16 / elem_size(prec));
+    const int CW = 32 * V;
+    const size_t cs = prec == MG_FP64 ? 8 : 4;
+    const int target = 4 * 152;
+    MarchShape s{};
+    if (mode == M_RESTRICT) {
+        const int nc = (n - 1) / 2;
+        s.xstep = P > CW ? CW - V : CW;
+        int nchunks = P > CW ? 1 + cdiv(P - CW, CW - V) : 1;
+        if (dim == 3) {
+            int TJ = clampi(nc, 1, 4);
+            s.ty = 2 * TJ + 1;
+            s.ystep = 2 * TJ;
+            s.gx = nchunks;
+            s.gy = cdiv(nc, TJ);
+            int TK = tz_hint > 0 ? tz_hint : clampi((int)((long long)nc * s.gx * s.gy / target), 1, 16);
+            TK = clampi(TK, 1, nc);
+            s.zlen = 2 * TK + 1;
+            s.zstep = 2 * TK;
+            s.gz = cdiv(nc, TK);
+            s.smem = (size_t)(2 * (s.ty + 2) * CW) * cs + (size_t)(s.ty * 32 * (V / 2 > 0 ? V / 2 : 1)) * cs;
+        } else {
+            int W = clampi(nchunks, 1, 4);
+            s.ty = W;
+            s.gx = cdiv(nchunks, W);
+            int TK = tz_hint > 0 ? tz_hint : clampi((int)((long long)nc * s.gx / target), 1, 16);
+            TK = clampi(TK, 1, nc);
+            s.zlen = 2 * TK + 1;
+            s.zstep = 2 * TK;
+            s.gy = cdiv(nc, TK);
+            s.gz = 1;
+            s.smem = 0;
+        }
+        return s;
+    }
+    s.xstep = CW;
+    const int nchunks = cdiv(P, CW);
+    if (dim == 3) {
+        s.ty = clampi(n, 1, 8);
+        s.ystep = s.ty;
+        s.gx = nchunks;
+        s.gy = cdiv(n, s.ty);
+        int zl = tz_hint > 0 ? tz_hint : clampi((int)((long long)n * s.gx * s.gy / target), 4, 64);
+        zl = clampi(zl, 1, n);
+        s.zlen = zl;
+        s.zstep = zl;
+        s.gz = cdiv(n, zl);
+        s.smem = (size_t)(2 * (s.ty + 2) * CW) * cs;
+    } else {
+        int W = clampi(nchunks, 1, 4);
+        s.ty = W;
+        s.gx = cdiv(nchunks, W);
+        int zl = tz_hint > 0 ? tz_hint : clampi((int)((long long)n * s.gx / target), 4, 64);
+        zl = clampi(zl, 1, n);
+        s.zlen = zl;
+        s.zstep = zl;
+        s.gy = cdiv(n, zl);
+        s.gz = 1;
+        s.smem = 0;
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------- base-level solve
+// c = A0^-1 g with the dense FP64 inverse computed on the host at setup
+// (exact solve on the coarsest level, Sec. 4.2); accumulation in FP64, the
+// result rounded to the level's storage type.
+template <class T>
+__global__ void k_coarse_solve(const double* __restrict__ minv, int m, const T* __restrict__ g, T* __restrict__ c,
+                               int n, int P, long long S, int dim, const DevState* st, int gate) {
+    if (gate && st->phase != 0) return;
+    extern __shared__ double gs[];
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        int i = q % n, j = (q / n) % n, k = q / (n * n);
+        long long o = (dim == 3 ? (long long)k * S : 0LL) + (long long)j * P + i;
+        gs[q] = (double)ld1(g + o);
+    }
+    __syncthreads();
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    double s = 0.0;
+    const double* row = minv + (long long)p * m;
+    for (int q = 0; q < m; ++q) s = fma(row[q], gs[q], s);
+    int i = p % n, j = (p / n) % n, k = p / (n * n);
+    long long o = (dim == 3 ? (long long)k * S : 0LL) + (long long)j * P + i;
+    st1(c + o, s);
+}
+
+int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void* c, const Geom& geo,
+                        const DevState* st, int gate, void* stream) {
+    dim3 grid((m + 255) / 256), block(256);
+    size_t sm = (size_t)m * sizeof(double);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (prec) {
+        case MG_FP64:
+            k_coarse_solve<double><<<grid, block, sm, s>>>(inv, m, (const double*)g, (double*)c, geo.n, geo.P, geo.S, geo.dim, st, gate);
+            break;
+        case MG_FP32:
+            k_coarse_solve<float><<<grid, block, sm, s>>>(inv, m, (const float*)g, (float*)c, geo.n, geo.P, geo.S, geo.dim, st, gate);
+            break;
+        case MG_FP16:
+            k_coarse_solve<__half><<<grid, block, sm, s>>>(inv, m, (const __half*)g, (__half*)c, geo.n, geo.P, geo.S, geo.dim, st, gate);
+            break;
+        case MG_BF16:
+            k_coarse_solve<__nv_bfloat16><<<grid, block, sm, s>>>(inv, m, (const __nv_bfloat16*)g, (__nv_bfloat16*)c, geo.n, geo.P, geo.S, geo.dim, st, gate);
+            break;
+        default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- stand-alone prolongation
+// c_fine += P c_coarse (Alg. 1 step 4) when no post-smoothing sweep follows.
+template <int DIM, class T, class TC>
+__global__ void k_prolong_add(KArgs a, const DevState* st, int gate) {
+    using C = typename Tr<T>::C;
+    constexpr int V = Tr<T>::V;
+    if (gate && st->phase != 0) return;
+    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= a.P || y >= a.n) return;
+    C v[V];
+    const long long o = offs<DIM>(x, y, z, a.P, a.S);
+    T* f = reinterpret_cast<T*>(a.dst) + o;
+    ldv(f, v);
+    Load<DIM, L_PROLONG, T, TC>::add_prolong_vec(a, x, y, z, v);
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+        if (x + i >= a.n) v[i] = 0;
+    stv(f, v);
+}
+
+template <int DIM, class T>
+static int prolong_tc(int prec_c, const KArgs& a, dim3 grid, dim3 block, cudaStream_t s, const DevState* st, int gate) {
+    switch (prec_c) {
+        case MG_FP64: k_prolong_add<DIM, T, double><<<grid, block, 0, s>>>(a, st, gate); break;
+        case MG_FP32: k_prolong_add<DIM, T, float><<<grid, block, 0, s>>>(a, st, gate); break;
+        case MG_FP16: k_prolong_add<DIM, T, __half><<<grid, block, 0, s>>>(a, st, gate); break;
+        case MG_BF16: k_prolong_add<DIM, T, __nv_bfloat16><<<grid, block, 0, s>>>(a, st, gate); break;
+        default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_prolong_add(int dim, int prec, int prec_c, const Geom& f, const Geom& c, void* fine,
+                       const void* coarse, const DevState* st, int gate, void* stream) {
+    KArgs a{};
+    a.n = f.n; a.P = f.P; a.S = f.S; a.nc = c.n; a.Pc = c.P; a.Sc = c.S;
+    a.dst = fine; a.coarse = coarse;
+    const int V = (int)(16 / elem_size(prec));
+    dim3 block(32, 4);
+    dim3 grid((unsigned)cdiv(f.P / V, 32), (unsigned)cdiv(f.n, 4), (unsigned)(dim == 3 ? f.n : 1));
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (prec) {
+        case MG_FP64: return dim == 3 ? prolong_tc<3, double>(prec_c, a, grid, block, s, st, gate) : prolong_tc<2, double>(prec_c, a, grid, block, s, st, gate);
+        case MG_FP32: return dim == 3 ? prolong_tc<3, float>(prec_c, a, grid, block, s, st, gate) : prolong_tc<2, float>(prec_c, a, grid, block, s, st, gate);
+        case MG_FP16: return dim == 3 ? prolong_tc<3, __half>(prec_c, a, grid, block, s, st, gate) : prolong_tc<2, __half>(prec_c, a, grid, block, s, st, gate);
+        case MG_BF16: return dim == 3 ? prolong_tc<3, __nv_bfloat16>(prec_c, a, grid, block, s, st, gate) : prolong_tc<2, __nv_bfloat16>(prec_c, a, grid, block, s, st, gate);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- FP64 residual (IR step 1)
+// r = b - A u in FP64 with per-CTA partials {sum r^2, max |r|, sum b^2, 0};
+// optionally copies u to the caller's contiguous array.  One thread per point.
+template <int DIM>
+__global__ void k_residual64(RArgs a, int init_copy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    double sr = 0.0, sb = 0.0;
+    unsigned long long mr = 0ull;
+    if (i < a.n && j < a.n) {
+        const long long o = offs<DIM>(i, j, k, a.P, a.S);
+        const long long oc = DIM == 3 ? ((long long)k * a.n + j) * a.n + i : (long long)j * a.n + i;
+        const double bv = __ldg(a.b + oc);
+        double r;
+        if (init_copy) {
+            r = bv;  // u = 0: r = b
+        } else {
+            const double* u = a.u + o;
+            double nb = __ldg(u - 1) + __ldg(u + 1) + __ldg(u - a.P) + __ldg(u + a.P);
+            if (DIM == 3) nb += __ldg(u - a.S) + __ldg(u + a.S);
+            const double uc = __ldg(u);
+            r = fma(-a.h2inv, fma(2.0 * DIM, uc, -nb), bv);
+            if (a.uout) a.uout[oc] = uc;
+        }
+        if (a.r) a.r[o] = r;
+        sr = r * r;
+        sb = bv * bv;
+        mr = abs_key(r);
+    }
+    __shared__ double s1[32], s2[32];
+    __shared__ unsigned long long s3[32];
+    const int lane = threadIdx.x & 31, wid = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+    sr = warp_sum(sr); sb = warp_sum(sb); mr = warp_max(mr);
+    if (lane == 0) { s1[wid] = sr; s2[wid] = sb; s3[wid] = mr; }
+    __syncthreads();
+    if (wid == 0) {
+        sr = lane < nw ? s1[lane] : 0.0;
+        sb = lane < nw ? s2[lane] : 0.0;
+        mr = lane < nw ? s3[lane] : 0ull;
+        sr = warp_sum(sr); sb = warp_sum(sb); mr = warp_max(mr);
+        if (lane == 0) {
+            const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+            a.partials[4 * bid + 0] = sr;
+            a.partials[4 * bid + 1] = __longlong_as_double((long long)mr);
+            a.partials[4 * bid + 2] = sb;
+            a.partials[4 * bid + 3] = 0.0;
+        }
+    }
+}
+
+static void residual_grid(int dim, int n, dim3& grid, dim3& block) {
+    block = dim3(64, 4);
+    grid = dim3((unsigned)cdiv(n, 64), (unsigned)cdiv(n, 4), (unsigned)(dim == 3 ? n : 1));
+}
+
+int residual64_blocks(int dim, int n) {
+    dim3 g, b;
+    residual_grid(dim, n, g, b);
+    return (int)(g.x * g.y * g.z);
+}
+
+int launch_residual64(int dim, const RArgs& a, int* nblocks, void* stream) {
+    dim3 grid, block;
+    residual_grid(dim, a.n, grid, block);
+    if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
+    if (dim == 3) k_residual64<3><<<grid, block, 0, (cudaStream_t)stream>>>(a, 0);
+    else k_residual64<2><<<grid, block, 0, (cudaStream_t)stream>>>(a, 0);
+    return (int)cudaGetLastError();
+}
+
+int launch_init_rb(int dim, const Geom& geo, const double* b, double* r, double* partials, int* nblocks,
+                   void* stream) {
+    RArgs a{};
+    a.n = geo.n; a.P = geo.P; a.S = geo.S; a.b = b; a.r = r; a.partials = partials;
+    dim3 grid, block;
+    residual_grid(dim, a.n, grid, block);
+    if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
+    if (dim == 3) k_residual64<3><<<grid, block, 0, (cudaStream_t)stream>>>(a, 1);
+    else k_residual64<2><<<grid, block, 0, (cudaStream_t)stream>>>(a, 1);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- norms and IR control
+// Reduces per-CTA partials in a fixed order (deterministic), then applies the
+// stopping test of Alg. 2 and sets alpha for the next step (line 4):
+// alpha = ||r||_inf / sigma (scaling 1), ||r||_2 / sigma (scaling 2) or 1.
+// kind: FIN_INIT after r = b - A u0, FIN_STEP after an update (partials of
+// stride 2), FIN_GUARD after the true residual, 3 = report only.
+__global__ void k_finalize(int kind, DevState* st, const double* __restrict__ partials, int nblocks) {
+    const int stride = kind == FIN_STEP ? 2 : 4;
+    double sr = 0.0, sb = 0.0;
+    unsigned long long mr = 0ull;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        sr += partials[(long long)stride * b];
+        unsigned long long m = (unsigned long long)__double_as_longlong(partials[(long long)stride * b + 1]);
+        mr = m > mr ? m : mr;
+        if (stride == 4) sb += partials[(long long)stride * b + 2];
+    }
+    __shared__ double s1[32], s2[32];
+    __shared__ unsigned long long s3[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    sr = warp_sum(sr); sb = warp_sum(sb); mr = warp_max(mr);
+    if (lane == 0) { s1[wid] = sr; s2[wid] = sb; s3[wid] = mr; }
+    __syncthreads();
+    if (wid != 0) return;
+    sr = lane < nw ? s1[lane] : 0.0;
+    sb = lane < nw ? s2[lane] : 0.0;
+    mr = lane < nw ? s3[lane] : 0ull;
+    sr = warp_sum(sr); sb = warp_sum(sb); mr = warp_max(mr);
+    if (lane != 0) return;
+    const double rn = sqrt(sr);
+    const double rinf = __longlong_as_double((long long)mr);
+    if (kind == FIN_INIT) {
+        st->bnorm2 = sqrt(sb);
+        st->tol_abs = st->tol_mode == 0 ? st->tol * st->bnorm2 : st->tol;
+        st->iter = 0;
+        st->guard_restarts = 0;
+        st->stag = 0;
+        st->status = MG_OK;
+    }
+    const double bn = st->bnorm2;
+    const double rel = bn > 0.0 ? rn / bn : rn;
+    if (kind == 3) {  // report only
+        st->rel_true = rel;
+        return;
+    }
+    if (kind == FIN_STEP) {
+        st->iter += 1;
+        st->stag = (rn >= 0.999 * st->rnorm2) ? st->stag + 1 : 0;
+    }
+    st->rnorm2 = rn;
+    st->rnorminf = rinf;
+    const int it = st->iter < kMaxHist ? st->iter : kMaxHist;
+    st->hist[it] = rel;
+    if (kind == FIN_GUARD) st->rel_true = rel;
+    if (!isfinite(rn) || !isfinite(rinf)) {
+        st->phase = 3;
+        st->status = MG_ERR_NUMERIC;
+        return;
+    }
+    if (rn <= st->tol_abs) {
+        if (kind == FIN_GUARD || !st->guard) {
+            st->phase = 2;
+            st->status = MG_OK;
+            return;
+        }
+        st->phase = 1;
+        return;
+    }
+    if (kind == FIN_GUARD) st->guard_restarts += 1;
+    if (st->iter >= st->max_iter || st->stag >= 5) {
+        st->phase = 3;
+        st->status = MG_ERR_NOT_CONVERGED;
+        return;
+    }
+    double alpha = 1.0, inv = 1.0;
+    if (st->scaling == 1) { alpha = rinf / st->sigma; inv = st->sigma / rinf; }
+    else if (st->scaling == 2) { alpha = rn / st->sigma; inv = st->sigma / rn; }
+    st->alpha = alpha;
+    st->inv = inv;
+    st->phase = 0;
+}
+
+int launch_finalize(int kind, DevState* st, const double* partials, int nblocks, void* stream) {
+    k_finalize<<<1, 1024, 0, (cudaStream_t)stream>>>(kind, st, partials, nblocks);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- packing
+template <class T>
+__global__ void k_pack(int dim, int n, int P, long long S, const T* __restrict__ src, T* __restrict__ dst, int unpack) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= n || j >= n) return;
+    const long long o = (dim == 3 ? (long long)k * S : 0LL) + (long long)j * P + i;
+    const long long oc = dim == 3 ? ((long long)k * n + j) * n + i : (long long)j * n + i;
+    if (unpack) dst[oc] = src[o];
+    else dst[o] = src[oc];
+}
+
+static int pack_any(int dim, int prec, const Geom& geo, const void* src, void* dst, int unpack, void* stream) {
+    dim3 block(64, 4), grid((unsigned)cdiv(geo.n, 64), (unsigned)cdiv(geo.n, 4), (unsigned)(dim == 3 ? geo.n : 1));
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (elem_size(prec)) {
+        case 8: k_pack<unsigned long long><<<grid, block, 0, s>>>(dim, geo.n, geo.P, geo.S, (const unsigned long long*)src, (unsigned long long*)dst, unpack); break;
+        case 4: k_pack<unsigned><<<grid, block, 0, s>>>(dim, geo.n, geo.P, geo.S, (const unsigned*)src, (unsigned*)dst, unpack); break;
+        default: k_pack<unsigned short><<<grid, block, 0, s>>>(dim, geo.n, geo.P, geo.S, (const unsigned short*)src, (unsigned short*)dst, unpack); break;
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_pack(int dim, int prec, const Geom& geo, const void* src_contig, void* dst_padded, void* stream) {
+    return pack_any(dim, prec, geo, src_contig, dst_padded, 0, stream);
+}
+int launch_unpack(int dim, int prec, const Geom& geo, const void* src_padded, void* dst_contig, void* stream) {
+    return pack_any(dim, prec, geo, src_padded, dst_contig, 1, stream);
+}
+
+}  // namespace mgi

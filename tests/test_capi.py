@@ -1,0 +1,77 @@
+"""The C-ABI library: builds, loads, exports every symbol of include/mg.h, and
+its host-side logic (coarsening rule, parameter validation, footprint) -- no
+GPU needed."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2007_07539_gb300 import mg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = mg.lib()
+    decl = declared_functions()
+    assert len(decl) >= 15
+    for name in decl:
+        assert hasattr(L, name), name
+    assert sorted(mg.EXPORTS) == decl
+
+
+def test_level_count_matches_oracle(oracle):
+    for n in (1, 2, 3, 5, 7, 31, 47, 63, 127, 255, 383, 511, 4095):
+        assert mg.level_count(n) == oracle.level_sizes(n)
+    for n, L in ((255, 3), (511, 2), (127, 6)):
+        assert mg.level_count(n, L) == oracle.level_sizes(n, L)
+    assert mg.level_count(0) == []
+
+
+def test_params_defaults():
+    p = mg.make_params(3, 255)
+    assert (p.nu1, p.nu2, p.gamma, p.scaling, p.tol_mode, p.max_iter) == (2, 2, 1, 1, 0, 100)
+    assert p.omega == 0.8 and p.tol == 1e-10
+    assert list(p.prec)[:7] == [mg.FP64] * 7
+
+
+def test_ladders():
+    assert mg.ladder("HSD", 8) == [0, 1, 1, 1, 1, 1, 2, 2]
+    assert mg.ladder("DSH", 6, 2, 1) == [2, 1, 1, 1, 0, 0]
+    assert mg.ladder("BSD", 7)[-2:] == [mg.BF16, mg.BF16]
+    assert mg.ladder("H", 3) == [2, 2, 2]
+
+
+@pytest.mark.parametrize("bad", [dict(dim=4), dict(n=0), dict(omega=2.5), dict(gamma=3), dict(scaling=7),
+                                 dict(max_iter=5000), dict(nu1=-1), dict(levels=9), dict(tol=-1.0)])
+def test_invalid_params_rejected_without_gpu(bad):
+    p = mg.make_params(3, 63)
+    for k, v in bad.items():
+        setattr(p, k, v)
+    h = ctypes.c_void_p()
+    st = mg.lib().mg_create_hierarchy(ctypes.byref(p), None, ctypes.byref(h))
+    assert st == 2 and not h.value
+    assert mg.last_error()
+    assert mg.footprint_bytes(p) == 0
+
+
+def test_coarsest_level_limit():
+    p = mg.make_params(3, 33)  # 33 -> 16: 4096 unknowns on the base level: allowed
+    assert mg.footprint_bytes(p) > 0
+    p = mg.make_params(3, 34)  # one level of 34^3 unknowns: too large for the dense base solve
+    assert mg.footprint_bytes(p) == 0
+
+
+def test_footprint_scales_with_precision():
+    d = mg.footprint_bytes(mg.make_params(3, 255, "D"))
+    h = mg.footprint_bytes(mg.make_params(3, 255, "H"))
+    assert 0 < h < d
+    # FP64 u, r plus three level vectors per level: about 2*8 + 3*8*8/7 bytes/DOF for D_MG
+    assert 40 * 255**3 < d < 56 * 255**3

@@ -1,0 +1,212 @@
+"""Solve parity through mg_solve (the C ABI): the GPU mixed-precision
+multigrid-preconditioned IR (Alg. 2 with Alg. 1 cycles) against the FP64
+oracle.  Bars: relative true residual <= 1e-10, ||u_gpu - u_oracle||_2 /
+||u_oracle||_2 <= 1e-6, iteration count equal to the oracle's in all-FP64
+mode and at most 2 more in the low-precision modes."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2007_07539_gb300 import inputs as I
+from paper_2007_07539_gb300 import mg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def gpu_solve(dim, n, lad, b, u0=None, **kw):
+    import torch
+    p = mg.make_params(dim, n, lad, zero_guess=1 if u0 is None else 0, **kw)
+    with mg.Hierarchy(p) as h:
+        bd = torch.from_numpy(b).cuda()
+        ud = torch.zeros_like(bd) if u0 is None else torch.from_numpy(u0).cuda()
+        res = h.solve(bd, ud)
+        return ud.cpu().numpy(), res
+
+
+def oracle_kw(lad, kw):
+    o = dict(nu1=kw.get("nu1", 2), nu2=kw.get("nu2", 2), gamma=kw.get("gamma", 1),
+             omega=kw.get("omega", 0.8), tol=kw.get("tol", 1e-10), tol_mode=kw.get("tol_mode", 0),
+             max_iter=kw.get("max_iter", 100), levels=kw.get("levels", 0))
+    o["scaling"] = kw.get("scaling", 1)
+    return o
+
+
+def check_solve(oracle, dim, n, lad, b, u0=None, extra_iters=0, **kw):
+    u, res = gpu_solve(dim, n, lad, b, u0, **kw)
+    uo, info, hist = oracle.ir_solve(b, u0, **oracle_kw(lad, kw))
+    assert info["converged"]
+    assert res["status"] == 0, res
+    tol = kw.get("tol", 1e-10)
+    if kw.get("tol_mode", 0) == 0:
+        assert res["rel_res_true"] <= tol
+        # independent check of the reported residual: the oracle's b - A u on the GPU's u
+        rt = np.linalg.norm(oracle.residual(b, u)) / np.linalg.norm(b)
+        assert rt <= tol and rt == pytest.approx(res["rel_res_true"], rel=1e-6)
+    else:
+        assert np.linalg.norm(oracle.residual(b, u)) < tol
+    assert np.linalg.norm(u - uo) <= 1e-6 * np.linalg.norm(uo)
+    if extra_iters == 0:
+        assert res["iters"] == info["iters"], (res["iters"], info["iters"], hist)
+    else:
+        assert res["iters"] <= info["iters"] + extra_iters, (res["iters"], info["iters"])
+    return u, res, info
+
+
+def test_config1_2d_manufactured_fp64(oracle):
+    """2D 127^2, u = sin(pi x) sin(pi y), all-FP64 V(2,2), omega 0.8, 6 levels, coarsest 3x3."""
+    n = 127
+    b = I.manufactured_rhs(2, n)
+    u, res, info = check_solve(oracle, 2, n, "D", b, scaling=0)
+    assert res["levels"] == 6
+    h = 1.0 / (n + 1)
+    uh = 2 * math.pi**2 / (8 / h**2 * math.sin(math.pi * h / 2) ** 2) * I.sine_product(2, n)
+    assert np.abs(u - uh).max() <= 1e-9 * np.abs(uh).max()
+
+
+@pytest.mark.parametrize("dim,n", [(2, 31), (2, 255), (3, 15), (3, 31), (3, 63), (2, 383), (3, 47)])
+def test_fp64_random_rhs_same_iterations(oracle, dim, n):
+    check_solve(oracle, dim, n, "D", I.random_rhs(dim, n, 100 + n), scaling=0)
+
+
+@pytest.mark.parametrize("dim,n,lad", [(3, 31, "H"), (3, 63, "H"), (3, 127, "H"), (2, 255, "H"),
+                                       (3, 63, "HSD"), (3, 127, "HSD"), (3, 63, "BSD"), (3, 63, "HS"),
+                                       (3, 63, "S"), (2, 511, "HSD"), (3, 95, "H")])
+def test_low_precision_within_two_iterations(oracle, dim, n, lad):
+    check_solve(oracle, dim, n, lad, I.random_rhs(dim, n, 200 + n), extra_iters=2)
+
+
+@pytest.mark.parametrize("lad", ["D", "H"])
+def test_wcycle(oracle, lad):
+    check_solve(oracle, 3, 63, lad, I.random_rhs(3, 63, 300), extra_iters=0 if lad == "D" else 2,
+                gamma=2, scaling=0 if lad == "D" else 1)
+
+
+def test_two_norm_scaling_fp16(oracle):
+    """The paper-literal alternative: alpha = ||r||_2 (Sec. 4.3)."""
+    check_solve(oracle, 3, 63, "H", I.random_rhs(3, 63, 301), extra_iters=2, scaling=2)
+
+
+@pytest.mark.parametrize("lad", ["D", "H"])
+def test_paper_setting_random_guess_absolute_tolerance(oracle, lad):
+    """Sec. 6 / 8.1: random initial guess in [0, 1), absolute stopping test 1e-9."""
+    n = 63
+    b = I.manufactured_rhs(3, n)
+    u0 = I.random_guess(3, n, 302)
+    check_solve(oracle, 3, n, lad, b, u0, extra_iters=0 if lad == "D" else 2, tol_mode=1, tol=1e-9,
+                scaling=0 if lad == "D" else 1)
+
+
+@pytest.mark.parametrize("dim,n", [(3, 1), (3, 2), (3, 3), (2, 1), (2, 3), (3, 5), (2, 6)])
+def test_tiny_grids(oracle, dim, n):
+    """Single- and two-level hierarchies: the base solve is the whole cycle."""
+    check_solve(oracle, dim, n, "D", I.random_rhs(dim, n, 303), scaling=0)
+
+
+def test_host_and_device_pointers_agree():
+    import torch
+    n = 47
+    b = I.random_rhs(3, n, 304)
+    p = mg.make_params(3, n, "H", zero_guess=1)
+    with mg.Hierarchy(p) as h:
+        bd = torch.from_numpy(b).cuda()
+        ud = torch.zeros_like(bd)
+        r1 = h.solve(bd, ud)
+        uh = np.zeros_like(b)
+        r2 = h.solve(b, uh)
+        bp = torch.from_numpy(b).pin_memory()
+        up = torch.zeros_like(bp).pin_memory()
+        r3 = h.solve(bp, up)
+    assert np.array_equal(ud.cpu().numpy(), uh) and np.array_equal(uh, up.numpy())
+    assert r1["iters"] == r2["iters"] == r3["iters"]
+
+
+def test_not_converged_reports_last_iterate(oracle):
+    n = 63
+    b = I.random_rhs(3, n, 305)
+    u, res = gpu_solve(3, n, "D", b, max_iter=2, scaling=0)
+    assert res["status"] == 5 and res["iters"] == 2
+    uo, info, _ = oracle.ir_solve(b, max_iter=2, scaling=0)
+    assert np.linalg.norm(u - uo) <= 1e-12 * np.linalg.norm(uo)
+    assert res["rel_res_true"] == pytest.approx(info["rel_res_true"], rel=1e-9)
+
+
+def test_non_finite_rhs_is_reported():
+    """Host-side fault injection: a corrupted (NaN) right-hand side ends the solve with
+    MG_ERR_NUMERIC instead of iterating."""
+    import torch
+    n = 31
+    b = I.random_rhs(3, n, 306)
+    b[3, 4, 5] = np.nan
+    p = mg.make_params(3, n, "H", zero_guess=1)
+    with mg.Hierarchy(p) as h:
+        with pytest.raises(mg.MGError) as e:
+            h.solve(torch.from_numpy(b).cuda(), torch.zeros(n, n, n, dtype=torch.float64, device="cuda"))
+    assert e.value.status == 6
+
+
+def test_zero_rhs():
+    import torch
+    n = 31
+    p = mg.make_params(3, n, "H", zero_guess=1)
+    with mg.Hierarchy(p) as h:
+        ud = torch.zeros(n, n, n, dtype=torch.float64, device="cuda")
+        res = h.solve(torch.zeros_like(ud), ud)
+    assert res["status"] == 0 and res["iters"] == 0 and float(ud.abs().max()) == 0.0
+
+
+def test_resume_from_previous_solution(oracle):
+    """Checkpoint/resume: a solve restarted from its own output is already converged."""
+    import torch
+    n = 63
+    b = I.random_rhs(3, n, 307)
+    p = mg.make_params(3, n, "H")
+    with mg.Hierarchy(p) as h:
+        bd = torch.from_numpy(b).cuda()
+        ud = torch.zeros_like(bd)
+        r1 = h.solve(bd, ud)
+        r2 = h.solve(bd, ud)
+    assert r1["status"] == 0 and r2["status"] == 0 and r2["iters"] == 0
+
+
+# ----------------------------------------------------------------------------- full sizes
+def test_config2_255_fp16_and_fp64(oracle):
+    """3D 255^3 (16.6M DOF), f ~ U[-1, 1] from seed 2: FP16 V(2,2) preconditioner vs all-FP64,
+    both against the oracle's full FP64 solve."""
+    n = 255
+    b = I.random_rhs(3, n, 2)
+    uo, info, _ = oracle.ir_solve(b, scaling=0, nthreads=16)
+    assert info["converged"]
+    for lad, extra in (("H", 2), ("D", 0)):
+        u, res = gpu_solve(3, n, lad, b, scaling=0 if lad == "D" else 1)
+        assert res["status"] == 0 and res["rel_res_true"] <= 1e-10
+        assert np.linalg.norm(u - uo) <= 1e-6 * np.linalg.norm(uo)
+        assert res["iters"] <= info["iters"] + extra
+        if extra == 0:
+            assert res["iters"] == info["iters"]
+        r = oracle.residual(b, u)
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("lad,gamma", [("HSD", 1), ("BSD", 1), ("D", 1), ("HSD", 2)])
+def test_config3_511_manufactured(oracle, lad, gamma):
+    """3D 511^3 (133M DOF), u = prod sin(pi x): ladders FP16/FP32/FP64 and BF16-finest, V and W.
+    Checked against the closed-form discrete solution (which the oracle reproduces to
+    1e-12) and the oracle's FP64 residual on the GPU's u."""
+    n = 511
+    b = I.manufactured_rhs(3, n)
+    u, res = gpu_solve(3, n, lad, b, gamma=gamma, scaling=0 if lad == "D" else 1)
+    assert res["status"] == 0 and res["rel_res_true"] <= 1e-10
+    h = 1.0 / (n + 1)
+    lam1 = 12 / h**2 * math.sin(math.pi * h / 2) ** 2
+    uh = 3 * math.pi**2 / lam1 * I.sine_product(3, n)
+    assert np.linalg.norm(u - uh) <= 1e-6 * np.linalg.norm(uh)
+    r = oracle.residual(b, u)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
+    assert res["iters"] <= 20
