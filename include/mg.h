@@ -184,6 +184,32 @@ mg_status mg_serve_configure(size_t budget_bytes, int32_t max_inflight);
 mg_status mg_solve_batch(int32_t count, mg_hierarchy* const* hs, const double* const* b,
                          double* const* u, mg_result* res);
 
+/* ---------------------------------------------------------------- no device allocation */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory where they need a residual check: a
+ * host application that has already reserved (nearly) all device memory for
+ * its own pool, or a latency-critical loop where cudaMalloc/cudaFree would
+ * synchronise the device and stall other streams.  mg_solve and the stage
+ * calls allocate (hierarchy buffers, staging); this call does not.
+ *
+ * Computes, for the operator A of this library (5/7-point, h = 1/(n+1)):
+ *   norms[0] = ||b - A u||_2,  norms[1] = ||b - A u||_inf,  norms[2] = ||b||_2
+ * b, u: n^d FP64 values, contiguous, x fastest, device memory, read only.
+ * norms: 3 doubles of device memory, written.  All three must be device
+ * pointers (else MG_ERR_INVALID).  Asynchronous: enqueued on cuda_stream
+ * (NULL = legacy default stream); the norms are valid once the stream has
+ * reached them.
+ * Scratch: per-CTA partial sums in one static device array of 2 MiB that
+ * every device loading this library keeps until exit; the largest accepted
+ * problem is n^d = 536,870,912 points (MG_ERR_INVALID beyond, with a message).
+ * All calls share that array: calls whose work overlaps on the GPU (e.g. on
+ * different streams) race and must be serialised by the caller.  The first
+ * call on a device looks up the array's device address with that device
+ * current; make it before any stream capture begins. */
+mg_status mg_residual_norms_noalloc(int32_t dim, int32_t n, const double* b, const double* u,
+                                    double* norms, void* cuda_stream);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Device time of one kernel of the IR step, summed over the steps of a solve. */

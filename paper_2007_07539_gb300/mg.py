@@ -30,7 +30,7 @@ VEC_C, VEC_G, VEC_T, VEC_U, VEC_R = range(5)
 EXPORTS = ["mg_params_init", "mg_level_count", "mg_last_error", "mg_footprint_bytes",
            "mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
            "mg_serve_configure", "mg_solve_batch", "mg_profile_solve", "mg_level_write", "mg_level_read",
-           "mg_level_info_get", "mg_run_stage"]
+           "mg_level_info_get", "mg_run_stage", "mg_residual_norms_noalloc"]
 
 
 class Params(ctypes.Structure):
@@ -124,6 +124,8 @@ def lib() -> ctypes.CDLL:
             L.mg_level_info_get.argtypes = [H, i32, ctypes.POINTER(LevelInfo)]
             L.mg_run_stage.argtypes = [H, i32, i32, dp, vp, dp]
             L.mg_profile_solve.argtypes = [H, vp, vp, R, ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
+            L.mg_residual_norms_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
+            L.mg_residual_norms_noalloc.restype = ctypes.c_int
             for f in ("mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
                       "mg_serve_configure", "mg_solve_batch", "mg_level_write", "mg_level_read",
                       "mg_level_info_get", "mg_run_stage", "mg_profile_solve"):
@@ -331,3 +333,13 @@ def solve_batch(hs: list[Hierarchy], bs: list, us: list) -> list[dict]:
 
 def serve_configure(budget_bytes: int = 0, max_inflight: int = 0) -> None:
     _check(lib().mg_serve_configure(int(budget_bytes), int(max_inflight)), "mg_serve_configure")
+
+
+def residual_norms_noalloc(dim: int, n: int, b, u, norms, stream=None) -> None:
+    """mg_residual_norms_noalloc: writes ||b - A u||_2, ||b - A u||_inf and ||b||_2 into the
+    3-element device array `norms`, enqueued on `stream` (default: torch's current stream).
+    Allocates no device memory (a static 2 MiB scratch array inside the library), for
+    callers that cannot allocate at that point; calls that overlap on the GPU race."""
+    _check(lib().mg_residual_norms_noalloc(int(dim), int(n), ctypes.c_void_p(_ptr(b)), ctypes.c_void_p(_ptr(u)),
+                                           ctypes.c_void_p(_ptr(norms)), ctypes.c_void_p(_stream_handle(stream))),
+           "mg_residual_norms_noalloc")
