@@ -19,6 +19,7 @@ WORKLOADS = {
     "3d_n255_random_seed2": dict(dim=3, n=255, rhs=("random", 2)),
     "2d_n127_manufactured": dict(dim=2, n=127, rhs=("manufactured", 1)),
     "3d_n63_random_seed2": dict(dim=3, n=63, rhs=("random", 2)),
+    "3d_n511_manufactured": dict(dim=3, n=511, rhs=("manufactured", 1)),
 }
 
 
