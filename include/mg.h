@@ -214,11 +214,12 @@ mg_status mg_residual_norms_noalloc(int32_t dim, int32_t n, const double* b, con
 
 /* Device time of one kernel of the IR step, summed over the steps of a solve. */
 typedef struct mg_kernel_time {
-    int32_t kind;        /* 0 stencil march, 1 base solve, 2 prolongation, 3 zero fill, 4 norm finalise */
+    int32_t kind;        /* 0 stencil sweep, 1 base solve, 2 prolongation, 3 zero fill, 4 norm
+                            finalise, 5 FP64 IR update, 6 scale and cast of the residual */
     int32_t level;       /* level index (0 = coarsest) */
-    int32_t mode;        /* march mode: 0 sweep, 1 two sweeps from zero, 2 one sweep from zero,
-                            3 residual + restriction, 4 FP64 IR update */
-    int32_t loader;      /* march input: 0 stored vector, 1 scaled FP64 residual, 2 with prolongation */
+    int32_t mode;        /* sweep mode: 0 Jacobi, 1 two sweeps from zero, 2 one sweep from zero,
+                            3 residual + restriction */
+    int32_t loader;      /* reserved (0) */
     int32_t prec;        /* mg_prec of the level */
     int32_t prec_coarse; /* mg_prec of the next coarser level */
     int32_t launches;    /* number of launches timed */
@@ -255,10 +256,10 @@ mg_status mg_level_info_get(const mg_hierarchy* h, int32_t level, mg_level_info*
  *   MG_STAGE_JACOBI_ZERO2  C <- two damped Jacobi sweeps from C = 0 on G
  *   MG_STAGE_RESTRICT      G_{l-1} <- cast(R (G_l - A_l C_l))     (Alg. 1 step 2)
  *   MG_STAGE_PROLONG       C_l <- C_l + cast(P C_{l-1})           (Alg. 1 step 4)
- *   MG_STAGE_JACOBI_PROLONG  C_l <- one sweep applied to C_l + P C_{l-1}
+ *   MG_STAGE_JACOBI_PROLONG  C_l <- C_l + P C_{l-1}, then one Jacobi sweep
  *   MG_STAGE_COARSE        C_0 <- A_0^-1 G_0 (level 0 only)
- *   MG_STAGE_SCALE_ZERO2   G_L <- cast(R * s), then JACOBI_ZERO2 on level L;
- *                          s = arg[0]
+ *   MG_STAGE_SCALE_ZERO2   G_L <- cast(R * s) (Alg. 2 line 4), then JACOBI_ZERO2 on
+ *                          level L; s = arg[0]
  *   MG_STAGE_IR_UPDATE     U <- U + a C_L;  R <- R - a A C_L;  a = arg[0]  (Alg. 2 l. 6-7)
  *   MG_STAGE_RESIDUAL      R <- B - A U with B = arg pointer (n^d FP64, device)
  *   MG_STAGE_CYCLE         C_L <- one full cycle on G_L (Alg. 1, recursive)

@@ -158,41 +158,33 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
     int rc = 0;
     switch (stage) {
         case MG_STAGE_JACOBI: {
-            if (level == 0 && L == 0 && false) break;
-            Op op = mgi_march_op(*h, level, M_JACOBI, L_PLAIN, lv.c, lv.t, lv.g, 0, nullptr);
+            Op op = mgi_kernel_op(*h, level, K_SWEEP, M_JACOBI, lv.c, lv.t, lv.g, 0, nullptr);
             rc = mgi_run_op(*h, op, s);
             if (!rc) { mg_status e = copy_back(*h, level, nullptr); if (e) return e; }
             break;
         }
         case MG_STAGE_JACOBI_ZERO2: {
-            Op op = mgi_march_op(*h, level, M_ZERO2, L_PLAIN, lv.g, lv.c, nullptr, 0, nullptr);
+            Op op = mgi_kernel_op(*h, level, K_SWEEP, M_ZERO2, lv.g, lv.c, nullptr, 0, nullptr);
             rc = mgi_run_op(*h, op, s);
             break;
         }
         case MG_STAGE_RESTRICT: {
             if (level < 1) SFAIL(MG_ERR_INVALID, "restriction needs level >= 1");
-            Op op = mgi_march_op(*h, level, M_RESTRICT, L_PLAIN, lv.c, h->lv[level - 1].g, lv.g, 0, nullptr);
+            Op op = mgi_kernel_op(*h, level, K_SWEEP, M_RESTRICT, lv.c, h->lv[level - 1].g, lv.g, 0, nullptr);
             rc = mgi_run_op(*h, op, s);
             break;
         }
-        case MG_STAGE_PROLONG: {
-            if (level < 1) SFAIL(MG_ERR_INVALID, "prolongation needs level >= 1");
-            Op op{};
-            op.kind = OP_PROLONG;
-            op.level = level;
-            op.prec = lv.prec;
-            op.prec_c = h->lv[level - 1].prec;
-            op.fine = lv.c;
-            op.coarse = h->lv[level - 1].c;
-            rc = mgi_run_op(*h, op, s);
-            break;
-        }
+        case MG_STAGE_PROLONG:
         case MG_STAGE_JACOBI_PROLONG: {
             if (level < 1) SFAIL(MG_ERR_INVALID, "prolongation needs level >= 1");
-            Op op = mgi_march_op(*h, level, M_JACOBI, L_PROLONG, lv.c, lv.t, lv.g, 0, nullptr);
+            Op op = mgi_kernel_op(*h, level, K_PROLONG, 0, nullptr, lv.c, nullptr, 0, nullptr);
             op.a.coarse = h->lv[level - 1].c;
             rc = mgi_run_op(*h, op, s);
-            if (!rc) { mg_status e = copy_back(*h, level, nullptr); if (e) return e; }
+            if (!rc && stage == MG_STAGE_JACOBI_PROLONG) {
+                Op sw = mgi_kernel_op(*h, level, K_SWEEP, M_JACOBI, lv.c, lv.t, lv.g, 0, nullptr);
+                rc = mgi_run_op(*h, sw, s);
+                if (!rc) { mg_status e = copy_back(*h, level, nullptr); if (e) return e; }
+            }
             break;
         }
         case MG_STAGE_COARSE: {
@@ -208,9 +200,13 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
         case MG_STAGE_SCALE_ZERO2: {
             if (level != L) SFAIL(MG_ERR_INVALID, "scale-cast runs on the finest level");
             if (!arg) SFAIL(MG_ERR_INVALID, "arg[0] (scale) required");
-            Op op = mgi_march_op(*h, level, L > 0 ? M_ZERO2 : M_ZERO1, L_SCALED, nullptr, lv.c, nullptr, 0, nullptr);
+            Op op = mgi_kernel_op(*h, level, K_SCALE, 0, nullptr, lv.g, nullptr, 0, nullptr);
             op.a.inv_explicit = arg[0];
             rc = mgi_run_op(*h, op, s);
+            if (!rc && L > 0) {
+                Op sw = mgi_kernel_op(*h, level, K_SWEEP, M_ZERO2, lv.g, lv.c, nullptr, 0, nullptr);
+                rc = mgi_run_op(*h, sw, s);
+            }
             break;
         }
         case MG_STAGE_IR_UPDATE: {

@@ -193,12 +193,12 @@ struct Gen {
         return h->lv[l].g;
     }
 
-    Op march(int l, int mode, int loader, const void* src, void* dst, const void* g) {
+    Op kernel(int l, int kkind, int mode, const void* src, void* dst, const void* g) {
         Op op{};
-        op.kind = OP_MARCH;
+        op.kind = OP_KERNEL;
         op.level = l;
+        op.kkind = kkind;
         op.mode = mode;
-        op.loader = loader;
         op.prec = h->lv[l].prec;
         op.prec_c = l > 0 ? h->lv[l - 1].prec : op.prec;
         const Geom& f = h->lv[l].geo;
@@ -207,33 +207,31 @@ struct Gen {
         if (l > 0) { const Geom& c = h->lv[l - 1].geo; a.nc = c.n; a.Pc = c.P; a.Sc = c.S; }
         a.src = src; a.dst = dst; a.g = g;
         a.r64 = h->r;
-        a.gside = h->lv[l].g;
         a.u64 = h->u; a.rw64 = h->r; a.partials = h->partials;
         a.st = st; a.gate = gate;
         a.omega = h->p.omega;
         a.h2inv = (double)(f.n + 1) * (double)(f.n + 1);
-        op.sh = march_shape(h->dim, mode, op.prec, f.n, f.P, 0);
+        op.sh = kernel_shape(h->dim, kkind, mode, op.prec, f.n, f.P, 0);
         a.xstep = op.sh.xstep; a.ystep = op.sh.ystep; a.zstep = op.sh.zstep; a.zlen = op.sh.zlen;
         return op;
     }
 
     void sweep(int l) {  // one Jacobi sweep on level l, ping-pong
-        out->push_back(march(l, M_JACOBI, L_PLAIN, cbuf(l), obuf(l), gbuf(l)));
+        out->push_back(kernel(l, K_SWEEP, M_JACOBI, cbuf(l), obuf(l), gbuf(l)));
         cur[l] ^= 1;
     }
 
+    // Alg. 1 on level l; first = zero initial correction (first visit).
     void cycle(int l, bool first) {
         const int L = h->nlev - 1;
-        const bool top = (l == L) && top_from_r && !h->g_alias_r;
+        if (l == L && top_from_r && !h->g_alias_r)  // Alg. 2 line 4: g_L = cast(r / alpha)
+            out->push_back(kernel(L, K_SCALE, 0, nullptr, h->lv[L].g, nullptr));
         if (l == 0) {
-            if (top) {  // single-level hierarchy: cast the scaled residual into g_0 first
-                Op op = march(0, M_ZERO1, L_SCALED, nullptr, obuf(0), nullptr);
-                out->push_back(op);
-            }
             Op op{};
             op.kind = OP_COARSE;
             op.level = 0;
             op.prec = h->lv[0].prec;
+            op.prec_c = op.prec;
             op.g = gbuf(0);
             op.c = cbuf(0);
             op.a.gate = gate;
@@ -242,17 +240,16 @@ struct Gen {
             return;
         }
         if (first) {
-            const int ld = top ? L_SCALED : L_PLAIN;
-            const void* src = top ? nullptr : gbuf(l);
             if (h->p.nu1 >= 2) {
-                out->push_back(march(l, M_ZERO2, ld, src, cbuf(l), nullptr));
+                out->push_back(kernel(l, K_SWEEP, M_ZERO2, gbuf(l), cbuf(l), nullptr));
                 for (int s = 2; s < h->p.nu1; ++s) sweep(l);
             } else if (h->p.nu1 == 1) {
-                out->push_back(march(l, M_ZERO1, ld, src, cbuf(l), nullptr));
+                out->push_back(kernel(l, K_SWEEP, M_ZERO1, gbuf(l), cbuf(l), nullptr));
             } else {
-                if (top) out->push_back(march(l, M_ZERO1, L_SCALED, nullptr, obuf(l), nullptr));
                 Op z{};
                 z.kind = OP_ZERO;
+                z.level = l;
+                z.prec = z.prec_c = h->lv[l].prec;
                 z.ptr = cbuf(l);
                 z.bytes = (size_t)h->lv[l].geo.total * h->lv[l].esz;
                 z.zero_base = h->lv[l].geo.base * h->lv[l].esz;
@@ -261,27 +258,13 @@ struct Gen {
         } else {
             for (int s = 0; s < h->p.nu1; ++s) sweep(l);
         }
-        out->push_back(march(l, M_RESTRICT, L_PLAIN, cbuf(l), h->lv[l - 1].g, gbuf(l)));
+        out->push_back(kernel(l, K_SWEEP, M_RESTRICT, cbuf(l), h->lv[l - 1].g, gbuf(l)));
         cur[l - 1] = 0;
         for (int k = 0; k < h->p.gamma; ++k) cycle(l - 1, k == 0);
-        if (h->p.nu2 >= 1) {
-            Op op = march(l, M_JACOBI, L_PROLONG, cbuf(l), obuf(l), gbuf(l));
-            op.a.coarse = cbuf(l - 1);
-            out->push_back(op);
-            cur[l] ^= 1;
-            for (int s = 1; s < h->p.nu2; ++s) sweep(l);
-        } else {
-            Op op{};
-            op.kind = OP_PROLONG;
-            op.level = l;
-            op.prec = h->lv[l].prec;
-            op.prec_c = h->lv[l - 1].prec;
-            op.fine = cbuf(l);
-            op.coarse = cbuf(l - 1);
-            op.a.gate = gate;
-            op.a.st = st;
-            out->push_back(op);
-        }
+        Op pr = kernel(l, K_PROLONG, 0, nullptr, cbuf(l), nullptr);
+        pr.a.coarse = cbuf(l - 1);
+        out->push_back(pr);
+        for (int s = 0; s < h->p.nu2; ++s) sweep(l);
     }
 };
 }  // namespace
@@ -300,14 +283,14 @@ void* mgi_build_cycle(mgi_hier& h, std::vector<Op>& ops, bool top_from_r, int ga
     return gen.cbuf(h.nlev - 1);
 }
 
-Op mgi_march_op(mgi_hier& h, int level, int mode, int loader, const void* src, void* dst, const void* g,
-                int gate, const DevState* st) {
+Op mgi_kernel_op(mgi_hier& h, int level, int kkind, int mode, const void* src, void* dst, const void* g,
+                 int gate, const DevState* st) {
     Gen gen{};
     gen.h = &h;
     gen.gate = gate;
     gen.st = st;
     gen.top_from_r = false;
-    return gen.march(level, mode, loader, src, dst, g);
+    return gen.kernel(level, kkind, mode, src, dst, g);
 }
 
 Op mgi_update_op(mgi_hier& h, const void* cL, int gate, const DevState* st) {
@@ -317,12 +300,12 @@ Op mgi_update_op(mgi_hier& h, const void* cL, int gate, const DevState* st) {
     gen.gate = gate;
     gen.st = st;
     gen.top_from_r = true;
-    return gen.march(L, M_UPDATE, L_PLAIN, cL, nullptr, nullptr);
+    return gen.kernel(L, K_UPDATE, 0, cL, nullptr, nullptr);
 }
 
 static size_t update_blocks_max(const mgi_hier& h) {
     const Geom& f = h.lv[h.nlev - 1].geo;
-    MarchShape s = march_shape(h.dim, M_UPDATE, h.lv[h.nlev - 1].prec, f.n, f.P, 0);
+    MarchShape s = kernel_shape(h.dim, K_UPDATE, 0, h.lv[h.nlev - 1].prec, f.n, f.P, 0);
     return (size_t)s.nblocks();
 }
 
@@ -342,14 +325,10 @@ static void build_step(mgi_hier& h) {
 
 int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
     switch (op.kind) {
-        case OP_MARCH:
-            return launch_march(h.dim, op.mode, op.loader, op.prec, op.prec_c, op.a, op.sh.gx, op.sh.gy,
-                                op.sh.gz, op.sh.ty, op.sh.smem, s);
+        case OP_KERNEL:
+            return launch_kernel(h.dim, op.kkind, op.mode, op.prec, op.prec_c, op.a, op.sh, s);
         case OP_COARSE:
             return launch_coarse_solve(op.prec, h.minv, h.m0, op.g, op.c, h.lv[0].geo, op.a.st, op.a.gate, s);
-        case OP_PROLONG:
-            return launch_prolong_add(h.dim, op.prec, op.prec_c, h.lv[op.level].geo, h.lv[op.level - 1].geo,
-                                      op.fine, op.coarse, op.a.st, op.a.gate, s);
         case OP_ZERO:
             return (int)cudaMemsetAsync((char*)op.ptr - op.zero_base, 0, op.bytes, s);
         case OP_FINALIZE:
@@ -365,6 +344,8 @@ static void free_hier(mgi_hier* h) {
     cudaGetDevice(&dev);
     cudaSetDevice(h->device);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->solve_exec) cudaGraphExecDestroy(h->solve_exec);
+    if (h->aux) cudaStreamDestroy(h->aux);
     if (h->arena) cudaFree(h->arena);
     if (h->bstage) cudaFree(h->bstage);
     if (h->ustage) cudaFree(h->ustage);
@@ -461,6 +442,7 @@ extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, 
         }                                                                                     \
     } while (0)
     CK_CREATE(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK_CREATE(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
     CK_CREATE(cudaEventCreate(&h->e0));
     CK_CREATE(cudaEventCreate(&h->e1));
     CK_CREATE(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
@@ -514,6 +496,14 @@ static int ensure_staging(mgi_hier& h) {
     return 0;
 }
 
+static int run_step_ops(mgi_hier& h, cudaStream_t s) {
+    for (const Op& op : h.step) {
+        int rc = mgi_run_op(h, op, s);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
 static int launch_step(mgi_hier& h) {
     cudaStream_t s = h.stream;
     h.ctx.launches += h.step_kernels;
@@ -534,11 +524,7 @@ static int launch_step(mgi_hier& h) {
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return (int)e;
-            int rc = 0;
-            for (const Op& op : h.step) {
-                rc = mgi_run_op(h, op, s);
-                if (rc) break;
-            }
+            int rc = run_step_ops(h, s);
             e = cudaStreamEndCapture(s, &g);
             if (rc) { if (g) cudaGraphDestroy(g); return rc; }
             if (e != cudaSuccess) return (int)e;
@@ -548,24 +534,98 @@ static int launch_step(mgi_hier& h) {
         }
         return (int)cudaGraphLaunch(h.graph_exec, s);
     }
-    for (const Op& op : h.step) {
-        int rc = mgi_run_op(h, op, s);
-        if (rc) return rc;
-    }
-    return 0;
+    return run_step_ops(h, s);
 }
 
-static int launch_residual(mgi_hier& h, const double* b, double* r, double* uout, int fin_kind) {
+// r = b - A u with b taken from the control state; gate: 0 always, 1 only when
+// the true-residual check is pending, 2 only when u must still be copied out.
+static int launch_residual(mgi_hier& h, cudaStream_t s, double* r, int copy_u, int gate, int fin_kind) {
     const Geom& g = h.lv[h.nlev - 1].geo;
     RArgs a{};
     a.n = g.n; a.P = g.P; a.S = g.S;
-    a.u = h.u; a.b = b; a.r = r; a.uout = uout; a.partials = h.partials;
+    a.u = h.u; a.b = nullptr; a.r = r; a.partials = h.partials; a.st = h.st;
+    a.use_st_uout = copy_u;
+    a.gate = gate;
     a.h2inv = (double)(g.n + 1) * (double)(g.n + 1);
     int nb = 0;
-    int rc = launch_residual64(h.dim, a, &nb, h.stream);
+    int rc = launch_residual64(h.dim, a, &nb, s);
     if (rc) return rc;
-    h.ctx.launches += 2;
-    return launch_finalize(fin_kind, h.st, h.partials, nb, h.stream);
+    return launch_finalize(fin_kind, h.st, h.partials, nb, s);
+}
+
+// Alg. 2 line 2: r = b - A u0 (or r = b for u0 = 0), then the first stopping test.
+static int launch_init(mgi_hier& h, cudaStream_t s) {
+    const Geom& g = h.lv[h.nlev - 1].geo;
+    if (h.p.zero_guess) {
+        cudaError_t e = cudaMemsetAsync(h.u_alloc, 0, (size_t)g.total * 8, s);
+        if (e != cudaSuccess) return (int)e;
+        int nb = 0;
+        int rc = launch_init_rb(h.dim, g, nullptr, h.r, h.partials, h.st, &nb, s);
+        if (rc) return rc;
+        return launch_finalize(FIN_INIT, h.st, h.partials, nb, s);
+    }
+    int rc = launch_pack_u0(h.dim, g, h.st, h.u, s);
+    if (rc) return rc;
+    return launch_residual(h, s, h.r, 0, 0, FIN_INIT);
+}
+static int init_kernels(const mgi_hier& h) { return h.p.zero_guess ? 2 : 3; }
+
+// The true-residual check (a11): recompute b - A u in FP64, copy u out.
+static int launch_guard(mgi_hier& h, cudaStream_t s) { return launch_residual(h, s, h.r, 1, 1, FIN_GUARD); }
+// Final report when u changed after the last check: ||b - A u|| and the copy-out.
+static int launch_report(mgi_hier& h, cudaStream_t s) { return launch_residual(h, s, nullptr, 1, 2, FIN_REPORT); }
+
+// The whole solve as one graph: init, then a WHILE node whose body is the IR
+// step (kernels gated on phase 0), the true-residual check (gated on phase 1)
+// and the loop condition; then the report (gated on u not yet copied out).
+// No host round trip per IR step.
+static int build_solve_graph(mgi_hier& h) {
+    cudaStream_t s = h.stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return (int)e;
+    int rc = launch_init(h, s);
+    if (!rc) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        cudaGraphConditionalHandle handle = 0;
+        cudaGraphNode_t cnode = nullptr;
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        rc = (int)cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &nd);
+        if (!rc) rc = (int)cudaGraphConditionalHandleCreate(&handle, cg, 1, cudaGraphCondAssignDefault);
+        if (!rc) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = handle;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            rc = (int)cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp);
+        }
+        if (!rc) rc = (int)cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (!rc) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            rc = (int)cudaStreamBeginCaptureToGraph(h.aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (!rc) {
+                int rc2 = run_step_ops(h, h.aux);
+                if (!rc2) rc2 = launch_guard(h, h.aux);
+                if (!rc2) rc2 = launch_loop_condition(h.st, (unsigned long long)handle, h.p.max_iter + 16, h.aux);
+                cudaGraph_t out = nullptr;
+                cudaError_t e2 = cudaStreamEndCapture(h.aux, &out);
+                rc = rc2 ? rc2 : (int)e2;
+            }
+        }
+    }
+    if (!rc) rc = launch_report(h, s);
+    e = cudaStreamEndCapture(s, &graph);
+    if (!rc) rc = (int)e;
+    if (!rc) rc = (int)cudaGraphInstantiate(&h.solve_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) {
+        h.solve_exec = nullptr;
+        cudaGetLastError();
+    }
+    return rc;
 }
 
 static int push_state(mgi_hier& h) {
@@ -575,7 +635,8 @@ static int push_state(mgi_hier& h) {
 }
 
 // Starts a solve: resolves host/device pointers, writes the control state,
-// launches r = b - A u0 (or r = b) and the first state copy.
+// then launches either the whole-solve graph or the initial residual (the
+// host-driven loop, used when graphs are off or for per-kernel profiling).
 mg_status mgi_solve_begin(mgi_hier& h, const double* b, double* u) {
     SolveCtx& c = h.ctx;
     c = SolveCtx{};
@@ -612,20 +673,20 @@ mg_status mgi_solve_begin(mgi_hier& h, const double* b, double* u) {
     sh.tol_mode = h.p.tol_mode;
     sh.guard = h.p.guard;
     sh.phase = 0;
+    sh.b = c.bd;
+    sh.uout = c.ud;
     CUCHK(cudaMemcpyAsync(h.st, &sh, offsetof(DevState, hist), cudaMemcpyHostToDevice, s));
-    const Geom& g = h.lv[h.nlev - 1].geo;
-    if (h.p.zero_guess) {
-        CUCHK(cudaMemsetAsync(h.u_alloc, 0, (size_t)g.total * 8, s));
-        int nb = 0;
-        CUCHK(launch_init_rb(h.dim, g, c.bd, h.r, h.partials, &nb, s));
-        CUCHK(launch_finalize(FIN_INIT, h.st, h.partials, nb, s));
-        c.launches += 2;
-    } else {
-        CUCHK(launch_pack(h.dim, MG_FP64, g, c.ud, h.u, s));
-        c.launches += 1;
-        CUCHK(launch_residual(h, c.bd, h.r, nullptr, FIN_INIT));
+    c.graph = h.p.graph && !h.prof && !h.solve_graph_failed;
+    if (c.graph && !h.solve_exec && build_solve_graph(h)) {
+        h.solve_graph_failed = true;  // conditional nodes unavailable: host-driven loop
+        c.graph = false;
     }
-    c.dirty = true;
+    if (c.graph) {
+        CUCHK(cudaGraphLaunch(h.solve_exec, s));
+    } else {
+        CUCHK(launch_init(h, s));
+        c.launches += init_kernels(h);
+    }
     CUCHK(push_state(h));
     c.active = true;
     return MG_OK;
@@ -648,33 +709,46 @@ int mgi_solve_advance(mgi_hier& h) {
         }
         h.prof_pending = false;
     }
+    auto fail = [&](int code) {
+        mgi_set_error(std::string("launch: ") + cudaGetErrorString((cudaError_t)code));
+        c.active = false;
+        return -MG_ERR_CUDA;
+    };
+    if (c.graph && !c.finishing) {
+        // the graph ran init, loop and report: count its kernel launches
+        c.launches += init_kernels(h) + s.loops * (h.step_kernels + 3) + 2;
+        c.finishing = true;
+        c.reported = true;
+    }
     if (!c.finishing) {
         if (s.phase == 0) {
             rc = launch_step(h);
-            c.dirty = true;
         } else if (s.phase == 1) {
-            rc = launch_residual(h, c.bd, h.r, c.ud, FIN_GUARD);
-            c.dirty = false;
+            rc = launch_guard(h, h.stream);
+            c.launches += 2;
         } else {
             c.finishing = true;
         }
         if (!c.finishing) {
-            if (rc || (rc = push_state(h))) { mgi_set_error(std::string("launch: ") + cudaGetErrorString((cudaError_t)rc)); c.active = false; return -MG_ERR_CUDA; }
+            if (rc || (rc = push_state(h))) return fail(rc);
             return 0;
         }
     }
-    if (c.dirty) {  // final report: b - A u in FP64 and the unpacked solution
-        rc = launch_residual(h, c.bd, nullptr, c.ud, 3);
-        c.dirty = false;
-        if (!rc) rc = push_state(h);
-        if (rc) { mgi_set_error(std::string("launch: ") + cudaGetErrorString((cudaError_t)rc)); c.active = false; return -MG_ERR_CUDA; }
-        return 0;
+    if (!c.reported) {  // ||b - A u|| and the copy-out, unless the last check already did both
+        c.reported = true;
+        if (s.dirty) {
+            rc = launch_report(h, h.stream);
+            c.launches += 2;
+            if (!rc) rc = push_state(h);
+            if (rc) return fail(rc);
+            return 0;
+        }
     }
     if (c.u_host && !c.copied_back) {
         rc = (int)cudaMemcpyAsync(c.u_user, c.ud, npoints(h) * 8, cudaMemcpyDeviceToHost, h.stream);
         c.copied_back = true;
         if (!rc) rc = (int)cudaEventRecord(h.ev_state, h.stream);
-        if (rc) { mgi_set_error(std::string("copy: ") + cudaGetErrorString((cudaError_t)rc)); c.active = false; return -MG_ERR_CUDA; }
+        if (rc) return fail(rc);
         return 0;
     }
     cudaEventRecord(h.e1, h.stream);
@@ -738,17 +812,18 @@ static double op_bytes(const mgi_hier& h, const Op& op) {
     const double N = pts(op.level);
     const double Nc = op.level > 0 ? pts(op.level - 1) : 0.0;
     switch (op.kind) {
-        case OP_MARCH:
-            switch (op.mode) {
-                case M_JACOBI: return 3 * s * N + (op.loader == L_PROLONG ? sc * Nc : 0.0);
-                case M_ZERO2:
-                case M_ZERO1: return op.loader == L_SCALED ? (8 + 2 * s) * N : 2 * s * N;
-                case M_RESTRICT: return 2 * s * N + sc * Nc;
-                case M_UPDATE: return (32 + s) * N;
+        case OP_KERNEL:
+            switch (op.kkind) {
+                case K_SWEEP:
+                    if (op.mode == M_JACOBI) return 3 * s * N;      // read c, g; write c'
+                    if (op.mode == M_RESTRICT) return 2 * s * N + sc * Nc;  // read c, g; write g_coarse
+                    return 2 * s * N;                               // read g; write c
+                case K_UPDATE: return (32 + s) * N;                 // read c; read+write u, r (FP64)
+                case K_SCALE: return (8 + s) * N;                   // read r (FP64); write g
+                case K_PROLONG: return 2 * s * N + sc * Nc;         // read+write c; read c_coarse
             }
             return 0.0;
         case OP_COARSE: return 2 * s * N + 8.0 * h.m0 * h.m0;
-        case OP_PROLONG: return 2 * s * N + sc * Nc;
         case OP_ZERO: return (double)op.bytes;
         case OP_FINALIZE: return 16.0 * op.nblocks;
     }
@@ -779,15 +854,17 @@ extern "C" mg_status mg_profile_solve(mg_hierarchy* hh, const double* b, double*
         const Op& op = h->step[i];
         mg_kernel_time& k = out[i];
         std::memset(&k, 0, sizeof(k));
-        k.kind = op.kind;
+        k.kind = op.kind == OP_KERNEL ? (op.kkind == K_SWEEP ? 0 : op.kkind == K_PROLONG ? 2
+                                         : op.kkind == K_UPDATE ? 5 : 6)
+                                      : op.kind;
         k.level = op.level;
         k.mode = op.mode;
-        k.loader = op.loader;
+        k.loader = 0;
         k.prec = op.prec;
         k.prec_coarse = op.prec_c;
         k.launches = h->prof_cnt[i];
-        if (op.kind == OP_MARCH) {
-            k.threads = 32 * op.sh.ty;
+        if (op.kind == OP_KERNEL) {
+            k.threads = op.sh.tx * op.sh.ty;
             k.grid[0] = op.sh.gx; k.grid[1] = op.sh.gy; k.grid[2] = op.sh.gz;
         }
         k.total_ms = h->prof_ms[i];

@@ -20,17 +20,18 @@ struct Level {
     void* alloc[3] = {nullptr, nullptr, nullptr};  // allocation starts of c, g, t
 };
 
-enum OpKind : int { OP_MARCH = 0, OP_COARSE = 1, OP_PROLONG = 2, OP_ZERO = 3, OP_FINALIZE = 4 };
+// OP_KERNEL covers the fine-level kernels (kernel kind in kkind: sweep,
+// IR update, scale-cast, prolongation); the values of `kind` follow
+// mg_kernel_time.kind of mg.h.
+enum OpKind : int { OP_KERNEL = 0, OP_COARSE = 1, OP_ZERO = 3, OP_FINALIZE = 4 };
 
 struct Op {
     int kind = 0, level = 0;
-    int mode = 0, loader = 0, prec = 0, prec_c = 0;
+    int kkind = 0, mode = 0, prec = 0, prec_c = 0;
     KArgs a{};
     MarchShape sh{};
     const void* g = nullptr;  // OP_COARSE
     void* c = nullptr;
-    void* fine = nullptr;     // OP_PROLONG
-    const void* coarse = nullptr;
     void* ptr = nullptr;      // OP_ZERO: padded base pointer
     size_t bytes = 0;
     size_t zero_base = 0;     // bytes between allocation start and ptr
@@ -43,10 +44,11 @@ struct SolveCtx {
     const double* bd = nullptr;  // device b (caller's or staging)
     double* ud = nullptr;        // device u (caller's or staging)
     bool b_host = false, u_host = false;
-    bool dirty = false;          // u changed since it was last unpacked
     bool finishing = false;
+    bool reported = false;
     bool copied_back = false;
     bool active = false;
+    bool graph = false;          // the whole solve runs as one graph launch
     int launches = 0;
     mg_result res{};
 };
@@ -74,7 +76,10 @@ struct mgi_hier {
     int device = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr, ev_in = nullptr, ev_state = nullptr;
     std::vector<Op> step;
-    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;  // one IR step (host-driven loop)
+    cudaGraphExec_t solve_exec = nullptr;  // whole solve with a device-side IR loop
+    bool solve_graph_failed = false;
+    cudaStream_t aux = nullptr;            // capture stream of the loop body
     void* arena = nullptr;
     size_t arena_bytes = 0;
     size_t footprint = 0;
@@ -95,8 +100,8 @@ int mgi_validate(const mg_params* p, std::string& why);
 int mgi_run_op(mgi::mgi_hier& h, const mgi::Op& op, cudaStream_t s);
 void* mgi_build_cycle(mgi::mgi_hier& h, std::vector<mgi::Op>& ops, bool top_from_r, int gate,
                       const mgi::DevState* st);
-mgi::Op mgi_march_op(mgi::mgi_hier& h, int level, int mode, int loader, const void* src, void* dst,
-                     const void* g, int gate, const mgi::DevState* st);
+mgi::Op mgi_kernel_op(mgi::mgi_hier& h, int level, int kkind, int mode, const void* src, void* dst,
+                      const void* g, int gate, const mgi::DevState* st);
 bool mgi_is_device_ptr(const void* p);
 mgi::Op mgi_update_op(mgi::mgi_hier& h, const void* cL, int gate, const mgi::DevState* st);
 mg_status mgi_solve_begin(mgi::mgi_hier& h, const double* b, double* u);

@@ -68,42 +68,46 @@ struct DevState {
     int tol_mode;
     int guard;
     int stag;         // consecutive steps without decrease
+    int dirty;        // u changed since it was last copied to the caller's array
+    int loops;        // body iterations of the device-side IR loop (bounded)
     int pad_;
+    const double* b;  // caller's right-hand side (device, contiguous)
+    double* uout;     // caller's solution (device, contiguous): u0 in, u out
     double hist[kMaxHist + 2];
 };
 
+// Kernel kinds of the fine-level TUs.
+enum Kind : int {
+    K_SWEEP = 0,    // stencil sweep (mode below)
+    K_UPDATE = 1,   // u += alpha c; r -= alpha A c; norm partials (Alg. 2 lines 6-7)
+    K_SCALE = 2,    // g = cast(r * inv) (Alg. 2 line 4)
+    K_PROLONG = 3,  // c += P c_coarse (Alg. 1 step 4)
+};
+
 enum Mode : int {
-    M_JACOBI = 0,   // dst = c + w D^-1 (g - A c), c from the loader
-    M_ZERO2 = 1,    // dst = two sweeps from zero; the marched values are g
+    M_JACOBI = 0,   // dst = c + w D^-1 (g - A c)
+    M_ZERO2 = 1,    // dst = two sweeps from zero; the swept vector is g
     M_ZERO1 = 2,    // dst = w D^-1 g
     M_RESTRICT = 3, // coarse dst = R (g - A c)
-    M_UPDATE = 4,   // u += alpha c; r -= alpha A c; norms
 };
 
-enum Loader : int {
-    L_PLAIN = 0,    // values of src (type T)
-    L_SCALED = 1,   // round_T(r64 * inv): the scaled, cast residual (Alg. 2 line 4)
-    L_PROLONG = 2,  // src + P coarse (coarse type TC)
-};
-
-// Arguments of the stencil march kernels (passed by value).
+// Arguments of the fine-level kernels (passed by value).
 struct KArgs {
     int n, P;            // this level
     long long S;
     int nc, Pc;          // coarser level (restrict target / prolong source)
     long long Sc;
-    const void* src;     // marched vector (T)
+    const void* src;     // swept vector / correction (T)
     const void* g;       // right-hand side (T)
     void* dst;           // output (T, or TC for M_RESTRICT)
-    const void* coarse;  // coarse correction (TC) for L_PROLONG
-    const double* r64;   // FP64 residual for L_SCALED (padded, finest geometry)
-    void* gside;         // L_SCALED: where the cast g is stored (T)
-    double* u64;         // M_UPDATE: FP64 solution (padded)
-    double* rw64;        // M_UPDATE: FP64 residual (padded)
-    double* partials;    // per-CTA norm partials (M_UPDATE): 2 doubles each
+    const void* coarse;  // coarse correction (TC) for K_PROLONG
+    const double* r64;   // FP64 residual for K_SCALE (padded, finest geometry)
+    double* u64;         // K_UPDATE: FP64 solution (padded)
+    double* rw64;        // K_UPDATE: FP64 residual (padded)
+    double* partials;    // per-CTA norm partials (K_UPDATE): 2 doubles each
     const DevState* st;  // alpha / inv, phase (early exit)
-    double a_step;       // M_UPDATE explicit alpha when st == nullptr
-    double inv_explicit; // L_SCALED explicit scale when st == nullptr
+    double a_step;       // K_UPDATE explicit alpha when st == nullptr
+    double inv_explicit; // K_SCALE explicit scale when st == nullptr
     double omega;
     double h2inv;        // 1/h^2 of this level
     int xstep, ystep, zstep, zlen;  // tile strides / march length
@@ -115,43 +119,46 @@ struct RArgs {
     int n, P;
     long long S;
     const double* u;      // padded
-    const double* b;      // contiguous interior (n^d)
+    const double* b;      // contiguous interior (n^d); from st->b when null
     double* r;            // padded output (may be null)
-    double* uout;         // contiguous interior copy of u (may be null)
+    double* uout;         // contiguous interior copy of u (may be null; st->uout with use_st_uout)
     double* partials;     // 4 doubles per CTA: sum r^2, max |r|, sum b^2, unused
+    const DevState* st;   // control state (gating, caller pointers); may be null
     double h2inv;
-    int zstep, zlen, ystep;
+    int gate;             // 0 always run; 1 only when st->phase == 1; 2 only when st->dirty
+    int use_st_uout;      // 1: copy u to st->uout
 };
 
-// Launchers (one translation unit per fine storage type).
-// prec codes follow mg_prec.
-int launch_march(int dim, int mode, int loader, int prec, int prec_c, const KArgs& a,
-                 int grid_x, int grid_y, int grid_z, int ty, size_t smem, void* stream);
-
 struct MarchShape {
-    int gx, gy, gz, ty;
+    int gx, gy, gz, tx, ty;
     size_t smem;
     int xstep, ystep, zstep, zlen;
     int nblocks() const { return gx * gy * gz; }
 };
-// Launch geometry for a stencil march over a level of size n (pitch P).
-MarchShape march_shape(int dim, int mode, int prec, int n, int P, int tz_hint);
+// Launch geometry of a fine-level kernel over a level of size n (pitch P).
+MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int tz_hint);
+// Launches a fine-level kernel (one translation unit per fine storage type).
+int launch_kernel(int dim, int kind, int mode, int prec, int prec_c, const KArgs& a, const MarchShape& s,
+                  void* stream);
 
 // Misc kernels (mg_misc.cu).
 int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void* c, const Geom& geo,
                         const DevState* st, int gate, void* stream);
-int launch_prolong_add(int dim, int prec, int prec_c, const Geom& f, const Geom& c, void* fine,
-                       const void* coarse, const DevState* st, int gate, void* stream);
 int launch_residual64(int dim, const RArgs& a, int* nblocks, void* stream);
-int launch_init_rb(int dim, const Geom& geo, const double* b, double* r, double* partials,
+int launch_init_rb(int dim, const Geom& geo, const double* b, double* r, double* partials, const DevState* st,
                    int* nblocks, void* stream);
 int launch_finalize(int kind, DevState* st, const double* partials, int nblocks, void* stream);
+// u (padded) <- st->uout (the caller's initial guess)
+int launch_pack_u0(int dim, const Geom& geo, const DevState* st, double* u_padded, void* stream);
+// Condition of the device-side IR loop: continue while phase is 0 or 1 and the
+// body has run fewer than `limit` times.
+int launch_loop_condition(DevState* st, unsigned long long handle, int limit, void* stream);
 int launch_pack(int dim, int prec, const Geom& geo, const void* src_contig, void* dst_padded,
                 void* stream);
 int launch_unpack(int dim, int prec, const Geom& geo, const void* src_padded, void* dst_contig,
                   void* stream);
 
-enum FinalizeKind : int { FIN_INIT = 0, FIN_STEP = 1, FIN_GUARD = 2 };
+enum FinalizeKind : int { FIN_INIT = 0, FIN_STEP = 1, FIN_GUARD = 2, FIN_REPORT = 3 };
 
 size_t elem_size(int prec);
 

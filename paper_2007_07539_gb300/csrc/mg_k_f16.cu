@@ -1,9 +1,9 @@
-// Stencil march kernels instantiated for fine-level storage type __half.
+// Stencil, update, scale-cast and prolongation kernels instantiated for the
+// fine-level storage type __half.
 #include "mg_dispatch.cuh"
 
 namespace mgi {
-int launch_march_f16(int dim, int mode, int loader, int prec_c, const KArgs& a, int gx, int gy, int gz,
-                     int ty, size_t smem, void* stream) {
-    return launch_march_t<__half>(dim, mode, loader, prec_c, a, gx, gy, gz, ty, smem, stream);
+int launch_kernel_f16(int dim, int kind, int mode, int prec_c, const KArgs& a, const MarchShape& s, void* stream) {
+    return launch_kernel_t<__half>(dim, kind, mode, prec_c, a, s, stream);
 }
 }  // namespace mgi

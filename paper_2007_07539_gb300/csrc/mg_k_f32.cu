@@ -1,9 +1,9 @@
-// Stencil march kernels instantiated for fine-level storage type float.
+// Stencil, update, scale-cast and prolongation kernels instantiated for the
+// fine-level storage type float.
 #include "mg_dispatch.cuh"
 
 namespace mgi {
-int launch_march_f32(int dim, int mode, int loader, int prec_c, const KArgs& a, int gx, int gy, int gz,
-                     int ty, size_t smem, void* stream) {
-    return launch_march_t<float>(dim, mode, loader, prec_c, a, gx, gy, gz, ty, smem, stream);
+int launch_kernel_f32(int dim, int kind, int mode, int prec_c, const KArgs& a, const MarchShape& s, void* stream) {
+    return launch_kernel_t<float>(dim, kind, mode, prec_c, a, s, stream);
 }
 }  // namespace mgi

@@ -1,0 +1,684 @@
+// Stencil kernels of libmgfp.
+//
+// k_sweep3 / k_sweep2: every grid pass that applies the 5/7-point operator
+// A_l (Sec. 5) to a stored level vector:
+//   M_JACOBI    damped Jacobi sweep (Sec. 4.2; Alg. 1 steps 1, 5)
+//   M_ZERO2     the first two sweeps of a pre-smoothing from c = 0, fused
+//               (Alg. 1 step 1 with a zero initial guess)
+//   M_ZERO1     one sweep from c = 0 (c = omega D^-1 g)
+//   M_RESTRICT  residual g - A c and its full-weighting restriction to the next
+//               coarser level with the precision change (Alg. 1 step 2)
+// k_update: Alg. 2 lines 6-7 fused (the paper's UpdateResiduum_Correction),
+//   u += alpha c and r -= alpha A c in FP64 with norm partials.
+// k_scale_cast: Alg. 2 line 4, the scaled FP64 residual cast to the finest
+//   level's storage type.
+// k_prolong: Alg. 1 step 4, prolongation and correction.
+//
+// 3D sweep decomposition: a CTA of TY warps owns TY consecutive rows of one
+// 32V-wide x-chunk (V = elements per 16-byte vector: 8 FP16/BF16, 4 FP32,
+// 2 FP64; every row chunk is 512 bytes) and marches over a z-range.  Planes
+// stream through a ring of S shared-memory stages filled by cp.async: each
+// stage holds the TY rows of the chunk plus one halo row above and below and
+// one halo element (pair) left and right of the chunk (zero-filled outside the
+// grid) and, for passes that need it, the TY rows of g.  While plane z is
+// computed from stages z-1, z, z+1, planes z+2 and z+3 are in flight, so
+// memory latency is hidden with few registers per thread.  In 2D each warp
+// owns one x-chunk and marches over rows with a per-warp ring.
+// Arithmetic is FP32 for FP16/BF16/FP32 levels and FP64 for FP64 levels.
+#pragma once
+#include <type_traits>
+
+#include "mg_device.cuh"
+
+namespace mgi {
+
+template <int DIM>
+__device__ __forceinline__ long long offs(int x, int y, int z, int P, long long S) {
+    return DIM == 3 ? (long long)z * S + (long long)y * P + x : (long long)y * P + x;
+}
+
+// ---------------------------------------------------------------- cp.async
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool ok) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(ok ? 16 : 0));
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem, bool ok) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(BYTES),
+                 "r"(ok ? BYTES : 0));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Shared-memory row: one 512-byte chunk with a 16-byte pad on each side (room
+// for the x-halo elements).
+constexpr int kRowBytes = 512 + 32;
+
+// x-halo copy: one element, or the aligned pair next to the edge for 2-byte
+// types (cp.async copies at least 4 bytes).
+template <class T> struct Halo {
+    static constexpr int E = sizeof(T) == 2 ? 2 : 1;
+    static constexpr int BYTES = sizeof(T) == 2 ? 4 : (int)sizeof(T);
+};
+
+// One row chunk into shared memory: 16 bytes per lane, halos by lanes 0 / 31;
+// zero-filled when the row is outside the grid or past the pitch.
+template <class T>
+__device__ __forceinline__ void issue_row(unsigned char* srow, const T* grow, int lane, int x0, int P, bool row_ok) {
+    constexpr int V = Tr<T>::V;
+    constexpr int CW = 32 * V;
+    const int x = x0 + lane * V;
+    T* d = reinterpret_cast<T*>(srow + 16);
+    const bool ok = row_ok && x < P;
+    cp_async16(d + lane * V, ok ? (const void*)(grow + x) : (const void*)grow, ok);
+    if (lane == 0)
+        cp_async_small<Halo<T>::BYTES>(d - Halo<T>::E, row_ok ? (const void*)(grow + x0 - Halo<T>::E) : (const void*)grow,
+                                       row_ok);
+    if (lane == 31) {
+        const bool okr = row_ok && x0 + CW < P;
+        cp_async_small<Halo<T>::BYTES>(d + CW, okr ? (const void*)(grow + x0 + CW) : (const void*)grow, okr);
+    }
+}
+
+// The lane's V values of a shared-memory row, in the arithmetic type.
+template <class T>
+__device__ __forceinline__ void lds_vec(const unsigned char* srow, int lane, typename Tr<T>::C (&v)[Tr<T>::V]) {
+    const T* d = reinterpret_cast<const T*>(srow + 16) + lane * Tr<T>::V;
+    const uint4 raw = *reinterpret_cast<const uint4*>(d);
+    if constexpr (sizeof(T) == 8) {
+        v[0] = __longlong_as_double(((long long)raw.y << 32) | raw.x);
+        v[1] = __longlong_as_double(((long long)raw.w << 32) | raw.z);
+    } else if constexpr (sizeof(T) == 4) {
+        v[0] = __uint_as_float(raw.x); v[1] = __uint_as_float(raw.y);
+        v[2] = __uint_as_float(raw.z); v[3] = __uint_as_float(raw.w);
+    } else {
+        const unsigned wd[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 f;
+            if constexpr (std::is_same<T, __half>::value) f = __half22float2(*reinterpret_cast<const __half2*>(&wd[k]));
+            else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wd[k]));
+            v[2 * k] = f.x; v[2 * k + 1] = f.y;
+        }
+    }
+}
+template <class T>
+__device__ __forceinline__ typename Tr<T>::C lds_one(const unsigned char* srow, int idx) {
+    const T* d = reinterpret_cast<const T*>(srow + 16);
+    if constexpr (sizeof(T) == 8 || sizeof(T) == 4) return d[idx];
+    else if constexpr (std::is_same<T, __half>::value) return __half2float(d[idx]);
+    else return __bfloat162float(d[idx]);
+}
+
+// ---------------------------------------------------------------- per-point values
+template <int MODE, class C>
+__device__ __forceinline__ C point_value(C c0, C nb, C g, C c1, C c2, C c3, C h2inv, C twod, C om) {
+    if (MODE == M_JACOBI) return c1 * c0 + c2 * nb + c3 * g;            // c + w D^-1 (g - A c)
+    if (MODE == M_ZERO2) return c3 * (((C)2 - om) * c0 + c2 * nb);       // two sweeps from 0, c0 = g
+    if (MODE == M_ZERO1) return c3 * c0;                                   // one sweep from 0
+    return g - h2inv * (twod * c0 - nb);                                   // residual g - A c
+}
+
+// Full weighting along x of one fine row: q[k] = (r[2k] + 2 r[2k+1] + r[2k+2]) / 4,
+// r[V] taken from the next lane.
+template <class C, int V, int VH>
+__device__ __forceinline__ void fw_x(const C (&out)[V], int lane, C (&q)[VH]) {
+    C rn = __shfl_down_sync(kFull, out[0], 1);
+    if (lane == 31) rn = 0;
+#pragma unroll
+    for (int k = 0; k < VH; ++k) {
+        C r2 = (2 * k + 2 < V) ? out[(2 * k + 2) % V] : rn;
+        q[k] = (C)0.25 * out[2 * k] + (C)0.5 * out[2 * k + 1] + (C)0.25 * r2;
+    }
+}
+
+// ---------------------------------------------------------------- 3D sweep
+template <int MODE, class T, class TC>
+__global__ void __launch_bounds__(320) k_sweep3(const KArgs a) {
+    using C = typename Tr<T>::C;
+    constexpr int V = Tr<T>::V;
+    constexpr int CW = 32 * V;
+    constexpr int VH = V / 2 > 0 ? V / 2 : 1;
+    constexpr int S = 5;  // ring stages: planes z-1, z, z+1 in use, z+2 and z+3 in flight
+    constexpr bool NEED_G = MODE == M_JACOBI || MODE == M_RESTRICT;
+    if (a.gate && a.st->phase != 0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TY = blockDim.y, lane = threadIdx.x, w = threadIdx.y;
+    const int stage_bytes = (TY + 2 + (NEED_G ? TY : 0)) * kRowBytes;
+    unsigned char* flush = smem_raw + S * stage_bytes;
+    const int x0 = blockIdx.x * a.xstep, x = x0 + lane * V;
+    const int y0 = blockIdx.y * a.ystep, y = y0 + w;
+    const int zb = blockIdx.z * a.zstep;
+    const int ze = min(zb + a.zlen, a.n);
+    const bool lane_in = x < a.P, row_in = y < a.n;
+    const T* src = reinterpret_cast<const T*>(a.src);
+    const T* gp = reinterpret_cast<const T*>(a.g);
+    auto stage_of = [&](int p) { return (p - zb + 1) % S; };
+    auto crow = [&](int st, int r) { return smem_raw + st * stage_bytes + r * kRowBytes; };
+    auto grow = [&](int st, int r) { return smem_raw + st * stage_bytes + (TY + 2 + r) * kRowBytes; };
+    // Issues the copies of plane p (c rows y0-1 .. y0+TY, g rows y0 .. y0+TY-1)
+    // into its stage; planes past ze are not needed and only commit a group.
+    auto issue = [&](int p) {
+        if (p <= ze) {
+            const int st = stage_of(p);
+            const long long po = (long long)p * a.S;
+            issue_row<T>(crow(st, w + 1), src + po + (long long)(y <= a.n ? y : 0) * a.P, lane, x0, a.P, y <= a.n);
+            if (w == 0) issue_row<T>(crow(st, 0), src + po + (long long)(y0 - 1) * a.P, lane, x0, a.P, true);
+            if (w == TY - 1) {
+                const int yh = y0 + TY;
+                issue_row<T>(crow(st, TY + 1), src + po + (long long)(yh <= a.n ? yh : 0) * a.P, lane, x0, a.P,
+                             yh <= a.n);
+            }
+            if (NEED_G && p >= zb && p < ze) {
+                const bool ok = row_in && lane_in;
+                const T* gr = ok ? gp + po + (long long)y * a.P + x : gp;
+                cp_async16(reinterpret_cast<T*>(grow(st, w) + 16) + lane * V, gr, ok);
+            }
+        }
+        cp_commit();
+    };
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) issue(zb - 1 + k);
+
+    const C h2inv = (C)a.h2inv, om = (C)a.omega, twod = (C)6;
+    const C c1 = (C)1 - om, c2 = om / twod, c3 = om / (twod * h2inv);
+    C acc[VH];
+#pragma unroll
+    for (int k = 0; k < VH; ++k) acc[k] = 0;
+    for (int z = zb; z < ze; ++z) {
+        cp_wait<S - 4>();  // planes up to z+1 have landed (this thread's copies)
+        __syncthreads();   // ... everyone's; and stage(z-2) is no longer read
+        issue(z + S - 2);
+        const int sm1 = stage_of(z - 1), s0 = stage_of(z), sp1 = stage_of(z + 1);
+        C c0[V], cm[V], cp[V], ym[V], yp[V], g[V];
+        lds_vec<T>(crow(s0, w + 1), lane, c0);
+        lds_vec<T>(crow(sm1, w + 1), lane, cm);
+        lds_vec<T>(crow(sp1, w + 1), lane, cp);
+        lds_vec<T>(crow(s0, w), lane, ym);
+        lds_vec<T>(crow(s0, w + 2), lane, yp);
+        const C left = lds_one<T>(crow(s0, w + 1), lane * V - 1);
+        const C right = lds_one<T>(crow(s0, w + 1), lane * V + V);
+        if (NEED_G) lds_vec<T>(grow(s0, w), lane, g);
+        C out[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const C nb = (i ? c0[i - 1] : left) + (i < V - 1 ? c0[i + 1] : right) + cm[i] + cp[i] + ym[i] + yp[i];
+            const C v = point_value<MODE, C>(c0[i], nb, NEED_G ? g[i] : (C)0, c1, c2, c3, h2inv, twod, om);
+            out[i] = (x + i < a.n && row_in) ? v : (C)0;
+        }
+        if constexpr (MODE != M_RESTRICT) {
+            if (row_in && lane_in) stv(reinterpret_cast<T*>(a.dst) + offs<3>(x, y, z, a.P, a.S), out);
+        } else {
+            C q[VH];
+            fw_x<C, V, VH>(out, lane, q);
+            const int t = z - zb;
+            if (t & 1) {
+#pragma unroll
+                for (int k = 0; k < VH; ++k) acc[k] += (C)0.5 * q[k];
+            } else {
+                if (t >= 2) {  // fine planes 2K, 2K+1, 2K+2 done: write coarse plane K
+                    C* fl = reinterpret_cast<C*>(flush) + (w * 32 + lane) * VH;
+#pragma unroll
+                    for (int k = 0; k < VH; ++k) fl[k] = acc[k] + (C)0.25 * q[k];
+                    __syncthreads();
+                    if ((w & 1) == 0 && w + 2 < TY) {
+                        const int J = (y0 >> 1) + (w >> 1), K = (zb >> 1) + (t >> 1) - 1;
+                        const C* f0 = reinterpret_cast<const C*>(flush) + (w * 32 + lane) * VH;
+                        const C* f1 = f0 + 32 * VH;
+                        const C* f2 = f1 + 32 * VH;
+                        const int I0 = (x0 + lane * V) >> 1;
+                        if (lane_in && J < a.nc && K < a.nc && (lane < 31 || x0 + CW >= a.P)) {
+                            TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
+#pragma unroll
+                            for (int k = 0; k < VH; ++k)
+                                if (I0 + k < a.nc)
+                                    st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * q[k];
+            }
+        }
+    }
+    cp_wait<0>();
+}
+
+// ---------------------------------------------------------------- 2D sweep
+template <int MODE, class T, class TC>
+__global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
+    using C = typename Tr<T>::C;
+    constexpr int V = Tr<T>::V;
+    constexpr int CW = 32 * V;
+    constexpr int VH = V / 2 > 0 ? V / 2 : 1;
+    constexpr int S = 6;  // per-warp ring of rows: y-1, y, y+1 in use, y+2..y+4 in flight
+    constexpr bool NEED_G = MODE == M_JACOBI || MODE == M_RESTRICT;
+    if (a.gate && a.st->phase != 0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = blockDim.y, lane = threadIdx.x, w = threadIdx.y;
+    const int wbytes = S * (NEED_G ? 2 : 1) * kRowBytes;
+    unsigned char* mine = smem_raw + w * wbytes;
+    const int x0 = (blockIdx.x * W + w) * a.xstep, x = x0 + lane * V;
+    const bool chunk_in = x0 < a.P, lane_in = chunk_in && x < a.P;
+    const int yb = blockIdx.y * a.zstep;
+    const int ye = min(yb + a.zlen, a.n);
+    const T* src = reinterpret_cast<const T*>(a.src);
+    const T* gp = reinterpret_cast<const T*>(a.g);
+    auto slot = [&](int p) { return (p - yb + 1) % S; };
+    auto crow = [&](int st) { return mine + st * kRowBytes; };
+    auto grow = [&](int st) { return mine + (S + st) * kRowBytes; };
+    auto issue = [&](int p) {
+        if (p <= ye && chunk_in) {
+            const int st = slot(p);
+            issue_row<T>(crow(st), src + (long long)p * a.P, lane, x0, a.P, true);
+            if (NEED_G && p >= yb && p < ye) {
+                const T* gr = lane_in ? gp + (long long)p * a.P + x : gp;
+                cp_async16(reinterpret_cast<T*>(grow(st) + 16) + lane * V, gr, lane_in);
+            }
+        }
+        cp_commit();
+    };
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) issue(yb - 1 + k);
+    const C h2inv = (C)a.h2inv, om = (C)a.omega, twod = (C)4;
+    const C c1 = (C)1 - om, c2 = om / twod, c3 = om / (twod * h2inv);
+    C acc[VH];
+#pragma unroll
+    for (int k = 0; k < VH; ++k) acc[k] = 0;
+    for (int y = yb; y < ye; ++y) {
+        cp_wait<S - 4>();
+        __syncwarp();
+        const int sm1 = slot(y - 1), s0 = slot(y), sp1 = slot(y + 1);
+        C c0[V], cm[V], cp[V], g[V];
+        lds_vec<T>(crow(s0), lane, c0);
+        lds_vec<T>(crow(sm1), lane, cm);
+        lds_vec<T>(crow(sp1), lane, cp);
+        const C left = lds_one<T>(crow(s0), lane * V - 1);
+        const C right = lds_one<T>(crow(s0), lane * V + V);
+        if (NEED_G) lds_vec<T>(grow(s0), lane, g);
+        __syncwarp();      // all lanes have read row y-1's slot before it is refilled
+        issue(y + S - 2);  // same slot as row y-2 ... y-1 is slot(y+S-1); y+S-2 reuses slot(y-2)
+        C out[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const C nb = (i ? c0[i - 1] : left) + (i < V - 1 ? c0[i + 1] : right) + cm[i] + cp[i];
+            const C v = point_value<MODE, C>(c0[i], nb, NEED_G ? g[i] : (C)0, c1, c2, c3, h2inv, twod, om);
+            out[i] = (x + i < a.n) ? v : (C)0;
+        }
+        if constexpr (MODE != M_RESTRICT) {
+            if (lane_in) stv(reinterpret_cast<T*>(a.dst) + offs<2>(x, y, 0, a.P, a.S), out);
+        } else {
+            C q[VH];
+            fw_x<C, V, VH>(out, lane, q);
+            const int t = y - yb;
+            if (t & 1) {
+#pragma unroll
+                for (int k = 0; k < VH; ++k) acc[k] += (C)0.5 * q[k];
+            } else {
+                if (t >= 2) {
+                    const int J = (yb >> 1) + (t >> 1) - 1;
+                    const int I0 = (x0 + lane * V) >> 1;
+                    if (lane_in && J < a.nc && (lane < 31 || x0 + CW >= a.P)) {
+                        TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)J * a.Pc;
+#pragma unroll
+                        for (int k = 0; k < VH; ++k)
+                            if (I0 + k < a.nc) st1(cd + I0 + k, acc[k] + (C)0.25 * q[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * q[k];
+            }
+        }
+    }
+    cp_wait<0>();
+}
+
+// ---------------------------------------------------------------- scale and cast (Alg. 2 line 4)
+// Multiplication by inv split as 2^E * m, m in [1, 2): the exponent is added
+// to the FP64 bit pattern with an integer add (exact), the significand product
+// is done in FP32, then one rounding to the storage type.  No FP64 instruction.
+struct ScaleK {
+    double inv;
+    long long eadd;
+    float mant;
+};
+__device__ __forceinline__ ScaleK make_scale(double inv) {
+    ScaleK k;
+    k.inv = inv;
+    long long b = __double_as_longlong(inv);
+    int E = (int)((b >> 52) & 0x7FF) - 1023;
+    k.eadd = (long long)E << 52;
+    k.mant = f64_to_f32_trunc(__longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll));
+    return k;
+}
+__device__ __forceinline__ float scaled_f32(double r, const ScaleK& k) {
+    long long b = __double_as_longlong(r);
+    long long ex = b & 0x7FF0000000000000ll;
+    if (ex == 0) return 0.0f;
+    if (ex == 0x7FF0000000000000ll) return f64_to_f32_trunc(r);
+    return __fmul_rn(f64_to_f32_trunc(__longlong_as_double(b + k.eadd)), k.mant);
+}
+
+// g = round_T(r * inv) over the padded rows of the finest level (pads stay 0).
+template <int DIM, class T>
+__global__ void __launch_bounds__(256) k_scale_cast(const KArgs a) {
+    using C = typename Tr<T>::C;
+    constexpr int V = Tr<T>::V;
+    if (a.gate && a.st->phase != 0) return;
+    const int vpr = a.P / V;  // vectors per padded row
+    const long long rows = DIM == 3 ? (long long)a.n * a.n : a.n;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * vpr) return;
+    const int x = (int)(idx % vpr) * V;
+    const long long row = idx / vpr;
+    const int y = (int)(row % a.n), z = DIM == 3 ? (int)(row / a.n) : 0;
+    const long long o = offs<DIM>(x, y, z, a.P, a.S);
+    const double inv = a.st ? a.st->inv : a.inv_explicit;
+    C v[V];
+    if constexpr (sizeof(T) == 8) {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(a.r64 + o));
+        v[0] = t.x * inv;
+        v[1] = t.y * inv;
+    } else {
+        const ScaleK k = make_scale(inv);
+#pragma unroll
+        for (int i = 0; i < V; i += 2) {
+            const double2 t = __ldg(reinterpret_cast<const double2*>(a.r64 + o + i));
+            v[i] = scaled_f32(t.x, k);
+            v[i + 1] = scaled_f32(t.y, k);
+        }
+    }
+    stv(reinterpret_cast<T*>(a.dst) + o, v);
+}
+
+// ---------------------------------------------------------------- FP64 IR update (Alg. 2 lines 6-7)
+// S = 2d c0 - (sum of neighbours) exactly, as FP64.
+template <class T> struct ExactStencil;
+template <> struct ExactStencil<__half> {
+    static constexpr bool kTwoTerm = false;
+    // FP16 values: exact integer arithmetic in units of 2^-24 (see h_split);
+    // NB = 2d neighbours, |H| < 2^26 and |L| < 2^21 so both sums are exact.
+    template <int NB>
+    __device__ static void sum(float c0, const float (&nb)[NB], double& s, double& s2) {
+        const float MAGIC = 12582912.0f;
+        HSplit q = h_split(c0);
+        int H = NB * q.hi;
+        float L = __fmul_rn((float)NB, q.lo);
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            HSplit t = h_split(nb[j]);
+            H -= t.hi;
+            L = __fsub_rn(L, t.lo);
+        }
+        int Li = __float_as_int(__fadd_rn(L, MAGIC)) - __float_as_int(MAGIC);
+        long long Sint = ((long long)H << 18) + (long long)Li;
+        s = i64_to_f64(Sint, -24);
+        s2 = 0.0;
+    }
+};
+template <class T> struct ExactStencil {
+    static constexpr bool kTwoTerm = true;
+    // FP32/BF16 values: double-float sum with error-free transformations.
+    template <int NB>
+    __device__ static void sum(float c0, const float (&nb)[NB], double& s, double& s2) {
+        float p = __fmul_rn((float)NB, c0);
+        float e = __fmaf_rn((float)NB, c0, -p);
+        float acc = p;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            float t, err;
+            two_sum(acc, -nb[j], t, err);
+            acc = t;
+            e = __fadd_rn(e, err);
+        }
+        s = f32_to_f64(acc);
+        s2 = f32_to_f64(e);
+    }
+};
+template <> struct ExactStencil<double> {
+    static constexpr bool kTwoTerm = false;
+    template <int NB>
+    __device__ static void sum(double c0, const double (&nb)[NB], double& s, double& s2) {
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) t += nb[j];
+        s = fma((double)NB, c0, -t);
+        s2 = 0.0;
+    }
+};
+
+__device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+
+// Sum of squares as an FP32 double-float (hi + lo) without FP64 instructions.
+// Each r is first scaled by 2^-E (E: exponent of the previous ||r||_inf, an
+// exact change of the exponent field; entries below 2^-70 of that scale are
+// dropped, their squares being < 2^-140 of the sum) and split from its bit
+// pattern into hi (top 24 significand bits, exact) and lo (the next 29 bits,
+// rounded to 24).  r^2 ~ hi^2 + 2 hi lo, hi^2 exact by FMA TwoProd, summed
+// with TwoSum: relative error ~1e-14.  The result is multiplied by 2^(2E).
+struct SqAcc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(double r, int E) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(r);
+        const int e = (int)((b >> 52) & 0x7FF) - E;  // biased exponent of r * 2^-E
+        if (e < 1023 - 70 || e > 1023 + 100) return;  // (the upper bound never binds: r <= ~100 * 2^E)
+        const unsigned long long bs = (b & 0x800FFFFFFFFFFFFFull) | ((unsigned long long)e << 52);
+        const float h = f64_to_f32_trunc(__longlong_as_double((long long)bs));
+        const unsigned mlo = (unsigned)(b & 0x1FFFFFFFull);
+        const float scale = __int_as_float((e - 1075 + 127) << 23);  // 2^(e - 1075), normal here
+        float l = __fmul_rn(__uint2float_rn(mlo), scale);
+        if (b >> 63) l = -l;
+        const float p = __fmul_rn(h, h);
+        const float pe = __fmaf_rn(h, h, -p);
+        const float t = __fmaf_rn(2.0f * h, l, pe);
+        float s, err;
+        two_sum(hi, p, s, err);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, t));
+    }
+    __device__ __forceinline__ void add_pair(float h2, float l2) {
+        float s, err;
+        two_sum(hi, h2, s, err);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, l2));
+    }
+};
+
+// Exponent E (unbiased) used to pre-scale the squares: that of the last ||r||_inf.
+__device__ __forceinline__ int sq_exponent(const DevState* st) {
+    if (!st) return 0;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(st->rnorminf);
+    const int e = (int)((b >> 52) & 0x7FF);
+    return (e == 0 || e == 0x7FF) ? 0 : e - 1023;
+}
+
+// Block reduction in a fixed order: {sum of squares, max |r| key} -> partials.
+// The double-float pairs are combined with TwoSum through warp shuffles; one
+// lane converts the block total to FP64 and rescales it by 2^(2E).
+__device__ __forceinline__ void write_partials(SqAcc sq, unsigned long long nmax, int E, double* partials) {
+    __shared__ float sh[32], sl[32];
+    __shared__ unsigned long long rm[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(kFull, sq.hi, o), l2 = __shfl_xor_sync(kFull, sq.lo, o);
+        sq.add_pair(h2, l2);
+    }
+    nmax = warp_max(nmax);
+    if (lane == 0) { sh[w] = sq.hi; sl[w] = sq.lo; rm[w] = nmax; }
+    __syncthreads();
+    if (w == 0) {
+        SqAcc t;
+        t.hi = lane < nw ? sh[lane] : 0.f;
+        t.lo = lane < nw ? sl[lane] : 0.f;
+        unsigned long long m = lane < nw ? rm[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(kFull, t.hi, o), l2 = __shfl_xor_sync(kFull, t.lo, o);
+            t.add_pair(h2, l2);
+        }
+        m = warp_max(m);
+        if (lane == 0) {
+            const double v = f32_to_f64(t.hi) + f32_to_f64(t.lo);
+            // exact rescaling by 2^(2E) through the exponent field (v is 0 or normal)
+            const long long vb = __double_as_longlong(v);
+            const double vs = (vb & 0x7FF0000000000000ll) ? __longlong_as_double(vb + ((long long)(2 * E) << 52)) : 0.0;
+            partials[2 * (long long)blockIdx.x] = vs;
+            partials[2 * (long long)blockIdx.x + 1] = __longlong_as_double((long long)m);
+        }
+    }
+}
+
+// Four consecutive values of a level vector (x multiple of 4), one vector load.
+template <class T>
+__device__ __forceinline__ void ld4(const T* p, typename Tr<T>::C (&v)[4]) {
+    if constexpr (sizeof(T) == 8) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else if constexpr (sizeof(T) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else {
+        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+        const unsigned wd[2] = {raw.x, raw.y};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            float2 f;
+            if constexpr (std::is_same<T, __half>::value) f = __half22float2(*reinterpret_cast<const __half2*>(&wd[k]));
+            else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wd[k]));
+            v[2 * k] = f.x; v[2 * k + 1] = f.y;
+        }
+    }
+}
+
+// One thread per 4 consecutive points of a padded row.  u and r (FP64, 32 of
+// the 34 bytes per point) stream through coalesced 16-byte loads and stores;
+// the stencil of c comes through the read-only cache as vector loads.  FP64
+// instructions: the two fused multiply-adds of Alg. 2 lines 6-7 per point
+// (three for FP32/BF16 corrections), nothing else.
+constexpr int kUpdQ = 4;
+template <int DIM, class T>
+__global__ void __launch_bounds__(256) k_update(const KArgs a) {
+    using C = typename Tr<T>::C;
+    constexpr int Q = kUpdQ;
+    if (a.gate && a.st->phase != 0) return;
+    const int vpr = a.P / Q;
+    const long long rows = DIM == 3 ? (long long)a.n * a.n : a.n;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int E = sq_exponent(a.st);
+    SqAcc sq;
+    unsigned long long nmax = 0ull;
+    const int x = (int)(idx % vpr) * Q;
+    if (idx < rows * vpr && x < a.n) {
+        const long long row = idx / vpr;
+        const int y = (int)(row % a.n), z = DIM == 3 ? (int)(row / a.n) : 0;
+        const long long o = offs<DIM>(x, y, z, a.P, a.S);
+        const double alpha = a.st ? a.st->alpha : a.a_step;
+        const double beta = alpha * a.h2inv;
+        const T* c = reinterpret_cast<const T*>(a.src) + o;
+        double* up = a.u64 + o;
+        double* rp = a.rw64 + o;
+        const double2 u01 = *reinterpret_cast<const double2*>(up);
+        const double2 u23 = *reinterpret_cast<const double2*>(up + 2);
+        const double2 r01 = *reinterpret_cast<const double2*>(rp);
+        const double2 r23 = *reinterpret_cast<const double2*>(rp + 2);
+        C c0[Q], ym[Q], yp[Q], zm[Q], zp[Q];
+        ld4(c, c0);
+        ld4(c - a.P, ym);
+        ld4(c + a.P, yp);
+        if (DIM == 3) {
+            ld4(c - a.S, zm);
+            ld4(c + a.S, zp);
+        }
+        const C left = ld1(c - 1), right = ld1(c + Q);
+        double uu[Q] = {u01.x, u01.y, u23.x, u23.y};
+        double rr[Q] = {r01.x, r01.y, r23.x, r23.y};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (x + i < a.n) {
+                const C xm = i ? c0[i - 1] : left, xp = i < Q - 1 ? c0[i + 1] : right;
+                double s, s2;
+                if (DIM == 3) {
+                    const C nb[6] = {xm, xp, ym[i], yp[i], zm[i], zp[i]};
+                    ExactStencil<T>::template sum<6>(c0[i], nb, s, s2);
+                } else {
+                    const C nb[4] = {xm, xp, ym[i], yp[i]};
+                    ExactStencil<T>::template sum<4>(c0[i], nb, s, s2);
+                }
+                double r = fma(-beta, s, rr[i]);
+                if (ExactStencil<T>::kTwoTerm) r = fma(-beta, s2, r);
+                rr[i] = r;
+                uu[i] = fma(alpha, to_f64(c0[i]), uu[i]);
+                sq.add(r, E);
+                const unsigned long long k = abs_key(r);
+                nmax = k > nmax ? k : nmax;
+            }
+        }
+        *reinterpret_cast<double2*>(up) = make_double2(uu[0], uu[1]);
+        *reinterpret_cast<double2*>(up + 2) = make_double2(uu[2], uu[3]);
+        *reinterpret_cast<double2*>(rp) = make_double2(rr[0], rr[1]);
+        *reinterpret_cast<double2*>(rp + 2) = make_double2(rr[2], rr[3]);
+    }
+    write_partials(sq, nmax, E, a.partials);
+}
+
+// ---------------------------------------------------------------- prolongation (Alg. 1 step 4)
+// c_fine += P c_coarse (bi/trilinear), V fine points per thread (x even); the
+// coarse values come through the read-only cache.
+template <int DIM, class T, class TC>
+__device__ __forceinline__ void add_prolong_vec(const KArgs& a, int x, int y, int z,
+                                                typename Tr<T>::C (&v)[Tr<T>::V]) {
+    using C = typename Tr<T>::C;
+    constexpr int V = Tr<T>::V;
+    const TC* cc = reinterpret_cast<const TC*>(a.coarse);
+    int Jl, Jh, Kl = 0, Kh = 0;
+    C w = 1;
+    if (y & 1) { Jl = Jh = (y - 1) >> 1; } else { Jl = (y >> 1) - 1; Jh = y >> 1; w *= (C)0.5; }
+    if (DIM == 3) {
+        if (z & 1) { Kl = Kh = (z - 1) >> 1; } else { Kl = (z >> 1) - 1; Kh = z >> 1; w *= (C)0.5; }
+    }
+    const int I0 = (x >> 1) - 1;
+    C s[V / 2 + 1];
+#pragma unroll
+    for (int k = 0; k <= V / 2; ++k) s[k] = 0;
+    for (int K = Kl; K <= Kh; ++K)
+        for (int J = Jl; J <= Jh; ++J) {
+            const TC* row = cc + (DIM == 3 ? (long long)K * a.Sc : 0LL) + (long long)J * a.Pc + I0;
+#pragma unroll
+            for (int k = 0; k <= V / 2; ++k) s[k] += (C)ld1(row + k);
+        }
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        C p = (i & 1) ? s[(i + 1) >> 1] : (C)0.5 * (s[i >> 1] + s[(i >> 1) + 1]);
+        v[i] += w * p;
+    }
+}
+
+template <int DIM, class T, class TC>
+__global__ void __launch_bounds__(256) k_prolong(const KArgs a) {
+    using C = typename Tr<T>::C;
+    constexpr int V = Tr<T>::V;
+    if (a.gate && a.st->phase != 0) return;
+    const int vpr = a.P / V;
+    const long long rows = DIM == 3 ? (long long)a.n * a.n : a.n;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * vpr) return;
+    const int x = (int)(idx % vpr) * V;
+    if (x >= a.n) return;
+    const long long row = idx / vpr;
+    const int y = (int)(row % a.n), z = DIM == 3 ? (int)(row / a.n) : 0;
+    T* f = reinterpret_cast<T*>(a.dst) + offs<DIM>(x, y, z, a.P, a.S);
+    C v[V];
+    ldv(f, v);
+    add_prolong_vec<DIM, T, TC>(a, x, y, z, v);
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+        if (x + i >= a.n) v[i] = 0;
+    stv(f, v);
+}
+
+}  // namespace mgi

@@ -8,10 +8,10 @@
 
 namespace mgi {
 
-int launch_march_f64(int, int, int, int, const KArgs&, int, int, int, int, size_t, void*);
-int launch_march_f32(int, int, int, int, const KArgs&, int, int, int, int, size_t, void*);
-int launch_march_f16(int, int, int, int, const KArgs&, int, int, int, int, size_t, void*);
-int launch_march_bf16(int, int, int, int, const KArgs&, int, int, int, int, size_t, void*);
+int launch_kernel_f64(int, int, int, int, const KArgs&, const MarchShape&, void*);
+int launch_kernel_f32(int, int, int, int, const KArgs&, const MarchShape&, void*);
+int launch_kernel_f16(int, int, int, int, const KArgs&, const MarchShape&, void*);
+int launch_kernel_bf16(int, int, int, int, const KArgs&, const MarchShape&, void*);
 
 size_t elem_size(int prec) {
     switch (prec) {
@@ -21,13 +21,13 @@ size_t elem_size(int prec) {
     }
 }
 
-int launch_march(int dim, int mode, int loader, int prec, int prec_c, const KArgs& a, int gx, int gy,
-                 int gz, int ty, size_t smem, void* stream) {
+int launch_kernel(int dim, int kind, int mode, int prec, int prec_c, const KArgs& a, const MarchShape& s,
+                  void* stream) {
     switch (prec) {
-        case MG_FP64: return launch_march_f64(dim, mode, loader, prec_c, a, gx, gy, gz, ty, smem, stream);
-        case MG_FP32: return launch_march_f32(dim, mode, loader, prec_c, a, gx, gy, gz, ty, smem, stream);
-        case MG_FP16: return launch_march_f16(dim, mode, loader, prec_c, a, gx, gy, gz, ty, smem, stream);
-        case MG_BF16: return launch_march_bf16(dim, mode, loader, prec_c, a, gx, gy, gz, ty, smem, stream);
+        case MG_FP64: return launch_kernel_f64(dim, kind, mode, prec_c, a, s, stream);
+        case MG_FP32: return launch_kernel_f32(dim, kind, mode, prec_c, a, s, stream);
+        case MG_FP16: return launch_kernel_f16(dim, kind, mode, prec_c, a, s, stream);
+        case MG_BF16: return launch_kernel_bf16(dim, kind, mode, prec_c, a, s, stream);
     }
     return (int)cudaErrorInvalidValue;
 }
@@ -35,45 +35,78 @@ int launch_march(int dim, int mode, int loader, int prec, int prec_c, const KArg
 static int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// Grid shape of a stencil march.  Non-restricting passes: 3D CTAs of 8 warps
-// (8 rows of one 32V-wide x-chunk) marching over z-ranges sized so that the
-// grid has >= ~4 CTAs per SM (152 SMs); 2D: 4 warps per CTA, one x-chunk per
-// warp, marching over row ranges.  Restriction: 2TJ+1 fine rows (TJ coarse
-// rows) per CTA and 2TK+1 fine planes per z-range, with one shared fine row /
-// plane between neighbouring tiles and x-chunks overlapping by one vector.
-MarchShape march_shape(int dim, int mode, int prec, int n, int P, int tz_hint) {
+constexpr int kSMs = 152;
+
+// Picks the march length L (planes or rows per CTA) for `units` positions to
+// march over and `tiles` CTAs per position: each CTA also reads the two planes
+// next to its range, and a grid that ends in a partial wave idles SMs, so L
+// maximises  (waves / ceil(waves)) * L / (L + 2)  over L in [lo, hi].
+static int pick_march_len(int units, long long tiles, int resident, int lo, int hi, int step_mult) {
+    double best = -1.0;
+    int bestL = lo;
+    for (int L = lo; L <= hi; ++L) {
+        const int span = L * step_mult;
+        const long long nb = tiles * cdiv(units, span);
+        const double waves = (double)nb / (double)(kSMs * resident);
+        const double eff = waves / std::ceil(waves) * (double)span / (double)(span + 2);
+        if (eff > best + 1e-9) { best = eff; bestL = L; }
+    }
+    return bestL;
+}
+
+// Launch geometry.  Sweeps (3D): CTAs of 8 warps = 8 rows of one 512-byte
+// x-chunk, marching over z through a 5-stage cp.async ring; restriction: 2TJ+1
+// fine rows per CTA (TJ coarse rows) and 2TK+1 fine planes per range, one fine
+// row / plane shared with the neighbouring tile, x-chunks overlapping by one
+// vector.  2D: one x-chunk per warp, 4 warps per CTA, marching over rows.
+// Streaming kernels (update, scale-cast, prolongation): 256 threads, one
+// thread per vector of a padded row.
+MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int tz_hint) {
     const int V = (int)(16 / elem_size(prec));
     const int CW = 32 * V;
     const size_t cs = prec == MG_FP64 ? 8 : 4;
-    const int target = 4 * 152;
+    const int VH = V / 2 > 0 ? V / 2 : 1;
     MarchShape s{};
+    s.tx = 32;
+    s.gz = 1;
+    if (kind != K_SWEEP) {
+        const int per = kind == K_UPDATE ? kUpdQ : V;
+        const long long rows = dim == 3 ? (long long)n * n : n;
+        s.tx = 256;
+        s.ty = 1;
+        s.gx = cdiv(rows * (P / per), 256);
+        s.gy = 1;
+        s.smem = 0;
+        return s;
+    }
+    const bool need_g = mode == M_JACOBI || mode == M_RESTRICT;
     if (mode == M_RESTRICT) {
         const int nc = (n - 1) / 2;
         s.xstep = P > CW ? CW - V : CW;
-        int nchunks = P > CW ? 1 + cdiv(P - CW, CW - V) : 1;
+        const int nchunks = P > CW ? 1 + cdiv(P - CW, CW - V) : 1;
         if (dim == 3) {
-            int TJ = clampi(nc, 1, 4);
+            const int TJ = clampi(nc, 1, 4);
             s.ty = 2 * TJ + 1;
             s.ystep = 2 * TJ;
             s.gx = nchunks;
             s.gy = cdiv(nc, TJ);
-            int TK = tz_hint > 0 ? tz_hint : clampi((int)((long long)nc * s.gx * s.gy / target), 1, 16);
+            s.smem = (size_t)5 * (s.ty + 2 + s.ty) * kRowBytes + (size_t)s.ty * 32 * VH * cs;
+            const int res = clampi((int)(220 * 1024 / (s.smem + 1024)), 1, 4);
+            int TK = tz_hint > 0 ? tz_hint : pick_march_len(nc, (long long)s.gx * s.gy, res, 2, 16, 2);
             TK = clampi(TK, 1, nc);
             s.zlen = 2 * TK + 1;
             s.zstep = 2 * TK;
             s.gz = cdiv(nc, TK);
-            s.smem = (size_t)(2 * (s.ty + 2) * CW) * cs + (size_t)(s.ty * 32 * (V / 2 > 0 ? V / 2 : 1)) * cs;
         } else {
-            int W = clampi(nchunks, 1, 4);
+            const int W = clampi(nchunks, 1, 4);
             s.ty = W;
             s.gx = cdiv(nchunks, W);
-            int TK = tz_hint > 0 ? tz_hint : clampi((int)((long long)nc * s.gx / target), 1, 16);
+            s.smem = (size_t)W * 6 * 2 * kRowBytes;
+            int TK = tz_hint > 0 ? tz_hint : pick_march_len(nc, s.gx, 8, 4, 32, 2);
             TK = clampi(TK, 1, nc);
             s.zlen = 2 * TK + 1;
             s.zstep = 2 * TK;
             s.gy = cdiv(nc, TK);
-            s.gz = 1;
-            s.smem = 0;
         }
         return s;
     }
@@ -84,23 +117,23 @@ MarchShape march_shape(int dim, int mode, int prec, int n, int P, int tz_hint) {
         s.ystep = s.ty;
         s.gx = nchunks;
         s.gy = cdiv(n, s.ty);
-        int zl = tz_hint > 0 ? tz_hint : clampi((int)((long long)n * s.gx * s.gy / target), 4, 64);
+        s.smem = (size_t)5 * (s.ty + 2 + (need_g ? s.ty : 0)) * kRowBytes;
+        const int res = clampi((int)(220 * 1024 / (s.smem + 1024)), 1, 4);
+        int zl = tz_hint > 0 ? tz_hint : pick_march_len(n, (long long)s.gx * s.gy, res, 4, 40, 1);
         zl = clampi(zl, 1, n);
         s.zlen = zl;
         s.zstep = zl;
         s.gz = cdiv(n, zl);
-        s.smem = (size_t)(2 * (s.ty + 2) * CW) * cs;
     } else {
-        int W = clampi(nchunks, 1, 4);
+        const int W = clampi(nchunks, 1, 4);
         s.ty = W;
         s.gx = cdiv(nchunks, W);
-        int zl = tz_hint > 0 ? tz_hint : clampi((int)((long long)n * s.gx / target), 4, 64);
+        s.smem = (size_t)W * 6 * (need_g ? 2 : 1) * kRowBytes;
+        int zl = tz_hint > 0 ? tz_hint : pick_march_len(n, s.gx, 8, 4, 64, 1);
         zl = clampi(zl, 1, n);
         s.zlen = zl;
         s.zstep = zl;
         s.gy = cdiv(n, zl);
-        s.gz = 1;
-        s.smem = 0;
     }
     return s;
 }
@@ -153,63 +186,15 @@ int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void*
     return (int)cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- stand-alone prolongation
-// c_fine += P c_coarse (Alg. 1 step 4) when no post-smoothing sweep follows.
-template <int DIM, class T, class TC>
-__global__ void k_prolong_add(KArgs a, const DevState* st, int gate) {
-    using C = typename Tr<T>::C;
-    constexpr int V = Tr<T>::V;
-    if (gate && st->phase != 0) return;
-    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= a.P || y >= a.n) return;
-    C v[V];
-    const long long o = offs<DIM>(x, y, z, a.P, a.S);
-    T* f = reinterpret_cast<T*>(a.dst) + o;
-    ldv(f, v);
-    Load<DIM, L_PROLONG, T, TC>::add_prolong_vec(a, x, y, z, v);
-#pragma unroll
-    for (int i = 0; i < V; ++i)
-        if (x + i >= a.n) v[i] = 0;
-    stv(f, v);
-}
-
-template <int DIM, class T>
-static int prolong_tc(int prec_c, const KArgs& a, dim3 grid, dim3 block, cudaStream_t s, const DevState* st, int gate) {
-    switch (prec_c) {
-        case MG_FP64: k_prolong_add<DIM, T, double><<<grid, block, 0, s>>>(a, st, gate); break;
-        case MG_FP32: k_prolong_add<DIM, T, float><<<grid, block, 0, s>>>(a, st, gate); break;
-        case MG_FP16: k_prolong_add<DIM, T, __half><<<grid, block, 0, s>>>(a, st, gate); break;
-        case MG_BF16: k_prolong_add<DIM, T, __nv_bfloat16><<<grid, block, 0, s>>>(a, st, gate); break;
-        default: return (int)cudaErrorInvalidValue;
-    }
-    return (int)cudaGetLastError();
-}
-
-int launch_prolong_add(int dim, int prec, int prec_c, const Geom& f, const Geom& c, void* fine,
-                       const void* coarse, const DevState* st, int gate, void* stream) {
-    KArgs a{};
-    a.n = f.n; a.P = f.P; a.S = f.S; a.nc = c.n; a.Pc = c.P; a.Sc = c.S;
-    a.dst = fine; a.coarse = coarse;
-    const int V = (int)(16 / elem_size(prec));
-    dim3 block(32, 4);
-    dim3 grid((unsigned)cdiv(f.P / V, 32), (unsigned)cdiv(f.n, 4), (unsigned)(dim == 3 ? f.n : 1));
-    cudaStream_t s = (cudaStream_t)stream;
-    switch (prec) {
-        case MG_FP64: return dim == 3 ? prolong_tc<3, double>(prec_c, a, grid, block, s, st, gate) : prolong_tc<2, double>(prec_c, a, grid, block, s, st, gate);
-        case MG_FP32: return dim == 3 ? prolong_tc<3, float>(prec_c, a, grid, block, s, st, gate) : prolong_tc<2, float>(prec_c, a, grid, block, s, st, gate);
-        case MG_FP16: return dim == 3 ? prolong_tc<3, __half>(prec_c, a, grid, block, s, st, gate) : prolong_tc<2, __half>(prec_c, a, grid, block, s, st, gate);
-        case MG_BF16: return dim == 3 ? prolong_tc<3, __nv_bfloat16>(prec_c, a, grid, block, s, st, gate) : prolong_tc<2, __nv_bfloat16>(prec_c, a, grid, block, s, st, gate);
-    }
-    return (int)cudaErrorInvalidValue;
-}
-
 // ---------------------------------------------------------------- FP64 residual (IR step 1)
 // r = b - A u in FP64 with per-CTA partials {sum r^2, max |r|, sum b^2, 0};
 // optionally copies u to the caller's contiguous array.  One thread per point.
 template <int DIM>
 __global__ void k_residual64(RArgs a, int init_copy) {
+    if (a.gate == 1 && a.st->phase != 1) return;
+    if (a.gate == 2 && !a.st->dirty) return;
+    const double* bsrc = a.b ? a.b : a.st->b;
+    double* uout = a.use_st_uout ? a.st->uout : a.uout;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
@@ -218,7 +203,7 @@ __global__ void k_residual64(RArgs a, int init_copy) {
     if (i < a.n && j < a.n) {
         const long long o = offs<DIM>(i, j, k, a.P, a.S);
         const long long oc = DIM == 3 ? ((long long)k * a.n + j) * a.n + i : (long long)j * a.n + i;
-        const double bv = __ldg(a.b + oc);
+        const double bv = __ldg(bsrc + oc);
         double r;
         if (init_copy) {
             r = bv;  // u = 0: r = b
@@ -228,7 +213,7 @@ __global__ void k_residual64(RArgs a, int init_copy) {
             if (DIM == 3) nb += __ldg(u - a.S) + __ldg(u + a.S);
             const double uc = __ldg(u);
             r = fma(-a.h2inv, fma(2.0 * DIM, uc, -nb), bv);
-            if (a.uout) a.uout[oc] = uc;
+            if (uout) uout[oc] = uc;
         }
         if (a.r) a.r[o] = r;
         sr = r * r;
@@ -277,10 +262,10 @@ int launch_residual64(int dim, const RArgs& a, int* nblocks, void* stream) {
     return (int)cudaGetLastError();
 }
 
-int launch_init_rb(int dim, const Geom& geo, const double* b, double* r, double* partials, int* nblocks,
-                   void* stream) {
+int launch_init_rb(int dim, const Geom& geo, const double* b, double* r, double* partials, const DevState* st,
+                   int* nblocks, void* stream) {
     RArgs a{};
-    a.n = geo.n; a.P = geo.P; a.S = geo.S; a.b = b; a.r = r; a.partials = partials;
+    a.n = geo.n; a.P = geo.P; a.S = geo.S; a.b = b; a.r = r; a.partials = partials; a.st = st;
     dim3 grid, block;
     residual_grid(dim, a.n, grid, block);
     if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
@@ -296,6 +281,12 @@ int launch_init_rb(int dim, const Geom& geo, const double* b, double* r, double*
 // kind: FIN_INIT after r = b - A u0, FIN_STEP after an update (partials of
 // stride 2), FIN_GUARD after the true residual, 3 = report only.
 __global__ void k_finalize(int kind, DevState* st, const double* __restrict__ partials, int nblocks) {
+    // gating (uniform across the block): a step's finalisation only while
+    // iterating, the true-residual check only when it is pending, the report
+    // only when u changed since it was last copied out
+    if (kind == FIN_STEP && st->phase != 0) return;
+    if (kind == FIN_GUARD && st->phase != 1) return;
+    if (kind == FIN_REPORT && !st->dirty) return;
     const int stride = kind == FIN_STEP ? 2 : 4;
     double sr = 0.0, sb = 0.0;
     unsigned long long mr = 0ull;
@@ -326,17 +317,21 @@ __global__ void k_finalize(int kind, DevState* st, const double* __restrict__ pa
         st->guard_restarts = 0;
         st->stag = 0;
         st->status = MG_OK;
+        st->dirty = 1;
     }
     const double bn = st->bnorm2;
     const double rel = bn > 0.0 ? rn / bn : rn;
-    if (kind == 3) {  // report only
+    if (kind == FIN_REPORT) {  // report only: u has been copied out
         st->rel_true = rel;
+        st->dirty = 0;
         return;
     }
     if (kind == FIN_STEP) {
         st->iter += 1;
+        st->dirty = 1;
         st->stag = (rn >= 0.999 * st->rnorm2) ? st->stag + 1 : 0;
     }
+    if (kind == FIN_GUARD) st->dirty = 0;
     st->rnorm2 = rn;
     st->rnorminf = rinf;
     const int it = st->iter < kMaxHist ? st->iter : kMaxHist;
@@ -372,6 +367,41 @@ __global__ void k_finalize(int kind, DevState* st, const double* __restrict__ pa
 
 int launch_finalize(int kind, DevState* st, const double* partials, int nblocks, void* stream) {
     k_finalize<<<1, 1024, 0, (cudaStream_t)stream>>>(kind, st, partials, nblocks);
+    return (int)cudaGetLastError();
+}
+
+// Sets the condition of the device-side IR loop (a WHILE node of the solve
+// graph).  The body-count limit ends the loop even if the state never leaves
+// phases 0/1, so the graph always terminates.
+__global__ void k_loop_condition(DevState* st, cudaGraphConditionalHandle h, int limit) {
+    const int loops = st->loops + 1;
+    st->loops = loops;
+    const bool more = (st->phase == 0 || st->phase == 1) && loops < limit;
+    if (!more && (st->phase == 0 || st->phase == 1)) {  // body-count limit hit: stop as not converged
+        st->phase = 3;
+        st->status = MG_ERR_NOT_CONVERGED;
+    }
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+int launch_loop_condition(DevState* st, unsigned long long handle, int limit, void* stream) {
+    k_loop_condition<<<1, 1, 0, (cudaStream_t)stream>>>(st, (cudaGraphConditionalHandle)handle, limit);
+    return (int)cudaGetLastError();
+}
+
+__global__ void k_pack_u0(int dim, int n, int P, long long S, const DevState* st, double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= n || j >= n) return;
+    const long long o = (dim == 3 ? (long long)k * S : 0LL) + (long long)j * P + i;
+    const long long oc = dim == 3 ? ((long long)k * n + j) * n + i : (long long)j * n + i;
+    dst[o] = st->uout[oc];
+}
+
+int launch_pack_u0(int dim, const Geom& geo, const DevState* st, double* u_padded, void* stream) {
+    dim3 block(64, 4), grid((unsigned)cdiv(geo.n, 64), (unsigned)cdiv(geo.n, 4), (unsigned)(dim == 3 ? geo.n : 1));
+    k_pack_u0<<<grid, block, 0, (cudaStream_t)stream>>>(dim, geo.n, geo.P, geo.S, st, u_padded);
     return (int)cudaGetLastError();
 }
 

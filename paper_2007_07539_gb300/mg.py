@@ -63,19 +63,18 @@ class KernelTime(ctypes.Structure):
                 ("launches", ctypes.c_int32), ("threads", ctypes.c_int32), ("grid", ctypes.c_int32 * 3),
                 ("reserved", ctypes.c_int32), ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
-    KIND = ["march", "base_solve", "prolong", "zero", "finalize"]
-    MODE = ["jacobi", "jacobi_x2_from_zero", "jacobi_from_zero", "residual_restrict", "ir_update"]
-    LOADER = ["", "+scale_cast", "+prolong"]
+    KIND = ["sweep", "base_solve", "prolong", "zero", "finalize", "ir_update", "scale_cast"]
+    MODE = ["jacobi", "jacobi_x2_from_zero", "jacobi_from_zero", "residual_restrict"]
 
     def name(self) -> str:
         p = ["fp64", "fp32", "fp16", "bf16"]
         if self.kind == 0:
-            nm = self.MODE[self.mode] + self.LOADER[self.loader]
+            nm = self.MODE[self.mode]
             if self.mode == 3:
-                nm += f"_{p[self.prec]}_to_{p[self.prec_coarse]}"
-            else:
-                nm += f"_{p[self.prec]}"
-            return nm
+                return nm + f"_{p[self.prec]}_to_{p[self.prec_coarse]}"
+            return nm + f"_{p[self.prec]}"
+        if self.kind == 2:
+            return f"prolong_{p[self.prec_coarse]}_to_{p[self.prec]}"
         return self.KIND[self.kind] + f"_{p[self.prec]}"
 
     def as_dict(self) -> dict:
