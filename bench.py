@@ -171,6 +171,9 @@ def main():
     ap.add_argument("--kernel-dump", default=None, help="write every kernel's profiled time to this JSON file")
     ap.add_argument("--ncu-case", action="store_true",
                     help="only two FP16 solves of the workload (a small launch list for ncu captures)")
+    ap.add_argument("--graph", type=int, default=1,
+                    help="1: each solve is one CUDA graph with a device-side IR loop; 0: kernels launched one "
+                         "by one from the host loop (ncu cannot profile kernels inside conditional graphs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -204,8 +207,9 @@ def main():
     bd = torch.from_numpy(b).cuda()
     ud = torch.zeros_like(bd)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    hH = mg.Hierarchy(mg.make_params(DIM, N, "H", zero_guess=1))
-    hD = mg.Hierarchy(mg.make_params(DIM, N, "D", zero_guess=1, scaling=0))
+    graph = 0 if args.ncu_case else args.graph
+    hH = mg.Hierarchy(mg.make_params(DIM, N, "H", zero_guess=1, graph=graph))
+    hD = mg.Hierarchy(mg.make_params(DIM, N, "D", zero_guess=1, scaling=0, graph=graph))
 
     def run(h, bb, uu, k):
         secs, res = [], None

@@ -87,8 +87,10 @@ typedef struct mg_params {
     int32_t zero_guess; /* 1: ignore u on entry and start from u0 = 0 (default 0) */
     int32_t guard;      /* 1 (default): when the recursively updated residual passes the
                            test, recompute b - A u in FP64 and continue from it if it fails */
-    int32_t graph;      /* 1 (default): run each IR step as one CUDA graph launch */
-    int32_t reserved[8];
+    int32_t graph;      /* 1 (default): run the whole solve as one CUDA graph launch with a
+                           device-side IR loop; 0: one launch per kernel from a host loop */
+    int32_t reserved[8];/* reserved[0] = 1: no coarse-tail kernel (every level as plain
+                           kernels); other entries must be 0 */
 } mg_params;
 
 /* Outcome of one solve. */
@@ -215,7 +217,8 @@ mg_status mg_residual_norms_noalloc(int32_t dim, int32_t n, const double* b, con
 /* Device time of one kernel of the IR step, summed over the steps of a solve. */
 typedef struct mg_kernel_time {
     int32_t kind;        /* 0 stencil sweep, 1 base solve, 2 prolongation, 3 zero fill, 4 norm
-                            finalise, 5 FP64 IR update, 6 scale and cast of the residual */
+                            finalise, 5 FP64 IR update, 6 scale and cast of the residual,
+                            7 coarse tail (the cycle below `level` in one cluster kernel) */
     int32_t level;       /* level index (0 = coarsest) */
     int32_t mode;        /* sweep mode: 0 Jacobi, 1 two sweeps from zero, 2 one sweep from zero,
                             3 residual + restriction */

@@ -240,7 +240,9 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
         case MG_STAGE_CYCLE: {
             if (level != L) SFAIL(MG_ERR_INVALID, "a cycle starts on the finest level");
             std::vector<Op> ops;
+            h->tail_host.resize(h->step_tail_ops);  // stage programs follow the IR step's
             void* cL = mgi_build_cycle(*h, ops, false, 0, nullptr);
+            if (!cL) SFAIL(MG_ERR_INVALID, "coarse-tail program capacity exceeded");
             for (const Op& op : ops) {
                 rc = mgi_run_op(*h, op, s);
                 if (rc) break;

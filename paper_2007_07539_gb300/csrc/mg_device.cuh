@@ -121,17 +121,26 @@ __device__ __forceinline__ float f64_to_f32_trunc(double d) {
     return __uint_as_float(sign | ((unsigned)e << 23) | m);
 }
 
-// Exact FP32 -> FP64 with integer instructions (zero, normal values); the rare
-// subnormal / non-finite inputs take the hardware conversion.
+// Exact FP32 -> FP64 with integer instructions only (no F2F on the FP64
+// pipe): zero, normal, subnormal (renormalised), inf and NaN.
 __device__ __forceinline__ double f32_to_f64(float f) {
-    unsigned b = __float_as_uint(f);
+    const unsigned b = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
     unsigned e = (b >> 23) & 0xFFu;
-    if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)((unsigned long long)(b & 0x80000000u) << 32));
-    if (e == 0u || e == 0xFFu) return (double)f;
-    unsigned long long bits = ((unsigned long long)(b & 0x80000000u) << 32) |
-                              ((unsigned long long)(e + 896u) << 52) |
-                              ((unsigned long long)(b & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)bits);
+    unsigned m = b & 0x7FFFFFu;
+    unsigned long long e64;
+    if (e == 0xFFu) {
+        e64 = 0x7FFull;
+    } else if (e != 0u) {
+        e64 = e + 896u;
+    } else if (m == 0u) {
+        e64 = 0ull;
+    } else {  // subnormal: shift the leading one into the implicit position
+        const int sh = __clz((int)m) - 8;  // m < 2^23: leading zeros within the 23-bit field, + 1
+        m = (m << sh) & 0x7FFFFFu;
+        e64 = (unsigned long long)(897 - sh);
+    }
+    return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)m << 29)));
 }
 
 // Exact s * 2^eoff as FP64 for |s| < 2^53 (result in the normal range), with

@@ -80,7 +80,8 @@ static bool prec_ok(int p) { return p >= MG_FP64 && p <= MG_BF16; }
 int mgi_validate(const mg_params* p, std::string& why) {
     if (!p) { why = "params is NULL"; return 0; }
     if (p->dim != 2 && p->dim != 3) { why = "dim must be 2 or 3"; return 0; }
-    if (p->n < 1 || p->n > (p->dim == 3 ? 2047 : 65535)) { why = "n out of range"; return 0; }
+    // point indices are 32-bit: n^d < 2^31
+    if (p->n < 1 || p->n > (p->dim == 3 ? 1290 : 46340)) { why = "n out of range (3D: n <= 1290, 2D: n <= 46340)"; return 0; }
     if (p->levels < 0 || p->levels > MG_MAX_LEVELS) { why = "levels out of range"; return 0; }
     int sizes[MG_MAX_LEVELS];
     int L = mg_level_count(p->n, p->levels, sizes);
@@ -106,7 +107,7 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
     size_t level_off[MG_MAX_LEVELS][3];
-    size_t u_off, r_off, part_off, st_off, minv_off, total;
+    size_t u_off, r_off, part_off, st_off, minv_off, tprog_off, tscr_off, total;
     size_t part_cap;
 };
 
@@ -127,6 +128,18 @@ static void compute_layout(mgi_hier& h, Layout& lay) {
     lay.part_off = off; off += align_up(nb * 8, 256);
     lay.st_off = off; off += align_up(sizeof(DevState), 256);
     lay.minv_off = off; off += align_up((size_t)h.m0 * h.m0 * 8, 256);
+    lay.tprog_off = off;
+    lay.tscr_off = off;
+    if (h.tail_level >= 0) {
+        off += align_up(sizeof(TailOp) * kTailMaxOps, 256);
+        lay.tscr_off = off;
+        size_t mx = 0;
+        for (int l = 0; l <= h.tail_level; ++l) {
+            const size_t n = (size_t)h.lv[l].geo.n;
+            mx = std::max(mx, h.dim == 3 ? n * n * n : n * n);
+        }
+        off += align_up(mx * 8, 256);
+    }
     lay.total = off;
 }
 
@@ -221,11 +234,81 @@ struct Gen {
         cur[l] ^= 1;
     }
 
+    // ---- coarse tail: the same recursion, emitted as stages of one cluster kernel
+    TailOp tbase(int l, int kind) {
+        TailOp t{};
+        t.kind = kind;
+        t.prec = h->lv[l].prec;
+        t.prec_c = l > 0 ? h->lv[l - 1].prec : t.prec;
+        const Geom& f = h->lv[l].geo;
+        t.n = f.n; t.P = f.P; t.S = f.S;
+        if (l > 0) { const Geom& c = h->lv[l - 1].geo; t.nc = c.n; t.Pc = c.P; t.Sc = c.S; }
+        t.h2inv = (double)(f.n + 1) * (double)(f.n + 1);
+        t.omega = h->p.omega;
+        t.scratch = h->tail_scratch;
+        return t;
+    }
+    void tpush(const TailOp& t) { h->tail_host.push_back(t); }
+    void tsweep(int l, int mode, const void* src, void* dst, const void* g) {
+        TailOp t = tbase(l, TK_SWEEP);
+        t.mode = mode; t.src = src; t.dst = dst; t.g = g;
+        tpush(t);
+    }
+    void tcycle(int l, bool first) {
+        if (l == 0) {
+            TailOp t = tbase(0, TK_COARSE);
+            t.g = gbuf(0);
+            t.dst = cbuf(0);
+            tpush(t);
+            return;
+        }
+        if (first) {
+            if (h->p.nu1 >= 2) {
+                tsweep(l, M_ZERO2, gbuf(l), cbuf(l), nullptr);
+                for (int k = 2; k < h->p.nu1; ++k) { tsweep(l, M_JACOBI, cbuf(l), obuf(l), gbuf(l)); cur[l] ^= 1; }
+            } else if (h->p.nu1 == 1) {
+                tsweep(l, M_ZERO1, gbuf(l), cbuf(l), nullptr);
+            } else {
+                TailOp t = tbase(l, TK_ZERO);
+                t.dst = cbuf(l);
+                tpush(t);
+            }
+        } else {
+            for (int k = 0; k < h->p.nu1; ++k) { tsweep(l, M_JACOBI, cbuf(l), obuf(l), gbuf(l)); cur[l] ^= 1; }
+        }
+        TailOp r = tbase(l, TK_RESID);
+        r.src = cbuf(l); r.g = gbuf(l);
+        tpush(r);
+        TailOp rs = tbase(l, TK_RESTRICT);
+        rs.dst = h->lv[l - 1].g;
+        tpush(rs);
+        cur[l - 1] = 0;
+        for (int k = 0; k < h->p.gamma; ++k) tcycle(l - 1, k == 0);
+        TailOp pr = tbase(l, TK_PROLONG);
+        pr.dst = cbuf(l); pr.coarse = cbuf(l - 1);
+        tpush(pr);
+        for (int k = 0; k < h->p.nu2; ++k) { tsweep(l, M_JACOBI, cbuf(l), obuf(l), gbuf(l)); cur[l] ^= 1; }
+    }
+
     // Alg. 1 on level l; first = zero initial correction (first visit).
     void cycle(int l, bool first) {
         const int L = h->nlev - 1;
         if (l == L && top_from_r && !h->g_alias_r)  // Alg. 2 line 4: g_L = cast(r / alpha)
             out->push_back(kernel(L, K_SCALE, 0, nullptr, h->lv[L].g, nullptr));
+        if (l == h->tail_level && h->tail_prog) {
+            Op op{};
+            op.kind = OP_TAIL;
+            op.level = l;
+            op.prec = h->lv[l].prec;
+            op.prec_c = l > 0 ? h->lv[l - 1].prec : op.prec;
+            op.prog_off = (int)h->tail_host.size();
+            tcycle(l, first);
+            op.prog_len = (int)h->tail_host.size() - op.prog_off;
+            op.a.gate = gate;
+            op.a.st = st;
+            out->push_back(op);
+            return;
+        }
         if (l == 0) {
             Op op{};
             op.kind = OP_COARSE;
@@ -279,7 +362,13 @@ void* mgi_build_cycle(mgi_hier& h, std::vector<Op>& ops, bool top_from_r, int ga
     gen.top_from_r = top_from_r;
     gen.out = &ops;
     for (int l = 0; l < MG_MAX_LEVELS; ++l) gen.cur[l] = 0;
+    const size_t t0 = h.tail_host.size();
     gen.cycle(h.nlev - 1, true);
+    if (h.tail_prog && h.tail_host.size() > t0) {
+        if (h.tail_host.size() > (size_t)kTailMaxOps) return nullptr;
+        cudaMemcpy(h.tail_prog + t0, h.tail_host.data() + t0, (h.tail_host.size() - t0) * sizeof(TailOp),
+                   cudaMemcpyHostToDevice);
+    }
     return gen.cbuf(h.nlev - 1);
 }
 
@@ -311,7 +400,16 @@ static size_t update_blocks_max(const mgi_hier& h) {
 
 static void build_step(mgi_hier& h) {
     h.step.clear();
+    h.tail_host.clear();
     void* cL = mgi_build_cycle(h, h.step, true, 1, h.st);
+    if (!cL) {  // tail programs beyond capacity (deep W-cycles): plain kernels on every level
+        h.tail_prog = nullptr;
+        h.tail_level = -1;
+        h.tail_host.clear();
+        h.step.clear();
+        cL = mgi_build_cycle(h, h.step, true, 1, h.st);
+    }
+    h.step_tail_ops = h.tail_host.size();
     Op up = mgi_update_op(h, cL, 1, h.st);
     h.step.push_back(up);
     Op fin{};
@@ -333,6 +431,8 @@ int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
             return (int)cudaMemsetAsync((char*)op.ptr - op.zero_base, 0, op.bytes, s);
         case OP_FINALIZE:
             return launch_finalize(op.fin_kind, h.st, h.partials, op.nblocks, s);
+        case OP_TAIL:
+            return launch_tail(h.dim, h.tail_prog + op.prog_off, op.prog_len, h.minv, h.m0, op.a.st, op.a.gate, s);
     }
     return (int)cudaErrorInvalidValue;
 }
@@ -379,6 +479,12 @@ static mg_status plan_hier(const mg_params* p, mgi_hier& h) {
     int sl = p->sigma_log2 >= 0 ? p->sigma_log2 : (any16 ? 14 : 0);
     h.sigma = p->scaling == 0 ? 1.0 : std::ldexp(1.0, sl);
     h.g_alias_r = (p->prec[L - 1] == MG_FP64 && p->scaling == 0);
+    h.tail_level = -1;
+    for (int l = 0; l < L; ++l) {
+        const long long n = sizes[l];
+        if ((p->dim == 3 ? n * n * n : n * n) <= kTailMaxPoints) h.tail_level = l;
+    }
+    if (h.tail_level < 1 || p->reserved[0] == 1) h.tail_level = -1;  // reserved[0] = 1: no coarse tail
     h.m0 = 1;
     for (int a = 0; a < p->dim; ++a) h.m0 *= sizes[0];
     Layout lay;
@@ -429,6 +535,10 @@ extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, 
     h->u = h->u_alloc + gf.base;
     h->r = h->r_alloc + gf.base;
     h->partials = (double*)(base + lay.part_off);
+    if (h->tail_level >= 0) {
+        h->tail_prog = (TailOp*)(base + lay.tprog_off);
+        h->tail_scratch = base + lay.tscr_off;
+    }
     h->st = (DevState*)(base + lay.st_off);
     h->minv = (double*)(base + lay.minv_off);
     std::vector<double> inv;
@@ -826,6 +936,25 @@ static double op_bytes(const mgi_hier& h, const Op& op) {
         case OP_COARSE: return 2 * s * N + 8.0 * h.m0 * h.m0;
         case OP_ZERO: return (double)op.bytes;
         case OP_FINALIZE: return 16.0 * op.nblocks;
+        case OP_TAIL: {
+            double b = 0.0;  // sum over the program's stages, each array touched once
+            for (int i = op.prog_off; i < op.prog_off + op.prog_len; ++i) {
+                const TailOp& t = h.tail_host[i];
+                const double ts = (double)elem_size(t.prec), tsc = (double)elem_size(t.prec_c);
+                const double tn = h.dim == 3 ? (double)t.n * t.n * t.n : (double)t.n * t.n;
+                const double tnc = h.dim == 3 ? (double)t.nc * t.nc * t.nc : (double)t.nc * t.nc;
+                const double cs = t.prec == MG_FP64 ? 8.0 : 4.0;
+                switch (t.kind) {
+                    case TK_SWEEP: b += (t.mode == M_JACOBI ? 3 : 2) * ts * tn; break;
+                    case TK_RESID: b += 2 * ts * tn + cs * tn; break;
+                    case TK_RESTRICT: b += cs * tn + tsc * tnc; break;
+                    case TK_PROLONG: b += 2 * ts * tn + tsc * tnc; break;
+                    case TK_COARSE: b += 2 * ts * tn + 8.0 * h.m0 * h.m0; break;
+                    default: b += ts * tn; break;
+                }
+            }
+            return b;
+        }
     }
     return 0.0;
 }
@@ -856,7 +985,7 @@ extern "C" mg_status mg_profile_solve(mg_hierarchy* hh, const double* b, double*
         std::memset(&k, 0, sizeof(k));
         k.kind = op.kind == OP_KERNEL ? (op.kkind == K_SWEEP ? 0 : op.kkind == K_PROLONG ? 2
                                          : op.kkind == K_UPDATE ? 5 : 6)
-                                      : op.kind;
+                                      : op.kind;  // OP_TAIL = 7
         k.level = op.level;
         k.mode = op.mode;
         k.loader = 0;

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "mg_internal.h"
+#include "mg_tail.h"
 
 namespace mgi {
 
@@ -23,7 +24,7 @@ struct Level {
 // OP_KERNEL covers the fine-level kernels (kernel kind in kkind: sweep,
 // IR update, scale-cast, prolongation); the values of `kind` follow
 // mg_kernel_time.kind of mg.h.
-enum OpKind : int { OP_KERNEL = 0, OP_COARSE = 1, OP_ZERO = 3, OP_FINALIZE = 4 };
+enum OpKind : int { OP_KERNEL = 0, OP_COARSE = 1, OP_ZERO = 3, OP_FINALIZE = 4, OP_TAIL = 7 };
 
 struct Op {
     int kind = 0, level = 0;
@@ -36,6 +37,7 @@ struct Op {
     size_t bytes = 0;
     size_t zero_base = 0;     // bytes between allocation start and ptr
     int fin_kind = 0, nblocks = 0;
+    int prog_off = 0, prog_len = 0;  // OP_TAIL: stages in the hierarchy's tail program
 };
 
 struct SolveCtx {
@@ -80,6 +82,11 @@ struct mgi_hier {
     cudaGraphExec_t solve_exec = nullptr;  // whole solve with a device-side IR loop
     bool solve_graph_failed = false;
     cudaStream_t aux = nullptr;            // capture stream of the loop body
+    int tail_level = -1;                   // coarse levels 0..tail_level run in one cluster kernel
+    std::vector<TailOp> tail_host;         // tail programs (all visits), mirrored on the device
+    size_t step_tail_ops = 0;              // tail stages of the IR step (stage calls append after)
+    TailOp* tail_prog = nullptr;           // device copy (capacity kTailMaxOps)
+    void* tail_scratch = nullptr;          // residual scratch of the tail levels
     void* arena = nullptr;
     size_t arena_bytes = 0;
     size_t footprint = 0;

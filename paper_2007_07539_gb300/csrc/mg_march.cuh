@@ -187,15 +187,20 @@ __global__ void __launch_bounds__(320) k_sweep3(const KArgs a) {
     C acc[VH];
 #pragma unroll
     for (int k = 0; k < VH; ++k) acc[k] = 0;
+    // the lane's own row of planes z-1, z, z+1 stays in registers (converted
+    // once); y-neighbours, x-halo and g come from the shared-memory ring
+    C cm[V], c0[V], cp[V];
+    cp_wait<S - 3>();  // planes zb-1 and zb have landed
+    __syncthreads();
+    lds_vec<T>(crow(stage_of(zb - 1), w + 1), lane, cm);
+    lds_vec<T>(crow(stage_of(zb), w + 1), lane, c0);
     for (int z = zb; z < ze; ++z) {
         cp_wait<S - 4>();  // planes up to z+1 have landed (this thread's copies)
         __syncthreads();   // ... everyone's; and stage(z-2) is no longer read
         issue(z + S - 2);
-        const int sm1 = stage_of(z - 1), s0 = stage_of(z), sp1 = stage_of(z + 1);
-        C c0[V], cm[V], cp[V], ym[V], yp[V], g[V];
-        lds_vec<T>(crow(s0, w + 1), lane, c0);
-        lds_vec<T>(crow(sm1, w + 1), lane, cm);
-        lds_vec<T>(crow(sp1, w + 1), lane, cp);
+        const int s0 = stage_of(z);
+        C ym[V], yp[V], g[V];
+        lds_vec<T>(crow(stage_of(z + 1), w + 1), lane, cp);
         lds_vec<T>(crow(s0, w), lane, ym);
         lds_vec<T>(crow(s0, w + 2), lane, yp);
         const C left = lds_one<T>(crow(s0, w + 1), lane * V - 1);
@@ -208,6 +213,8 @@ __global__ void __launch_bounds__(320) k_sweep3(const KArgs a) {
             const C v = point_value<MODE, C>(c0[i], nb, NEED_G ? g[i] : (C)0, c1, c2, c3, h2inv, twod, om);
             out[i] = (x + i < a.n && row_in) ? v : (C)0;
         }
+#pragma unroll
+        for (int i = 0; i < V; ++i) { cm[i] = c0[i]; c0[i] = cp[i]; }
         if constexpr (MODE != M_RESTRICT) {
             if (row_in && lane_in) stv(reinterpret_cast<T*>(a.dst) + offs<3>(x, y, z, a.P, a.S), out);
         } else {
@@ -287,19 +294,22 @@ __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
     C acc[VH];
 #pragma unroll
     for (int k = 0; k < VH; ++k) acc[k] = 0;
+    // rows y-1, y, y+1 of the lane's chunk stay in registers (converted once)
+    C cm[V], c0[V], cp[V];
+    cp_wait<S - 3>();
+    __syncwarp();
+    lds_vec<T>(crow(slot(yb - 1)), lane, cm);
+    lds_vec<T>(crow(slot(yb)), lane, c0);
     for (int y = yb; y < ye; ++y) {
         cp_wait<S - 4>();
-        __syncwarp();
-        const int sm1 = slot(y - 1), s0 = slot(y), sp1 = slot(y + 1);
-        C c0[V], cm[V], cp[V], g[V];
-        lds_vec<T>(crow(s0), lane, c0);
-        lds_vec<T>(crow(sm1), lane, cm);
-        lds_vec<T>(crow(sp1), lane, cp);
+        __syncwarp();      // the lanes' copies of row y+1 have landed; row y-2's slot is free
+        issue(y + S - 2);  // reuses the slot of row y-2
+        const int s0 = slot(y);
+        C g[V];
+        lds_vec<T>(crow(slot(y + 1)), lane, cp);
         const C left = lds_one<T>(crow(s0), lane * V - 1);
         const C right = lds_one<T>(crow(s0), lane * V + V);
         if (NEED_G) lds_vec<T>(grow(s0), lane, g);
-        __syncwarp();      // all lanes have read row y-1's slot before it is refilled
-        issue(y + S - 2);  // same slot as row y-2 ... y-1 is slot(y+S-1); y+S-2 reuses slot(y-2)
         C out[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
@@ -307,6 +317,8 @@ __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
             const C v = point_value<MODE, C>(c0[i], nb, NEED_G ? g[i] : (C)0, c1, c2, c3, h2inv, twod, om);
             out[i] = (x + i < a.n) ? v : (C)0;
         }
+#pragma unroll
+        for (int i = 0; i < V; ++i) { cm[i] = c0[i]; c0[i] = cp[i]; }
         if constexpr (MODE != M_RESTRICT) {
             if (lane_in) stv(reinterpret_cast<T*>(a.dst) + offs<2>(x, y, 0, a.P, a.S), out);
         } else {
@@ -368,12 +380,13 @@ __global__ void __launch_bounds__(256) k_scale_cast(const KArgs a) {
     constexpr int V = Tr<T>::V;
     if (a.gate && a.st->phase != 0) return;
     const int vpr = a.P / V;  // vectors per padded row
-    const long long rows = DIM == 3 ? (long long)a.n * a.n : a.n;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int rows = DIM == 3 ? a.n * a.n : a.n;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * vpr) return;
-    const int x = (int)(idx % vpr) * V;
-    const long long row = idx / vpr;
-    const int y = (int)(row % a.n), z = DIM == 3 ? (int)(row / a.n) : 0;
+    const int row = idx / vpr;
+    const int x = (idx - row * vpr) * V;
+    const int z = DIM == 3 ? row / a.n : 0;
+    const int y = row - z * a.n;
     const long long o = offs<DIM>(x, y, z, a.P, a.S);
     const double inv = a.st ? a.st->inv : a.inv_explicit;
     C v[V];
@@ -567,18 +580,22 @@ __global__ void __launch_bounds__(256) k_update(const KArgs a) {
     constexpr int Q = kUpdQ;
     if (a.gate && a.st->phase != 0) return;
     const int vpr = a.P / Q;
-    const long long rows = DIM == 3 ? (long long)a.n * a.n : a.n;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int rows = DIM == 3 ? a.n * a.n : a.n;
+    const int total = rows * vpr;
     const int E = sq_exponent(a.st);
+    const double alpha = a.st ? a.st->alpha : a.a_step;
+    const double beta = alpha * a.h2inv;
     SqAcc sq;
     unsigned long long nmax = 0ull;
-    const int x = (int)(idx % vpr) * Q;
-    if (idx < rows * vpr && x < a.n) {
-        const long long row = idx / vpr;
-        const int y = (int)(row % a.n), z = DIM == 3 ? (int)(row / a.n) : 0;
+    // grid-stride over the row vectors: each CTA owns a fixed set, so the
+    // partial sums (one per CTA) are accumulated in a fixed order
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int row = idx / vpr;
+        const int x = (idx - row * vpr) * Q;
+        if (x >= a.n) continue;
+        const int z = DIM == 3 ? row / a.n : 0;
+        const int y = row - z * a.n;
         const long long o = offs<DIM>(x, y, z, a.P, a.S);
-        const double alpha = a.st ? a.st->alpha : a.a_step;
-        const double beta = alpha * a.h2inv;
         const T* c = reinterpret_cast<const T*>(a.src) + o;
         double* up = a.u64 + o;
         double* rp = a.rw64 + o;
@@ -664,13 +681,14 @@ __global__ void __launch_bounds__(256) k_prolong(const KArgs a) {
     constexpr int V = Tr<T>::V;
     if (a.gate && a.st->phase != 0) return;
     const int vpr = a.P / V;
-    const long long rows = DIM == 3 ? (long long)a.n * a.n : a.n;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int rows = DIM == 3 ? a.n * a.n : a.n;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * vpr) return;
-    const int x = (int)(idx % vpr) * V;
+    const int row = idx / vpr;
+    const int x = (idx - row * vpr) * V;
     if (x >= a.n) return;
-    const long long row = idx / vpr;
-    const int y = (int)(row % a.n), z = DIM == 3 ? (int)(row / a.n) : 0;
+    const int z = DIM == 3 ? row / a.n : 0;
+    const int y = row - z * a.n;
     T* f = reinterpret_cast<T*>(a.dst) + offs<DIM>(x, y, z, a.P, a.S);
     C v[V];
     ldv(f, v);

@@ -2,6 +2,7 @@
 // FP64 residual b - A u with norms, norm finalisation and the IR control
 // state, and packing between the caller's contiguous layout and the padded
 // device layout.  Also the launch-geometry rule of the stencil march.
+#include <algorithm>
 #include <cmath>
 
 #include "mg_march.cuh"
@@ -75,6 +76,7 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
         s.tx = 256;
         s.ty = 1;
         s.gx = cdiv(rows * (P / per), 256);
+        if (kind == K_UPDATE) s.gx = std::min(s.gx, 4 * kSMs);  // grid-stride: one partial per CTA
         s.gy = 1;
         s.smem = 0;
         return s;
@@ -190,19 +192,22 @@ int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void*
 // r = b - A u in FP64 with per-CTA partials {sum r^2, max |r|, sum b^2, 0};
 // optionally copies u to the caller's contiguous array.  One thread per point.
 template <int DIM>
-__global__ void k_residual64(RArgs a, int init_copy) {
+__global__ void __launch_bounds__(256) k_residual64(RArgs a, int init_copy) {
     if (a.gate == 1 && a.st->phase != 1) return;
     if (a.gate == 2 && !a.st->dirty) return;
     const double* bsrc = a.b ? a.b : a.st->b;
     double* uout = a.use_st_uout ? a.st->uout : a.uout;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
+    const int npts = DIM == 3 ? a.n * a.n * a.n : a.n * a.n;
     double sr = 0.0, sb = 0.0;
     unsigned long long mr = 0ull;
-    if (i < a.n && j < a.n) {
+    // grid-stride over the interior points (contiguous order): fixed
+    // per-CTA sets, so the partial sums are accumulated in a fixed order
+    for (int oc = blockIdx.x * blockDim.x + threadIdx.x; oc < npts; oc += gridDim.x * blockDim.x) {
+        const int q = oc / a.n;
+        const int i = oc - q * a.n;
+        const int k = DIM == 3 ? q / a.n : 0;
+        const int j = q - k * a.n;
         const long long o = offs<DIM>(i, j, k, a.P, a.S);
-        const long long oc = DIM == 3 ? ((long long)k * a.n + j) * a.n + i : (long long)j * a.n + i;
         const double bv = __ldg(bsrc + oc);
         double r;
         if (init_copy) {
@@ -216,14 +221,15 @@ __global__ void k_residual64(RArgs a, int init_copy) {
             if (uout) uout[oc] = uc;
         }
         if (a.r) a.r[o] = r;
-        sr = r * r;
-        sb = bv * bv;
-        mr = abs_key(r);
+        sr = fma(r, r, sr);
+        sb = fma(bv, bv, sb);
+        const unsigned long long key = abs_key(r);
+        mr = key > mr ? key : mr;
     }
     __shared__ double s1[32], s2[32];
     __shared__ unsigned long long s3[32];
-    const int lane = threadIdx.x & 31, wid = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (blockDim.x * blockDim.y) >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
     sr = warp_sum(sr); sb = warp_sum(sb); mr = warp_max(mr);
     if (lane == 0) { s1[wid] = sr; s2[wid] = sb; s3[wid] = mr; }
     __syncthreads();
@@ -233,18 +239,18 @@ __global__ void k_residual64(RArgs a, int init_copy) {
         mr = lane < nw ? s3[lane] : 0ull;
         sr = warp_sum(sr); sb = warp_sum(sb); mr = warp_max(mr);
         if (lane == 0) {
-            const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-            a.partials[4 * bid + 0] = sr;
-            a.partials[4 * bid + 1] = __longlong_as_double((long long)mr);
-            a.partials[4 * bid + 2] = sb;
-            a.partials[4 * bid + 3] = 0.0;
+            a.partials[4LL * blockIdx.x + 0] = sr;
+            a.partials[4LL * blockIdx.x + 1] = __longlong_as_double((long long)mr);
+            a.partials[4LL * blockIdx.x + 2] = sb;
+            a.partials[4LL * blockIdx.x + 3] = 0.0;
         }
     }
 }
 
 static void residual_grid(int dim, int n, dim3& grid, dim3& block) {
-    block = dim3(64, 4);
-    grid = dim3((unsigned)cdiv(n, 64), (unsigned)cdiv(n, 4), (unsigned)(dim == 3 ? n : 1));
+    const long long npts = dim == 3 ? (long long)n * n * n : (long long)n * n;
+    block = dim3(256);
+    grid = dim3((unsigned)std::min<long long>(cdiv(npts, 256), 8LL * kSMs));
 }
 
 int residual64_blocks(int dim, int n) {

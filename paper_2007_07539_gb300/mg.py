@@ -63,7 +63,7 @@ class KernelTime(ctypes.Structure):
                 ("launches", ctypes.c_int32), ("threads", ctypes.c_int32), ("grid", ctypes.c_int32 * 3),
                 ("reserved", ctypes.c_int32), ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
-    KIND = ["sweep", "base_solve", "prolong", "zero", "finalize", "ir_update", "scale_cast"]
+    KIND = ["sweep", "base_solve", "prolong", "zero", "finalize", "ir_update", "scale_cast", "coarse_tail"]
     MODE = ["jacobi", "jacobi_x2_from_zero", "jacobi_from_zero", "residual_restrict"]
 
     def name(self) -> str:
