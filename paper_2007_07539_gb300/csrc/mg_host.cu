@@ -107,7 +107,7 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
     size_t level_off[MG_MAX_LEVELS][3];
-    size_t u_off, r_off, part_off, st_off, minv_off, tprog_off, tscr_off, total;
+    size_t u_off, r_off, part_off, st_off, minv_off, tprog_off, total;
     size_t part_cap;
 };
 
@@ -129,17 +129,7 @@ static void compute_layout(mgi_hier& h, Layout& lay) {
     lay.st_off = off; off += align_up(sizeof(DevState), 256);
     lay.minv_off = off; off += align_up((size_t)h.m0 * h.m0 * 8, 256);
     lay.tprog_off = off;
-    lay.tscr_off = off;
-    if (h.tail_level >= 0) {
-        off += align_up(sizeof(TailOp) * kTailMaxOps, 256);
-        lay.tscr_off = off;
-        size_t mx = 0;
-        for (int l = 0; l <= h.tail_level; ++l) {
-            const size_t n = (size_t)h.lv[l].geo.n;
-            mx = std::max(mx, h.dim == 3 ? n * n * n : n * n);
-        }
-        off += align_up(mx * 8, 256);
-    }
+    if (h.tail_level >= 0) off += align_up(sizeof(TailOp) * kTailMaxOps, 256);
     lay.total = off;
 }
 
@@ -234,60 +224,81 @@ struct Gen {
         cur[l] ^= 1;
     }
 
-    // ---- coarse tail: the same recursion, emitted as stages of one cluster kernel
+    // ---- coarse tail: the same recursion on shared-memory copies of levels
+    // 0..tail_level, emitted as the stages of one single-CTA kernel
+    int sc(int l) const { return h->tail_soff[l][cur[l]]; }
+    int so(int l) const { return h->tail_soff[l][cur[l] ^ 1]; }
+    int sg(int l) const { return h->tail_soff[l][2]; }
     TailOp tbase(int l, int kind) {
         TailOp t{};
         t.kind = kind;
         t.prec = h->lv[l].prec;
         t.prec_c = l > 0 ? h->lv[l - 1].prec : t.prec;
         const Geom& f = h->lv[l].geo;
-        t.n = f.n; t.P = f.P; t.S = f.S;
-        if (l > 0) { const Geom& c = h->lv[l - 1].geo; t.nc = c.n; t.Pc = c.P; t.Sc = c.S; }
+        t.n = f.n; t.P = f.P; t.S = (int)f.S;
+        t.mn = tail_magic(f.n);
+        if (l > 0) { t.nc = h->lv[l - 1].geo.n; t.mnc = tail_magic(t.nc); }
         t.h2inv = (double)(f.n + 1) * (double)(f.n + 1);
         t.omega = h->p.omega;
-        t.scratch = h->tail_scratch;
         return t;
     }
     void tpush(const TailOp& t) { h->tail_host.push_back(t); }
-    void tsweep(int l, int mode, const void* src, void* dst, const void* g) {
+    void tsweep(int l, int mode, int src, int dst, int g) {
         TailOp t = tbase(l, TK_SWEEP);
         t.mode = mode; t.src = src; t.dst = dst; t.g = g;
         tpush(t);
     }
+    void tjacobi(int l) { tsweep(l, M_JACOBI, sc(l), so(l), sg(l)); cur[l] ^= 1; }
     void tcycle(int l, bool first) {
         if (l == 0) {
             TailOp t = tbase(0, TK_COARSE);
-            t.g = gbuf(0);
-            t.dst = cbuf(0);
+            t.g = sg(0);
+            t.dst = sc(0);
             tpush(t);
             return;
         }
         if (first) {
             if (h->p.nu1 >= 2) {
-                tsweep(l, M_ZERO2, gbuf(l), cbuf(l), nullptr);
-                for (int k = 2; k < h->p.nu1; ++k) { tsweep(l, M_JACOBI, cbuf(l), obuf(l), gbuf(l)); cur[l] ^= 1; }
+                tsweep(l, M_ZERO2, sg(l), sc(l), 0);
+                for (int k = 2; k < h->p.nu1; ++k) tjacobi(l);
             } else if (h->p.nu1 == 1) {
-                tsweep(l, M_ZERO1, gbuf(l), cbuf(l), nullptr);
+                tsweep(l, M_ZERO1, sg(l), sc(l), 0);
             } else {
                 TailOp t = tbase(l, TK_ZERO);
-                t.dst = cbuf(l);
+                t.dst = sc(l);
                 tpush(t);
             }
         } else {
-            for (int k = 0; k < h->p.nu1; ++k) { tsweep(l, M_JACOBI, cbuf(l), obuf(l), gbuf(l)); cur[l] ^= 1; }
+            for (int k = 0; k < h->p.nu1; ++k) tjacobi(l);
         }
         TailOp r = tbase(l, TK_RESID);
-        r.src = cbuf(l); r.g = gbuf(l);
+        r.src = sc(l); r.g = sg(l); r.dst = h->tail_rscr;
         tpush(r);
         TailOp rs = tbase(l, TK_RESTRICT);
-        rs.dst = h->lv[l - 1].g;
+        rs.src = h->tail_rscr; rs.dst = sg(l - 1);
         tpush(rs);
         cur[l - 1] = 0;
         for (int k = 0; k < h->p.gamma; ++k) tcycle(l - 1, k == 0);
         TailOp pr = tbase(l, TK_PROLONG);
-        pr.dst = cbuf(l); pr.coarse = cbuf(l - 1);
+        pr.dst = sc(l); pr.coarse = sc(l - 1);
         tpush(pr);
-        for (int k = 0; k < h->p.nu2; ++k) { tsweep(l, M_JACOBI, cbuf(l), obuf(l), gbuf(l)); cur[l] ^= 1; }
+        for (int k = 0; k < h->p.nu2; ++k) tjacobi(l);
+    }
+    // one visit of level l = tail_level: load its g (and, on later W-cycle
+    // visits, its c) from the global level arrays, recurse, store c back
+    void tvisit(int l, bool first) {
+        TailOp ld = tbase(l, TK_LOAD);
+        ld.dst = sg(l); ld.gptr = const_cast<void*>(gbuf(l));
+        tpush(ld);
+        if (!first) {
+            TailOp lc = tbase(l, TK_LOAD);
+            lc.dst = sc(l); lc.gptr = cbuf(l);
+            tpush(lc);
+        }
+        tcycle(l, first);
+        TailOp stc = tbase(l, TK_STORE);
+        stc.src = sc(l); stc.gptr = cbuf(l);
+        tpush(stc);
     }
 
     // Alg. 1 on level l; first = zero initial correction (first visit).
@@ -302,7 +313,7 @@ struct Gen {
             op.prec = h->lv[l].prec;
             op.prec_c = l > 0 ? h->lv[l - 1].prec : op.prec;
             op.prog_off = (int)h->tail_host.size();
-            tcycle(l, first);
+            tvisit(l, first);
             op.prog_len = (int)h->tail_host.size() - op.prog_off;
             op.a.gate = gate;
             op.a.st = st;
@@ -432,7 +443,8 @@ int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
         case OP_FINALIZE:
             return launch_finalize(op.fin_kind, h.st, h.partials, op.nblocks, s);
         case OP_TAIL:
-            return launch_tail(h.dim, h.tail_prog + op.prog_off, op.prog_len, h.minv, h.m0, op.a.st, op.a.gate, s);
+            return launch_tail(h.dim, h.tail_prec, h.tail_prog + op.prog_off, op.prog_len, h.minv, h.m0, op.a.st,
+                               op.a.gate, h.tail_smem, s);
     }
     return (int)cudaErrorInvalidValue;
 }
@@ -460,6 +472,40 @@ static void free_hier(mgi_hier* h) {
     delete h;
 }
 
+// Shared-memory plan of the coarse tail: the deepest level T >= 1 with at
+// most kTailMaxPoints points whose arrays (c, t, g of levels 0..T in their
+// storage types, plus one residual scratch in the arithmetic type) fit in
+// kTailMaxSmem bytes; tail_level = -1 when no level qualifies.
+static void plan_tail(mgi_hier& h, bool disabled) {
+    h.tail_level = -1;
+    h.tail_smem = 0;
+    if (disabled) return;
+    for (int T = h.nlev - 1; T >= 1; --T) {
+        size_t off = 0, rmax = 0;
+        bool ok = true;
+        for (int l = 0; l <= T && ok; ++l) {
+            const long long n = h.lv[l].geo.n;
+            const long long N = h.dim == 3 ? n * n * n : n * n;
+            if (N > kTailMaxPoints) { ok = false; break; }
+            for (int v = 0; v < 3; ++v) {
+                h.tail_soff[l][v] = (int)off;
+                off = align_up(off + (size_t)N * h.lv[l].esz, 16);
+            }
+            rmax = std::max(rmax, (size_t)N * (h.lv[l].prec == MG_FP64 ? 8 : 4));
+        }
+        if (!ok) continue;
+        h.tail_rscr = (int)off;
+        off = align_up(off + rmax, 16);
+        if (off > kTailMaxSmem) continue;
+        h.tail_level = T;
+        h.tail_smem = off;
+        h.tail_prec = h.lv[0].prec;
+        for (int l = 1; l <= T; ++l)
+            if (h.lv[l].prec != h.tail_prec) h.tail_prec = -1;
+        return;
+    }
+}
+
 static mg_status plan_hier(const mg_params* p, mgi_hier& h) {
     std::string why;
     int L = mgi_validate(p, why);
@@ -479,12 +525,7 @@ static mg_status plan_hier(const mg_params* p, mgi_hier& h) {
     int sl = p->sigma_log2 >= 0 ? p->sigma_log2 : (any16 ? 14 : 0);
     h.sigma = p->scaling == 0 ? 1.0 : std::ldexp(1.0, sl);
     h.g_alias_r = (p->prec[L - 1] == MG_FP64 && p->scaling == 0);
-    h.tail_level = -1;
-    for (int l = 0; l < L; ++l) {
-        const long long n = sizes[l];
-        if ((p->dim == 3 ? n * n * n : n * n) <= kTailMaxPoints) h.tail_level = l;
-    }
-    if (h.tail_level < 1 || p->reserved[0] == 1) h.tail_level = -1;  // reserved[0] = 1: no coarse tail
+    plan_tail(h, p->reserved[0] == 1);  // reserved[0] = 1: no coarse tail
     h.m0 = 1;
     for (int a = 0; a < p->dim; ++a) h.m0 *= sizes[0];
     Layout lay;
@@ -535,10 +576,7 @@ extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, 
     h->u = h->u_alloc + gf.base;
     h->r = h->r_alloc + gf.base;
     h->partials = (double*)(base + lay.part_off);
-    if (h->tail_level >= 0) {
-        h->tail_prog = (TailOp*)(base + lay.tprog_off);
-        h->tail_scratch = base + lay.tscr_off;
-    }
+    if (h->tail_level >= 0) h->tail_prog = (TailOp*)(base + lay.tprog_off);
     h->st = (DevState*)(base + lay.st_off);
     h->minv = (double*)(base + lay.minv_off);
     std::vector<double> inv;
@@ -937,21 +975,12 @@ static double op_bytes(const mgi_hier& h, const Op& op) {
         case OP_ZERO: return (double)op.bytes;
         case OP_FINALIZE: return 16.0 * op.nblocks;
         case OP_TAIL: {
-            double b = 0.0;  // sum over the program's stages, each array touched once
+            double b = 0.0;  // global traffic only: the level arrays of the tail live in shared memory
             for (int i = op.prog_off; i < op.prog_off + op.prog_len; ++i) {
                 const TailOp& t = h.tail_host[i];
-                const double ts = (double)elem_size(t.prec), tsc = (double)elem_size(t.prec_c);
                 const double tn = h.dim == 3 ? (double)t.n * t.n * t.n : (double)t.n * t.n;
-                const double tnc = h.dim == 3 ? (double)t.nc * t.nc * t.nc : (double)t.nc * t.nc;
-                const double cs = t.prec == MG_FP64 ? 8.0 : 4.0;
-                switch (t.kind) {
-                    case TK_SWEEP: b += (t.mode == M_JACOBI ? 3 : 2) * ts * tn; break;
-                    case TK_RESID: b += 2 * ts * tn + cs * tn; break;
-                    case TK_RESTRICT: b += cs * tn + tsc * tnc; break;
-                    case TK_PROLONG: b += 2 * ts * tn + tsc * tnc; break;
-                    case TK_COARSE: b += 2 * ts * tn + 8.0 * h.m0 * h.m0; break;
-                    default: b += ts * tn; break;
-                }
+                if (t.kind == TK_LOAD || t.kind == TK_STORE) b += (double)elem_size(t.prec) * tn;
+                if (t.kind == TK_COARSE) b += 8.0 * h.m0 * h.m0;
             }
             return b;
         }

@@ -82,11 +82,14 @@ struct mgi_hier {
     cudaGraphExec_t solve_exec = nullptr;  // whole solve with a device-side IR loop
     bool solve_graph_failed = false;
     cudaStream_t aux = nullptr;            // capture stream of the loop body
-    int tail_level = -1;                   // coarse levels 0..tail_level run in one cluster kernel
+    int tail_level = -1;                   // coarse levels 0..tail_level run in one single-CTA kernel
     std::vector<TailOp> tail_host;         // tail programs (all visits), mirrored on the device
     size_t step_tail_ops = 0;              // tail stages of the IR step (stage calls append after)
     TailOp* tail_prog = nullptr;           // device copy (capacity kTailMaxOps)
-    void* tail_scratch = nullptr;          // residual scratch of the tail levels
+    int tail_soff[MG_MAX_LEVELS][3] = {};  // shared-memory byte offsets of c, t, g of tail levels
+    int tail_rscr = 0;                     // shared-memory byte offset of the tail's residual scratch
+    size_t tail_smem = 0;                  // dynamic shared memory of the tail kernel
+    int tail_prec = -1;                    // storage type of every tail level, -1 if they differ
     void* arena = nullptr;
     size_t arena_bytes = 0;
     size_t footprint = 0;

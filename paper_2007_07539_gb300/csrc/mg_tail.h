@@ -1,33 +1,51 @@
 // Coarse-tail program: the stages of the multigrid cycle on the coarsest
-// levels, executed in order by one thread-block cluster (mg_tail.cu).
+// levels, executed in order by one CTA with every tail level held in shared
+// memory (mg_tail.cu).
 #pragma once
 #include "mg_internal.h"
 
 namespace mgi {
 
 constexpr int kTailThreads = 1024;
-constexpr long long kTailMaxPoints = 32768;  // levels with n^d up to this run in the tail
+constexpr long long kTailMaxPoints = 8192;   // levels with n^d up to this run in the tail
+constexpr size_t kTailMaxSmem = 200 * 1024;  // shared-memory budget of the tail's level arrays
 constexpr int kTailMaxOps = 16384;
 
-enum TailKind : int { TK_SWEEP = 0, TK_RESID = 1, TK_RESTRICT = 2, TK_PROLONG = 3, TK_COARSE = 4, TK_ZERO = 5 };
+enum TailKind : int {
+    TK_SWEEP = 0,     // Jacobi family (mode M_JACOBI / M_ZERO2 / M_ZERO1) on level n
+    TK_RESID = 1,     // scratch r = g - A c (arithmetic type)
+    TK_RESTRICT = 2,  // coarse g = R r (cast to the coarse storage type)
+    TK_PROLONG = 3,   // c += P c_coarse
+    TK_COARSE = 4,    // c = A0^-1 g
+    TK_ZERO = 5,      // c = 0
+    TK_LOAD = 6,      // shared array <- padded global array
+    TK_STORE = 7      // padded global array <- shared array
+};
 
+// One stage.  src / g / dst / coarse are byte offsets into the kernel's
+// dynamic shared memory, where level arrays are compact (x fastest, n^d
+// values, no pads); gptr is the padded global array of TK_LOAD / TK_STORE.
+// mn / mnc are ceil(2^40 / n) and ceil(2^40 / nc): q = (p * mn) >> 40 is p / n
+// for every p < 2^13 (division by an invariant integer through a fixed-point
+// reciprocal, exact here because p * (mn - 2^40 / n) < 2^40 / n).
 struct TailOp {
     int kind, mode, prec, prec_c;
-    int n, P;
-    long long S;
-    int nc, Pc;
-    long long Sc;
-    const void* src;
-    const void* g;
-    void* dst;
-    const void* coarse;
-    void* scratch;
+    int n, nc, P, S;
+    int src, g, dst, coarse;
+    unsigned long long mn, mnc;
+    void* gptr;
     double h2inv;
     double omega;
 };
+static_assert(sizeof(TailOp) % 8 == 0, "TailOp is copied as 8-byte words");
+constexpr int kTailOpWords = (int)(sizeof(TailOp) / 8);
+constexpr int kTailChunk = 32;  // stages staged in shared memory at a time
 
-int launch_tail(int dim, const TailOp* prog, int nops, const double* minv, int m0, const DevState* st, int gate,
-                void* stream);
-int tail_cluster_size(int dim);
+inline unsigned long long tail_magic(int n) { return ((1ull << 40) + (unsigned long long)n - 1) / (unsigned long long)n; }
+
+// uniform_prec: the storage type of every tail level (selects a kernel
+// specialised for it), or -1 for a mixed-precision tail.
+int launch_tail(int dim, int uniform_prec, const TailOp* prog, int nops, const double* minv, int m0,
+                const DevState* st, int gate, size_t smem, void* stream);
 
 }  // namespace mgi

@@ -78,7 +78,7 @@ def test_fp64_random_rhs_same_iterations(oracle, dim, n):
 
 
 @pytest.mark.parametrize("dim,n,lad", [(3, 31, "H"), (3, 63, "H"), (3, 127, "H"), (2, 255, "H"),
-                                       (3, 63, "HSD"), (3, 127, "HSD"), (3, 63, "BSD"), (3, 63, "HS"),
+                                       (3, 63, "HSD"), (3, 127, "HSD"), (3, 63, "BSD"), (3, 63, "HS"), (3, 15, "HSD"), (2, 63, "BSD"),
                                        (3, 63, "S"), (2, 511, "HSD"), (3, 95, "H")])
 def test_low_precision_within_two_iterations(oracle, dim, n, lad):
     check_solve(oracle, dim, n, lad, I.random_rhs(dim, n, 200 + n), extra_iters=2)
