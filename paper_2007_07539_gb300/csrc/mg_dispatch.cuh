@@ -6,21 +6,39 @@
 namespace mgi {
 
 using KFn = void (*)(KArgs);
+using KFn3 = void (*)(KArgs, SweepMaps);  // 3D sweeps (TMA descriptors by value)
+
+template <class T>
+KFn3 pick_sweep3(int mode, int prec_c) {
+    switch (mode) {
+        case M_JACOBI: return &k_sweep3<M_JACOBI, T, T>;
+        case M_ZERO2: return &k_sweep3<M_ZERO2, T, T>;
+        case M_ZERO1: return &k_sweep3<M_ZERO1, T, T>;
+        case M_RESTRICT:
+            switch (prec_c) {
+                case MG_FP64: return &k_sweep3<M_RESTRICT, T, double>;
+                case MG_FP32: return &k_sweep3<M_RESTRICT, T, float>;
+                case MG_FP16: return &k_sweep3<M_RESTRICT, T, __half>;
+                case MG_BF16: return &k_sweep3<M_RESTRICT, T, __nv_bfloat16>;
+            }
+    }
+    return nullptr;
+}
 
 template <int DIM, class T, class TC>
 KFn pick_tc(int kind, int mode) {
-    if (kind == K_SWEEP && mode == M_RESTRICT) return DIM == 3 ? &k_sweep3<M_RESTRICT, T, TC> : &k_sweep2<M_RESTRICT, T, TC>;
+    if (kind == K_SWEEP && mode == M_RESTRICT && DIM == 2) return &k_sweep2<M_RESTRICT, T, TC>;
     if (kind == K_PROLONG) return &k_prolong<DIM, T, TC>;
     return nullptr;
 }
 
 template <int DIM, class T>
 KFn pick(int kind, int mode, int prec_c) {
-    if (kind == K_SWEEP) {
+    if (kind == K_SWEEP && DIM == 2) {
         switch (mode) {
-            case M_JACOBI: return DIM == 3 ? &k_sweep3<M_JACOBI, T, T> : &k_sweep2<M_JACOBI, T, T>;
-            case M_ZERO2: return DIM == 3 ? &k_sweep3<M_ZERO2, T, T> : &k_sweep2<M_ZERO2, T, T>;
-            case M_ZERO1: return DIM == 3 ? &k_sweep3<M_ZERO1, T, T> : &k_sweep2<M_ZERO1, T, T>;
+            case M_JACOBI: return &k_sweep2<M_JACOBI, T, T>;
+            case M_ZERO2: return &k_sweep2<M_ZERO2, T, T>;
+            case M_ZERO1: return &k_sweep2<M_ZERO1, T, T>;
             default: break;
         }
     }
@@ -36,7 +54,18 @@ KFn pick(int kind, int mode, int prec_c) {
 }
 
 template <class T>
-int launch_kernel_t(int dim, int kind, int mode, int prec_c, const KArgs& a, const MarchShape& s, void* stream) {
+int launch_kernel_t(int dim, int kind, int mode, int prec_c, const KArgs& a, const MarchShape& s,
+                    const SweepMaps* maps, void* stream) {
+    if (dim == 3 && kind == K_SWEEP) {
+        KFn3 f3 = pick_sweep3<T>(mode, prec_c);
+        if (!f3 || !maps) return (int)cudaErrorInvalidValue;
+        if (s.smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(f3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+            if (e != cudaSuccess) return (int)e;
+        }
+        f3<<<dim3(s.gx, s.gy, s.gz), dim3(s.tx, s.ty), s.smem, (cudaStream_t)stream>>>(a, *maps);
+        return (int)cudaGetLastError();
+    }
     KFn f = dim == 3 ? pick<3, T>(kind, mode, prec_c) : pick<2, T>(kind, mode, prec_c);
     if (!f) return (int)cudaErrorInvalidValue;
     if (s.smem > 48 * 1024) {
@@ -45,6 +74,28 @@ int launch_kernel_t(int dim, int kind, int mode, int prec_c, const KArgs& a, con
     }
     f<<<dim3(s.gx, s.gy, s.gz), dim3(s.tx, s.ty), s.smem, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
+}
+
+// CTAs of this kernel resident per SM for the given block size and dynamic
+// shared memory (registers, shared memory and warp slots), 0 if unknown.
+template <class F>
+int occupancy_f(F f, int threads, size_t smem) {
+    if (!f) return 0;
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+template <class T>
+int occupancy_t(int dim, int kind, int mode, int prec_c, int threads, size_t smem) {
+    if (dim == 3 && kind == K_SWEEP) return occupancy_f(pick_sweep3<T>(mode, prec_c), threads, smem);
+    return occupancy_f(dim == 3 ? pick<3, T>(kind, mode, prec_c) : pick<2, T>(kind, mode, prec_c), threads, smem);
 }
 
 }  // namespace mgi

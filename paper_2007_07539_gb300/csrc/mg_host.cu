@@ -216,6 +216,13 @@ struct Gen {
         a.h2inv = (double)(f.n + 1) * (double)(f.n + 1);
         op.sh = kernel_shape(h->dim, kkind, mode, op.prec, f.n, f.P, 0);
         a.xstep = op.sh.xstep; a.ystep = op.sh.ystep; a.zstep = op.sh.zstep; a.zlen = op.sh.zlen;
+        a.err = &h->st->kerr;
+        if (h->dim == 3 && kkind == K_SWEEP) {  // TMA boxes: TY+2 rows of the swept vector, TY rows of g
+            op.has_maps = true;
+            if (make_sweep_map(&op.maps.src, op.prec, f, src, op.sh.ty + 2, true) != 0) op.has_maps = false;
+            const void* gm = g ? g : src;  // modes without g never read it
+            if (make_sweep_map(&op.maps.g, op.prec, f, gm, op.sh.ty, false) != 0) op.has_maps = false;
+        }
         return op;
     }
 
@@ -435,7 +442,9 @@ static void build_step(mgi_hier& h) {
 int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
     switch (op.kind) {
         case OP_KERNEL:
-            return launch_kernel(h.dim, op.kkind, op.mode, op.prec, op.prec_c, op.a, op.sh, s);
+            if (h.dim == 3 && op.kkind == K_SWEEP && !op.has_maps) return (int)cudaErrorNotSupported;
+            return launch_kernel(h.dim, op.kkind, op.mode, op.prec, op.prec_c, op.a, op.sh,
+                                 op.has_maps ? &op.maps : nullptr, s);
         case OP_COARSE:
             return launch_coarse_solve(op.prec, h.minv, h.m0, op.g, op.c, h.lv[0].geo, op.a.st, op.a.gate, s);
         case OP_ZERO:
@@ -913,6 +922,10 @@ int mgi_solve_advance(mgi_hier& h) {
     r.rel_res_true = s.rel_true;
     r.seconds = ms * 1e-3;
     r.launches = c.launches;
+    if (s.kerr) {  // a stencil kernel's bounded wait for its tile copies ran out: results are not valid
+        r.status = MG_ERR_CUDA;
+        mgi_set_error("a stencil kernel timed out waiting for its TMA tile copies");
+    }
     c.active = false;
     return 1;
 }

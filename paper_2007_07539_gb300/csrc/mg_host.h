@@ -38,6 +38,8 @@ struct Op {
     size_t zero_base = 0;     // bytes between allocation start and ptr
     int fin_kind = 0, nblocks = 0;
     int prog_off = 0, prog_len = 0;  // OP_TAIL: stages in the hierarchy's tail program
+    bool has_maps = false;           // 3D sweeps: TMA descriptors of src and g
+    SweepMaps maps{};
 };
 
 struct SolveCtx {

@@ -11,6 +11,8 @@
 // Dirichlet boundary value without a branch.  P is a multiple of 16 elements,
 // so x = 0 of every row is 16-byte aligned for all types.
 #pragma once
+#include <cuda.h>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -70,7 +72,7 @@ struct DevState {
     int stag;         // consecutive steps without decrease
     int dirty;        // u changed since it was last copied to the caller's array
     int loops;        // body iterations of the device-side IR loop (bounded)
-    int pad_;
+    int kerr;         // non-zero: a kernel's bounded wait for its tile copies ran out
     const double* b;  // caller's right-hand side (device, contiguous)
     double* uout;     // caller's solution (device, contiguous): u0 in, u out
     double hist[kMaxHist + 2];
@@ -112,6 +114,7 @@ struct KArgs {
     double h2inv;        // 1/h^2 of this level
     int xstep, ystep, zstep, zlen;  // tile strides / march length
     int gate;            // 1: return at once unless st->phase == 0
+    int* err;            // set to 1 when a bounded copy wait runs out (3D sweeps)
 };
 
 // Arguments of the FP64 residual kernel r = b - A u.
@@ -137,9 +140,43 @@ struct MarchShape {
 };
 // Launch geometry of a fine-level kernel over a level of size n (pitch P).
 MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int tz_hint);
-// Launches a fine-level kernel (one translation unit per fine storage type).
+
+// TMA descriptors of the 3D sweeps: the swept vector (boxes of TY+2 rows with
+// a 16-byte x-halo on each side) and the right-hand side (TY rows, no halo).
+// Both describe a padded level vector as a 3D tensor of 4-byte units (2-byte
+// types) or 8-byte units (4- and 8-byte types): x over the pitch, y over rows
+// 0..n (the pad row included), z over planes -1..n.
+struct alignas(64) SweepMaps {
+    CUtensorMap src;
+    CUtensorMap g;
+};
+// Encodes one map for level vector `x0` (the address of element (0,0,0)).
+int make_sweep_map(CUtensorMap* m, int prec, const Geom& geo, const void* x0, int rows, bool halo);
+
+// Shared-memory plan of the 3D sweep, identical on host and device.
+// Ring of 5 stages, each [c box: (TY+2) rows x 544 B, 128-aligned][g box: TY
+// rows x 512 B], then the restriction's flush area, then 5 mbarriers.
+constexpr int kSweepStages = 5;
+constexpr int kSweepRowBytes = 544;
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int sweep3_cbytes(int ty) { return ((ty + 2) * kSweepRowBytes + 127) / 128 * 128; }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int sweep3_stage_bytes(int ty, bool need_g) { return (sweep3_cbytes(ty) + (need_g ? ty * 512 : 0) + 127) / 128 * 128; }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int sweep3_smem(int ty, bool need_g, int flush_bytes) {
+    return 128 + kSweepStages * sweep3_stage_bytes(ty, need_g) + (flush_bytes + 15) / 16 * 16 + kSweepStages * 8;
+}
+
+// Launches a fine-level kernel (one translation unit per fine storage type);
+// maps: the TMA descriptors of a 3D sweep (nullptr for other kernels).
 int launch_kernel(int dim, int kind, int mode, int prec, int prec_c, const KArgs& a, const MarchShape& s,
-                  void* stream);
+                  const SweepMaps* maps, void* stream);
 
 // Misc kernels (mg_misc.cu).
 int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void* c, const Geom& geo,

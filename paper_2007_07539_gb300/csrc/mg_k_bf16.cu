@@ -3,7 +3,11 @@
 #include "mg_dispatch.cuh"
 
 namespace mgi {
-int launch_kernel_bf16(int dim, int kind, int mode, int prec_c, const KArgs& a, const MarchShape& s, void* stream) {
-    return launch_kernel_t<__nv_bfloat16>(dim, kind, mode, prec_c, a, s, stream);
+int launch_kernel_bf16(int dim, int kind, int mode, int prec_c, const KArgs& a, const MarchShape& s,
+                      const SweepMaps* maps, void* stream) {
+    return launch_kernel_t<__nv_bfloat16>(dim, kind, mode, prec_c, a, s, maps, stream);
+}
+int occupancy_bf16(int dim, int kind, int mode, int prec_c, int threads, size_t smem) {
+    return occupancy_t<__nv_bfloat16>(dim, kind, mode, prec_c, threads, smem);
 }
 }  // namespace mgi

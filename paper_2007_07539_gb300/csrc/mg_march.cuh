@@ -121,6 +121,96 @@ __device__ __forceinline__ C point_value(C c0, C nb, C g, C c1, C c2, C c3, C h2
     return g - h2inv * (twod * c0 - nb);                                   // residual g - A c
 }
 
+// ---------------------------------------------------------------- pair arithmetic
+// Values of a row chunk are handled in pairs: FP32 pairs use the packed
+// FP32x2 instructions of sm_100+ (one instruction for two lanes of the pair,
+// each rounded as the scalar operation), FP64 pairs two scalar operations.
+template <class C> struct Pair;
+template <> struct Pair<float> {
+    using t = float2;
+    static __device__ __forceinline__ t mk(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ t splat(float a) { return make_float2(a, a); }
+    static __device__ __forceinline__ t add(t a, t b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ t mul(t a, t b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ t fma(t a, t b, t c) { return __ffma2_rn(a, b, c); }
+};
+template <> struct Pair<double> {
+    using t = double2;
+    static __device__ __forceinline__ t mk(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ t splat(double a) { return make_double2(a, a); }
+    static __device__ __forceinline__ t add(t a, t b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ t mul(t a, t b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ t fma(t a, t b, t c) {
+        return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
+    }
+};
+
+// The lane's V values of a shared-memory row as V/2 pairs of the arithmetic type.
+template <class T>
+__device__ __forceinline__ void lds_pairs(const unsigned char* srow, int lane,
+                                          typename Pair<typename Tr<T>::C>::t (&v)[Tr<T>::V / 2]) {
+    const T* d = reinterpret_cast<const T*>(srow + 16) + lane * Tr<T>::V;
+    const uint4 raw = *reinterpret_cast<const uint4*>(d);
+    if constexpr (sizeof(T) == 8) {
+        v[0] = make_double2(__longlong_as_double(((long long)raw.y << 32) | raw.x),
+                            __longlong_as_double(((long long)raw.w << 32) | raw.z));
+    } else if constexpr (sizeof(T) == 4) {
+        v[0] = make_float2(__uint_as_float(raw.x), __uint_as_float(raw.y));
+        v[1] = make_float2(__uint_as_float(raw.z), __uint_as_float(raw.w));
+    } else {
+        const unsigned wd[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if constexpr (std::is_same<T, __half>::value) v[k] = __half22float2(*reinterpret_cast<const __half2*>(&wd[k]));
+            else v[k] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wd[k]));
+        }
+    }
+}
+
+// V values (as pairs) rounded to T, masked bitwise (wm: all-ones words keep,
+// zero words clear) and stored with one 16-byte store.
+template <class T>
+__device__ __forceinline__ void st_pairs(T* p, const typename Pair<typename Tr<T>::C>::t (&v)[Tr<T>::V / 2], uint4 wm) {
+    uint4 raw;
+    if constexpr (sizeof(T) == 8) {
+        const unsigned long long b0 = (unsigned long long)__double_as_longlong(v[0].x);
+        const unsigned long long b1 = (unsigned long long)__double_as_longlong(v[0].y);
+        raw = make_uint4((unsigned)b0, (unsigned)(b0 >> 32), (unsigned)b1, (unsigned)(b1 >> 32));
+    } else if constexpr (sizeof(T) == 4) {
+        raw = make_uint4(__float_as_uint(v[0].x), __float_as_uint(v[0].y), __float_as_uint(v[1].x),
+                         __float_as_uint(v[1].y));
+    } else {
+        unsigned w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if constexpr (std::is_same<T, __half>::value) {
+                const __half2 h = __float22half2_rn(v[k]);
+                w[k] = *reinterpret_cast<const unsigned*>(&h);
+            } else {
+                const __nv_bfloat162 h = __float22bfloat162_rn(v[k]);
+                w[k] = *reinterpret_cast<const unsigned*>(&h);
+            }
+        }
+        raw = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    raw.x &= wm.x; raw.y &= wm.y; raw.z &= wm.z; raw.w &= wm.w;
+    *reinterpret_cast<uint4*>(p) = raw;
+}
+
+// Word masks of a lane's 16-byte chunk starting at element x: elements at
+// x + i >= n (the pad column and beyond) are cleared.
+template <class T>
+__device__ __forceinline__ uint4 pad_mask(int x, int n) {
+    unsigned m[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if constexpr (sizeof(T) == 8) m[k] = x + k / 2 < n ? 0xffffffffu : 0u;
+        else if constexpr (sizeof(T) == 4) m[k] = x + k < n ? 0xffffffffu : 0u;
+        else m[k] = (x + 2 * k < n ? 0x0000ffffu : 0u) | (x + 2 * k + 1 < n ? 0xffff0000u : 0u);
+    }
+    return make_uint4(m[0], m[1], m[2], m[3]);
+}
+
 // Full weighting along x of one fine row: q[k] = (r[2k] + 2 r[2k+1] + r[2k+2]) / 4,
 // r[V] taken from the next lane.
 template <class C, int V, int VH>
@@ -134,92 +224,176 @@ __device__ __forceinline__ void fw_x(const C (&out)[V], int lane, C (&q)[VH]) {
     }
 }
 
+// ---------------------------------------------------------------- TMA / mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase with the given parity to complete, at most `tries`
+// polls (each poll may suspend the thread for a short hardware-chosen time).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigned tries) {
+    for (unsigned i = 0; i < tries; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* m, int x, int y, int z, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(m)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+constexpr unsigned kWaitTries = 1u << 20;  // first wait of a thread
+constexpr unsigned kDrainTries = 1u << 10; // every wait after one ran out
+
 // ---------------------------------------------------------------- 3D sweep
+// One CTA = TY warps; warp w owns fine row y0 + w of a 32*V-point x-chunk and
+// marches z from zb to ze.  Each plane of the march is one TMA box of the
+// swept vector (rows y0-1 .. y0+TY, x0-16B .. x0+512B+16B; the tensor map's
+// out-of-range fill supplies the zero boundary outside the padded array) and,
+// for Jacobi and residual, one box of g (rows y0 .. y0+TY-1), issued by one
+// thread into a 5-stage ring and completed on the stage's mbarrier.  The
+// lane's own row of planes z-1, z, z+1 stays in registers (three arrays that
+// swap roles each plane: the loop body is unrolled three times).
+// Launch bounds: 8 warps (4 CTAs per SM) for the sweeps, 9 warps (3 CTAs per
+// SM) for the residual-restriction tiles.
+template <int MODE>
+struct SweepLB {
+    static constexpr int kThreads = MODE == M_RESTRICT ? 288 : 256;
+    static constexpr int kMinBlocks = MODE == M_RESTRICT ? 3 : 4;
+};
 template <int MODE, class T, class TC>
-__global__ void __launch_bounds__(320) k_sweep3(const KArgs a) {
+__global__ void __launch_bounds__(SweepLB<MODE>::kThreads, SweepLB<MODE>::kMinBlocks)
+    k_sweep3(const KArgs a, const __grid_constant__ SweepMaps maps) {
     using C = typename Tr<T>::C;
+    using PR = Pair<C>;
+    using P2 = typename PR::t;
     constexpr int V = Tr<T>::V;
+    constexpr int NP = V / 2;
     constexpr int CW = 32 * V;
     constexpr int VH = V / 2 > 0 ? V / 2 : 1;
-    constexpr int S = 5;  // ring stages: planes z-1, z, z+1 in use, z+2 and z+3 in flight
+    constexpr int S = kSweepStages;  // planes z-1, z, z+1 in use, z+2 and z+3 in flight
     constexpr bool NEED_G = MODE == M_JACOBI || MODE == M_RESTRICT;
+    constexpr int UB = sizeof(T) == 2 ? 4 : 8;  // bytes of one tensor-map unit
     if (a.gate && a.st->phase != 0) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     const int TY = blockDim.y, lane = threadIdx.x, w = threadIdx.y;
-    const int stage_bytes = (TY + 2 + (NEED_G ? TY : 0)) * kRowBytes;
-    unsigned char* flush = smem_raw + S * stage_bytes;
+    const int CB = sweep3_cbytes(TY);
+    const int SB = sweep3_stage_bytes(TY, NEED_G);
+    unsigned char* flush = base + S * SB;
+    const int flush_bytes = MODE == M_RESTRICT ? TY * 32 * VH * (int)sizeof(C) : 0;
+    const unsigned bar0 = smem_u32(flush + (flush_bytes + 15) / 16 * 16);
     const int x0 = blockIdx.x * a.xstep, x = x0 + lane * V;
     const int y0 = blockIdx.y * a.ystep, y = y0 + w;
     const int zb = blockIdx.z * a.zstep;
     const int ze = min(zb + a.zlen, a.n);
     const bool lane_in = x < a.P, row_in = y < a.n;
-    const T* src = reinterpret_cast<const T*>(a.src);
-    const T* gp = reinterpret_cast<const T*>(a.g);
-    auto stage_of = [&](int p) { return (p - zb + 1) % S; };
-    auto crow = [&](int st, int r) { return smem_raw + st * stage_bytes + r * kRowBytes; };
-    auto grow = [&](int st, int r) { return smem_raw + st * stage_bytes + (TY + 2 + r) * kRowBytes; };
-    // Issues the copies of plane p (c rows y0-1 .. y0+TY, g rows y0 .. y0+TY-1)
-    // into its stage; planes past ze are not needed and only commit a group.
+    const bool leader = w == 0 && lane == 0;
+    const unsigned cbox = (unsigned)((TY + 2) * kSweepRowBytes), gbox = (unsigned)(TY * 512);
+    const int xc = (x0 * (int)sizeof(T) - 16) / UB, xg = x0 * (int)sizeof(T) / UB;  // 16-byte aligned starts
+    // plane p (zb-1 <= p <= ze) is the q-th of the march, q = p - zb + 1: stage q % S, phase (q / S) & 1
     auto issue = [&](int p) {
-        if (p <= ze) {
-            const int st = stage_of(p);
-            const long long po = (long long)p * a.S;
-            issue_row<T>(crow(st, w + 1), src + po + (long long)(y <= a.n ? y : 0) * a.P, lane, x0, a.P, y <= a.n);
-            if (w == 0) issue_row<T>(crow(st, 0), src + po + (long long)(y0 - 1) * a.P, lane, x0, a.P, true);
-            if (w == TY - 1) {
-                const int yh = y0 + TY;
-                issue_row<T>(crow(st, TY + 1), src + po + (long long)(yh <= a.n ? yh : 0) * a.P, lane, x0, a.P,
-                             yh <= a.n);
-            }
-            if (NEED_G && p >= zb && p < ze) {
-                const bool ok = row_in && lane_in;
-                const T* gr = ok ? gp + po + (long long)y * a.P + x : gp;
-                cp_async16(reinterpret_cast<T*>(grow(st, w) + 16) + lane * V, gr, ok);
-            }
-        }
-        cp_commit();
+        if (p > ze) return;
+        const int q = p - zb + 1, s = q % S;
+        const unsigned bar = bar0 + 8 * s;
+        const unsigned st = smem_u32(base + s * SB);
+        const bool with_g = NEED_G && p >= zb && p < ze;
+        mbar_expect_tx(bar, cbox + (with_g ? gbox : 0u));
+        tma_load_3d(st, &maps.src, xc, y0 - 1, p + 1, bar);
+        if (with_g) tma_load_3d(st + CB, &maps.g, xg, y0, p + 1, bar);
     };
-#pragma unroll
-    for (int k = 0; k < S - 1; ++k) issue(zb - 1 + k);
+    bool failed = false;
+    auto wait_plane = [&](int p) {
+        const int q = p - zb + 1;
+        if (!mbar_wait(bar0 + 8 * (q % S), (unsigned)(q / S) & 1u, failed ? kDrainTries : kWaitTries)) {
+            if (!failed) {
+                if (a.err) atomicExch(a.err, 1);
+                // stop the solve: every later gated kernel returns at once
+                if (a.st) *reinterpret_cast<volatile int*>(&const_cast<DevState*>(a.st)->phase) = 3;
+            }
+            failed = true;
+        }
+    };
+    if (leader) {
+        for (int s = 0; s < S; ++s) mbar_init(bar0 + 8 * s, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (leader)
+        for (int k = 0; k < S - 1; ++k) issue(zb - 1 + k);
 
     const C h2inv = (C)a.h2inv, om = (C)a.omega, twod = (C)6;
-    const C c1 = (C)1 - om, c2 = om / twod, c3 = om / (twod * h2inv);
+    const P2 c1 = PR::splat((C)1 - om), c2 = PR::splat(om / twod), c3 = PR::splat(om / (twod * h2inv));
+    const P2 k2 = PR::splat((C)2 - om);
+    const P2 h2v = PR::splat(h2inv), mh6 = PR::splat(-twod * h2inv);
+    // points x >= n of the chunk are stored as 0 (they are the boundary)
+    const uint4 wm = pad_mask<T>(x, a.n);
     C acc[VH];
 #pragma unroll
     for (int k = 0; k < VH; ++k) acc[k] = 0;
-    // the lane's own row of planes z-1, z, z+1 stays in registers (converted
-    // once); y-neighbours, x-halo and g come from the shared-memory ring
-    C cm[V], c0[V], cp[V];
-    cp_wait<S - 3>();  // planes zb-1 and zb have landed
-    __syncthreads();
-    lds_vec<T>(crow(stage_of(zb - 1), w + 1), lane, cm);
-    lds_vec<T>(crow(stage_of(zb), w + 1), lane, c0);
-    for (int z = zb; z < ze; ++z) {
-        cp_wait<S - 4>();  // planes up to z+1 have landed (this thread's copies)
-        __syncthreads();   // ... everyone's; and stage(z-2) is no longer read
-        issue(z + S - 2);
-        const int s0 = stage_of(z);
-        C ym[V], yp[V], g[V];
-        lds_vec<T>(crow(stage_of(z + 1), w + 1), lane, cp);
-        lds_vec<T>(crow(s0, w), lane, ym);
-        lds_vec<T>(crow(s0, w + 2), lane, yp);
-        const C left = lds_one<T>(crow(s0, w + 1), lane * V - 1);
-        const C right = lds_one<T>(crow(s0, w + 1), lane * V + V);
-        if (NEED_G) lds_vec<T>(grow(s0, w), lane, g);
-        C out[V];
+    T* dst_row = reinterpret_cast<T*>(a.dst) + (long long)(row_in ? y : 0) * a.P + (lane_in ? x : 0);
+    const bool do_store = row_in && lane_in;
+    const int own = (w + 1) * kSweepRowBytes;  // the warp's row within a c box
+
+    P2 pa[NP], pb[NP], pc[NP];
+    wait_plane(zb - 1);
+    wait_plane(zb);
+    lds_pairs<T>(base + own, lane, pa);
+    lds_pairs<T>(base + SB + own, lane, pb);
+    int so = SB;  // stage of plane z
+
+    // One plane: cm / c0 hold planes z-1 / z, cp receives plane z+1.
+    auto step = [&](int z, const P2 (&cm)[NP], const P2 (&c0)[NP], P2 (&cp)[NP]) {
+        __syncthreads();  // every warp is done with plane z-2's stage
+        if (leader) issue(z + S - 2);
+        wait_plane(z + 1);
+        int s1 = so + SB;
+        if (s1 >= S * SB) s1 -= S * SB;
+        const unsigned char* st0 = base + so;
+        P2 ym[NP], yp[NP], g[NP];
+        lds_pairs<T>(base + s1 + own, lane, cp);
+        lds_pairs<T>(st0 + own - kSweepRowBytes, lane, ym);
+        lds_pairs<T>(st0 + own + kSweepRowBytes, lane, yp);
+        const C left = lds_one<T>(st0 + own, lane * V - 1);
+        const C right = lds_one<T>(st0 + own, lane * V + V);
+        if (NEED_G) lds_pairs<T>(st0 + CB + w * 512 - 16, lane, g);
+        so = s1;
+        P2 out[NP];
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const C nb = (i ? c0[i - 1] : left) + (i < V - 1 ? c0[i + 1] : right) + cm[i] + cp[i] + ym[i] + yp[i];
-            const C v = point_value<MODE, C>(c0[i], nb, NEED_G ? g[i] : (C)0, c1, c2, c3, h2inv, twod, om);
-            out[i] = (x + i < a.n && row_in) ? v : (C)0;
+        for (int k = 0; k < NP; ++k) {
+            // x-neighbour sums: element 2k has 2k-1 and 2k+1, element 2k+1 has 2k and 2k+2
+            const C xl = k ? c0[k - 1].y : left;
+            const C xr = k < NP - 1 ? c0[k + 1].x : right;
+            const P2 xs = PR::mk(xl + c0[k].y, c0[k].x + xr);
+            const P2 nb = PR::add(PR::add(xs, PR::add(ym[k], yp[k])), PR::add(cm[k], cp[k]));
+            P2 v;
+            if (MODE == M_JACOBI) v = PR::fma(c2, nb, PR::fma(c1, c0[k], PR::mul(c3, g[k])));  // c + w D^-1 (g - A c)
+            else if (MODE == M_ZERO2) v = PR::mul(c3, PR::fma(c2, nb, PR::mul(k2, c0[k])));     // two sweeps from 0, c0 = g
+            else if (MODE == M_ZERO1) v = PR::mul(c3, c0[k]);                                    // one sweep from 0
+            else v = PR::fma(h2v, nb, PR::fma(mh6, c0[k], g[k]));                               // residual g - A c
+            out[k] = v;
         }
-#pragma unroll
-        for (int i = 0; i < V; ++i) { cm[i] = c0[i]; c0[i] = cp[i]; }
         if constexpr (MODE != M_RESTRICT) {
-            if (row_in && lane_in) stv(reinterpret_cast<T*>(a.dst) + offs<3>(x, y, z, a.P, a.S), out);
+            if (do_store) st_pairs<T>(dst_row + (long long)z * a.S, out, wm);
         } else {
+            C o1[V];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) { o1[2 * k] = out[k].x; o1[2 * k + 1] = out[k].y; }
             C q[VH];
-            fw_x<C, V, VH>(out, lane, q);
+            fw_x<C, V, VH>(o1, lane, q);
             const int t = z - zb;
             if (t & 1) {
 #pragma unroll
@@ -249,8 +423,15 @@ __global__ void __launch_bounds__(320) k_sweep3(const KArgs a) {
                 for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * q[k];
             }
         }
+    };
+    for (int z = zb; z < ze;) {
+        step(z, pa, pb, pc);
+        if (++z >= ze) break;
+        step(z, pb, pc, pa);
+        if (++z >= ze) break;
+        step(z, pc, pa, pb);
+        ++z;
     }
-    cp_wait<0>();
 }
 
 // ---------------------------------------------------------------- 2D sweep

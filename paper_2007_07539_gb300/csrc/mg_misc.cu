@@ -4,15 +4,23 @@
 // device layout.  Also the launch-geometry rule of the stencil march.
 #include <algorithm>
 #include <cmath>
+#include <cudaTypedefs.h>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "mg_march.cuh"
 
 namespace mgi {
 
-int launch_kernel_f64(int, int, int, int, const KArgs&, const MarchShape&, void*);
-int launch_kernel_f32(int, int, int, int, const KArgs&, const MarchShape&, void*);
-int launch_kernel_f16(int, int, int, int, const KArgs&, const MarchShape&, void*);
-int launch_kernel_bf16(int, int, int, int, const KArgs&, const MarchShape&, void*);
+int launch_kernel_f64(int, int, int, int, const KArgs&, const MarchShape&, const SweepMaps*, void*);
+int launch_kernel_f32(int, int, int, int, const KArgs&, const MarchShape&, const SweepMaps*, void*);
+int launch_kernel_f16(int, int, int, int, const KArgs&, const MarchShape&, const SweepMaps*, void*);
+int launch_kernel_bf16(int, int, int, int, const KArgs&, const MarchShape&, const SweepMaps*, void*);
+int occupancy_f64(int, int, int, int, int, size_t);
+int occupancy_f32(int, int, int, int, int, size_t);
+int occupancy_f16(int, int, int, int, int, size_t);
+int occupancy_bf16(int, int, int, int, int, size_t);
 
 size_t elem_size(int prec) {
     switch (prec) {
@@ -23,14 +31,72 @@ size_t elem_size(int prec) {
 }
 
 int launch_kernel(int dim, int kind, int mode, int prec, int prec_c, const KArgs& a, const MarchShape& s,
-                  void* stream) {
+                  const SweepMaps* maps, void* stream) {
     switch (prec) {
-        case MG_FP64: return launch_kernel_f64(dim, kind, mode, prec_c, a, s, stream);
-        case MG_FP32: return launch_kernel_f32(dim, kind, mode, prec_c, a, s, stream);
-        case MG_FP16: return launch_kernel_f16(dim, kind, mode, prec_c, a, s, stream);
-        case MG_BF16: return launch_kernel_bf16(dim, kind, mode, prec_c, a, s, stream);
+        case MG_FP64: return launch_kernel_f64(dim, kind, mode, prec_c, a, s, maps, stream);
+        case MG_FP32: return launch_kernel_f32(dim, kind, mode, prec_c, a, s, maps, stream);
+        case MG_FP16: return launch_kernel_f16(dim, kind, mode, prec_c, a, s, maps, stream);
+        case MG_BF16: return launch_kernel_bf16(dim, kind, mode, prec_c, a, s, maps, stream);
     }
     return (int)cudaErrorInvalidValue;
+}
+
+// Resident CTAs per SM of a kernel, from the runtime's occupancy calculator
+// (cached: the answer depends only on the arguments), else from shared memory.
+static int resident_ctas(int dim, int kind, int mode, int prec, int prec_c, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int, int, size_t>, int> cache;
+    const auto key = std::make_tuple(dim, kind, mode, prec, prec_c, threads, smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int nb = 0;
+    switch (prec) {
+        case MG_FP64: nb = occupancy_f64(dim, kind, mode, prec_c, threads, smem); break;
+        case MG_FP32: nb = occupancy_f32(dim, kind, mode, prec_c, threads, smem); break;
+        case MG_FP16: nb = occupancy_f16(dim, kind, mode, prec_c, threads, smem); break;
+        default: nb = occupancy_bf16(dim, kind, mode, prec_c, threads, smem); break;
+    }
+    if (nb <= 0) nb = std::max(1, std::min(4, (int)(220 * 1024 / (smem + 1024))));
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = nb;
+    return nb;
+}
+
+// ---------------------------------------------------------------- TMA descriptors
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+int make_sweep_map(CUtensorMap* m, int prec, const Geom& geo, const void* x0, int rows, bool halo) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return (int)cudaErrorNotSupported;
+    const size_t esz = elem_size(prec);
+    const size_t ub = esz == 2 ? 4 : 8;  // bytes per unit
+    const CUtensorMapDataType dt = esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64;
+    const cuuint64_t dims[3] = {(cuuint64_t)(geo.P * esz / ub), (cuuint64_t)geo.n + 1, (cuuint64_t)geo.n + 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)geo.P * esz, (cuuint64_t)geo.S * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)((halo ? kSweepRowBytes : 512) / ub), (cuuint32_t)rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    void* gaddr = const_cast<char*>(static_cast<const char*>(x0)) - geo.S * (long long)esz;  // plane -1
+    const CUresult r = enc(m, dt, 3, gaddr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : (int)cudaErrorInvalidValue;
 }
 
 static int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -92,8 +158,8 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
             s.ystep = 2 * TJ;
             s.gx = nchunks;
             s.gy = cdiv(nc, TJ);
-            s.smem = (size_t)5 * (s.ty + 2 + s.ty) * kRowBytes + (size_t)s.ty * 32 * VH * cs;
-            const int res = clampi((int)(220 * 1024 / (s.smem + 1024)), 1, 4);
+            s.smem = (size_t)sweep3_smem(s.ty, true, s.ty * 32 * VH * (int)cs);
+            const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem);
             int TK = tz_hint > 0 ? tz_hint : pick_march_len(nc, (long long)s.gx * s.gy, res, 2, 16, 2);
             TK = clampi(TK, 1, nc);
             s.zlen = 2 * TK + 1;
@@ -119,8 +185,8 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
         s.ystep = s.ty;
         s.gx = nchunks;
         s.gy = cdiv(n, s.ty);
-        s.smem = (size_t)5 * (s.ty + 2 + (need_g ? s.ty : 0)) * kRowBytes;
-        const int res = clampi((int)(220 * 1024 / (s.smem + 1024)), 1, 4);
+        s.smem = (size_t)sweep3_smem(s.ty, need_g, 0);
+        const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem);
         int zl = tz_hint > 0 ? tz_hint : pick_march_len(n, (long long)s.gx * s.gy, res, 4, 40, 1);
         zl = clampi(zl, 1, n);
         s.zlen = zl;
