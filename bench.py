@@ -161,6 +161,24 @@ def reference_arm(args):
     return 0
 
 
+def rank_max(x: float, world: int, device: str) -> float:
+    """Max of x over the ranks of the default process group (the slowest rank's time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds: float, world: int, device: str) -> float:
+    """Whole-job throughput: the units of all ranks (each rank solves its own
+    instance of the same size, no data-path collective) over the slowest
+    rank's time."""
+    return world * units_per_rank / rank_max(seconds, world, device)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,11 +214,7 @@ def main():
             dist.barrier()
 
     def allmax(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(x, world, "cuda")
 
     ndof = N**DIM
     b = I.random_rhs(DIM, N, SEED + rank)
@@ -242,7 +256,7 @@ def main():
     clocks = clk.stop()
     launches = resH["launches"] * args.steps
     t_dev = allmax(sum(secs))
-    value = world * ndof * args.steps / t_dev
+    value = whole_job_rate(ndof * args.steps, sum(secs), world, "cuda")
     uH = ud.cpu().numpy().copy()
 
     # all-FP64 MG on the same grid
@@ -257,7 +271,7 @@ def main():
     uh = torch.zeros_like(bh).pin_memory()
     run(hH, bh, uh, 1)
     secsE, _ = run(hH, bh, uh, args.steps)
-    e2e = world * ndof * args.steps / allmax(sum(secsE))
+    e2e = whole_job_rate(ndof * args.steps, sum(secsE), world, "cuda")
 
     # per-kernel device times of one profiled solve (events around every kernel)
     resP, ktimes = hH.profile_solve(bd, ud)

@@ -228,6 +228,7 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
             RArgs a{};
             a.n = g.n; a.P = g.P; a.S = g.S;
             a.u = h->u; a.b = (const double*)ptr_arg; a.r = h->r; a.partials = h->partials;
+            a.need_b = 1;
             a.h2inv = (double)(g.n + 1) * (double)(g.n + 1);
             int nb = 0;
             rc = launch_residual64(h->dim, a, &nb, s);

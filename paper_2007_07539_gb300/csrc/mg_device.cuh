@@ -25,6 +25,11 @@ template <> struct Tr<float> { static constexpr int V = 4; using C = float; };
 template <> struct Tr<__half> { static constexpr int V = 8; using C = float; };
 template <> struct Tr<__nv_bfloat16> { static constexpr int V = 8; using C = float; };
 
+// Host-computed coefficient i of a SweepCoef in the arithmetic type C.
+template <class C> __device__ __forceinline__ C coef(const SweepCoef& c, int i);
+template <> __device__ __forceinline__ float coef<float>(const SweepCoef& c, int i) { return c.f[i]; }
+template <> __device__ __forceinline__ double coef<double>(const SweepCoef& c, int i) { return c.d[i]; }
+
 // ---------------------------------------------------------------- 16-byte vector loads (RO path)
 __device__ __forceinline__ void ldv(const double* p, double (&v)[2]) {
     double2 t = __ldg(reinterpret_cast<const double2*>(p));
@@ -121,6 +126,15 @@ __device__ __forceinline__ float f64_to_f32_trunc(double d) {
     return __uint_as_float(sign | ((unsigned)e << 23) | m);
 }
 
+// Bit pattern -> FP64 through an opaque move: the integer construction below
+// stays integer work (the compiler does not turn it back into a conversion
+// instruction, which would run on the FP64 pipe).
+__device__ __forceinline__ double bits_to_f64(unsigned long long b) {
+    double d;
+    asm("mov.b64 %0, %1;" : "=d"(d) : "l"(b));
+    return d;
+}
+
 // Exact FP32 -> FP64 with integer instructions only (no F2F on the FP64
 // pipe): zero, normal, subnormal (renormalised), inf and NaN.
 __device__ __forceinline__ double f32_to_f64(float f) {
@@ -140,7 +154,7 @@ __device__ __forceinline__ double f32_to_f64(float f) {
         m = (m << sh) & 0x7FFFFFu;
         e64 = (unsigned long long)(897 - sh);
     }
-    return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)m << 29)));
+    return bits_to_f64(sign | (e64 << 52) | ((unsigned long long)m << 29));
 }
 
 // Exact s * 2^eoff as FP64 for |s| < 2^53 (result in the normal range), with
@@ -153,7 +167,7 @@ __device__ __forceinline__ double i64_to_f64(long long s, int eoff = 0) {
     unsigned long long m = (a << (lz - 11)) & 0x000FFFFFFFFFFFFFull;
     unsigned long long bits = ((unsigned long long)(1023 + e) << 52) | m |
                               (s < 0 ? 0x8000000000000000ull : 0ull);
-    return __longlong_as_double((long long)bits);
+    return bits_to_f64(bits);
 }
 
 // An FP16 value (held exactly in a float) is a multiple of 2^-24 with
@@ -186,17 +200,28 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
+// max of two keys as an explicit compare and select (an integer compare pair),
+// not a 64-bit max instruction
+__device__ __forceinline__ unsigned long long key_max(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("{\n .reg .pred p;\n setp.gt.u64 p, %1, %2;\n selp.b64 %0, %1, %2, p;\n}\n" : "=l"(r) : "l"(b), "l"(a));
+    return r;
+}
 __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long t = __shfl_xor_sync(kFull, v, o);
-        v = t > v ? t : v;
+        v = key_max(v, t);
     }
     return v;
 }
-// |d| as an order-preserving unsigned key (NaN keys exceed +inf).
+// |d| as an order-preserving unsigned key (NaN keys exceed +inf).  The sign
+// is cleared on the high word taken apart by an opaque move, so the compiler
+// does not turn the mask into an FP64 absolute value (an FP64-pipe add).
 __device__ __forceinline__ unsigned long long abs_key(double d) {
-    return (unsigned long long)__double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFull;
+    unsigned lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(d));
+    return ((unsigned long long)(hi & 0x7FFFFFFFu) << 32) | lo;
 }
 
 }  // namespace mgi

@@ -9,17 +9,18 @@ using KFn = void (*)(KArgs);
 using KFn3 = void (*)(KArgs, SweepMaps);  // 3D sweeps (TMA descriptors by value)
 
 template <class T>
-KFn3 pick_sweep3(int mode, int prec_c) {
+KFn3 pick_sweep3(int mode, int prec_c, int rpw) {
     switch (mode) {
-        case M_JACOBI: return &k_sweep3<M_JACOBI, T, T>;
-        case M_ZERO2: return &k_sweep3<M_ZERO2, T, T>;
-        case M_ZERO1: return &k_sweep3<M_ZERO1, T, T>;
+        case M_JACOBI: return rpw == 2 ? &k_sweep3<M_JACOBI, T, T, 2> : &k_sweep3<M_JACOBI, T, T, 1>;
+        case M_ZERO2: return rpw == 2 ? &k_sweep3<M_ZERO2, T, T, 2> : &k_sweep3<M_ZERO2, T, T, 1>;
+        case M_ZERO1: return rpw == 2 ? &k_sweep3<M_ZERO1, T, T, 2> : &k_sweep3<M_ZERO1, T, T, 1>;
         case M_RESTRICT:
+            if (rpw != 1) return nullptr;
             switch (prec_c) {
-                case MG_FP64: return &k_sweep3<M_RESTRICT, T, double>;
-                case MG_FP32: return &k_sweep3<M_RESTRICT, T, float>;
-                case MG_FP16: return &k_sweep3<M_RESTRICT, T, __half>;
-                case MG_BF16: return &k_sweep3<M_RESTRICT, T, __nv_bfloat16>;
+                case MG_FP64: return &k_sweep3<M_RESTRICT, T, double, 1>;
+                case MG_FP32: return &k_sweep3<M_RESTRICT, T, float, 1>;
+                case MG_FP16: return &k_sweep3<M_RESTRICT, T, __half, 1>;
+                case MG_BF16: return &k_sweep3<M_RESTRICT, T, __nv_bfloat16, 1>;
             }
     }
     return nullptr;
@@ -57,7 +58,7 @@ template <class T>
 int launch_kernel_t(int dim, int kind, int mode, int prec_c, const KArgs& a, const MarchShape& s,
                     const SweepMaps* maps, void* stream) {
     if (dim == 3 && kind == K_SWEEP) {
-        KFn3 f3 = pick_sweep3<T>(mode, prec_c);
+        KFn3 f3 = pick_sweep3<T>(mode, prec_c, s.rpw);
         if (!f3 || !maps) return (int)cudaErrorInvalidValue;
         if (s.smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(f3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
@@ -93,8 +94,8 @@ int occupancy_f(F f, int threads, size_t smem) {
     return nb;
 }
 template <class T>
-int occupancy_t(int dim, int kind, int mode, int prec_c, int threads, size_t smem) {
-    if (dim == 3 && kind == K_SWEEP) return occupancy_f(pick_sweep3<T>(mode, prec_c), threads, smem);
+int occupancy_t(int dim, int kind, int mode, int prec_c, int threads, size_t smem, int rpw) {
+    if (dim == 3 && kind == K_SWEEP) return occupancy_f(pick_sweep3<T>(mode, prec_c, rpw), threads, smem);
     return occupancy_f(dim == 3 ? pick<3, T>(kind, mode, prec_c) : pick<2, T>(kind, mode, prec_c), threads, smem);
 }
 

@@ -214,14 +214,16 @@ struct Gen {
         a.st = st; a.gate = gate;
         a.omega = h->p.omega;
         a.h2inv = (double)(f.n + 1) * (double)(f.n + 1);
+        a.cf = make_sweep_coef(h->dim, a.omega, a.h2inv);
         op.sh = kernel_shape(h->dim, kkind, mode, op.prec, f.n, f.P, 0);
         a.xstep = op.sh.xstep; a.ystep = op.sh.ystep; a.zstep = op.sh.zstep; a.zlen = op.sh.zlen;
         a.err = &h->st->kerr;
         if (h->dim == 3 && kkind == K_SWEEP) {  // TMA boxes: TY+2 rows of the swept vector, TY rows of g
             op.has_maps = true;
-            if (make_sweep_map(&op.maps.src, op.prec, f, src, op.sh.ty + 2, true) != 0) op.has_maps = false;
+            const int rows = op.sh.ty * op.sh.rpw;
+            if (make_sweep_map(&op.maps.src, op.prec, f, src, rows + 2, true) != 0) op.has_maps = false;
             const void* gm = g ? g : src;  // modes without g never read it
-            if (make_sweep_map(&op.maps.g, op.prec, f, gm, op.sh.ty, false) != 0) op.has_maps = false;
+            if (make_sweep_map(&op.maps.g, op.prec, f, gm, rows, false) != 0) op.has_maps = false;
         }
         return op;
     }
@@ -247,6 +249,7 @@ struct Gen {
         if (l > 0) { t.nc = h->lv[l - 1].geo.n; t.mnc = tail_magic(t.nc); }
         t.h2inv = (double)(f.n + 1) * (double)(f.n + 1);
         t.omega = h->p.omega;
+        t.cf = make_sweep_coef(h->dim, t.omega, t.h2inv);
         return t;
     }
     void tpush(const TailOp& t) { h->tail_host.push_back(t); }
@@ -702,6 +705,7 @@ static int launch_residual(mgi_hier& h, cudaStream_t s, double* r, int copy_u, i
     a.n = g.n; a.P = g.P; a.S = g.S;
     a.u = h.u; a.b = nullptr; a.r = r; a.partials = h.partials; a.st = h.st;
     a.use_st_uout = copy_u;
+    a.need_b = fin_kind == FIN_INIT;
     a.gate = gate;
     a.h2inv = (double)(g.n + 1) * (double)(g.n + 1);
     int nb = 0;

@@ -94,6 +94,22 @@ enum Mode : int {
 };
 
 // Arguments of the fine-level kernels (passed by value).
+// Sweep coefficients, computed once on the host in the arithmetic type (the
+// same IEEE operations the kernels would do): c1 = 1 - w, c2 = w/2d,
+// c3 = w/(2d h^-2), k2 = 2 - w, h^-2, -2d h^-2.
+struct SweepCoef {
+    float f[6];
+    double d[6];
+};
+inline SweepCoef make_sweep_coef(int dim, double omega, double h2inv) {
+    SweepCoef c;
+    const float om = (float)omega, h2 = (float)h2inv, twod = (float)(2 * dim);
+    c.f[0] = 1.0f - om; c.f[1] = om / twod; c.f[2] = om / (twod * h2); c.f[3] = 2.0f - om; c.f[4] = h2; c.f[5] = -twod * h2;
+    const double dom = omega, dh2 = h2inv, dtwod = (double)(2 * dim);
+    c.d[0] = 1.0 - dom; c.d[1] = dom / dtwod; c.d[2] = dom / (dtwod * dh2); c.d[3] = 2.0 - dom; c.d[4] = dh2; c.d[5] = -dtwod * dh2;
+    return c;
+}
+
 struct KArgs {
     int n, P;            // this level
     long long S;
@@ -115,6 +131,7 @@ struct KArgs {
     int xstep, ystep, zstep, zlen;  // tile strides / march length
     int gate;            // 1: return at once unless st->phase == 0
     int* err;            // set to 1 when a bounded copy wait runs out (3D sweeps)
+    SweepCoef cf;        // sweep coefficients of this level (host-computed)
 };
 
 // Arguments of the FP64 residual kernel r = b - A u.
@@ -130,10 +147,12 @@ struct RArgs {
     double h2inv;
     int gate;             // 0 always run; 1 only when st->phase == 1; 2 only when st->dirty
     int use_st_uout;      // 1: copy u to st->uout
+    int need_b;           // 1: also the partial sums of b^2 (initial residual, stage calls)
 };
 
 struct MarchShape {
     int gx, gy, gz, tx, ty;
+    int rpw;  // 3D sweeps: rows per warp (the CTA tile has ty * rpw rows)
     size_t smem;
     int xstep, ystep, zstep, zlen;
     int nblocks() const { return gx * gy * gz; }
@@ -154,9 +173,10 @@ struct alignas(64) SweepMaps {
 int make_sweep_map(CUtensorMap* m, int prec, const Geom& geo, const void* x0, int rows, bool halo);
 
 // Shared-memory plan of the 3D sweep, identical on host and device.
-// Ring of 5 stages, each [c box: (TY+2) rows x 544 B, 128-aligned][g box: TY
-// rows x 512 B], then the restriction's flush area, then 5 mbarriers.
-constexpr int kSweepStages = 5;
+// Ring of kSweepStages stages, each [c box: (R+2) rows x 544 B, 128-aligned]
+// [g box: R rows x 512 B] for a tile of R rows, then the restriction's flush
+// area, then one mbarrier per stage.
+constexpr int kSweepStages = 6;
 constexpr int kSweepRowBytes = 544;
 #ifdef __CUDACC__
 __host__ __device__

@@ -7,7 +7,7 @@ int launch_kernel_f16(int dim, int kind, int mode, int prec_c, const KArgs& a, c
                       const SweepMaps* maps, void* stream) {
     return launch_kernel_t<__half>(dim, kind, mode, prec_c, a, s, maps, stream);
 }
-int occupancy_f16(int dim, int kind, int mode, int prec_c, int threads, size_t smem) {
-    return occupancy_t<__half>(dim, kind, mode, prec_c, threads, smem);
+int occupancy_f16(int dim, int kind, int mode, int prec_c, int threads, size_t smem, int rpw) {
+    return occupancy_t<__half>(dim, kind, mode, prec_c, threads, smem, rpw);
 }
 }  // namespace mgi

@@ -114,9 +114,9 @@ __device__ __forceinline__ typename Tr<T>::C lds_one(const unsigned char* srow, 
 
 // ---------------------------------------------------------------- per-point values
 template <int MODE, class C>
-__device__ __forceinline__ C point_value(C c0, C nb, C g, C c1, C c2, C c3, C h2inv, C twod, C om) {
+__device__ __forceinline__ C point_value(C c0, C nb, C g, C c1, C c2, C c3, C h2inv, C twod, C k2) {
     if (MODE == M_JACOBI) return c1 * c0 + c2 * nb + c3 * g;            // c + w D^-1 (g - A c)
-    if (MODE == M_ZERO2) return c3 * (((C)2 - om) * c0 + c2 * nb);       // two sweeps from 0, c0 = g
+    if (MODE == M_ZERO2) return c3 * (k2 * c0 + c2 * nb);                 // two sweeps from 0, c0 = g
     if (MODE == M_ZERO1) return c3 * c0;                                   // one sweep from 0
     return g - h2inv * (twod * c0 - nb);                                   // residual g - A c
 }
@@ -133,6 +133,16 @@ template <> struct Pair<float> {
     static __device__ __forceinline__ t add(t a, t b) { return __fadd2_rn(a, b); }
     static __device__ __forceinline__ t mul(t a, t b) { return __fmul2_rn(a, b); }
     static __device__ __forceinline__ t fma(t a, t b, t c) { return __ffma2_rn(a, b, c); }
+};
+// The same operations as two scalar instructions (used where the pair
+// operands would need register moves: the residual-restriction kernel).
+template <class C> struct ScalarPair {
+    using t = typename Pair<C>::t;
+    static __device__ __forceinline__ t mk(C a, C b) { return Pair<C>::mk(a, b); }
+    static __device__ __forceinline__ t splat(C a) { return Pair<C>::mk(a, a); }
+    static __device__ __forceinline__ t add(t a, t b) { return Pair<C>::mk(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ t mul(t a, t b) { return Pair<C>::mk(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ t fma(t a, t b, t c) { return Pair<C>::mk(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
 };
 template <> struct Pair<double> {
     using t = double2;
@@ -264,45 +274,48 @@ constexpr unsigned kDrainTries = 1u << 10; // every wait after one ran out
 // swept vector (rows y0-1 .. y0+TY, x0-16B .. x0+512B+16B; the tensor map's
 // out-of-range fill supplies the zero boundary outside the padded array) and,
 // for Jacobi and residual, one box of g (rows y0 .. y0+TY-1), issued by one
-// thread into a 5-stage ring and completed on the stage's mbarrier.  The
+// thread into a 6-stage ring and completed on the stage's mbarrier.  The
 // lane's own row of planes z-1, z, z+1 stays in registers (three arrays that
 // swap roles each plane: the loop body is unrolled three times).
-// Launch bounds: 8 warps (4 CTAs per SM) for the sweeps, 9 warps (3 CTAs per
-// SM) for the residual-restriction tiles.
-template <int MODE>
+// Launch bounds: 8 warps.  One row per warp: 4 CTAs per SM (9 warps and 3
+// CTAs for the residual-restriction tiles); two rows per warp: 2 CTAs per SM.
+template <int MODE, int RPW>
 struct SweepLB {
     static constexpr int kThreads = MODE == M_RESTRICT ? 288 : 256;
-    static constexpr int kMinBlocks = MODE == M_RESTRICT ? 3 : 4;
+    static constexpr int kMinBlocks = RPW == 2 ? 2 : (MODE == M_RESTRICT ? 3 : 4);
 };
-template <int MODE, class T, class TC>
-__global__ void __launch_bounds__(SweepLB<MODE>::kThreads, SweepLB<MODE>::kMinBlocks)
+template <int MODE, class T, class TC, int RPW>
+__global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RPW>::kMinBlocks)
     k_sweep3(const KArgs a, const __grid_constant__ SweepMaps maps) {
+    static_assert(RPW == 1 || (RPW == 2 && MODE != M_RESTRICT), "two rows per warp: sweeps only");
     using C = typename Tr<T>::C;
-    using PR = Pair<C>;
+    using PR = typename std::conditional<MODE == M_RESTRICT, ScalarPair<C>, Pair<C>>::type;
     using P2 = typename PR::t;
     constexpr int V = Tr<T>::V;
     constexpr int NP = V / 2;
     constexpr int CW = 32 * V;
     constexpr int VH = V / 2 > 0 ? V / 2 : 1;
-    constexpr int S = kSweepStages;  // planes z-1, z, z+1 in use, z+2 and z+3 in flight
+    constexpr int S = kSweepStages;  // planes z-1, z, z+1 in use, z+2 .. z+S-2 in flight
     constexpr bool NEED_G = MODE == M_JACOBI || MODE == M_RESTRICT;
     constexpr int UB = sizeof(T) == 2 ? 4 : 8;  // bytes of one tensor-map unit
+    constexpr int RB = kSweepRowBytes;
     if (a.gate && a.st->phase != 0) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     const int TY = blockDim.y, lane = threadIdx.x, w = threadIdx.y;
-    const int CB = sweep3_cbytes(TY);
-    const int SB = sweep3_stage_bytes(TY, NEED_G);
+    const int R = RPW * TY;  // rows of the CTA tile; warp w owns rows w, w + TY, ...
+    const int CB = sweep3_cbytes(R);
+    const int SB = sweep3_stage_bytes(R, NEED_G);
     unsigned char* flush = base + S * SB;
     const int flush_bytes = MODE == M_RESTRICT ? TY * 32 * VH * (int)sizeof(C) : 0;
     const unsigned bar0 = smem_u32(flush + (flush_bytes + 15) / 16 * 16);
     const int x0 = blockIdx.x * a.xstep, x = x0 + lane * V;
-    const int y0 = blockIdx.y * a.ystep, y = y0 + w;
+    const int y0 = blockIdx.y * a.ystep;
     const int zb = blockIdx.z * a.zstep;
     const int ze = min(zb + a.zlen, a.n);
-    const bool lane_in = x < a.P, row_in = y < a.n;
+    const bool lane_in = x < a.P;
     const bool leader = w == 0 && lane == 0;
-    const unsigned cbox = (unsigned)((TY + 2) * kSweepRowBytes), gbox = (unsigned)(TY * 512);
+    const unsigned cbox = (unsigned)((R + 2) * RB), gbox = (unsigned)(R * 512);
     const int xc = (x0 * (int)sizeof(T) - 16) / UB, xg = x0 * (int)sizeof(T) / UB;  // 16-byte aligned starts
     // plane p (zb-1 <= p <= ze) is the q-th of the march, q = p - zb + 1: stage q % S, phase (q / S) & 1
     auto issue = [&](int p) {
@@ -315,10 +328,12 @@ __global__ void __launch_bounds__(SweepLB<MODE>::kThreads, SweepLB<MODE>::kMinBl
         tma_load_3d(st, &maps.src, xc, y0 - 1, p + 1, bar);
         if (with_g) tma_load_3d(st + CB, &maps.g, xg, y0, p + 1, bar);
     };
+    // the next plane to wait for: its stage and phase advance one plane at a time
+    int wst = 0;
+    unsigned wpar = 0;
     bool failed = false;
-    auto wait_plane = [&](int p) {
-        const int q = p - zb + 1;
-        if (!mbar_wait(bar0 + 8 * (q % S), (unsigned)(q / S) & 1u, failed ? kDrainTries : kWaitTries)) {
+    auto wait_next = [&]() {
+        if (!mbar_wait(bar0 + 8 * wst, wpar, failed ? kDrainTries : kWaitTries)) {
             if (!failed) {
                 if (a.err) atomicExch(a.err, 1);
                 // stop the solve: every later gated kernel returns at once
@@ -326,6 +341,7 @@ __global__ void __launch_bounds__(SweepLB<MODE>::kThreads, SweepLB<MODE>::kMinBl
             }
             failed = true;
         }
+        if (++wst == S) { wst = 0; wpar ^= 1u; }
     };
     if (leader) {
         for (int s = 0; s < S; ++s) mbar_init(bar0 + 8 * s, 1);
@@ -335,94 +351,108 @@ __global__ void __launch_bounds__(SweepLB<MODE>::kThreads, SweepLB<MODE>::kMinBl
     if (leader)
         for (int k = 0; k < S - 1; ++k) issue(zb - 1 + k);
 
-    const C h2inv = (C)a.h2inv, om = (C)a.omega, twod = (C)6;
-    const P2 c1 = PR::splat((C)1 - om), c2 = PR::splat(om / twod), c3 = PR::splat(om / (twod * h2inv));
-    const P2 k2 = PR::splat((C)2 - om);
-    const P2 h2v = PR::splat(h2inv), mh6 = PR::splat(-twod * h2inv);
+    const P2 c1 = PR::splat(coef<C>(a.cf, 0)), c2 = PR::splat(coef<C>(a.cf, 1)), c3 = PR::splat(coef<C>(a.cf, 2));
+    const P2 k2 = PR::splat(coef<C>(a.cf, 3));
+    const P2 h2v = PR::splat(coef<C>(a.cf, 4)), mh6 = PR::splat(coef<C>(a.cf, 5));
     // points x >= n of the chunk are stored as 0 (they are the boundary)
     const uint4 wm = pad_mask<T>(x, a.n);
     C acc[VH];
 #pragma unroll
     for (int k = 0; k < VH; ++k) acc[k] = 0;
-    T* dst_row = reinterpret_cast<T*>(a.dst) + (long long)(row_in ? y : 0) * a.P + (lane_in ? x : 0);
-    const bool do_store = row_in && lane_in;
-    const int own = (w + 1) * kSweepRowBytes;  // the warp's row within a c box
+    T* dst_row[RPW];
+    bool do_store[RPW];
+    int own[RPW];   // byte offset of the warp's row r within a c box
+    int gown[RPW];  // ... within a g box, minus the 16-byte halo lds_pairs skips
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+        const int y = y0 + w + r * TY;
+        do_store[r] = y < a.n && lane_in;
+        dst_row[r] = reinterpret_cast<T*>(a.dst) + (long long)(y < a.n ? y : 0) * a.P + (lane_in ? x : 0);
+        own[r] = (w + r * TY + 1) * RB;
+        gown[r] = CB + (w + r * TY) * 512 - 16;
+    }
 
-    P2 pa[NP], pb[NP], pc[NP];
-    wait_plane(zb - 1);
-    wait_plane(zb);
-    lds_pairs<T>(base + own, lane, pa);
-    lds_pairs<T>(base + SB + own, lane, pb);
+    P2 pa[RPW][NP], pb[RPW][NP], pc[RPW][NP];
+    wait_next();  // plane zb-1
+    wait_next();  // plane zb
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+        lds_pairs<T>(base + own[r], lane, pa[r]);
+        lds_pairs<T>(base + SB + own[r], lane, pb[r]);
+    }
     int so = SB;  // stage of plane z
 
     // One plane: cm / c0 hold planes z-1 / z, cp receives plane z+1.
-    auto step = [&](int z, const P2 (&cm)[NP], const P2 (&c0)[NP], P2 (&cp)[NP]) {
+    auto step = [&](int z, const P2 (&cm)[RPW][NP], const P2 (&c0)[RPW][NP], P2 (&cp)[RPW][NP]) {
         __syncthreads();  // every warp is done with plane z-2's stage
         if (leader) issue(z + S - 2);
-        wait_plane(z + 1);
+        wait_next();      // plane z+1
         int s1 = so + SB;
         if (s1 >= S * SB) s1 -= S * SB;
         const unsigned char* st0 = base + so;
-        P2 ym[NP], yp[NP], g[NP];
-        lds_pairs<T>(base + s1 + own, lane, cp);
-        lds_pairs<T>(st0 + own - kSweepRowBytes, lane, ym);
-        lds_pairs<T>(st0 + own + kSweepRowBytes, lane, yp);
-        const C left = lds_one<T>(st0 + own, lane * V - 1);
-        const C right = lds_one<T>(st0 + own, lane * V + V);
-        if (NEED_G) lds_pairs<T>(st0 + CB + w * 512 - 16, lane, g);
-        so = s1;
-        P2 out[NP];
 #pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            // x-neighbour sums: element 2k has 2k-1 and 2k+1, element 2k+1 has 2k and 2k+2
-            const C xl = k ? c0[k - 1].y : left;
-            const C xr = k < NP - 1 ? c0[k + 1].x : right;
-            const P2 xs = PR::mk(xl + c0[k].y, c0[k].x + xr);
-            const P2 nb = PR::add(PR::add(xs, PR::add(ym[k], yp[k])), PR::add(cm[k], cp[k]));
-            P2 v;
-            if (MODE == M_JACOBI) v = PR::fma(c2, nb, PR::fma(c1, c0[k], PR::mul(c3, g[k])));  // c + w D^-1 (g - A c)
-            else if (MODE == M_ZERO2) v = PR::mul(c3, PR::fma(c2, nb, PR::mul(k2, c0[k])));     // two sweeps from 0, c0 = g
-            else if (MODE == M_ZERO1) v = PR::mul(c3, c0[k]);                                    // one sweep from 0
-            else v = PR::fma(h2v, nb, PR::fma(mh6, c0[k], g[k]));                               // residual g - A c
-            out[k] = v;
-        }
-        if constexpr (MODE != M_RESTRICT) {
-            if (do_store) st_pairs<T>(dst_row + (long long)z * a.S, out, wm);
-        } else {
-            C o1[V];
+        for (int r = 0; r < RPW; ++r) {
+            P2 ym[NP], yp[NP], g[NP];
+            lds_pairs<T>(base + s1 + own[r], lane, cp[r]);
+            lds_pairs<T>(st0 + own[r] - RB, lane, ym);
+            lds_pairs<T>(st0 + own[r] + RB, lane, yp);
+            const C left = lds_one<T>(st0 + own[r], lane * V - 1);
+            const C right = lds_one<T>(st0 + own[r], lane * V + V);
+            if (NEED_G) lds_pairs<T>(st0 + gown[r], lane, g);
+            P2 out[NP];
 #pragma unroll
-            for (int k = 0; k < NP; ++k) { o1[2 * k] = out[k].x; o1[2 * k + 1] = out[k].y; }
-            C q[VH];
-            fw_x<C, V, VH>(o1, lane, q);
-            const int t = z - zb;
-            if (t & 1) {
-#pragma unroll
-                for (int k = 0; k < VH; ++k) acc[k] += (C)0.5 * q[k];
+            for (int k = 0; k < NP; ++k) {
+                // x-neighbour sums: element 2k has 2k-1 and 2k+1, element 2k+1 has 2k and 2k+2
+                const C xl = k ? c0[r][k - 1].y : left;
+                const C xr = k < NP - 1 ? c0[r][k + 1].x : right;
+                const P2 xs = PR::mk(xl + c0[r][k].y, c0[r][k].x + xr);
+                const P2 nb = PR::add(PR::add(xs, PR::add(ym[k], yp[k])), PR::add(cm[r][k], cp[r][k]));
+                P2 v;
+                if (MODE == M_JACOBI) v = PR::fma(c2, nb, PR::fma(c1, c0[r][k], PR::mul(c3, g[k])));  // c + w D^-1 (g - A c)
+                else if (MODE == M_ZERO2) v = PR::mul(c3, PR::fma(c2, nb, PR::mul(k2, c0[r][k])));     // two sweeps from 0, c0 = g
+                else if (MODE == M_ZERO1) v = PR::mul(c3, c0[r][k]);                                    // one sweep from 0
+                else v = PR::fma(h2v, nb, PR::fma(mh6, c0[r][k], g[k]));                               // residual g - A c
+                out[k] = v;
+            }
+            if constexpr (MODE != M_RESTRICT) {
+                if (do_store[r]) st_pairs<T>(dst_row[r] + (long long)z * a.S, out, wm);
             } else {
-                if (t >= 2) {  // fine planes 2K, 2K+1, 2K+2 done: write coarse plane K
-                    C* fl = reinterpret_cast<C*>(flush) + (w * 32 + lane) * VH;
+                C o1[V];
 #pragma unroll
-                    for (int k = 0; k < VH; ++k) fl[k] = acc[k] + (C)0.25 * q[k];
-                    __syncthreads();
-                    if ((w & 1) == 0 && w + 2 < TY) {
-                        const int J = (y0 >> 1) + (w >> 1), K = (zb >> 1) + (t >> 1) - 1;
-                        const C* f0 = reinterpret_cast<const C*>(flush) + (w * 32 + lane) * VH;
-                        const C* f1 = f0 + 32 * VH;
-                        const C* f2 = f1 + 32 * VH;
-                        const int I0 = (x0 + lane * V) >> 1;
-                        if (lane_in && J < a.nc && K < a.nc && (lane < 31 || x0 + CW >= a.P)) {
-                            TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
+                for (int k = 0; k < NP; ++k) { o1[2 * k] = out[k].x; o1[2 * k + 1] = out[k].y; }
+                C q[VH];
+                fw_x<C, V, VH>(o1, lane, q);
+                const int t = z - zb;
+                if (t & 1) {
 #pragma unroll
-                            for (int k = 0; k < VH; ++k)
-                                if (I0 + k < a.nc)
-                                    st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
+                    for (int k = 0; k < VH; ++k) acc[k] += (C)0.5 * q[k];
+                } else {
+                    if (t >= 2) {  // fine planes 2K, 2K+1, 2K+2 done: write coarse plane K
+                        C* fl = reinterpret_cast<C*>(flush) + (w * 32 + lane) * VH;
+#pragma unroll
+                        for (int k = 0; k < VH; ++k) fl[k] = acc[k] + (C)0.25 * q[k];
+                        __syncthreads();
+                        if ((w & 1) == 0 && w + 2 < TY) {
+                            const int J = (y0 >> 1) + (w >> 1), K = (zb >> 1) + (t >> 1) - 1;
+                            const C* f0 = reinterpret_cast<const C*>(flush) + (w * 32 + lane) * VH;
+                            const C* f1 = f0 + 32 * VH;
+                            const C* f2 = f1 + 32 * VH;
+                            const int I0 = (x0 + lane * V) >> 1;
+                            if (lane_in && J < a.nc && K < a.nc && (lane < 31 || x0 + CW >= a.P)) {
+                                TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
+#pragma unroll
+                                for (int k = 0; k < VH; ++k)
+                                    if (I0 + k < a.nc)
+                                        st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
+                            }
                         }
                     }
-                }
 #pragma unroll
-                for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * q[k];
+                    for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * q[k];
+                }
             }
         }
+        so = s1;
     };
     for (int z = zb; z < ze;) {
         step(z, pa, pb, pc);
@@ -470,8 +500,8 @@ __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
     };
 #pragma unroll
     for (int k = 0; k < S - 1; ++k) issue(yb - 1 + k);
-    const C h2inv = (C)a.h2inv, om = (C)a.omega, twod = (C)4;
-    const C c1 = (C)1 - om, c2 = om / twod, c3 = om / (twod * h2inv);
+    const C c1 = coef<C>(a.cf, 0), c2 = coef<C>(a.cf, 1), c3 = coef<C>(a.cf, 2), k2 = coef<C>(a.cf, 3);
+    const C h2inv = coef<C>(a.cf, 4), twod = (C)4;
     C acc[VH];
 #pragma unroll
     for (int k = 0; k < VH; ++k) acc[k] = 0;
@@ -495,7 +525,7 @@ __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const C nb = (i ? c0[i - 1] : left) + (i < V - 1 ? c0[i + 1] : right) + cm[i] + cp[i];
-            const C v = point_value<MODE, C>(c0[i], nb, NEED_G ? g[i] : (C)0, c1, c2, c3, h2inv, twod, om);
+            const C v = point_value<MODE, C>(c0[i], nb, NEED_G ? g[i] : (C)0, c1, c2, c3, h2inv, twod, k2);
             out[i] = (x + i < a.n) ? v : (C)0;
         }
 #pragma unroll
@@ -646,25 +676,28 @@ template <> struct ExactStencil<double> {
 __device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
 
-// Sum of squares as an FP32 double-float (hi + lo) without FP64 instructions.
-// Each r is first scaled by 2^-E (E: exponent of the previous ||r||_inf, an
-// exact change of the exponent field; entries below 2^-70 of that scale are
-// dropped, their squares being < 2^-140 of the sum) and split from its bit
-// pattern into hi (top 24 significand bits, exact) and lo (the next 29 bits,
-// rounded to 24).  r^2 ~ hi^2 + 2 hi lo, hi^2 exact by FMA TwoProd, summed
-// with TwoSum: relative error ~1e-14.  The result is multiplied by 2^(2E).
+// Sum of squares as an FP32 double-float (hi + lo) without FP64-pipe
+// instructions (no FP64 arithmetic, no int/float conversion).  Each r is
+// first scaled by 2^-E (E: exponent of the previous ||r||_inf, an exact change
+// of the exponent field; entries below 2^-70 of that scale are dropped, their
+// squares being < 2^-140 of the sum) and split from its bit pattern into hi
+// (top 24 significand bits, exact) and lo (the next 23 bits, truncated; the
+// last 6 bits, < 2^-47 of r, are dropped).  r^2 ~ hi^2 + 2 hi lo, hi^2 exact
+// by FMA TwoProd, summed with TwoSum: relative error ~1e-14.  The result is
+// multiplied by 2^(2E).
 struct SqAcc {
     float hi = 0.f, lo = 0.f;
     __device__ __forceinline__ void add(double r, int E) {
         const unsigned long long b = (unsigned long long)__double_as_longlong(r);
         const int e = (int)((b >> 52) & 0x7FF) - E;  // biased exponent of r * 2^-E
         if (e < 1023 - 70 || e > 1023 + 100) return;  // (the upper bound never binds: r <= ~100 * 2^E)
-        const unsigned long long bs = (b & 0x800FFFFFFFFFFFFFull) | ((unsigned long long)e << 52);
-        const float h = f64_to_f32_trunc(__longlong_as_double((long long)bs));
-        const unsigned mlo = (unsigned)(b & 0x1FFFFFFFull);
-        const float scale = __int_as_float((e - 1075 + 127) << 23);  // 2^(e - 1075), normal here
-        float l = __fmul_rn(__uint2float_rn(mlo), scale);
-        if (b >> 63) l = -l;
+        const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+        // r 2^-E truncated to 24 significand bits: FP32 exponent field e - 1023 + 127
+        const float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu));
+        // significand bits 28..6 as an exact FP32 integer (magic 2^23), times
+        // sign * 2^(e - 1069), the weight of bit 6
+        const float m = __fsub_rn(__uint_as_float(0x4B000000u | ((unsigned)(b >> 6) & 0x7FFFFFu)), 8388608.0f);
+        const float l = __fmul_rn(m, __uint_as_float(sign | ((unsigned)(e - 1069 + 127) << 23)));
         const float p = __fmul_rn(h, h);
         const float pe = __fmaf_rn(h, h, -p);
         const float t = __fmaf_rn(2.0f * h, l, pe);
@@ -813,7 +846,7 @@ __global__ void __launch_bounds__(256) k_update(const KArgs a) {
                 uu[i] = fma(alpha, to_f64(c0[i]), uu[i]);
                 sq.add(r, E);
                 const unsigned long long k = abs_key(r);
-                nmax = k > nmax ? k : nmax;
+                nmax = key_max(nmax, k);
             }
         }
         *reinterpret_cast<double2*>(up) = make_double2(uu[0], uu[1]);

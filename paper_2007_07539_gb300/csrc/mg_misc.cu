@@ -17,10 +17,10 @@ int launch_kernel_f64(int, int, int, int, const KArgs&, const MarchShape&, const
 int launch_kernel_f32(int, int, int, int, const KArgs&, const MarchShape&, const SweepMaps*, void*);
 int launch_kernel_f16(int, int, int, int, const KArgs&, const MarchShape&, const SweepMaps*, void*);
 int launch_kernel_bf16(int, int, int, int, const KArgs&, const MarchShape&, const SweepMaps*, void*);
-int occupancy_f64(int, int, int, int, int, size_t);
-int occupancy_f32(int, int, int, int, int, size_t);
-int occupancy_f16(int, int, int, int, int, size_t);
-int occupancy_bf16(int, int, int, int, int, size_t);
+int occupancy_f64(int, int, int, int, int, size_t, int);
+int occupancy_f32(int, int, int, int, int, size_t, int);
+int occupancy_f16(int, int, int, int, int, size_t, int);
+int occupancy_bf16(int, int, int, int, int, size_t, int);
 
 size_t elem_size(int prec) {
     switch (prec) {
@@ -43,10 +43,10 @@ int launch_kernel(int dim, int kind, int mode, int prec, int prec_c, const KArgs
 
 // Resident CTAs per SM of a kernel, from the runtime's occupancy calculator
 // (cached: the answer depends only on the arguments), else from shared memory.
-static int resident_ctas(int dim, int kind, int mode, int prec, int prec_c, int threads, size_t smem) {
+static int resident_ctas(int dim, int kind, int mode, int prec, int prec_c, int threads, size_t smem, int rpw = 1) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int, int, size_t>, int> cache;
-    const auto key = std::make_tuple(dim, kind, mode, prec, prec_c, threads, smem);
+    static std::map<std::tuple<int, int, int, int, int, int, size_t, int>, int> cache;
+    const auto key = std::make_tuple(dim, kind, mode, prec, prec_c, threads, smem, rpw);
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
@@ -54,10 +54,10 @@ static int resident_ctas(int dim, int kind, int mode, int prec, int prec_c, int 
     }
     int nb = 0;
     switch (prec) {
-        case MG_FP64: nb = occupancy_f64(dim, kind, mode, prec_c, threads, smem); break;
-        case MG_FP32: nb = occupancy_f32(dim, kind, mode, prec_c, threads, smem); break;
-        case MG_FP16: nb = occupancy_f16(dim, kind, mode, prec_c, threads, smem); break;
-        default: nb = occupancy_bf16(dim, kind, mode, prec_c, threads, smem); break;
+        case MG_FP64: nb = occupancy_f64(dim, kind, mode, prec_c, threads, smem, rpw); break;
+        case MG_FP32: nb = occupancy_f32(dim, kind, mode, prec_c, threads, smem, rpw); break;
+        case MG_FP16: nb = occupancy_f16(dim, kind, mode, prec_c, threads, smem, rpw); break;
+        default: nb = occupancy_bf16(dim, kind, mode, prec_c, threads, smem, rpw); break;
     }
     if (nb <= 0) nb = std::max(1, std::min(4, (int)(220 * 1024 / (smem + 1024))));
     std::lock_guard<std::mutex> lk(mu);
@@ -121,9 +121,10 @@ static int pick_march_len(int units, long long tiles, int resident, int lo, int 
     return bestL;
 }
 
-// Launch geometry.  Sweeps (3D): CTAs of 8 warps = 8 rows of one 512-byte
-// x-chunk, marching over z through a 5-stage cp.async ring; restriction: 2TJ+1
-// fine rows per CTA (TJ coarse rows) and 2TK+1 fine planes per range, one fine
+// Launch geometry.  Sweeps (3D): CTAs of 8 warps over 8 rows (16 rows, two
+// per warp, once n >= 16) of one 512-byte x-chunk, marching over z through a
+// 6-stage TMA ring; restriction: 2TJ+1 fine rows per CTA (TJ coarse rows) and
+// 2TK+1 fine planes per range, one fine
 // row / plane shared with the neighbouring tile, x-chunks overlapping by one
 // vector.  2D: one x-chunk per warp, 4 warps per CTA, marching over rows.
 // Streaming kernels (update, scale-cast, prolongation): 256 threads, one
@@ -158,6 +159,7 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
             s.ystep = 2 * TJ;
             s.gx = nchunks;
             s.gy = cdiv(nc, TJ);
+            s.rpw = 1;
             s.smem = (size_t)sweep3_smem(s.ty, true, s.ty * 32 * VH * (int)cs);
             const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem);
             int TK = tz_hint > 0 ? tz_hint : pick_march_len(nc, (long long)s.gx * s.gy, res, 2, 16, 2);
@@ -181,12 +183,16 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
     s.xstep = CW;
     const int nchunks = cdiv(P, CW);
     if (dim == 3) {
+        // two rows per warp (16-row tiles) once the level has 16 rows: the
+        // per-plane work of a warp (waits, barrier, copy issue, addressing)
+        // is shared by twice the points
         s.ty = clampi(n, 1, 8);
-        s.ystep = s.ty;
+        s.rpw = n >= 16 ? 2 : 1;
+        s.ystep = s.ty * s.rpw;
         s.gx = nchunks;
-        s.gy = cdiv(n, s.ty);
-        s.smem = (size_t)sweep3_smem(s.ty, need_g, 0);
-        const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem);
+        s.gy = cdiv(n, s.ystep);
+        s.smem = (size_t)sweep3_smem(s.ystep, need_g, 0);
+        const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem, s.rpw);
         int zl = tz_hint > 0 ? tz_hint : pick_march_len(n, (long long)s.gx * s.gy, res, 4, 40, 1);
         zl = clampi(zl, 1, n);
         s.zlen = zl;
@@ -257,8 +263,8 @@ int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void*
 // ---------------------------------------------------------------- FP64 residual (IR step 1)
 // r = b - A u in FP64 with per-CTA partials {sum r^2, max |r|, sum b^2, 0};
 // optionally copies u to the caller's contiguous array.  One thread per point.
-template <int DIM>
-__global__ void __launch_bounds__(256) k_residual64(RArgs a, int init_copy) {
+template <int DIM, bool init_copy>
+__global__ void __launch_bounds__(256) k_residual64(RArgs a) {
     if (a.gate == 1 && a.st->phase != 1) return;
     if (a.gate == 2 && !a.st->dirty) return;
     const double* bsrc = a.b ? a.b : a.st->b;
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(256) k_residual64(RArgs a, int init_copy) {
         const long long o = offs<DIM>(i, j, k, a.P, a.S);
         const double bv = __ldg(bsrc + oc);
         double r;
-        if (init_copy) {
+        if constexpr (init_copy) {
             r = bv;  // u = 0: r = b
         } else {
             const double* u = a.u + o;
@@ -287,11 +293,14 @@ __global__ void __launch_bounds__(256) k_residual64(RArgs a, int init_copy) {
             if (uout) uout[oc] = uc;
         }
         if (a.r) a.r[o] = r;
-        sr = fma(r, r, sr);
-        sb = fma(bv, bv, sb);
+        // FP64 instructions are scarce on this GPU: b^2 only when asked, and
+        // once for r = b
+        if (!init_copy) sr = fma(r, r, sr);
+        if (init_copy || a.need_b) sb = fma(bv, bv, sb);
         const unsigned long long key = abs_key(r);
-        mr = key > mr ? key : mr;
+        mr = key_max(mr, key);
     }
+    if (init_copy) sr = sb;
     __shared__ double s1[32], s2[32];
     __shared__ unsigned long long s3[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -329,8 +338,8 @@ int launch_residual64(int dim, const RArgs& a, int* nblocks, void* stream) {
     dim3 grid, block;
     residual_grid(dim, a.n, grid, block);
     if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
-    if (dim == 3) k_residual64<3><<<grid, block, 0, (cudaStream_t)stream>>>(a, 0);
-    else k_residual64<2><<<grid, block, 0, (cudaStream_t)stream>>>(a, 0);
+    if (dim == 3) k_residual64<3, false><<<grid, block, 0, (cudaStream_t)stream>>>(a);
+    else k_residual64<2, false><<<grid, block, 0, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
 }
 
@@ -341,8 +350,8 @@ int launch_init_rb(int dim, const Geom& geo, const double* b, double* r, double*
     dim3 grid, block;
     residual_grid(dim, a.n, grid, block);
     if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
-    if (dim == 3) k_residual64<3><<<grid, block, 0, (cudaStream_t)stream>>>(a, 1);
-    else k_residual64<2><<<grid, block, 0, (cudaStream_t)stream>>>(a, 1);
+    if (dim == 3) k_residual64<3, true><<<grid, block, 0, (cudaStream_t)stream>>>(a);
+    else k_residual64<2, true><<<grid, block, 0, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
 }
 

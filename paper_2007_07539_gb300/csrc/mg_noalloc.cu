@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kThreads) k_resnorm_partials(int n, double h2i
         sr = fma(r, r, sr);
         sb = fma(bv, bv, sb);
         const unsigned long long key = mgi::abs_key(r);
-        mr = key > mr ? key : mr;
+        mr = mgi::key_max(mr, key);
     }
     __shared__ double s1[kThreads / 32], s2[kThreads / 32];
     __shared__ unsigned long long s3[kThreads / 32];

@@ -73,8 +73,7 @@ __device__ void t_sweep(const TailOp& op, unsigned char* sm) {
     using C = typename Tr<T>::C;
     const int n = op.n;
     const int N = DIM == 3 ? n * n * n : n * n;
-    const C h2inv = (C)op.h2inv, om = (C)op.omega, twod = (C)(2 * DIM);
-    const C c1 = (C)1 - om, c2 = om / twod, c3 = om / (twod * h2inv);
+    const C c1 = coef<C>(op.cf, 0), c2 = coef<C>(op.cf, 1), c3 = coef<C>(op.cf, 2), k2 = coef<C>(op.cf, 3);
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
         int i, j, k;
         decode<DIM>(p, n, op.mn, i, j, k);
@@ -82,7 +81,7 @@ __device__ void t_sweep(const TailOp& op, unsigned char* sm) {
         const C nb = nbsum<DIM, T>(sm, op.src, p, n, i, j, k);
         C v;
         if (op.mode == M_JACOBI) v = c1 * c0 + c2 * nb + c3 * sget<T>(sm, op.g, p);
-        else if (op.mode == M_ZERO2) v = c3 * (((C)2 - om) * c0 + c2 * nb);
+        else if (op.mode == M_ZERO2) v = c3 * (k2 * c0 + c2 * nb);
         else v = c3 * c0;
         sput<T>(sm, op.dst, p, v);
     }
@@ -94,7 +93,7 @@ __device__ void t_resid(const TailOp& op, unsigned char* sm) {
     using C = typename Tr<T>::C;
     const int n = op.n;
     const int N = DIM == 3 ? n * n * n : n * n;
-    const C h2inv = (C)op.h2inv, twod = (C)(2 * DIM);
+    const C h2inv = coef<C>(op.cf, 4), twod = (C)(2 * DIM);
     C* r = reinterpret_cast<C*>(sm + op.dst);
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
         int i, j, k;

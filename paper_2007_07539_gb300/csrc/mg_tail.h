@@ -36,6 +36,7 @@ struct TailOp {
     void* gptr;
     double h2inv;
     double omega;
+    SweepCoef cf;  // host-computed sweep coefficients of level n
 };
 static_assert(sizeof(TailOp) % 8 == 0, "TailOp is copied as 8-byte words");
 constexpr int kTailOpWords = (int)(sizeof(TailOp) / 8);
