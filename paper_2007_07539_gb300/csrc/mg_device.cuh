@@ -157,6 +157,16 @@ __device__ __forceinline__ double f32_to_f64(float f) {
     return bits_to_f64(sign | (e64 << 52) | ((unsigned long long)m << 29));
 }
 
+// Exact FP64 of a float holding an FP16 value (an FP32 normal, zero, inf or
+// NaN: FP16 subnormals are FP32 normals), with integer instructions only.
+__device__ __forceinline__ double half_to_f64(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long e64 = e == 0xFFu ? 0x7FFull : (e ? e + 896ull : 0ull);
+    return bits_to_f64(((unsigned long long)(b & 0x80000000u) << 32) | (e64 << 52) |
+                       ((unsigned long long)(b & 0x7FFFFFu) << 29));
+}
+
 // Exact s * 2^eoff as FP64 for |s| < 2^53 (result in the normal range), with
 // integer instructions only.
 __device__ __forceinline__ double i64_to_f64(long long s, int eoff = 0) {

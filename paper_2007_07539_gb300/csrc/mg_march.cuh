@@ -828,6 +828,39 @@ __global__ void __launch_bounds__(256) k_update(const KArgs a) {
         const C left = ld1(c - 1), right = ld1(c + Q);
         double uu[Q] = {u01.x, u01.y, u23.x, u23.y};
         double rr[Q] = {r01.x, r01.y, r23.x, r23.y};
+        if constexpr (DIM == 3 && std::is_same<T, __half>::value) {
+            // FP16 corrections: every loaded value is split once (22 splits
+            // for 4 points), the exact stencil sum S = 6 c0 - sum of neighbours
+            // is then an integer sum of the hi parts and an exact FP32 sum of
+            // the lo parts (|lo| <= 2^17, six of them < 2^21)
+            HSplit h0[Q + 2], hy[Q], hz[Q];
+            h0[0] = h_split(left);
+            h0[Q + 1] = h_split(right);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                h0[i + 1] = h_split(c0[i]);
+                const HSplit a1 = h_split(ym[i]), a2 = h_split(yp[i]), a3 = h_split(zm[i]), a4 = h_split(zp[i]);
+                hy[i].hi = a1.hi + a2.hi + a3.hi + a4.hi;
+                hy[i].lo = __fadd_rn(__fadd_rn(a1.lo, a2.lo), __fadd_rn(a3.lo, a4.lo));
+            }
+            const int active = min(Q, a.n - x);  // points of the vector inside the row
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (i < active) {
+                    const HSplit& m = h0[i + 1];
+                    const int H = 6 * m.hi - (h0[i].hi + h0[i + 2].hi) - hy[i].hi;
+                    const float L = __fmaf_rn(6.0f, m.lo, -__fadd_rn(__fadd_rn(h0[i].lo, h0[i + 2].lo), hy[i].lo));
+                    const float MAGIC = 12582912.0f;
+                    const int Li = __float_as_int(__fadd_rn(L, MAGIC)) - __float_as_int(MAGIC);
+                    const double sx = i64_to_f64(((long long)H << 18) + (long long)Li, -24);
+                    const double r = fma(-beta, sx, rr[i]);
+                    rr[i] = r;
+                    uu[i] = fma(alpha, half_to_f64(c0[i]), uu[i]);
+                    sq.add(r, E);
+                    nmax = key_max(nmax, abs_key(r));
+                }
+            }
+        } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             if (x + i < a.n) {
@@ -849,6 +882,7 @@ __global__ void __launch_bounds__(256) k_update(const KArgs a) {
                 nmax = key_max(nmax, k);
             }
         }
+        }
         *reinterpret_cast<double2*>(up) = make_double2(uu[0], uu[1]);
         *reinterpret_cast<double2*>(up + 2) = make_double2(uu[2], uu[3]);
         *reinterpret_cast<double2*>(rp) = make_double2(rr[0], rr[1]);
@@ -858,59 +892,75 @@ __global__ void __launch_bounds__(256) k_update(const KArgs a) {
 }
 
 // ---------------------------------------------------------------- prolongation (Alg. 1 step 4)
-// c_fine += P c_coarse (bi/trilinear), V fine points per thread (x even); the
-// coarse values come through the read-only cache.
-template <int DIM, class T, class TC>
-__device__ __forceinline__ void add_prolong_vec(const KArgs& a, int x, int y, int z,
-                                                typename Tr<T>::C (&v)[Tr<T>::V]) {
-    using C = typename Tr<T>::C;
-    constexpr int V = Tr<T>::V;
-    const TC* cc = reinterpret_cast<const TC*>(a.coarse);
-    int Jl, Jh, Kl = 0, Kh = 0;
-    C w = 1;
-    if (y & 1) { Jl = Jh = (y - 1) >> 1; } else { Jl = (y >> 1) - 1; Jh = y >> 1; w *= (C)0.5; }
-    if (DIM == 3) {
-        if (z & 1) { Kl = Kh = (z - 1) >> 1; } else { Kl = (z >> 1) - 1; Kh = z >> 1; w *= (C)0.5; }
-    }
-    const int I0 = (x >> 1) - 1;
-    C s[V / 2 + 1];
-#pragma unroll
-    for (int k = 0; k <= V / 2; ++k) s[k] = 0;
-    for (int K = Kl; K <= Kh; ++K)
-        for (int J = Jl; J <= Jh; ++J) {
-            const TC* row = cc + (DIM == 3 ? (long long)K * a.Sc : 0LL) + (long long)J * a.Pc + I0;
-#pragma unroll
-            for (int k = 0; k <= V / 2; ++k) s[k] += (C)ld1(row + k);
-        }
-#pragma unroll
-    for (int i = 0; i < V; ++i) {
-        C p = (i & 1) ? s[(i + 1) >> 1] : (C)0.5 * (s[i >> 1] + s[(i >> 1) + 1]);
-        v[i] += w * p;
-    }
-}
-
+// c_fine += P c_coarse (bi/trilinear).  One thread per V consecutive fine x
+// (x even) and a pair of fine rows (2j+1, 2j+2) -- and in 3D a pair of fine
+// planes (2k+1, 2k+2) -- which share coarse rows j, j+1 and planes k, k+1:
+// the odd row lies on coarse row j, the even one halfway to j+1.  Coarse rows
+// and planes -1 and nc, and the coarse x just outside, are zero pads of the
+// padded layout, so no bounds checks are needed on the coarse side.
 template <int DIM, class T, class TC>
 __global__ void __launch_bounds__(256) k_prolong(const KArgs a) {
     using C = typename Tr<T>::C;
     constexpr int V = Tr<T>::V;
+    constexpr int NZ = DIM == 3 ? 2 : 1;
     if (a.gate && a.st->phase != 0) return;
     const int vpr = a.P / V;
-    const int rows = DIM == 3 ? a.n * a.n : a.n;
+    const int np = a.nc + 1;  // pairs j = -1 .. nc-1
+    const int total = DIM == 3 ? vpr * np * np : vpr * np;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= rows * vpr) return;
-    const int row = idx / vpr;
-    const int x = (idx - row * vpr) * V;
+    if (idx >= total) return;
+    const int q = idx / vpr;
+    const int x = (idx - q * vpr) * V;
     if (x >= a.n) return;
-    const int z = DIM == 3 ? row / a.n : 0;
-    const int y = row - z * a.n;
-    T* f = reinterpret_cast<T*>(a.dst) + offs<DIM>(x, y, z, a.P, a.S);
-    C v[V];
-    ldv(f, v);
-    add_prolong_vec<DIM, T, TC>(a, x, y, z, v);
+    const int jk = DIM == 3 ? q / np : 0;
+    const int j = q - jk * np - 1, k = DIM == 3 ? jk - 1 : 0;
+    // X[b][c]: coarse row j+b of plane k+c interpolated to the V fine x's
+    const TC* cc = reinterpret_cast<const TC*>(a.coarse) + ((x >> 1) - 1);
+    C X[2][NZ][V];
 #pragma unroll
-    for (int i = 0; i < V; ++i)
-        if (x + i >= a.n) v[i] = 0;
-    stv(f, v);
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) {
+            const TC* row = cc + (DIM == 3 ? (long long)(k + c) * a.Sc : 0LL) + (long long)(j + b) * a.Pc;
+            C sv[V / 2 + 1];
+#pragma unroll
+            for (int m = 0; m <= V / 2; ++m) sv[m] = (C)ld1(row + m);
+#pragma unroll
+            for (int i = 0; i < V; ++i) X[b][c][i] = (i & 1) ? sv[(i + 1) >> 1] : (C)0.5 * (sv[i >> 1] + sv[(i >> 1) + 1]);
+        }
+    // all fine rows of the block are loaded before any is stored (no
+    // load-after-store ordering between them)
+    T* f0 = reinterpret_cast<T*>(a.dst) + x;
+    T* fr[NZ][2];
+    bool ok[NZ][2];
+    C v[NZ][2][V];
+#pragma unroll
+    for (int dz = 0; dz < NZ; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int z = DIM == 3 ? 2 * k + 1 + dz : 0, y = 2 * j + 1 + dy;
+            ok[dz][dy] = y >= 0 && (DIM == 2 || z >= 0);
+            fr[dz][dy] = f0 + (DIM == 3 ? (long long)(ok[dz][dy] ? z : 0) * a.S : 0LL) + (long long)(ok[dz][dy] ? y : 0) * a.P;
+            if (ok[dz][dy]) ldv(fr[dz][dy], v[dz][dy]);
+        }
+#pragma unroll
+    for (int dz = 0; dz < NZ; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            if (!ok[dz][dy]) continue;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                // odd row / plane: the coarse row / plane itself; even: the mean of two
+                const C pz0 = dy ? (C)0.5 * (X[0][0][i] + X[1][0][i]) : X[0][0][i];
+                C p = pz0;
+                if (DIM == 3) {
+                    const C pz1 = dy ? (C)0.5 * (X[0][NZ - 1][i] + X[1][NZ - 1][i]) : X[0][NZ - 1][i];
+                    p = dz ? (C)0.5 * (pz0 + pz1) : pz0;
+                }
+                v[dz][dy][i] = x + i < a.n ? v[dz][dy][i] + p : (C)0;
+            }
+            stv(fr[dz][dy], v[dz][dy]);
+        }
 }
 
 }  // namespace mgi

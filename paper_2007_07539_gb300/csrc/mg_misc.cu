@@ -139,7 +139,9 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
     s.gz = 1;
     if (kind != K_SWEEP) {
         const int per = kind == K_UPDATE ? kUpdQ : V;
-        const long long rows = dim == 3 ? (long long)n * n : n;
+        // prolongation: one thread per vector of a pair of rows (and planes)
+        const long long np = (n - 1) / 2 + 1;
+        const long long rows = kind == K_PROLONG ? (dim == 3 ? np * np : np) : (dim == 3 ? (long long)n * n : n);
         s.tx = 256;
         s.ty = 1;
         s.gx = cdiv(rows * (P / per), 256);
