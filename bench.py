@@ -209,6 +209,120 @@ def whole_job_rate(units_per_rank: float, seconds: float, world: int, device: st
     return world * units_per_rank / rank_max(seconds, world, device)
 
 
+def extra_workloads(mg, I, torch, flush, quick=False):
+    """Secondary measurements reported inside config (not the headline): the
+    511^3 manufactured problem with the FP16/FP32/FP64 ladder against all-FP64
+    MG, the batched workload (64 independent 3D instances, n log-uniform in
+    [31, 255]) through mg_solve_batch against the same instances one by one,
+    and a serving stream (Poisson arrivals at 0.8x the serial FP16 capacity,
+    half 2D / half 3D) through mg_submit / mg_poll with p50 / p99 latency
+    against serial all-FP64 solves of the same stream."""
+    import numpy as np
+    out = {}
+
+    def solve_ms(h, b, u, k):
+        ts, res = [], None
+        for _ in range(k):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            res = h.solve(b, u)
+            if res["status"] != 0:
+                raise RuntimeError(f"solve failed: {res}")
+            ts.append(1e3 * res["seconds"])
+        return statistics.median(ts), res
+
+    # ---- 511^3, manufactured u = prod sin(pi x): HSD ladder vs D
+    n = 511
+    b = torch.from_numpy(I.manufactured_rhs(3, n)).cuda()
+    u = torch.zeros_like(b)
+    with mg.Hierarchy(mg.make_params(3, n, "HSD", zero_guess=1)) as h:
+        solve_ms(h, b, u, 1)
+        t_h, r_h = solve_ms(h, b, u, 1 if quick else 3)
+    with mg.Hierarchy(mg.make_params(3, n, "D", zero_guess=1, scaling=0)) as h:
+        solve_ms(h, b, u, 1)
+        t_d, r_d = solve_ms(h, b, u, 1 if quick else 2)
+    out["n511_manufactured"] = {"dof": n ** 3, "ladder": "FP16 on 511, 255; FP32 on 127..7; FP64 on 3",
+                                "hsd_ms": t_h, "hsd_dofs": n ** 3 / (t_h * 1e-3), "hsd_iters": r_h["iters"],
+                                "hsd_rel_res_true": r_h["rel_res_true"], "fp64_mg_ms": t_d,
+                                "fp64_mg_iters": r_d["iters"], "speedup_vs_fp64_mg": t_d / t_h}
+    del b, u
+    torch.cuda.empty_cache()
+
+    # ---- batched: 64 independent instances in one mg_solve_batch call
+    work = I.batched_workload(count=16 if quick else 64)
+    hs = [mg.Hierarchy(mg.make_params(3, nn, "H", zero_guess=1)) for nn, _ in work]
+    bs = [torch.from_numpy(I.random_rhs(3, nn, sd)).cuda() for nn, sd in work]
+    us = [torch.zeros_like(x) for x in bs]
+    dof = sum(nn ** 3 for nn, _ in work)
+    t_one = 0.0
+    for h, bb, uu in zip(hs, bs, us):  # one by one (also the warm-up)
+        t_one += solve_ms(h, bb, uu, 1)[0]
+    mg.solve_batch(hs, bs, us)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rb = mg.solve_batch(hs, bs, us)
+    torch.cuda.synchronize()
+    t_b = time.perf_counter() - t0
+    for h in hs:
+        h.close()
+    del hs, bs, us
+    out["batched_64"] = {"instances": len(work), "dof": dof, "sizes": sorted({nn for nn, _ in work}),
+                         "batch_wall_ms": 1e3 * t_b, "batch_dofs": dof / t_b,
+                         "one_by_one_device_ms": t_one, "one_by_one_dofs": dof / (t_one * 1e-3),
+                         "all_converged": all(r["status"] == 0 for r in rb),
+                         "max_iters": max(r["iters"] for r in rb)}
+
+    # ---- serving stream
+    reqs = I.serving_workload(count=24 if quick else 64)
+    pool = {}
+
+    def hier(d, nn, lad):
+        key = (d, nn, lad)
+        if key not in pool:
+            pool[key] = mg.Hierarchy(mg.make_params(d, nn, lad, zero_guess=1))
+        return pool[key]
+
+    bufs = [(torch.from_numpy(I.random_rhs(q["dim"], q["n"], q["seed"])).cuda(),) for q in reqs]
+    t_fp16 = t_fp64 = 0.0
+    for q, (bb,) in zip(reqs, bufs):  # serial FP16 and FP64 references of the same stream
+        uu = torch.zeros_like(bb)
+        t_fp16 += solve_ms(hier(q["dim"], q["n"], "HS"), bb, uu, 1)[0]
+        t_fp64 += solve_ms(hier(q["dim"], q["n"], "D"), bb, uu, 1)[0]
+    rate = 0.8 * len(reqs) / (t_fp16 * 1e-3)
+    # arrivals: the workload's exponential gaps rescaled to this rate
+    mean_gap = reqs[-1]["arrival_s"] / len(reqs)
+    arr = [q["arrival_s"] / (mean_gap * rate) for q in reqs]
+    # one resident hierarchy per request (a request for a busy hierarchy queues behind it)
+    served = [mg.Hierarchy(mg.make_params(q["dim"], q["n"], "HS", zero_guess=1)) for q in reqs]
+    us = [torch.zeros_like(bb) for (bb,) in bufs]
+    mg.serve_configure(0, 16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pending, lat = {}, []
+    i = 0
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and arr[i] <= now:
+            pending[i] = served[i].submit(bufs[i][0], us[i])
+            i += 1
+        for j in list(pending):
+            r = served[j].poll(pending[j])
+            if r is not None:
+                lat.append(time.perf_counter() - t0 - arr[j])
+                del pending[j]
+        time.sleep(0.0002)
+    t_s = time.perf_counter() - t0
+    dof_s = sum(q["n"] ** q["dim"] for q in reqs)
+    lat_ms = sorted(1e3 * x for x in lat)
+    out["serving"] = {"requests": len(reqs), "ladder": "FP16 fine / FP32 coarse (HS)", "rate_per_s": rate,
+                      "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                      "served_dofs": dof_s / t_s, "serial_fp16_device_ms": t_fp16,
+                      "serial_fp64_device_ms": t_fp64, "serial_fp64_dofs": dof_s / (t_fp64 * 1e-3)}
+    for h in served + list(pool.values()):
+        h.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +330,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the 511^3, batched and serving measurements")
     ap.add_argument("--kernel-dump", default=None, help="write every kernel's profiled time to this JSON file")
     ap.add_argument("--ncu-case", action="store_true",
                     help="only two FP16 solves of the workload (a small launch list for ncu captures)")
@@ -344,6 +459,10 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if rank == 0 and world == 1 and not args.no_extras:
+        hH.close()
+        hD.close()
+        line["config"]["extras"] = extra_workloads(mg, I, torch, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, _ = cpu_oracle_sample(b, 1)
         line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": sample}
