@@ -14,7 +14,7 @@ KFn3 pick_sweep3(int mode, int prec_c, int rpw) {
         case M_JACOBI: return rpw == 2 ? &k_sweep3<M_JACOBI, T, T, 2> : &k_sweep3<M_JACOBI, T, T, 1>;
         case M_ZERO2: return rpw == 2 ? &k_sweep3<M_ZERO2, T, T, 2> : &k_sweep3<M_ZERO2, T, T, 1>;
         case M_ZERO1: return rpw == 2 ? &k_sweep3<M_ZERO1, T, T, 2> : &k_sweep3<M_ZERO1, T, T, 1>;
-        case M_RESTRICT:
+        case M_RESTRICT:  // one row per warp (two rows per warp measured no faster here)
             if (rpw != 1) return nullptr;
             switch (prec_c) {
                 case MG_FP64: return &k_sweep3<M_RESTRICT, T, double, 1>;

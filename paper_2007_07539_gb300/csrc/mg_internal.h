@@ -177,6 +177,10 @@ int make_sweep_map(CUtensorMap* m, int prec, const Geom& geo, const void* x0, in
 // [g box: R rows x 512 B] for a tile of R rows, then the restriction's flush
 // area, then one mbarrier per stage.
 constexpr int kSweepStages = 6;
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int sweep3_stages(int, int) { return kSweepStages; }
 constexpr int kSweepRowBytes = 544;
 #ifdef __CUDACC__
 __host__ __device__
@@ -189,8 +193,8 @@ inline int sweep3_stage_bytes(int ty, bool need_g) { return (sweep3_cbytes(ty) +
 #ifdef __CUDACC__
 __host__ __device__
 #endif
-inline int sweep3_smem(int ty, bool need_g, int flush_bytes) {
-    return 128 + kSweepStages * sweep3_stage_bytes(ty, need_g) + (flush_bytes + 15) / 16 * 16 + kSweepStages * 8;
+inline int sweep3_smem(int ty, bool need_g, int flush_bytes, int stages = kSweepStages) {
+    return 128 + stages * sweep3_stage_bytes(ty, need_g) + (flush_bytes + 15) / 16 * 16 + stages * 8;
 }
 
 // Launches a fine-level kernel (one translation unit per fine storage type);

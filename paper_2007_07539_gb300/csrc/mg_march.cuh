@@ -277,8 +277,8 @@ constexpr unsigned kDrainTries = 1u << 10; // every wait after one ran out
 // thread into a 6-stage ring and completed on the stage's mbarrier.  The
 // lane's own row of planes z-1, z, z+1 stays in registers (three arrays that
 // swap roles each plane: the loop body is unrolled three times).
-// Launch bounds: 8 warps.  One row per warp: 4 CTAs per SM (9 warps and 3
-// CTAs for the residual-restriction tiles); two rows per warp: 2 CTAs per SM.
+// Launch bounds: 8 warps (9 for the residual-restriction tiles).  One row per
+// warp: 4 CTAs per SM (3 for restriction); two rows per warp: 2 CTAs per SM.
 template <int MODE, int RPW>
 struct SweepLB {
     static constexpr int kThreads = MODE == M_RESTRICT ? 288 : 256;
@@ -287,7 +287,6 @@ struct SweepLB {
 template <int MODE, class T, class TC, int RPW>
 __global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RPW>::kMinBlocks)
     k_sweep3(const KArgs a, const __grid_constant__ SweepMaps maps) {
-    static_assert(RPW == 1 || (RPW == 2 && MODE != M_RESTRICT), "two rows per warp: sweeps only");
     using C = typename Tr<T>::C;
     using PR = typename std::conditional<MODE == M_RESTRICT, ScalarPair<C>, Pair<C>>::type;
     using P2 = typename PR::t;
@@ -295,7 +294,7 @@ __global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RP
     constexpr int NP = V / 2;
     constexpr int CW = 32 * V;
     constexpr int VH = V / 2 > 0 ? V / 2 : 1;
-    constexpr int S = kSweepStages;  // planes z-1, z, z+1 in use, z+2 .. z+S-2 in flight
+    constexpr int S = sweep3_stages(MODE, RPW);  // planes z-1, z, z+1 in use, z+2 .. z+S-2 in flight
     constexpr bool NEED_G = MODE == M_JACOBI || MODE == M_RESTRICT;
     constexpr int UB = sizeof(T) == 2 ? 4 : 8;  // bytes of one tensor-map unit
     constexpr int RB = kSweepRowBytes;
@@ -307,7 +306,7 @@ __global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RP
     const int CB = sweep3_cbytes(R);
     const int SB = sweep3_stage_bytes(R, NEED_G);
     unsigned char* flush = base + S * SB;
-    const int flush_bytes = MODE == M_RESTRICT ? TY * 32 * VH * (int)sizeof(C) : 0;
+    const int flush_bytes = MODE == M_RESTRICT ? R * 32 * VH * (int)sizeof(C) : 0;
     const unsigned bar0 = smem_u32(flush + (flush_bytes + 15) / 16 * 16);
     const int x0 = blockIdx.x * a.xstep, x = x0 + lane * V;
     const int y0 = blockIdx.y * a.ystep;
@@ -356,9 +355,11 @@ __global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RP
     const P2 h2v = PR::splat(coef<C>(a.cf, 4)), mh6 = PR::splat(coef<C>(a.cf, 5));
     // points x >= n of the chunk are stored as 0 (they are the boundary)
     const uint4 wm = pad_mask<T>(x, a.n);
-    C acc[VH];
+    C acc[RPW][VH];  // restriction: z-weighted sums of the rows' x-restricted residuals
 #pragma unroll
-    for (int k = 0; k < VH; ++k) acc[k] = 0;
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+        for (int k = 0; k < VH; ++k) acc[r][k] = 0;
     T* dst_row[RPW];
     bool do_store[RPW];
     int own[RPW];   // byte offset of the warp's row r within a c box
@@ -390,6 +391,7 @@ __global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RP
         int s1 = so + SB;
         if (s1 >= S * SB) s1 -= S * SB;
         const unsigned char* st0 = base + so;
+        C q[RPW][VH];  // restriction: the rows' x-restricted residuals of this plane
 #pragma unroll
         for (int r = 0; r < RPW; ++r) {
             P2 ym[NP], yp[NP], g[NP];
@@ -420,36 +422,49 @@ __global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RP
                 C o1[V];
 #pragma unroll
                 for (int k = 0; k < NP; ++k) { o1[2 * k] = out[k].x; o1[2 * k + 1] = out[k].y; }
-                C q[VH];
-                fw_x<C, V, VH>(o1, lane, q);
-                const int t = z - zb;
-                if (t & 1) {
+                fw_x<C, V, VH>(o1, lane, q[r]);
+            }
+        }
+        if constexpr (MODE == M_RESTRICT) {
+            // z: fine planes 2K, 2K+1, 2K+2 (t = 0, 1, 2 from the range start)
+            // weigh 1/4, 1/2, 1/4; after an even plane t >= 2 the rows' z-sums go
+            // through shared memory and warp w forms coarse row J0 + w from
+            // tile rows 2w, 2w+1, 2w+2 (y weights 1/4, 1/2, 1/4)
+            const int t = z - zb;
+            if (t & 1) {
 #pragma unroll
-                    for (int k = 0; k < VH; ++k) acc[k] += (C)0.5 * q[k];
-                } else {
-                    if (t >= 2) {  // fine planes 2K, 2K+1, 2K+2 done: write coarse plane K
-                        C* fl = reinterpret_cast<C*>(flush) + (w * 32 + lane) * VH;
+                for (int r = 0; r < RPW; ++r)
 #pragma unroll
-                        for (int k = 0; k < VH; ++k) fl[k] = acc[k] + (C)0.25 * q[k];
-                        __syncthreads();
-                        if ((w & 1) == 0 && w + 2 < TY) {
-                            const int J = (y0 >> 1) + (w >> 1), K = (zb >> 1) + (t >> 1) - 1;
-                            const C* f0 = reinterpret_cast<const C*>(flush) + (w * 32 + lane) * VH;
-                            const C* f1 = f0 + 32 * VH;
-                            const C* f2 = f1 + 32 * VH;
-                            const int I0 = (x0 + lane * V) >> 1;
-                            if (lane_in && J < a.nc && K < a.nc && (lane < 31 || x0 + CW >= a.P)) {
-                                TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
+                    for (int k = 0; k < VH; ++k) acc[r][k] += (C)0.5 * q[r][k];
+            } else {
+                if (t >= 2) {
 #pragma unroll
-                                for (int k = 0; k < VH; ++k)
-                                    if (I0 + k < a.nc)
-                                        st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
-                            }
+                    for (int r = 0; r < RPW; ++r) {
+                        C* fl = reinterpret_cast<C*>(flush) + ((w + r * TY) * 32 + lane) * VH;
+#pragma unroll
+                        for (int k = 0; k < VH; ++k) fl[k] = acc[r][k] + (C)0.25 * q[r][k];
+                    }
+                    __syncthreads();
+                    const int TJ = (R - 1) / 2;
+                    if (w < TJ) {
+                        const int J = (y0 >> 1) + w, K = (zb >> 1) + (t >> 1) - 1;
+                        const C* f0 = reinterpret_cast<const C*>(flush) + ((2 * w) * 32 + lane) * VH;
+                        const C* f1 = f0 + 32 * VH;
+                        const C* f2 = f1 + 32 * VH;
+                        const int I0 = (x0 + lane * V) >> 1;
+                        if (lane_in && J < a.nc && K < a.nc && (lane < 31 || x0 + CW >= a.P)) {
+                            TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
+#pragma unroll
+                            for (int k = 0; k < VH; ++k)
+                                if (I0 + k < a.nc)
+                                    st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
                         }
                     }
-#pragma unroll
-                    for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * q[k];
                 }
+#pragma unroll
+                for (int r = 0; r < RPW; ++r)
+#pragma unroll
+                    for (int k = 0; k < VH; ++k) acc[r][k] = (C)0.25 * q[r][k];
             }
         }
         so = s1;

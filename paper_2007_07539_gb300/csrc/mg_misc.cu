@@ -104,8 +104,9 @@ static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v
 
 constexpr int kSMs = 152;
 
-// Picks the march length L (planes or rows per CTA) for `units` positions to
-// march over and `tiles` CTAs per position: each CTA also reads the two planes
+// Picks the march length L for `units` fine planes (rows in 2D) to march over
+// in spans of L * step_mult (the restriction's CTAs take 2TK of them, for TK
+// coarse planes) and `tiles` CTAs per span: each CTA also reads the two planes
 // next to its range, and a grid that ends in a partial wave idles SMs, so L
 // maximises  (waves / ceil(waves)) * L / (L + 2)  over L in [lo, hi].
 static int pick_march_len(int units, long long tiles, int resident, int lo, int hi, int step_mult) {
@@ -156,15 +157,17 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
         s.xstep = P > CW ? CW - V : CW;
         const int nchunks = P > CW ? 1 + cdiv(P - CW, CW - V) : 1;
         if (dim == 3) {
+            // TJ coarse rows per CTA from 2TJ+1 fine rows, one per warp
+            s.rpw = 1;
             const int TJ = clampi(nc, 1, 4);
             s.ty = 2 * TJ + 1;
+            const int rows = s.ty;
             s.ystep = 2 * TJ;
             s.gx = nchunks;
             s.gy = cdiv(nc, TJ);
-            s.rpw = 1;
-            s.smem = (size_t)sweep3_smem(s.ty, true, s.ty * 32 * VH * (int)cs);
-            const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem);
-            int TK = tz_hint > 0 ? tz_hint : pick_march_len(nc, (long long)s.gx * s.gy, res, 2, 16, 2);
+            s.smem = (size_t)sweep3_smem(rows, true, rows * 32 * VH * (int)cs, sweep3_stages(M_RESTRICT, s.rpw));
+            const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem, s.rpw);
+            int TK = tz_hint > 0 ? tz_hint : pick_march_len(2 * nc, (long long)s.gx * s.gy, res, 2, 16, 2);
             TK = clampi(TK, 1, nc);
             s.zlen = 2 * TK + 1;
             s.zstep = 2 * TK;
@@ -174,7 +177,7 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
             s.ty = W;
             s.gx = cdiv(nchunks, W);
             s.smem = (size_t)W * 6 * 2 * kRowBytes;
-            int TK = tz_hint > 0 ? tz_hint : pick_march_len(nc, s.gx, 8, 4, 32, 2);
+            int TK = tz_hint > 0 ? tz_hint : pick_march_len(2 * nc, s.gx, 8, 4, 32, 2);
             TK = clampi(TK, 1, nc);
             s.zlen = 2 * TK + 1;
             s.zstep = 2 * TK;
