@@ -270,6 +270,8 @@ def extra_workloads(mg, I, torch, flush, quick=False):
                          "batch_wall_ms": 1e3 * t_b, "batch_dofs": dof / t_b,
                          "one_by_one_device_ms": t_one, "one_by_one_dofs": dof / (t_one * 1e-3),
                          "all_converged": all(r["status"] == 0 for r in rb),
+                         "level_synchronous_merged_launches": all(r["merged"] == 1 for r in rb),
+                         "launches_per_solve": rb[0]["launches"],
                          "max_iters": max(r["iters"] for r in rb)}
 
     # ---- serving stream

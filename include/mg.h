@@ -100,7 +100,7 @@ typedef struct mg_result {
     int32_t levels;         /* levels used */
     int32_t guard_restarts; /* times the true residual replaced the recursive one */
     int32_t launches;       /* kernels of this library launched by the solve */
-    int32_t reserved;
+    int32_t merged;         /* mg_solve_batch: 1 if the level-synchronous merged launches ran */
     double rel_res;         /* recursive ||r||_2 / ||b||_2 at exit */
     double rel_res_true;    /* ||b - A u||_2 / ||b||_2 at exit, computed in FP64 */
     double bnorm;           /* ||b||_2 */
@@ -176,13 +176,20 @@ mg_status mg_destroy(mg_hierarchy* h);
  * mg_submit of the process. */
 mg_status mg_serve_configure(size_t budget_bytes, int32_t max_inflight);
 
-/* Solves `count` independent problems together, one per hierarchy, with
- * level-synchronous launches: each launch of a given kernel covers that
- * level of every instance that still iterates.  b[i], u[i], res[i] as for
- * mg_solve.  All hierarchies must share dim and the per-level precision of
- * the finest levels, and were created on the same stream.  Instances stop
- * independently when they converge.  Returns MG_OK if every instance
- * converged, else the first failing status. */
+/* Solves `count` independent problems together, one per hierarchy (each
+ * hierarchy at most once; none with serving requests in flight).  b[i], u[i],
+ * res[i] as for mg_solve.  When every instance is 3D, uses V-cycles with a
+ * coarse tail and a zero initial guess, and b and u are device pointers on
+ * one device, the whole batch runs as one CUDA graph of level-synchronous
+ * launches: each step operation (scale-cast, the pre-smoothing and
+ * residual-restriction of the k-th level below each instance's finest, all
+ * coarse tails, the prolongation and post-smoothing, the update, the norms)
+ * is one launch over a work list of (instance, tile) items, instances of
+ * different sizes included; res[i].merged = 1.  Otherwise the instances run
+ * as concurrent solves on their own streams (res[i].merged = 0).  Each
+ * instance keeps its own residual scale, norms and stopping test and stops
+ * independently; its result equals its solve alone bit for bit.  Returns
+ * MG_OK if every instance converged, else the first failing status. */
 mg_status mg_solve_batch(int32_t count, mg_hierarchy* const* hs, const double* const* b,
                          double* const* u, mg_result* res);
 

@@ -77,6 +77,54 @@ int launch_kernel_t(int dim, int kind, int mode, int prec_c, const KArgs& a, con
     return (int)cudaGetLastError();
 }
 
+// Batched launch of one step kind for many instances (3D): items is a device
+// array of SweepItem (sweeps) or KItem (update, scale-cast, prolongation).
+template <class T>
+int launch_batch_t(int kind, int mode, int prec_c, int rpw, const void* items, const int* cta_item, int ncta, int ty,
+                   size_t smem, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (kind == K_SWEEP) {
+        using FB = void (*)(const SweepItem*, const int*);
+        FB f = nullptr;
+        switch (mode) {
+            case M_JACOBI: f = rpw == 2 ? &k_sweep3_batch<M_JACOBI, T, T, 2> : &k_sweep3_batch<M_JACOBI, T, T, 1>; break;
+            case M_ZERO2: f = rpw == 2 ? &k_sweep3_batch<M_ZERO2, T, T, 2> : &k_sweep3_batch<M_ZERO2, T, T, 1>; break;
+            case M_ZERO1: f = rpw == 2 ? &k_sweep3_batch<M_ZERO1, T, T, 2> : &k_sweep3_batch<M_ZERO1, T, T, 1>; break;
+            case M_RESTRICT:
+                if (rpw != 1) return (int)cudaErrorInvalidValue;
+                switch (prec_c) {
+                    case MG_FP64: f = &k_sweep3_batch<M_RESTRICT, T, double, 1>; break;
+                    case MG_FP32: f = &k_sweep3_batch<M_RESTRICT, T, float, 1>; break;
+                    case MG_FP16: f = &k_sweep3_batch<M_RESTRICT, T, __half, 1>; break;
+                    case MG_BF16: f = &k_sweep3_batch<M_RESTRICT, T, __nv_bfloat16, 1>; break;
+                }
+                break;
+        }
+        if (!f) return (int)cudaErrorInvalidValue;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return (int)e;
+        }
+        f<<<ncta, dim3(32, ty), smem, st>>>(static_cast<const SweepItem*>(items), cta_item);
+        return (int)cudaGetLastError();
+    }
+    using FK = void (*)(const KItem*, const int*);
+    FK f = nullptr;
+    if (kind == K_UPDATE) f = &k_update_batch<3, T>;
+    else if (kind == K_SCALE) f = &k_scale_cast_batch<3, T>;
+    else if (kind == K_PROLONG) {
+        switch (prec_c) {
+            case MG_FP64: f = &k_prolong_batch<3, T, double>; break;
+            case MG_FP32: f = &k_prolong_batch<3, T, float>; break;
+            case MG_FP16: f = &k_prolong_batch<3, T, __half>; break;
+            case MG_BF16: f = &k_prolong_batch<3, T, __nv_bfloat16>; break;
+        }
+    }
+    if (!f) return (int)cudaErrorInvalidValue;
+    f<<<ncta, 256, 0, st>>>(static_cast<const KItem*>(items), cta_item);
+    return (int)cudaGetLastError();
+}
+
 // CTAs of this kernel resident per SM for the given block size and dynamic
 // shared memory (registers, shared memory and warp slots), 0 if unknown.
 template <class F>

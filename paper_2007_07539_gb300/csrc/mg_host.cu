@@ -622,6 +622,7 @@ extern "C" mg_status mg_destroy(mg_hierarchy* hh) {
     mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
     if (!h) return MG_OK;
     mgi_serve_forget(h);
+    mgi_batch_forget(h);
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_hier(h);
@@ -962,7 +963,12 @@ extern "C" mg_status mg_solve_batch(int32_t count, mg_hierarchy* const* hs, cons
         if (!H[i] || !b[i] || !u[i]) FAIL(MG_ERR_INVALID, "NULL entry in batch");
         for (int j = 0; j < i; ++j)
             if (H[j] == H[i]) FAIL(MG_ERR_INVALID, "a hierarchy appears twice in the batch");
+        if (mgi_serve_busy(H[i])) FAIL(MG_ERR_INVALID, "hierarchy has serving requests in flight");
     }
+    // level-synchronous merged launches where the batch allows, else one
+    // concurrent state machine per instance
+    mg_status st = MG_OK;
+    if (count > 0 && mgi_batch_merged(H, b, u, res, &st)) return st;
     return mgi_batch_run(H, b, u, res);
 }
 

@@ -120,6 +120,9 @@ mg_status mgi_solve_begin(mgi::mgi_hier& h, const double* b, double* u);
 int mgi_solve_advance(mgi::mgi_hier& h);
 mg_status mgi_batch_run(std::vector<mgi::mgi_hier*>& hs, const double* const* b, double* const* u,
                         mg_result* res);
+bool mgi_batch_merged(std::vector<mgi::mgi_hier*>& hs, const double* const* b, double* const* u, mg_result* res,
+                      mg_status* status);
+void mgi_batch_forget(mgi::mgi_hier* h);
 // serving engine hooks
 void mgi_serve_forget(mgi::mgi_hier* h);
 bool mgi_serve_busy(mgi::mgi_hier* h);

@@ -150,6 +150,16 @@ struct RArgs {
     int need_b;           // 1: also the partial sums of b^2 (initial residual, stage calls)
 };
 
+struct RItem {
+    RArgs a;
+    int ncta, cta_begin;
+};
+struct FinItem {
+    DevState* st;
+    const double* partials;
+    int nblocks;
+};
+
 struct MarchShape {
     int gx, gy, gz, tx, ty;
     int rpw;  // 3D sweeps: rows per warp (the CTA tile has ty * rpw rows)
@@ -169,6 +179,18 @@ struct alignas(64) SweepMaps {
     CUtensorMap src;
     CUtensorMap g;
 };
+// Work items of the batched (level-synchronous) launches: one per instance,
+// owning CTAs [cta_begin, cta_begin + its grid size) of the merged grid.
+struct alignas(64) SweepItem {
+    SweepMaps maps;
+    KArgs a;
+    int gx, gy, gz, cta_begin;
+};
+struct KItem {
+    KArgs a;
+    int ncta, cta_begin;
+};
+
 // Encodes one map for level vector `x0` (the address of element (0,0,0)).
 int make_sweep_map(CUtensorMap* m, int prec, const Geom& geo, const void* x0, int rows, bool halo);
 
@@ -214,6 +236,14 @@ int launch_pack_u0(int dim, const Geom& geo, const DevState* st, double* u_padde
 // Condition of the device-side IR loop: continue while phase is 0 or 1 and the
 // body has run fewer than `limit` times.
 int launch_loop_condition(DevState* st, unsigned long long handle, int limit, void* stream);
+// Batched counterparts (level-synchronous batch solves): one launch for all
+// instances; cta_item maps each CTA of the merged grid to its work item.
+int launch_finalize_batch(int kind, const FinItem* items, int nitems, void* stream);
+int launch_loop_condition_batch(DevState* const* sts, int n, unsigned long long handle, int limit, void* stream);
+int launch_residual64_batch(int dim, bool init_copy, const RItem* items, const int* cta_item, int ncta, void* stream);
+int residual64_ctas(int dim, int n);
+int launch_kernel_batch(int kind, int mode, int prec, int prec_c, int rpw, const void* items, const int* cta_item,
+                        int ncta, int ty, size_t smem, void* stream);
 int launch_pack(int dim, int prec, const Geom& geo, const void* src_contig, void* dst_padded,
                 void* stream);
 int launch_unpack(int dim, int prec, const Geom& geo, const void* src_padded, void* dst_contig,

@@ -284,9 +284,12 @@ struct SweepLB {
     static constexpr int kThreads = MODE == M_RESTRICT ? 288 : 256;
     static constexpr int kMinBlocks = RPW == 2 ? 2 : (MODE == M_RESTRICT ? 3 : 4);
 };
+// The body takes the CTA's tile coordinates (bx, by, bz) explicitly: the
+// single-grid kernel passes blockIdx, the batched kernel the coordinates of
+// its (instance, tile) work item.  maps may live in parameter space or in
+// global memory (64-byte aligned; written before the launch).
 template <int MODE, class T, class TC, int RPW>
-__global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RPW>::kMinBlocks)
-    k_sweep3(const KArgs a, const __grid_constant__ SweepMaps maps) {
+__device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& maps, int bx, int by, int bz) {
     using C = typename Tr<T>::C;
     using PR = typename std::conditional<MODE == M_RESTRICT, ScalarPair<C>, Pair<C>>::type;
     using P2 = typename PR::t;
@@ -308,9 +311,9 @@ __global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RP
     unsigned char* flush = base + S * SB;
     const int flush_bytes = MODE == M_RESTRICT ? R * 32 * VH * (int)sizeof(C) : 0;
     const unsigned bar0 = smem_u32(flush + (flush_bytes + 15) / 16 * 16);
-    const int x0 = blockIdx.x * a.xstep, x = x0 + lane * V;
-    const int y0 = blockIdx.y * a.ystep;
-    const int zb = blockIdx.z * a.zstep;
+    const int x0 = bx * a.xstep, x = x0 + lane * V;
+    const int y0 = by * a.ystep;
+    const int zb = bz * a.zstep;
     const int ze = min(zb + a.zlen, a.n);
     const bool lane_in = x < a.P;
     const bool leader = w == 0 && lane == 0;
@@ -479,6 +482,22 @@ __global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RP
     }
 }
 
+template <int MODE, class T, class TC, int RPW>
+__global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RPW>::kMinBlocks)
+    k_sweep3(const KArgs a, const __grid_constant__ SweepMaps maps) {
+    sweep3_body<MODE, T, TC, RPW>(a, maps, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+// Batched: CTA -> work item through a table; the item's grid (gx, gy, gz)
+// decodes the CTA's tile.
+template <int MODE, class T, class TC, int RPW>
+__global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RPW>::kMinBlocks)
+    k_sweep3_batch(const SweepItem* __restrict__ items, const int* __restrict__ cta_item) {
+    const SweepItem& it = items[cta_item[blockIdx.x]];
+    const int local = blockIdx.x - it.cta_begin;
+    const int bx = local % it.gx, rest = local / it.gx;
+    sweep3_body<MODE, T, TC, RPW>(it.a, it.maps, bx, rest % it.gy, rest / it.gy);
+}
+
 // ---------------------------------------------------------------- 2D sweep
 template <int MODE, class T, class TC>
 __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
@@ -601,13 +620,13 @@ __device__ __forceinline__ float scaled_f32(double r, const ScaleK& k) {
 
 // g = round_T(r * inv) over the padded rows of the finest level (pads stay 0).
 template <int DIM, class T>
-__global__ void __launch_bounds__(256) k_scale_cast(const KArgs a) {
+__device__ __forceinline__ void scale_cast_body(const KArgs& a, int cta) {
     using C = typename Tr<T>::C;
     constexpr int V = Tr<T>::V;
     if (a.gate && a.st->phase != 0) return;
     const int vpr = a.P / V;  // vectors per padded row
     const int rows = DIM == 3 ? a.n * a.n : a.n;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int idx = cta * blockDim.x + threadIdx.x;
     if (idx >= rows * vpr) return;
     const int row = idx / vpr;
     const int x = (idx - row * vpr) * V;
@@ -630,6 +649,13 @@ __global__ void __launch_bounds__(256) k_scale_cast(const KArgs a) {
         }
     }
     stv(reinterpret_cast<T*>(a.dst) + o, v);
+}
+template <int DIM, class T>
+__global__ void __launch_bounds__(256) k_scale_cast(const KArgs a) { scale_cast_body<DIM, T>(a, blockIdx.x); }
+template <int DIM, class T>
+__global__ void __launch_bounds__(256) k_scale_cast_batch(const KItem* __restrict__ items, const int* __restrict__ cta_item) {
+    const KItem& it = items[cta_item[blockIdx.x]];
+    scale_cast_body<DIM, T>(it.a, blockIdx.x - it.cta_begin);
 }
 
 // ---------------------------------------------------------------- FP64 IR update (Alg. 2 lines 6-7)
@@ -740,7 +766,7 @@ __device__ __forceinline__ int sq_exponent(const DevState* st) {
 // Block reduction in a fixed order: {sum of squares, max |r| key} -> partials.
 // The double-float pairs are combined with TwoSum through warp shuffles; one
 // lane converts the block total to FP64 and rescales it by 2^(2E).
-__device__ __forceinline__ void write_partials(SqAcc sq, unsigned long long nmax, int E, double* partials) {
+__device__ __forceinline__ void write_partials(SqAcc sq, unsigned long long nmax, int E, double* partials, int cta) {
     __shared__ float sh[32], sl[32];
     __shared__ unsigned long long rm[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -768,8 +794,8 @@ __device__ __forceinline__ void write_partials(SqAcc sq, unsigned long long nmax
             // exact rescaling by 2^(2E) through the exponent field (v is 0 or normal)
             const long long vb = __double_as_longlong(v);
             const double vs = (vb & 0x7FF0000000000000ll) ? __longlong_as_double(vb + ((long long)(2 * E) << 52)) : 0.0;
-            partials[2 * (long long)blockIdx.x] = vs;
-            partials[2 * (long long)blockIdx.x + 1] = __longlong_as_double((long long)m);
+            partials[2 * (long long)cta] = vs;
+            partials[2 * (long long)cta + 1] = __longlong_as_double((long long)m);
         }
     }
 }
@@ -804,7 +830,7 @@ __device__ __forceinline__ void ld4(const T* p, typename Tr<T>::C (&v)[4]) {
 // (three for FP32/BF16 corrections), nothing else.
 constexpr int kUpdQ = 4;
 template <int DIM, class T>
-__global__ void __launch_bounds__(256) k_update(const KArgs a) {
+__device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
     using C = typename Tr<T>::C;
     constexpr int Q = kUpdQ;
     if (a.gate && a.st->phase != 0) return;
@@ -818,7 +844,7 @@ __global__ void __launch_bounds__(256) k_update(const KArgs a) {
     unsigned long long nmax = 0ull;
     // grid-stride over the row vectors: each CTA owns a fixed set, so the
     // partial sums (one per CTA) are accumulated in a fixed order
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    for (int idx = cta * blockDim.x + threadIdx.x; idx < total; idx += ncta * blockDim.x) {
         const int row = idx / vpr;
         const int x = (idx - row * vpr) * Q;
         if (x >= a.n) continue;
@@ -903,7 +929,14 @@ __global__ void __launch_bounds__(256) k_update(const KArgs a) {
         *reinterpret_cast<double2*>(rp) = make_double2(rr[0], rr[1]);
         *reinterpret_cast<double2*>(rp + 2) = make_double2(rr[2], rr[3]);
     }
-    write_partials(sq, nmax, E, a.partials);
+    write_partials(sq, nmax, E, a.partials, cta);
+}
+template <int DIM, class T>
+__global__ void __launch_bounds__(256) k_update(const KArgs a) { update_body<DIM, T>(a, blockIdx.x, gridDim.x); }
+template <int DIM, class T>
+__global__ void __launch_bounds__(256) k_update_batch(const KItem* __restrict__ items, const int* __restrict__ cta_item) {
+    const KItem& it = items[cta_item[blockIdx.x]];
+    update_body<DIM, T>(it.a, blockIdx.x - it.cta_begin, it.ncta);
 }
 
 // ---------------------------------------------------------------- prolongation (Alg. 1 step 4)
@@ -914,7 +947,7 @@ __global__ void __launch_bounds__(256) k_update(const KArgs a) {
 // and planes -1 and nc, and the coarse x just outside, are zero pads of the
 // padded layout, so no bounds checks are needed on the coarse side.
 template <int DIM, class T, class TC>
-__global__ void __launch_bounds__(256) k_prolong(const KArgs a) {
+__device__ __forceinline__ void prolong_body(const KArgs& a, int cta) {
     using C = typename Tr<T>::C;
     constexpr int V = Tr<T>::V;
     constexpr int NZ = DIM == 3 ? 2 : 1;
@@ -922,7 +955,7 @@ __global__ void __launch_bounds__(256) k_prolong(const KArgs a) {
     const int vpr = a.P / V;
     const int np = a.nc + 1;  // pairs j = -1 .. nc-1
     const int total = DIM == 3 ? vpr * np * np : vpr * np;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int idx = cta * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     const int q = idx / vpr;
     const int x = (idx - q * vpr) * V;
@@ -976,6 +1009,14 @@ __global__ void __launch_bounds__(256) k_prolong(const KArgs a) {
             }
             stv(fr[dz][dy], v[dz][dy]);
         }
+}
+
+template <int DIM, class T, class TC>
+__global__ void __launch_bounds__(256) k_prolong(const KArgs a) { prolong_body<DIM, T, TC>(a, blockIdx.x); }
+template <int DIM, class T, class TC>
+__global__ void __launch_bounds__(256) k_prolong_batch(const KItem* __restrict__ items, const int* __restrict__ cta_item) {
+    const KItem& it = items[cta_item[blockIdx.x]];
+    prolong_body<DIM, T, TC>(it.a, blockIdx.x - it.cta_begin);
 }
 
 }  // namespace mgi

@@ -18,6 +18,21 @@ int launch_kernel_f32(int, int, int, int, const KArgs&, const MarchShape&, const
 int launch_kernel_f16(int, int, int, int, const KArgs&, const MarchShape&, const SweepMaps*, void*);
 int launch_kernel_bf16(int, int, int, int, const KArgs&, const MarchShape&, const SweepMaps*, void*);
 int occupancy_f64(int, int, int, int, int, size_t, int);
+int launch_kernel_batch_f64(int, int, int, int, const void*, const int*, int, int, size_t, void*);
+int launch_kernel_batch_f32(int, int, int, int, const void*, const int*, int, int, size_t, void*);
+int launch_kernel_batch_f16(int, int, int, int, const void*, const int*, int, int, size_t, void*);
+int launch_kernel_batch_bf16(int, int, int, int, const void*, const int*, int, int, size_t, void*);
+
+int launch_kernel_batch(int kind, int mode, int prec, int prec_c, int rpw, const void* items, const int* cta_item,
+                        int ncta, int ty, size_t smem, void* stream) {
+    switch (prec) {
+        case MG_FP64: return launch_kernel_batch_f64(kind, mode, prec_c, rpw, items, cta_item, ncta, ty, smem, stream);
+        case MG_FP32: return launch_kernel_batch_f32(kind, mode, prec_c, rpw, items, cta_item, ncta, ty, smem, stream);
+        case MG_FP16: return launch_kernel_batch_f16(kind, mode, prec_c, rpw, items, cta_item, ncta, ty, smem, stream);
+        case MG_BF16: return launch_kernel_batch_bf16(kind, mode, prec_c, rpw, items, cta_item, ncta, ty, smem, stream);
+    }
+    return (int)cudaErrorInvalidValue;
+}
 int occupancy_f32(int, int, int, int, int, size_t, int);
 int occupancy_f16(int, int, int, int, int, size_t, int);
 int occupancy_bf16(int, int, int, int, int, size_t, int);
@@ -269,7 +284,7 @@ int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void*
 // r = b - A u in FP64 with per-CTA partials {sum r^2, max |r|, sum b^2, 0};
 // optionally copies u to the caller's contiguous array.  One thread per point.
 template <int DIM, bool init_copy>
-__global__ void __launch_bounds__(256) k_residual64(RArgs a) {
+__device__ __forceinline__ void residual64_body(const RArgs& a, int cta, int ncta) {
     if (a.gate == 1 && a.st->phase != 1) return;
     if (a.gate == 2 && !a.st->dirty) return;
     const double* bsrc = a.b ? a.b : a.st->b;
@@ -279,7 +294,7 @@ __global__ void __launch_bounds__(256) k_residual64(RArgs a) {
     unsigned long long mr = 0ull;
     // grid-stride over the interior points (contiguous order): fixed
     // per-CTA sets, so the partial sums are accumulated in a fixed order
-    for (int oc = blockIdx.x * blockDim.x + threadIdx.x; oc < npts; oc += gridDim.x * blockDim.x) {
+    for (int oc = cta * blockDim.x + threadIdx.x; oc < npts; oc += ncta * blockDim.x) {
         const int q = oc / a.n;
         const int i = oc - q * a.n;
         const int k = DIM == 3 ? q / a.n : 0;
@@ -319,12 +334,19 @@ __global__ void __launch_bounds__(256) k_residual64(RArgs a) {
         mr = lane < nw ? s3[lane] : 0ull;
         sr = warp_sum(sr); sb = warp_sum(sb); mr = warp_max(mr);
         if (lane == 0) {
-            a.partials[4LL * blockIdx.x + 0] = sr;
-            a.partials[4LL * blockIdx.x + 1] = __longlong_as_double((long long)mr);
-            a.partials[4LL * blockIdx.x + 2] = sb;
-            a.partials[4LL * blockIdx.x + 3] = 0.0;
+            a.partials[4LL * cta + 0] = sr;
+            a.partials[4LL * cta + 1] = __longlong_as_double((long long)mr);
+            a.partials[4LL * cta + 2] = sb;
+            a.partials[4LL * cta + 3] = 0.0;
         }
     }
+}
+template <int DIM, bool init_copy>
+__global__ void __launch_bounds__(256) k_residual64(RArgs a) { residual64_body<DIM, init_copy>(a, blockIdx.x, gridDim.x); }
+template <int DIM, bool init_copy>
+__global__ void __launch_bounds__(256) k_residual64_batch(const RItem* __restrict__ items, const int* __restrict__ cta_item) {
+    const RItem& it = items[cta_item[blockIdx.x]];
+    residual64_body<DIM, init_copy>(it.a, blockIdx.x - it.cta_begin, it.ncta);
 }
 
 static void residual_grid(int dim, int n, dim3& grid, dim3& block) {
@@ -366,7 +388,7 @@ int launch_init_rb(int dim, const Geom& geo, const double* b, double* r, double*
 // alpha = ||r||_inf / sigma (scaling 1), ||r||_2 / sigma (scaling 2) or 1.
 // kind: FIN_INIT after r = b - A u0, FIN_STEP after an update (partials of
 // stride 2), FIN_GUARD after the true residual, 3 = report only.
-__global__ void k_finalize(int kind, DevState* st, const double* __restrict__ partials, int nblocks) {
+__device__ __forceinline__ void finalize_body(int kind, DevState* st, const double* __restrict__ partials, int nblocks) {
     // gating (uniform across the block): a step's finalisation only while
     // iterating, the true-residual check only when it is pending, the report
     // only when u changed since it was last copied out
@@ -451,6 +473,19 @@ __global__ void k_finalize(int kind, DevState* st, const double* __restrict__ pa
     st->phase = 0;
 }
 
+__global__ void k_finalize(int kind, DevState* st, const double* __restrict__ partials, int nblocks) {
+    finalize_body(kind, st, partials, nblocks);
+}
+// Batched: one CTA per instance.
+__global__ void k_finalize_batch(int kind, const FinItem* __restrict__ items) {
+    const FinItem& it = items[blockIdx.x];
+    finalize_body(kind, it.st, it.partials, it.nblocks);
+}
+int launch_finalize_batch(int kind, const FinItem* items, int nitems, void* stream) {
+    k_finalize_batch<<<nitems, 1024, 0, (cudaStream_t)stream>>>(kind, items);
+    return (int)cudaGetLastError();
+}
+
 int launch_finalize(int kind, DevState* st, const double* partials, int nblocks, void* stream) {
     k_finalize<<<1, 1024, 0, (cudaStream_t)stream>>>(kind, st, partials, nblocks);
     return (int)cudaGetLastError();
@@ -468,6 +503,46 @@ __global__ void k_loop_condition(DevState* st, cudaGraphConditionalHandle h, int
         st->status = MG_ERR_NOT_CONVERGED;
     }
     cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// Batched: the loop runs while any instance is iterating or has its true-
+// residual check pending; every instance counts the body's iterations.
+__global__ void k_loop_condition_batch(DevState* const* sts, int n, cudaGraphConditionalHandle h, int limit) {
+    bool more = false;
+    for (int i = 0; i < n; ++i) {
+        DevState* st = sts[i];
+        const int loops = st->loops + 1;
+        st->loops = loops;
+        if (st->phase == 0 || st->phase == 1) {
+            if (loops < limit) {
+                more = true;
+            } else {
+                st->phase = 3;
+                st->status = MG_ERR_NOT_CONVERGED;
+            }
+        }
+    }
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+int launch_loop_condition_batch(DevState* const* sts, int n, unsigned long long handle, int limit, void* stream) {
+    k_loop_condition_batch<<<1, 1, 0, (cudaStream_t)stream>>>(sts, n, (cudaGraphConditionalHandle)handle, limit);
+    return (int)cudaGetLastError();
+}
+int launch_residual64_batch(int dim, bool init_copy, const RItem* items, const int* cta_item, int ncta, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dim == 3) {
+        if (init_copy) k_residual64_batch<3, true><<<ncta, 256, 0, s>>>(items, cta_item);
+        else k_residual64_batch<3, false><<<ncta, 256, 0, s>>>(items, cta_item);
+    } else {
+        if (init_copy) k_residual64_batch<2, true><<<ncta, 256, 0, s>>>(items, cta_item);
+        else k_residual64_batch<2, false><<<ncta, 256, 0, s>>>(items, cta_item);
+    }
+    return (int)cudaGetLastError();
+}
+int residual64_ctas(int dim, int n) {
+    dim3 grid, block;
+    residual_grid(dim, n, grid, block);
+    return (int)grid.x;
 }
 
 int launch_loop_condition(DevState* st, unsigned long long handle, int limit, void* stream) {

@@ -246,9 +246,8 @@ __device__ void run_tail_op_t(const TailOp& op, unsigned char* sm, const double*
 }
 
 template <int DIM, class TU>
-__global__ void __launch_bounds__(kTailThreads) k_tail(const TailOp* __restrict__ prog, int nops,
-                                                        const double* __restrict__ minv, int m0,
-                                                        const DevState* st, int gate) {
+__device__ __forceinline__ void tail_body(const TailOp* __restrict__ prog, int nops, const double* __restrict__ minv,
+                                          int m0, const DevState* st, int gate) {
     if (gate && st->phase != 0) return;  // one CTA: the branch is uniform
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ TailOp chunk[kTailChunk];  // the next stages, staged once per chunk
@@ -275,7 +274,42 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailOp* __restrict_
     }
 }
 
+template <int DIM, class TU>
+__global__ void __launch_bounds__(kTailThreads) k_tail(const TailOp* __restrict__ prog, int nops,
+                                                        const double* __restrict__ minv, int m0,
+                                                        const DevState* st, int gate) {
+    tail_body<DIM, TU>(prog, nops, minv, m0, st, gate);
+}
+// Batched: one CTA per instance, each with its own program, base inverse and state.
+template <int DIM, class TU>
+__global__ void __launch_bounds__(kTailThreads) k_tail_batch(const TailItem* __restrict__ items) {
+    const TailItem& it = items[blockIdx.x];
+    tail_body<DIM, TU>(it.prog, it.nops, it.minv, it.m0, it.st, 1);
+}
+
 using TailFn = void (*)(const TailOp*, int, const double*, int, const DevState*, int);
+using TailBatchFn = void (*)(const TailItem*);
+
+template <int DIM>
+static TailBatchFn pick_tail_batch(int uniform_prec) {
+    switch (uniform_prec) {
+        case MG_FP64: return &k_tail_batch<DIM, double>;
+        case MG_FP32: return &k_tail_batch<DIM, float>;
+        case MG_FP16: return &k_tail_batch<DIM, __half>;
+        case MG_BF16: return &k_tail_batch<DIM, __nv_bfloat16>;
+        default: return &k_tail_batch<DIM, void>;
+    }
+}
+
+int launch_tail_batch(int dim, int uniform_prec, const TailItem* items, int nitems, size_t smem, void* stream) {
+    const TailBatchFn f = dim == 3 ? pick_tail_batch<3>(uniform_prec) : pick_tail_batch<2>(uniform_prec);
+    if (smem > 32 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
+    f<<<nitems, kTailThreads, smem, (cudaStream_t)stream>>>(items);
+    return (int)cudaGetLastError();
+}
 
 template <int DIM>
 static TailFn pick_tail(int uniform_prec) {

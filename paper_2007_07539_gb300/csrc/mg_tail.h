@@ -44,6 +44,15 @@ constexpr int kTailChunk = 32;  // stages staged in shared memory at a time
 
 inline unsigned long long tail_magic(int n) { return ((1ull << 40) + (unsigned long long)n - 1) / (unsigned long long)n; }
 
+// One instance of a batched tail launch (one CTA each; gated on its state).
+struct TailItem {
+    const TailOp* prog;
+    const double* minv;
+    const DevState* st;
+    int nops, m0;
+};
+int launch_tail_batch(int dim, int uniform_prec, const TailItem* items, int nitems, size_t smem, void* stream);
+
 // uniform_prec: the storage type of every tail level (selects a kernel
 // specialised for it), or -1 for a mixed-precision tail.
 int launch_tail(int dim, int uniform_prec, const TailOp* prog, int nops, const double* minv, int m0,

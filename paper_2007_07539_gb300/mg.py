@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("levels", ctypes.c_int32),
-                ("guard_restarts", ctypes.c_int32), ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("guard_restarts", ctypes.c_int32), ("launches", ctypes.c_int32), ("merged", ctypes.c_int32),
                 ("rel_res", ctypes.c_double),
                 ("rel_res_true", ctypes.c_double), ("bnorm", ctypes.c_double), ("seconds", ctypes.c_double)]
 

@@ -39,11 +39,36 @@ def test_batch_equals_alone(oracle):
         us.append(torch.zeros_like(bs[-1]))
     res = mg.solve_batch(hs, bs, us)
     for (u_ref, r_ref), u, r, (n, seed) in zip(refs, us, res, work):
+        assert r["merged"] == 1  # level-synchronous merged launches
         assert r["status"] == 0 and r["rel_res_true"] <= 1e-10
         assert np.array_equal(u.cpu().numpy(), u_ref), n
         assert r["iters"] == r_ref["iters"]
         uo, info, _ = oracle.ir_solve(I.random_rhs(3, n, seed))
         assert np.linalg.norm(u.cpu().numpy() - uo) <= 1e-6 * np.linalg.norm(uo)
+    for h in hs:
+        h.close()
+
+
+@pytest.mark.parametrize("mix", ["ladders", "dims"])
+def test_batch_mixed_equals_alone(mix):
+    """Instances with different ladders (merged launches split by launch shape) and a
+    2D/3D mix (the concurrent path) give their alone results bit for bit; a second call
+    reuses the cached plan."""
+    import torch
+    if mix == "ladders":
+        specs = [(3, 63, "H", 11), (3, 95, "HSD", 12), (3, 47, "S", 13), (3, 127, "H", 14), (3, 31, "BSD", 15)]
+    else:
+        specs = [(3, 63, "H", 21), (2, 255, "H", 22), (3, 47, "H", 23)]
+    refs = [alone(d, n, lad, I.random_rhs(d, n, sd)) for d, n, lad, sd in specs]
+    hs = [mg.Hierarchy(mg.make_params(d, n, lad, zero_guess=1)) for d, n, lad, sd in specs]
+    bs = [torch.from_numpy(I.random_rhs(d, n, sd)).cuda() for d, n, lad, sd in specs]
+    for rep in range(2):
+        us = [torch.zeros_like(b) for b in bs]
+        res = mg.solve_batch(hs, bs, us)
+        for (u_ref, r_ref), u, r in zip(refs, us, res):
+            assert r["merged"] == (1 if mix == "ladders" else 0)
+            assert r["status"] == 0 and r["iters"] == r_ref["iters"]
+            assert np.array_equal(u.cpu().numpy(), u_ref)
     for h in hs:
         h.close()
 
