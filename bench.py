@@ -235,10 +235,10 @@ def extra_workloads(mg, I, torch, flush, quick=False):
     n = 511
     b = torch.from_numpy(I.manufactured_rhs(3, n)).cuda()
     u = torch.zeros_like(b)
-    with mg.Hierarchy(mg.make_params(3, n, "HSD", zero_guess=1)) as h:
+    with mg.Hierarchy(mg.make_params(3, n, "HSD", zero_guess=1, tune=1)) as h:
         solve_ms(h, b, u, 1)
         t_h, r_h = solve_ms(h, b, u, 1 if quick else 3)
-    with mg.Hierarchy(mg.make_params(3, n, "D", zero_guess=1, scaling=0)) as h:
+    with mg.Hierarchy(mg.make_params(3, n, "D", zero_guess=1, scaling=0, tune=1)) as h:
         solve_ms(h, b, u, 1)
         t_d, r_d = solve_ms(h, b, u, 1 if quick else 2)
     out["n511_manufactured"] = {"dof": n ** 3, "ladder": "FP16 on 511, 255; FP32 on 127..7; FP64 on 3",
@@ -250,7 +250,7 @@ def extra_workloads(mg, I, torch, flush, quick=False):
 
     # ---- batched: 64 independent instances in one mg_solve_batch call
     work = I.batched_workload(count=16 if quick else 64)
-    hs = [mg.Hierarchy(mg.make_params(3, nn, "H", zero_guess=1)) for nn, _ in work]
+    hs = [mg.Hierarchy(mg.make_params(3, nn, "H", zero_guess=1, tune=1)) for nn, _ in work]
     bs = [torch.from_numpy(I.random_rhs(3, nn, sd)).cuda() for nn, sd in work]
     us = [torch.zeros_like(x) for x in bs]
     dof = sum(nn ** 3 for nn, _ in work)
@@ -333,6 +333,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the 511^3, batched and serving measurements")
+    ap.add_argument("--no-tune", action="store_true", help="tile shapes from the wave model instead of the autotuner")
     ap.add_argument("--kernel-dump", default=None, help="write every kernel's profiled time to this JSON file")
     ap.add_argument("--ncu-case", action="store_true",
                     help="only two FP16 solves of the workload (a small launch list for ncu captures)")
@@ -369,8 +370,10 @@ def main():
     ud = torch.zeros_like(bd)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     graph = 0 if args.ncu_case else args.graph
-    hH = mg.Hierarchy(mg.make_params(DIM, N, "H", zero_guess=1, graph=graph))
-    hD = mg.Hierarchy(mg.make_params(DIM, N, "D", zero_guess=1, scaling=0, graph=graph))
+    # tile shapes of the stencil kernels autotuned at creation (results do not depend on them)
+    tune = 0 if args.no_tune else 1
+    hH = mg.Hierarchy(mg.make_params(DIM, N, "H", zero_guess=1, graph=graph, tune=tune))
+    hD = mg.Hierarchy(mg.make_params(DIM, N, "D", zero_guess=1, scaling=0, graph=graph, tune=tune))
 
     def run(h, bb, uu, k):
         secs, res = [], None
@@ -448,6 +451,7 @@ def main():
                    "rel_diff_u_fp16_vs_fp64": rel_diff, "l2": "256 MiB L2 flush before every step; "
                    "b and u (133 MB each) exceed the 129 MB L2", "wall_s_timed_region": wall,
                    "parallelism": f"{world} independent instance(s), one per GPU, no collective on the data path",
+                   "tile_shapes": "autotuned at creation" if tune else "wave model",
                    "finest_sweeps_gbs": sweep_bytes / (sweep_ms * 1e-3) / 1e9 if sweep_ms else None,
                    "kernel_shares": [{"kernel": f"{k['name']}@L{k['level']}", "ms": round(k["total_ms"], 4),
                                       "share": round(k["total_ms"] / tot_ms, 4),

@@ -89,8 +89,14 @@ typedef struct mg_params {
                            test, recompute b - A u in FP64 and continue from it if it fails */
     int32_t graph;      /* 1 (default): run the whole solve as one CUDA graph launch with a
                            device-side IR loop; 0: one launch per kernel from a host loop */
-    int32_t reserved[8];/* reserved[0] = 1: no coarse-tail kernel (every level as plain
-                           kernels); other entries must be 0 */
+    int32_t no_tail;    /* 1: no coarse-tail kernel (every level as plain kernels); default 0 */
+    int32_t tune;       /* 1: autotune at creation: every 3D stencil kernel of the hierarchy
+                           (sweeps from zero, residual-restriction, Jacobi; per level) is timed
+                           on the device with candidate tile shapes -- rows per warp and march
+                           length -- and the fastest is kept for this process (shared by later
+                           hierarchies with the same level sizes and types).  Results do not
+                           depend on the tile shape.  Default 0: shapes from the wave model */
+    int32_t reserved[6];/* must be 0 */
 } mg_params;
 
 /* Outcome of one solve. */

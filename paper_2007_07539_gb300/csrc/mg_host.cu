@@ -99,6 +99,9 @@ int mgi_validate(const mg_params* p, std::string& why) {
     if (p->tol_mode != 0 && p->tol_mode != 1) { why = "tol_mode must be 0 or 1"; return 0; }
     if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) { why = "tol must be finite and >= 0"; return 0; }
     if (p->max_iter < 0 || p->max_iter > kMaxIter) { why = "max_iter out of range"; return 0; }
+    if ((p->no_tail != 0 && p->no_tail != 1) || (p->tune != 0 && p->tune != 1)) { why = "no_tail and tune must be 0 or 1"; return 0; }
+    for (int i = 0; i < 6; ++i)
+        if (p->reserved[i] != 0) { why = "reserved fields must be 0"; return 0; }
     return L;
 }
 
@@ -518,6 +521,89 @@ static void plan_tail(mgi_hier& h, bool disabled) {
     }
 }
 
+// Autotuner (tune = 1): for every 3D stencil kernel of the step -- sweeps
+// from zero, residual-restriction, Jacobi on each level above the coarse
+// tail -- time candidate tile shapes (rows per warp 1/2; the model's march
+// length, half and double it; best of five runs; a candidate must beat the
+// model's shape by 3%) on this hierarchy's level
+// arrays (their contents at creation do not matter; pads stay zero) and keep
+// the fastest.
+// The choice is process-wide per (kernel, type, level size): later
+// hierarchies of the same sizes reuse it without timing.
+static void autotune(mgi_hier& h) {
+    if (h.dim != 3) return;
+    cudaStream_t s = h.stream;
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess) {
+        cudaGetLastError();
+        if (ea) cudaEventDestroy(ea);
+        return;
+    }
+    // Inside a solve the finest levels stream from DRAM while the small ones
+    // stay in L2: kernels on levels whose arrays exceed a quarter of L2 are
+    // timed after a 256 MB L2 flush, the others warm.
+    void* flush = nullptr;
+    const size_t kFlush = 256u << 20;
+    if (cudaMalloc(&flush, kFlush) != cudaSuccess) {
+        cudaGetLastError();
+        flush = nullptr;
+    }
+    bool cold = false;
+    auto time_op = [&](const Op& op) -> float {
+        float best = 1e30f;
+        if (mgi_run_op(h, op, s)) return best;  // warm-up (and launch check)
+        for (int rep = 0; rep < 5; ++rep) {
+            if (cold && flush) cudaMemsetAsync(flush, rep + 1, kFlush, s);
+            cudaEventRecord(ea, s);
+            if (mgi_run_op(h, op, s)) return 1e30f;
+            cudaEventRecord(eb, s);
+            cudaEventSynchronize(eb);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ea, eb);
+            best = std::min(best, ms);
+        }
+        return best;
+    };
+    const int lo = h.tail_level >= 0 ? h.tail_level + 1 : 1;
+    for (int l = h.nlev - 1; l >= lo; --l) {
+        Level& lv = h.lv[l];
+        const int n = lv.geo.n;
+        cold = 3.0 * (double)lv.geo.total * (double)lv.esz > 32.0 * 1048576.0;
+        for (int mode : {M_ZERO2, M_RESTRICT, M_JACOBI}) {
+            TileChoice have;
+            if (tile_choice_get(3, K_SWEEP, mode, lv.prec, n, &have)) continue;
+            const void* src = mode == M_ZERO2 ? lv.g : lv.c;
+            void* dst = mode == M_RESTRICT ? h.lv[l - 1].g : (mode == M_ZERO2 ? lv.c : lv.t);
+            const void* g = mode == M_ZERO2 ? nullptr : lv.g;
+            const Op base = mgi_kernel_op(h, l, K_SWEEP, mode, src, dst, g, 0, nullptr);
+            const int z0 = mode == M_RESTRICT ? (base.sh.zlen - 1) / 2 : base.sh.zlen;
+            const int zmax = mode == M_RESTRICT ? (n - 1) / 2 : n;
+            TileChoice best{base.sh.rpw, z0};
+            float tbest = time_op(base);
+            // a candidate replaces the model's shape only when clearly faster
+            // (timing noise of short kernels is a few percent)
+            tbest *= 0.97f;
+            for (int rpw = 1; rpw <= 2; ++rpw) {
+                if (rpw == 2 && (mode == M_RESTRICT || n < 16)) continue;
+                for (int z : {z0 / 2, z0, z0 * 2}) {
+                    z = std::max(1, std::min(z, zmax));
+                    if (rpw == base.sh.rpw && z == z0) continue;  // the model's shape, timed above
+                    const TileChoice c{rpw, z};
+                    tile_choice_set(3, K_SWEEP, mode, lv.prec, n, &c);
+                    const float t = time_op(mgi_kernel_op(h, l, K_SWEEP, mode, src, dst, g, 0, nullptr));
+                    if (t < tbest) { tbest = t; best = c; }
+                }
+            }
+            tile_choice_set(3, K_SWEEP, mode, lv.prec, n, &best);
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    if (flush) cudaFree(flush);
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+}
+
 static mg_status plan_hier(const mg_params* p, mgi_hier& h) {
     std::string why;
     int L = mgi_validate(p, why);
@@ -537,7 +623,7 @@ static mg_status plan_hier(const mg_params* p, mgi_hier& h) {
     int sl = p->sigma_log2 >= 0 ? p->sigma_log2 : (any16 ? 14 : 0);
     h.sigma = p->scaling == 0 ? 1.0 : std::ldexp(1.0, sl);
     h.g_alias_r = (p->prec[L - 1] == MG_FP64 && p->scaling == 0);
-    plan_tail(h, p->reserved[0] == 1);  // reserved[0] = 1: no coarse tail
+    plan_tail(h, p->no_tail == 1);
     h.m0 = 1;
     for (int a = 0; a < p->dim; ++a) h.m0 *= sizes[0];
     Layout lay;
@@ -613,6 +699,7 @@ extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, 
     CK_CREATE(cudaMemcpyAsync(h->minv, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, h->stream));
     CK_CREATE(cudaStreamSynchronize(h->stream));
 #undef CK_CREATE
+    if (p->tune == 1) autotune(*h);
     build_step(*h);
     *out = reinterpret_cast<mg_hierarchy*>(h);
     return MG_OK;

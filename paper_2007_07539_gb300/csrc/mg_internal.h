@@ -170,6 +170,16 @@ struct MarchShape {
 // Launch geometry of a fine-level kernel over a level of size n (pitch P).
 MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int tz_hint);
 
+// Autotuned tile shapes of the 3D stencil kernels, per (kind, mode, storage
+// type, level size): rows per warp and march length (planes per CTA for the
+// sweeps, coarse planes per CTA for the residual-restriction).  kernel_shape
+// uses an entry when there is one, else its wave model.
+struct TileChoice {
+    int rpw, zlen;
+};
+void tile_choice_set(int dim, int kind, int mode, int prec, int n, const TileChoice* c);  // nullptr: erase
+bool tile_choice_get(int dim, int kind, int mode, int prec, int n, TileChoice* c);
+
 // TMA descriptors of the 3D sweeps: the swept vector (boxes of TY+2 rows with
 // a 16-byte x-halo on each side) and the right-hand side (TY rows, no halo).
 // Both describe a padded level vector as a 3D tensor of 4-byte units (2-byte

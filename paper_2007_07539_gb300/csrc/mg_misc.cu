@@ -56,6 +56,25 @@ int launch_kernel(int dim, int kind, int mode, int prec, int prec_c, const KArgs
     return (int)cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------- autotuned tile shapes
+namespace {
+std::mutex g_tile_mu;
+std::map<std::tuple<int, int, int, int, int>, TileChoice> g_tile;
+}  // namespace
+void tile_choice_set(int dim, int kind, int mode, int prec, int n, const TileChoice* c) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    const auto key = std::make_tuple(dim, kind, mode, prec, n);
+    if (c) g_tile[key] = *c;
+    else g_tile.erase(key);
+}
+bool tile_choice_get(int dim, int kind, int mode, int prec, int n, TileChoice* c) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tile.find(std::make_tuple(dim, kind, mode, prec, n));
+    if (it == g_tile.end()) return false;
+    *c = it->second;
+    return true;
+}
+
 // Resident CTAs per SM of a kernel, from the runtime's occupancy calculator
 // (cached: the answer depends only on the arguments), else from shared memory.
 static int resident_ctas(int dim, int kind, int mode, int prec, int prec_c, int threads, size_t smem, int rpw = 1) {
@@ -182,6 +201,8 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
             s.gy = cdiv(nc, TJ);
             s.smem = (size_t)sweep3_smem(rows, true, rows * 32 * VH * (int)cs, sweep3_stages(M_RESTRICT, s.rpw));
             const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem, s.rpw);
+            TileChoice tc;
+            if (tz_hint <= 0 && tile_choice_get(dim, kind, mode, prec, n, &tc)) tz_hint = tc.zlen;
             int TK = tz_hint > 0 ? tz_hint : pick_march_len(2 * nc, (long long)s.gx * s.gy, res, 2, 16, 2);
             TK = clampi(TK, 1, nc);
             s.zlen = 2 * TK + 1;
@@ -208,6 +229,12 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
         // is shared by twice the points
         s.ty = clampi(n, 1, 8);
         s.rpw = n >= 16 ? 2 : 1;
+        TileChoice tc;
+        const bool tuned = tile_choice_get(dim, kind, mode, prec, n, &tc);
+        if (tuned) {
+            s.rpw = n >= 16 ? clampi(tc.rpw, 1, 2) : 1;
+            if (tz_hint <= 0) tz_hint = tc.zlen;
+        }
         s.ystep = s.ty * s.rpw;
         s.gx = nchunks;
         s.gy = cdiv(n, s.ystep);

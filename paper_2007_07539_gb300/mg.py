@@ -39,7 +39,8 @@ class Params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("gamma", ctypes.c_int32), ("scaling", ctypes.c_int32),
                 ("sigma_log2", ctypes.c_int32), ("tol_mode", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("zero_guess", ctypes.c_int32), ("guard", ctypes.c_int32),
-                ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("graph", ctypes.c_int32), ("no_tail", ctypes.c_int32), ("tune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class Result(ctypes.Structure):

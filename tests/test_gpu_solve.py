@@ -218,3 +218,19 @@ def test_config3_511_manufactured(oracle, lad, gamma):
         assert res["iters"] == ref_iters
     else:
         assert res["iters"] <= ref_iters + 2
+
+
+def test_autotuned_tiles_give_identical_results():
+    """tune = 1 times candidate tile shapes of every 3D stencil kernel at creation and
+    keeps the fastest; the solution does not depend on the tile shape (bitwise)."""
+    import torch
+    n = 95
+    b = torch.from_numpy(I.random_rhs(3, n, 401)).cuda()
+    out = []
+    for tune in (0, 1):
+        with mg.Hierarchy(mg.make_params(3, n, "H", zero_guess=1, tune=tune)) as h:
+            u = torch.zeros_like(b)
+            r = h.solve(b, u)
+            assert r["status"] == 0
+            out.append((u.cpu().numpy(), r["iters"]))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
