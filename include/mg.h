@@ -96,7 +96,11 @@ typedef struct mg_params {
                            length -- and the fastest is kept for this process (shared by later
                            hierarchies with the same level sizes and types).  Results do not
                            depend on the tile shape.  Default 0: shapes from the wave model */
-    int32_t reserved[6];/* must be 0 */
+    int32_t fuse_pre;   /* 1: pre-smoothing (two sweeps from zero) and residual-restriction in
+                           one pass over each level (3D; temporal blocking: half the bytes, but
+                           slower on GB300, where both kernels are bound by latency rather than
+                           DRAM); default 0: two kernels */
+    int32_t reserved[5];/* must be 0 */
 } mg_params;
 
 /* Outcome of one solve. */
@@ -279,12 +283,14 @@ mg_status mg_level_info_get(const mg_hierarchy* h, int32_t level, mg_level_info*
  *   MG_STAGE_IR_UPDATE     U <- U + a C_L;  R <- R - a A C_L;  a = arg[0]  (Alg. 2 l. 6-7)
  *   MG_STAGE_RESIDUAL      R <- B - A U with B = arg pointer (n^d FP64, device)
  *   MG_STAGE_CYCLE         C_L <- one full cycle on G_L (Alg. 1, recursive)
+ *   MG_STAGE_PRE_RESTRICT  C <- two damped Jacobi sweeps from C = 0 on G, then
+ *                          G_{l-1} <- cast(R (G_l - A_l C_l)): one pass (3D)
  * out (may be NULL) receives, where the stage computes them, ||R||_2 and
  * ||R||_inf (IR_UPDATE, RESIDUAL).  Synchronous. */
 typedef enum {
     MG_STAGE_JACOBI = 0, MG_STAGE_JACOBI_ZERO2 = 1, MG_STAGE_RESTRICT = 2, MG_STAGE_PROLONG = 3,
     MG_STAGE_JACOBI_PROLONG = 4, MG_STAGE_COARSE = 5, MG_STAGE_SCALE_ZERO2 = 6,
-    MG_STAGE_IR_UPDATE = 7, MG_STAGE_RESIDUAL = 8, MG_STAGE_CYCLE = 9
+    MG_STAGE_IR_UPDATE = 7, MG_STAGE_RESIDUAL = 8, MG_STAGE_CYCLE = 9, MG_STAGE_PRE_RESTRICT = 10
 } mg_stage;
 mg_status mg_run_stage(mg_hierarchy* h, int32_t stage, int32_t level, const double* arg,
                        const void* ptr_arg, double* out);

@@ -168,6 +168,13 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
             rc = mgi_run_op(*h, op, s);
             break;
         }
+        case MG_STAGE_PRE_RESTRICT: {
+            if (level < 1 || h->dim != 3) SFAIL(MG_ERR_INVALID, "the one-pass pre-smoothing needs 3D and level >= 1");
+            Op op = mgi_kernel_op(*h, level, K_SWEEP, M_PRE, lv.g, h->lv[level - 1].g, lv.g, 0, nullptr);
+            op.a.dst2 = lv.c;
+            rc = mgi_run_op(*h, op, s);
+            break;
+        }
         case MG_STAGE_RESTRICT: {
             if (level < 1) SFAIL(MG_ERR_INVALID, "restriction needs level >= 1");
             Op op = mgi_kernel_op(*h, level, K_SWEEP, M_RESTRICT, lv.c, h->lv[level - 1].g, lv.g, 0, nullptr);

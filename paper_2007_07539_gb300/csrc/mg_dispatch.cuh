@@ -14,6 +14,15 @@ KFn3 pick_sweep3(int mode, int prec_c, int rpw) {
         case M_JACOBI: return rpw == 2 ? &k_sweep3<M_JACOBI, T, T, 2> : &k_sweep3<M_JACOBI, T, T, 1>;
         case M_ZERO2: return rpw == 2 ? &k_sweep3<M_ZERO2, T, T, 2> : &k_sweep3<M_ZERO2, T, T, 1>;
         case M_ZERO1: return rpw == 2 ? &k_sweep3<M_ZERO1, T, T, 2> : &k_sweep3<M_ZERO1, T, T, 1>;
+        case M_PRE:  // one-pass pre-smoothing + residual-restriction
+            if (rpw != 1) return nullptr;
+            switch (prec_c) {
+                case MG_FP64: return &k_pre3<T, double>;
+                case MG_FP32: return &k_pre3<T, float>;
+                case MG_FP16: return &k_pre3<T, __half>;
+                case MG_BF16: return &k_pre3<T, __nv_bfloat16>;
+            }
+            return nullptr;
         case M_RESTRICT:  // one row per warp (two rows per warp measured no faster here)
             if (rpw != 1) return nullptr;
             switch (prec_c) {
@@ -90,6 +99,14 @@ int launch_batch_t(int kind, int mode, int prec_c, int rpw, const void* items, c
             case M_JACOBI: f = rpw == 2 ? &k_sweep3_batch<M_JACOBI, T, T, 2> : &k_sweep3_batch<M_JACOBI, T, T, 1>; break;
             case M_ZERO2: f = rpw == 2 ? &k_sweep3_batch<M_ZERO2, T, T, 2> : &k_sweep3_batch<M_ZERO2, T, T, 1>; break;
             case M_ZERO1: f = rpw == 2 ? &k_sweep3_batch<M_ZERO1, T, T, 2> : &k_sweep3_batch<M_ZERO1, T, T, 1>; break;
+            case M_PRE:
+                switch (prec_c) {
+                    case MG_FP64: f = &k_pre3_batch<T, double>; break;
+                    case MG_FP32: f = &k_pre3_batch<T, float>; break;
+                    case MG_FP16: f = &k_pre3_batch<T, __half>; break;
+                    case MG_BF16: f = &k_pre3_batch<T, __nv_bfloat16>; break;
+                }
+                break;
             case M_RESTRICT:
                 if (rpw != 1) return (int)cudaErrorInvalidValue;
                 switch (prec_c) {

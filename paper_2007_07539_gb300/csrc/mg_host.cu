@@ -99,8 +99,11 @@ int mgi_validate(const mg_params* p, std::string& why) {
     if (p->tol_mode != 0 && p->tol_mode != 1) { why = "tol_mode must be 0 or 1"; return 0; }
     if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) { why = "tol must be finite and >= 0"; return 0; }
     if (p->max_iter < 0 || p->max_iter > kMaxIter) { why = "max_iter out of range"; return 0; }
-    if ((p->no_tail != 0 && p->no_tail != 1) || (p->tune != 0 && p->tune != 1)) { why = "no_tail and tune must be 0 or 1"; return 0; }
-    for (int i = 0; i < 6; ++i)
+    if ((p->no_tail != 0 && p->no_tail != 1) || (p->tune != 0 && p->tune != 1) || (p->fuse_pre != 0 && p->fuse_pre != 1)) {
+        why = "no_tail, tune and fuse_pre must be 0 or 1";
+        return 0;
+    }
+    for (int i = 0; i < 5; ++i)
         if (p->reserved[i] != 0) { why = "reserved fields must be 0"; return 0; }
     return L;
 }
@@ -224,7 +227,8 @@ struct Gen {
         if (h->dim == 3 && kkind == K_SWEEP) {  // TMA boxes: TY+2 rows of the swept vector, TY rows of g
             op.has_maps = true;
             const int rows = op.sh.ty * op.sh.rpw;
-            if (make_sweep_map(&op.maps.src, op.prec, f, src, rows + 2, true) != 0) op.has_maps = false;
+            // the one-pass pre-smoothing + restriction reads g boxes of TY+4 rows
+            if (make_sweep_map(&op.maps.src, op.prec, f, src, rows + (mode == M_PRE ? 4 : 2), true) != 0) op.has_maps = false;
             const void* gm = g ? g : src;  // modes without g never read it
             if (make_sweep_map(&op.maps.g, op.prec, f, gm, rows, false) != 0) op.has_maps = false;
         }
@@ -346,7 +350,13 @@ struct Gen {
             out->push_back(op);
             return;
         }
-        if (first) {
+        // one pass for the two sweeps from zero and the residual-restriction
+        const bool fused = first && h->p.nu1 == 2 && h->dim == 3 && h->p.fuse_pre;
+        if (fused) {
+            Op op = kernel(l, K_SWEEP, M_PRE, gbuf(l), h->lv[l - 1].g, gbuf(l));
+            op.a.dst2 = cbuf(l);
+            out->push_back(op);
+        } else if (first) {
             if (h->p.nu1 >= 2) {
                 out->push_back(kernel(l, K_SWEEP, M_ZERO2, gbuf(l), cbuf(l), nullptr));
                 for (int s = 2; s < h->p.nu1; ++s) sweep(l);
@@ -365,7 +375,7 @@ struct Gen {
         } else {
             for (int s = 0; s < h->p.nu1; ++s) sweep(l);
         }
-        out->push_back(kernel(l, K_SWEEP, M_RESTRICT, cbuf(l), h->lv[l - 1].g, gbuf(l)));
+        if (!fused) out->push_back(kernel(l, K_SWEEP, M_RESTRICT, cbuf(l), h->lv[l - 1].g, gbuf(l)));
         cur[l - 1] = 0;
         for (int k = 0; k < h->p.gamma; ++k) cycle(l - 1, k == 0);
         Op pr = kernel(l, K_PROLONG, 0, nullptr, cbuf(l), nullptr);
@@ -569,28 +579,34 @@ static void autotune(mgi_hier& h) {
         Level& lv = h.lv[l];
         const int n = lv.geo.n;
         cold = 3.0 * (double)lv.geo.total * (double)lv.esz > 32.0 * 1048576.0;
-        for (int mode : {M_ZERO2, M_RESTRICT, M_JACOBI}) {
+        for (int mode : {M_PRE, M_ZERO2, M_RESTRICT, M_JACOBI}) {
             TileChoice have;
             if (tile_choice_get(3, K_SWEEP, mode, lv.prec, n, &have)) continue;
-            const void* src = mode == M_ZERO2 ? lv.g : lv.c;
-            void* dst = mode == M_RESTRICT ? h.lv[l - 1].g : (mode == M_ZERO2 ? lv.c : lv.t);
+            const bool coarse_out = mode == M_RESTRICT || mode == M_PRE;
+            const void* src = mode == M_ZERO2 || mode == M_PRE ? lv.g : lv.c;
+            void* dst = coarse_out ? h.lv[l - 1].g : (mode == M_ZERO2 ? lv.c : lv.t);
             const void* g = mode == M_ZERO2 ? nullptr : lv.g;
-            const Op base = mgi_kernel_op(h, l, K_SWEEP, mode, src, dst, g, 0, nullptr);
-            const int z0 = mode == M_RESTRICT ? (base.sh.zlen - 1) / 2 : base.sh.zlen;
-            const int zmax = mode == M_RESTRICT ? (n - 1) / 2 : n;
+            auto make = [&]() {
+                Op op = mgi_kernel_op(h, l, K_SWEEP, mode, src, dst, g, 0, nullptr);
+                op.a.dst2 = lv.c;  // M_PRE's smoothed correction
+                return op;
+            };
+            const Op base = make();
+            const int z0 = coarse_out ? (base.sh.zlen - 1) / 2 : base.sh.zlen;
+            const int zmax = coarse_out ? (n - 1) / 2 : n;
             TileChoice best{base.sh.rpw, z0};
             float tbest = time_op(base);
             // a candidate replaces the model's shape only when clearly faster
             // (timing noise of short kernels is a few percent)
             tbest *= 0.97f;
             for (int rpw = 1; rpw <= 2; ++rpw) {
-                if (rpw == 2 && (mode == M_RESTRICT || n < 16)) continue;
+                if (rpw == 2 && (coarse_out || n < 16)) continue;
                 for (int z : {z0 / 2, z0, z0 * 2}) {
                     z = std::max(1, std::min(z, zmax));
                     if (rpw == base.sh.rpw && z == z0) continue;  // the model's shape, timed above
                     const TileChoice c{rpw, z};
                     tile_choice_set(3, K_SWEEP, mode, lv.prec, n, &c);
-                    const float t = time_op(mgi_kernel_op(h, l, K_SWEEP, mode, src, dst, g, 0, nullptr));
+                    const float t = time_op(make());
                     if (t < tbest) { tbest = t; best = c; }
                 }
             }
@@ -1075,6 +1091,7 @@ static double op_bytes(const mgi_hier& h, const Op& op) {
                 case K_SWEEP:
                     if (op.mode == M_JACOBI) return 3 * s * N;      // read c, g; write c'
                     if (op.mode == M_RESTRICT) return 2 * s * N + sc * Nc;  // read c, g; write g_coarse
+                    if (op.mode == M_PRE) return 2 * s * N + sc * Nc;       // read g; write c, g_coarse
                     return 2 * s * N;                               // read g; write c
                 case K_UPDATE: return (32 + s) * N;                 // read c; read+write u, r (FP64)
                 case K_SCALE: return (8 + s) * N;                   // read r (FP64); write g

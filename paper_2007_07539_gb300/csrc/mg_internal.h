@@ -91,6 +91,7 @@ enum Mode : int {
     M_ZERO2 = 1,    // dst = two sweeps from zero; the swept vector is g
     M_ZERO1 = 2,    // dst = w D^-1 g
     M_RESTRICT = 3, // coarse dst = R (g - A c)
+    M_PRE = 4,      // dst2 = two sweeps from zero of g (src = g); coarse dst = R (g - A dst2): one pass
 };
 
 // Arguments of the fine-level kernels (passed by value).
@@ -117,7 +118,8 @@ struct KArgs {
     long long Sc;
     const void* src;     // swept vector / correction (T)
     const void* g;       // right-hand side (T)
-    void* dst;           // output (T, or TC for M_RESTRICT)
+    void* dst;           // output (T, or TC for M_RESTRICT / M_PRE)
+    void* dst2;          // M_PRE: the smoothed correction (T)
     const void* coarse;  // coarse correction (TC) for K_PROLONG
     const double* r64;   // FP64 residual for K_SCALE (padded, finest geometry)
     double* u64;         // K_UPDATE: FP64 solution (padded)
@@ -222,6 +224,26 @@ inline int sweep3_cbytes(int ty) { return ((ty + 2) * kSweepRowBytes + 127) / 12
 __host__ __device__
 #endif
 inline int sweep3_stage_bytes(int ty, bool need_g) { return (sweep3_cbytes(ty) + (need_g ? ty * 512 : 0) + 127) / 128 * 128; }
+// One-pass pre-smoothing + residual + restriction (M_PRE) on a tile of R
+// residual rows: a 6-stage ring of g boxes (R+4 rows), a 3-plane ring of the
+// smoothed correction (R+2 rows, in the storage type), the restriction's
+// flush area, 6 mbarriers.
+constexpr int kPreStagesG = 6;
+constexpr int kPreStagesC = 3;
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int pre3_gbytes(int r) { return ((r + 4) * kSweepRowBytes + 127) / 128 * 128; }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int pre3_cbytes(int r) { return ((r + 2) * kSweepRowBytes + 127) / 128 * 128; }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int pre3_smem(int r, int flush_bytes) {
+    return 128 + kPreStagesG * pre3_gbytes(r) + kPreStagesC * pre3_cbytes(r) + (flush_bytes + 15) / 16 * 16 + kPreStagesG * 8;
+}
 #ifdef __CUDACC__
 __host__ __device__
 #endif

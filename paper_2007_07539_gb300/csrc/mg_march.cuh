@@ -498,6 +498,227 @@ __global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RP
     sweep3_body<MODE, T, TC, RPW>(it.a, it.maps, bx, rest % it.gy, rest / it.gy);
 }
 
+// ---------------------------------------------------------------- 3D one-pass pre-smoothing + restriction
+// Temporal blocking of Alg. 1 steps 1-2 on one level (M_PRE): for a tile of
+// R = 2TJ+1 fine rows and 2TK+1 fine planes it computes the two damped
+// Jacobi sweeps from zero, c = w D^-1 [(2 - w) g + (w/2d) N g], on R+2 rows
+// (one halo row each side), rounds c to the storage type and writes it, then
+// the residual g - A c on the R rows and its full weighting onto the coarse
+// level -- reading g once instead of g for the sweeps, then c and g again for
+// the residual.  Per plane p of g (TMA boxes of R+4 rows with 16-byte x-halos
+// into a 6-stage ring): stage A forms c on plane p-1 from g planes p-2..p into
+// a 3-plane ring of c rows (in the storage type, x-halo elements included),
+// stage B the residual on plane p-2 from c planes p-3..p-1, then the
+// restriction exactly as M_RESTRICT does.  One row per warp (warps 0 and R-1
+// also form the two halo rows of c).
+template <class T, class TC>
+__device__ __forceinline__ void pre3_body(const KArgs& a, const SweepMaps& maps, int bx, int by, int bz) {
+    using C = typename Tr<T>::C;
+    using PR = ScalarPair<C>;
+    using P2 = typename PR::t;
+    constexpr int V = Tr<T>::V;
+    constexpr int NP = V / 2;
+    constexpr int CW = 32 * V;
+    constexpr int VH = V / 2 > 0 ? V / 2 : 1;
+    constexpr int SG = kPreStagesG, SC = kPreStagesC;
+    constexpr int UB = sizeof(T) == 2 ? 4 : 8;
+    constexpr int RB = kSweepRowBytes;
+    if (a.gate && a.st->phase != 0) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+    const int TY = blockDim.y, lane = threadIdx.x, w = threadIdx.y;
+    const int R = TY;                        // residual rows of the tile
+    const int GBs = pre3_gbytes(R), CBs = pre3_cbytes(R);
+    unsigned char* gring = base;
+    unsigned char* cring = base + SG * GBs;
+    unsigned char* flush = cring + SC * CBs;
+    const int flush_bytes = R * 32 * VH * (int)sizeof(C);
+    const unsigned bar0 = smem_u32(flush + (flush_bytes + 15) / 16 * 16);
+    const int x0 = bx * a.xstep, x = x0 + lane * V;
+    const int y0 = by * a.ystep;
+    const int zb = bz * a.zstep;
+    const int ze = min(zb + a.zlen, a.n);  // residual planes [zb, ze)
+    const bool lane_in = x < a.P;
+    const bool leader = w == 0 && lane == 0;
+    const unsigned gbox = (unsigned)((R + 4) * RB);
+    const int xc = (x0 * (int)sizeof(T) - 16) / UB;
+    auto gslot = [&](int p) { return gring + ((p - zb + 2) % SG) * GBs; };   // p >= zb - 2
+    auto cslot = [&](int p) { return cring + ((p - zb + 1) % SC) * CBs; };   // p >= zb - 1
+    auto issue = [&](int p) {
+        if (p > ze + 1) return;
+        const int q = p - zb + 2, s = q % SG;
+        const unsigned bar = bar0 + 8 * s;
+        mbar_expect_tx(bar, gbox);
+        tma_load_3d(smem_u32(gring + s * GBs), &maps.src, xc, y0 - 2, p + 1, bar);
+    };
+    int wst = 0;
+    unsigned wpar = 0;
+    bool failed = false;
+    auto wait_next = [&]() {
+        if (!mbar_wait(bar0 + 8 * wst, wpar, failed ? kDrainTries : kWaitTries)) {
+            if (!failed) {
+                if (a.err) atomicExch(a.err, 1);
+                if (a.st) *reinterpret_cast<volatile int*>(&const_cast<DevState*>(a.st)->phase) = 3;
+            }
+            failed = true;
+        }
+        if (++wst == SG) { wst = 0; wpar ^= 1u; }
+    };
+    if (leader) {
+        for (int s = 0; s < SG; ++s) mbar_init(bar0 + 8 * s, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (leader)
+        for (int k = 0; k < 3; ++k) issue(zb - 2 + k);
+
+    const P2 c2 = PR::splat(coef<C>(a.cf, 1)), c3 = PR::splat(coef<C>(a.cf, 2)), k2 = PR::splat(coef<C>(a.cf, 3));
+    const P2 h2v = PR::splat(coef<C>(a.cf, 4)), mh6 = PR::splat(coef<C>(a.cf, 5));
+    const uint4 wm = pad_mask<T>(x, a.n);
+    const bool left_zero = x0 == 0, right_zero = x0 + CW >= a.P;
+    C acc[VH];
+#pragma unroll
+    for (int k = 0; k < VH; ++k) acc[k] = 0;
+
+    // c = ZERO2(g) from the pair of centre values and neighbour sums, with the
+    // operations (and so the roundings) of the M_ZERO2 sweep
+    auto zero2 = [&](P2 g0, P2 nb) { return PR::mul(c3, PR::fma(c2, nb, PR::mul(k2, g0))); };
+    auto zero2_1 = [&](C g0, C nb) { return zero2(PR::mk(g0, g0), PR::mk(nb, nb)).x; };
+    // c row cr (fine row y0-1+cr) of plane pc from the g ring; writes the c
+    // ring row (with its halo elements) and, for the tile's rows, global c
+    auto c_row = [&](int cr, int pc, unsigned char* cs) {
+        unsigned char* crow = cs + cr * RB;
+        const int fy = y0 - 1 + cr;
+        T* d = reinterpret_cast<T*>(crow + 16);
+        if (fy < 0 || fy >= a.n || pc < 0 || pc >= a.n) {  // outside the grid: the zero boundary
+            *reinterpret_cast<uint4*>(d + lane * V) = make_uint4(0, 0, 0, 0);
+            if (lane == 0) d[-1] = T(0.0f);
+            if (lane == 31) d[CW] = T(0.0f);
+            return;
+        }
+        const unsigned char* g1 = gslot(pc) + (cr + 1) * RB;  // g row fy on plane pc
+        P2 g0[NP], ym[NP], yp[NP], zm[NP], zp[NP];
+        lds_pairs<T>(g1, lane, g0);
+        lds_pairs<T>(g1 - RB, lane, ym);
+        lds_pairs<T>(g1 + RB, lane, yp);
+        lds_pairs<T>(gslot(pc - 1) + (cr + 1) * RB, lane, zm);
+        lds_pairs<T>(gslot(pc + 1) + (cr + 1) * RB, lane, zp);
+        const C left = lds_one<T>(g1, lane * V - 1), right = lds_one<T>(g1, lane * V + V);
+        P2 out[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const C xl = k ? g0[k - 1].y : left;
+            const C xr = k < NP - 1 ? g0[k + 1].x : right;
+            const P2 xs = PR::mk(xl + g0[k].y, g0[k].x + xr);
+            const P2 nb = PR::add(PR::add(xs, PR::add(ym[k], yp[k])), PR::add(zm[k], zp[k]));
+            out[k] = zero2(g0[k], nb);
+        }
+        // into the c ring (pads masked to zero), and to global for the tile's rows
+        st_pairs<T>(d + lane * V, out, wm);
+        if (lane_in && fy >= y0 && pc >= zb && pc < ze)
+            st_pairs<T>(reinterpret_cast<T*>(a.dst2) + (long long)pc * a.S + (long long)fy * a.P + x, out, wm);
+        // x-halo elements of the c row: zero at the boundary, else c there
+        if (lane == 0) {
+            C v = 0;
+            if (!left_zero) {
+                const C nb = ((lds_one<T>(g1, -2) + lds_one<T>(g1, 0)) +
+                              (lds_one<T>(g1 - RB, -1) + lds_one<T>(g1 + RB, -1))) +
+                             (lds_one<T>(gslot(pc - 1) + (cr + 1) * RB, -1) + lds_one<T>(gslot(pc + 1) + (cr + 1) * RB, -1));
+                v = zero2_1(lds_one<T>(g1, -1), nb);
+            }
+            st1(d - 1, v);
+        }
+        if (lane == 31) {
+            C v = 0;
+            if (!right_zero) {
+                const C nb = ((lds_one<T>(g1, CW - 1) + lds_one<T>(g1, CW + 1)) +
+                              (lds_one<T>(g1 - RB, CW) + lds_one<T>(g1 + RB, CW))) +
+                             (lds_one<T>(gslot(pc - 1) + (cr + 1) * RB, CW) + lds_one<T>(gslot(pc + 1) + (cr + 1) * RB, CW));
+                v = x0 + CW < a.n ? zero2_1(lds_one<T>(g1, CW), nb) : (C)0;
+            }
+            st1(d + CW, v);
+        }
+    };
+
+    for (int p = zb - 2; p <= ze + 1; ++p) {
+        __syncthreads();  // the g slot of p+3 and the c slot of p-1 are free
+        if (leader) issue(p + 3);
+        wait_next();      // g plane p
+        // ---- stage A: c on plane p-1, rows y0-1 .. y0+R
+        if (p >= zb) {
+            unsigned char* cs = cslot(p - 1);
+            c_row(w + 1, p - 1, cs);
+            if (w == 0) c_row(0, p - 1, cs);
+            if (w == TY - 1) c_row(R + 1, p - 1, cs);
+        }
+        __syncthreads();
+        // ---- stage B: residual on plane q = p-2, rows y0 .. y0+R-1, and the restriction
+        const int q = p - 2;
+        if (q < zb) continue;
+        const unsigned char* c0s = cslot(q) + (w + 1) * RB;
+        P2 c0[NP], ym[NP], yp[NP], zm[NP], zp[NP], g[NP];
+        lds_pairs<T>(c0s, lane, c0);
+        lds_pairs<T>(c0s - RB, lane, ym);
+        lds_pairs<T>(c0s + RB, lane, yp);
+        lds_pairs<T>(cslot(q - 1) + (w + 1) * RB, lane, zm);
+        lds_pairs<T>(cslot(q + 1) + (w + 1) * RB, lane, zp);
+        lds_pairs<T>(gslot(q) + (w + 2) * RB, lane, g);
+        const C left = lds_one<T>(c0s, lane * V - 1), right = lds_one<T>(c0s, lane * V + V);
+        C o1[V];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const C xl = k ? c0[k - 1].y : left;
+            const C xr = k < NP - 1 ? c0[k + 1].x : right;
+            const P2 xs = PR::mk(xl + c0[k].y, c0[k].x + xr);
+            const P2 nb = PR::add(PR::add(xs, PR::add(ym[k], yp[k])), PR::add(zm[k], zp[k]));
+            const P2 v = PR::fma(h2v, nb, PR::fma(mh6, c0[k], g[k]));  // residual g - A c
+            o1[2 * k] = v.x;
+            o1[2 * k + 1] = v.y;
+        }
+        C qv[VH];
+        fw_x<C, V, VH>(o1, lane, qv);
+        const int t = q - zb;
+        if (t & 1) {
+#pragma unroll
+            for (int k = 0; k < VH; ++k) acc[k] += (C)0.5 * qv[k];
+        } else {
+            if (t >= 2) {  // fine planes 2K, 2K+1, 2K+2 done: coarse plane K
+                C* fl = reinterpret_cast<C*>(flush) + (w * 32 + lane) * VH;
+#pragma unroll
+                for (int k = 0; k < VH; ++k) fl[k] = acc[k] + (C)0.25 * qv[k];
+                __syncthreads();
+                const int TJ = (R - 1) / 2;
+                if (w < TJ) {
+                    const int J = (y0 >> 1) + w, K = (zb >> 1) + (t >> 1) - 1;
+                    const C* f0 = reinterpret_cast<const C*>(flush) + ((2 * w) * 32 + lane) * VH;
+                    const C* f1 = f0 + 32 * VH;
+                    const C* f2 = f1 + 32 * VH;
+                    const int I0 = (x0 + lane * V) >> 1;
+                    if (lane_in && J < a.nc && K < a.nc && (lane < 31 || x0 + CW >= a.P)) {
+                        TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
+#pragma unroll
+                        for (int k = 0; k < VH; ++k)
+                            if (I0 + k < a.nc) st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * qv[k];
+        }
+    }
+}
+template <class T, class TC>
+__global__ void __launch_bounds__(288, 3) k_pre3(const KArgs a, const __grid_constant__ SweepMaps maps) {
+    pre3_body<T, TC>(a, maps, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+template <class T, class TC>
+__global__ void __launch_bounds__(288, 3) k_pre3_batch(const SweepItem* __restrict__ items, const int* __restrict__ cta_item) {
+    const SweepItem& it = items[cta_item[blockIdx.x]];
+    const int local = blockIdx.x - it.cta_begin;
+    const int bx = local % it.gx, rest = local / it.gx;
+    pre3_body<T, TC>(it.a, it.maps, bx, rest % it.gy, rest / it.gy);
+}
+
 // ---------------------------------------------------------------- 2D sweep
 template <int MODE, class T, class TC>
 __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {

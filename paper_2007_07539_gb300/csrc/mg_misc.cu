@@ -186,7 +186,7 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
         return s;
     }
     const bool need_g = mode == M_JACOBI || mode == M_RESTRICT;
-    if (mode == M_RESTRICT) {
+    if (mode == M_RESTRICT || mode == M_PRE) {
         const int nc = (n - 1) / 2;
         s.xstep = P > CW ? CW - V : CW;
         const int nchunks = P > CW ? 1 + cdiv(P - CW, CW - V) : 1;
@@ -199,7 +199,8 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
             s.ystep = 2 * TJ;
             s.gx = nchunks;
             s.gy = cdiv(nc, TJ);
-            s.smem = (size_t)sweep3_smem(rows, true, rows * 32 * VH * (int)cs, sweep3_stages(M_RESTRICT, s.rpw));
+            s.smem = mode == M_PRE ? (size_t)pre3_smem(rows, rows * 32 * VH * (int)cs)
+                                   : (size_t)sweep3_smem(rows, true, rows * 32 * VH * (int)cs, sweep3_stages(M_RESTRICT, s.rpw));
             const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem, s.rpw);
             TileChoice tc;
             if (tz_hint <= 0 && tile_choice_get(dim, kind, mode, prec, n, &tc)) tz_hint = tc.zlen;

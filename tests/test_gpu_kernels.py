@@ -138,6 +138,38 @@ def test_residual_restriction(oracle, case):
     check_close(out, ref, mag, worst, "restrict")
 
 
+@pytest.mark.parametrize("case", [c for c in RCASES if c[0] == 3], ids=rids)
+def test_one_pass_presmoothing_and_restriction(oracle, case):
+    """Alg. 1 steps 1-2 in one pass (temporal blocking): c = two sweeps from zero on g,
+    g_{l-1} = cast(R (g - A c)).  Against the oracle, and bit for bit against the two
+    separate kernels."""
+    dim, n, pf, pc = case
+    precs = two_level_precs(n, pf, pc)
+    nc = (n - 1) // 2
+    gin = rnd(dim, n, 6, 2.0**13 if pf == mg.FP16 else 1.0)
+    outs = []
+    for fused in (True, False):
+        with hier(dim, n, precs) as h:
+            L = h.nlev - 1
+            g = write(h, L, mg.VEC_G, gin, pf)
+            if fused:
+                h.run_stage(mg.STAGE_PRE_RESTRICT, L)
+            else:
+                h.run_stage(mg.STAGE_JACOBI_ZERO2, L)
+                h.run_stage(mg.STAGE_RESTRICT, L)
+            outs.append((read(h, L, mg.VEC_C, n, dim, pf), read(h, L - 1, mg.VEC_G, nc, dim, pc)))
+    (c, gc), (c2, gc2) = outs
+    assert np.array_equal(c, c2) and np.array_equal(gc, gc2)
+    ref = oracle.jacobi(g, oracle.jacobi(g, np.zeros_like(g), OMEGA), OMEGA)
+    c1 = OMEGA * dinv(dim, n) * np.abs(g)
+    mag = c1 + OMEGA * dinv(dim, n) * (np.abs(g) + oracle.apply_A(c1, absmode=True))
+    check_close(c, ref, mag, pf, "pre-smoothing")
+    refc = oracle.restrict(oracle.residual(g, c))
+    magc = oracle.restrict(np.abs(g) + oracle.apply_A(c, absmode=True))
+    worst = pf if TOL[pf] > TOL[pc] else pc
+    check_close(gc, refc, magc, worst, "restriction")
+
+
 @pytest.mark.parametrize("case", RCASES, ids=rids)
 def test_prolongation_and_correction(oracle, case):
     """Alg. 1 step 4: c_l += cast(P c_{l-1}), bi/trilinear interpolation."""

@@ -234,3 +234,21 @@ def test_autotuned_tiles_give_identical_results():
             assert r["status"] == 0
             out.append((u.cpu().numpy(), r["iters"]))
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+@pytest.mark.parametrize("lad", ["H", "HSD", "D"])
+def test_one_pass_presmoothing_same_solve(lad):
+    """The one-pass pre-smoothing + restriction (fuse_pre = 1) and the default two-kernel
+    schedule give the same solve bit for bit."""
+    import torch
+    n = 127
+    b = torch.from_numpy(I.random_rhs(3, n, 402)).cuda()
+    out = []
+    for fuse_pre in (1, 0):
+        with mg.Hierarchy(mg.make_params(3, n, lad, zero_guess=1, fuse_pre=fuse_pre,
+                                         scaling=0 if lad == "D" else 1)) as h:
+            u = torch.zeros_like(b)
+            r = h.solve(b, u)
+            assert r["status"] == 0
+            out.append((u.cpu().numpy(), r["iters"]))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
