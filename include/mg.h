@@ -96,10 +96,11 @@ typedef struct mg_params {
                            length -- and the fastest is kept for this process (shared by later
                            hierarchies with the same level sizes and types).  Results do not
                            depend on the tile shape.  Default 0: shapes from the wave model */
-    int32_t fuse_pre;   /* 1: pre-smoothing (two sweeps from zero) and residual-restriction in
-                           one pass over each level (3D; temporal blocking: half the bytes, but
-                           slower on GB300, where both kernels are bound by latency rather than
-                           DRAM); default 0: two kernels */
+    int32_t fuse_pre;   /* 1: pre-smoothing (two sweeps from zero) and residual-restriction in one
+                           pass over each level (3D; temporal blocking: half the bytes and one
+                           launch, bit-identical results).  Default 0: two kernels, which are
+                           faster on GB300 at every level size measured (both forms are bound
+                           by latency, not DRAM) */
     int32_t reserved[5];/* must be 0 */
 } mg_params;
 

@@ -351,7 +351,7 @@ struct Gen {
             return;
         }
         // one pass for the two sweeps from zero and the residual-restriction
-        const bool fused = first && h->p.nu1 == 2 && h->dim == 3 && h->p.fuse_pre;
+        const bool fused = first && h->p.nu1 == 2 && h->dim == 3 && h->p.fuse_pre == 1;
         if (fused) {
             Op op = kernel(l, K_SWEEP, M_PRE, gbuf(l), h->lv[l - 1].g, gbuf(l));
             op.a.dst2 = cbuf(l);
@@ -580,6 +580,7 @@ static void autotune(mgi_hier& h) {
         const int n = lv.geo.n;
         cold = 3.0 * (double)lv.geo.total * (double)lv.esz > 32.0 * 1048576.0;
         for (int mode : {M_PRE, M_ZERO2, M_RESTRICT, M_JACOBI}) {
+            if (mode == M_PRE && h.p.fuse_pre != 1) continue;
             TileChoice have;
             if (tile_choice_get(3, K_SWEEP, mode, lv.prec, n, &have)) continue;
             const bool coarse_out = mode == M_RESTRICT || mode == M_PRE;

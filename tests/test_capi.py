@@ -51,7 +51,7 @@ def test_ladders():
 
 @pytest.mark.parametrize("bad", [dict(dim=4), dict(n=0), dict(omega=2.5), dict(gamma=3), dict(scaling=7),
                                  dict(max_iter=5000), dict(nu1=-1), dict(levels=9), dict(tol=-1.0), dict(tune=2),
-                                 dict(no_tail=5)])
+                                 dict(no_tail=5), dict(fuse_pre=3)])
 def test_invalid_params_rejected_without_gpu(bad):
     p = mg.make_params(3, 63)
     for k, v in bad.items():
