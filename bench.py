@@ -322,6 +322,30 @@ def extra_workloads(mg, I, torch, flush, quick=False):
                       "serial_fp64_device_ms": t_fp64, "serial_fp64_dofs": dof_s / (t_fp64 * 1e-3)}
     for h in served + list(pool.values()):
         h.close()
+
+    # ---- vector bandwidth versus size (Sec. 8.2, Fig. 6): y <- a x + y, 3 bytes-moved
+    # vectors per value (read x, read y, write y), event-timed on torch's stream
+    dtypes = {mg.FP16: torch.float16, mg.BF16: torch.bfloat16, mg.FP32: torch.float32, mg.FP64: torch.float64}
+    axpy = {}
+    for prec, tdt in dtypes.items():
+        pts = []
+        for lg in range(12, 29, 2):
+            nv = 1 << lg
+            xv = torch.ones(nv, dtype=tdt, device="cuda")
+            yv = torch.zeros(nv, dtype=tdt, device="cuda")
+            reps = 20 if nv < (1 << 24) else 5
+            mg.axpy(prec, 0.5, xv, yv)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                mg.axpy(prec, 0.5, xv, yv)
+            e1.record()
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3 / reps
+            pts.append([nv, round(3 * nv * xv.element_size() / sec / 1e9, 1)])
+            del xv, yv
+        axpy[["fp64", "fp32", "fp16", "bf16"][prec]] = pts
+    out["axpy_gbs_vs_n"] = axpy
     return out
 
 

@@ -204,6 +204,15 @@ mg_status mg_serve_configure(size_t budget_bytes, int32_t max_inflight);
 mg_status mg_solve_batch(int32_t count, mg_hierarchy* const* hs, const double* const* b,
                          double* const* u, mg_result* res);
 
+/* ---------------------------------------------------------------- vector bandwidth study */
+
+/* y <- a x + y for n values of type prec in caller-owned device arrays x, y
+ * (16-byte aligned; n a multiple of 16 bytes of values), asynchronous on
+ * `stream`: the AXPY of the bandwidth-versus-size study of Sec. 8.2 (Fig. 6),
+ * with the widest vector accesses for every type (FP16/BF16 in half2 /
+ * bfloat162 arithmetic).  MG_ERR_INVALID on bad arguments. */
+mg_status mg_axpy(int32_t prec, int64_t n, double a, const void* x, void* y, void* stream);
+
 /* ---------------------------------------------------------------- no device allocation */
 
 /* The paper has no counterpart to this entry point; it exists for callers

@@ -30,7 +30,7 @@ VEC_C, VEC_G, VEC_T, VEC_U, VEC_R = range(5)
 EXPORTS = ["mg_params_init", "mg_level_count", "mg_last_error", "mg_footprint_bytes",
            "mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
            "mg_serve_configure", "mg_solve_batch", "mg_profile_solve", "mg_level_write", "mg_level_read",
-           "mg_level_info_get", "mg_run_stage", "mg_residual_norms_noalloc"]
+           "mg_level_info_get", "mg_run_stage", "mg_residual_norms_noalloc", "mg_axpy"]
 
 
 class Params(ctypes.Structure):
@@ -126,6 +126,8 @@ def lib() -> ctypes.CDLL:
             L.mg_profile_solve.argtypes = [H, vp, vp, R, ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
             L.mg_residual_norms_noalloc.argtypes = [i32, i32, vp, vp, vp, vp]
             L.mg_residual_norms_noalloc.restype = ctypes.c_int
+            L.mg_axpy.argtypes = [i32, ctypes.c_int64, ctypes.c_double, vp, vp, vp]
+            L.mg_axpy.restype = ctypes.c_int
             for f in ("mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
                       "mg_serve_configure", "mg_solve_batch", "mg_level_write", "mg_level_read",
                       "mg_level_info_get", "mg_run_stage", "mg_profile_solve"):
@@ -343,3 +345,10 @@ def residual_norms_noalloc(dim: int, n: int, b, u, norms, stream=None) -> None:
     _check(lib().mg_residual_norms_noalloc(int(dim), int(n), ctypes.c_void_p(_ptr(b)), ctypes.c_void_p(_ptr(u)),
                                            ctypes.c_void_p(_ptr(norms)), ctypes.c_void_p(_stream_handle(stream))),
            "mg_residual_norms_noalloc")
+
+
+def axpy(prec: int, a: float, x, y, stream=None) -> None:
+    """mg_axpy: y <- a x + y on device tensors of the storage type prec (Sec. 8.2, Fig. 6)."""
+    n = x.numel()
+    _check(lib().mg_axpy(int(prec), ctypes.c_int64(n), ctypes.c_double(a), ctypes.c_void_p(_ptr(x)),
+                         ctypes.c_void_p(_ptr(y)), ctypes.c_void_p(_stream_handle(stream))), "mg_axpy")

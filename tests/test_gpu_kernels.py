@@ -315,3 +315,20 @@ def test_full_cycle_low_precision(oracle, dim, n, lad, bound):
         out = read(h, L, mg.VEC_C, n, dim, fp)
     ref = oracle.mg_cycle(gb)
     assert np.linalg.norm(out - ref) <= bound * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec", ALLP)
+@pytest.mark.parametrize("n", [8, 4096, 1 << 20, 3 * (1 << 16) + 8])
+def test_axpy(prec, n):
+    """mg_axpy (Sec. 8.2, Fig. 6): y <- a x + y in the storage type (FP16/BF16 in pairs),
+    against the FP64 result on the same rounded inputs."""
+    import torch
+    tdt = {mg.FP64: torch.float64, mg.FP32: torch.float32, mg.FP16: torch.float16, mg.BF16: torch.bfloat16}[prec]
+    x = torch.from_numpy(I.uniform(31, (n,))).to(tdt).cuda()
+    y = torch.from_numpy(I.uniform(32, (n,))).to(tdt).cuda()
+    a = 0.75
+    ref = a * x.double().cpu().numpy() + y.double().cpu().numpy()
+    mg.axpy(prec, a, x, y)
+    got = y.double().cpu().numpy()
+    mag = np.abs(a * x.double().cpu().numpy()) + np.abs(ref)
+    check_close(got, ref, mag, prec, "axpy")
