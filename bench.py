@@ -212,7 +212,7 @@ def whole_job_rate(units_per_rank: float, seconds: float, world: int, device: st
 def extra_workloads(mg, I, torch, flush, quick=False):
     """Secondary measurements reported inside config (not the headline): the
     511^3 manufactured problem with the FP16/FP32/FP64 ladder against all-FP64
-    MG, the batched workload (64 independent 3D instances, n log-uniform in
+    MG, the four precision variants of Table 2 at 255^3, the batched workload (64 independent 3D instances, n log-uniform in
     [31, 255]) through mg_solve_batch against the same instances one by one,
     and a serving stream (Poisson arrivals at 0.8x the serial FP16 capacity,
     half 2D / half 3D) through mg_submit / mg_poll with p50 / p99 latency
@@ -245,6 +245,29 @@ def extra_workloads(mg, I, torch, flush, quick=False):
                                 "hsd_ms": t_h, "hsd_dofs": n ** 3 / (t_h * 1e-3), "hsd_iters": r_h["iters"],
                                 "hsd_rel_res_true": r_h["rel_res_true"], "fp64_mg_ms": t_d,
                                 "fp64_mg_iters": r_d["iters"], "speedup_vs_fp64_mg": t_d / t_h}
+    del b, u
+    torch.cuda.empty_cache()
+
+    # ---- Table 2's four variants on the 255^3 random problem: D_MG (no scaling), H_MG,
+    # HSD_MG and DSH_MG with the level split of Sec. 6 (HSD: FP64 base and level 1, FP32
+    # level 2, FP16 above; DSH: the reverse, CG base solver in FP16, residual rescaled
+    # into the FP16 levels)
+    n = 255
+    b = torch.from_numpy(I.random_rhs(3, n, 2)).cuda()
+    u = torch.zeros_like(b)
+    nlev = len(mg.level_count(n))
+    variants = {"D_MG": ("D", dict(scaling=0)), "H_MG": ("H", {}),
+                "HSD_MG": (mg.ladder("HSD", nlev, nlev - 3, 2), {}),
+                "DSH_MG": (mg.ladder("DSH", nlev, nlev - 3, 2), dict(base_solver=1))}
+    t2 = {}
+    for name, (lad, kw) in variants.items():
+        with mg.Hierarchy(mg.make_params(3, n, lad, zero_guess=1, tune=1, **kw)) as h:
+            solve_ms(h, b, u, 1)
+            t, r = solve_ms(h, b, u, 1 if quick else 3)
+        t2[name] = {"ms": t, "iters": r["iters"], "dofs": n ** 3 / (t * 1e-3), "rel_res_true": r["rel_res_true"]}
+    for name in t2:
+        t2[name]["speedup_vs_D_MG"] = t2["D_MG"]["ms"] / t2[name]["ms"]
+    out["table2_variants_255"] = t2
     del b, u
     torch.cuda.empty_cache()
 

@@ -101,7 +101,19 @@ typedef struct mg_params {
                            launch, bit-identical results).  Default 0: two kernels, which are
                            faster on GB300 at every level size measured (both forms are bound
                            by latency, not DRAM) */
-    int32_t reserved[5];/* must be 0 */
+    int32_t rescale16;  /* 1 (default): when a restriction goes from a non-FP16 level into an
+                           FP16 level (DSH_MG, Sec. 6), the restricted residual is divided by a
+                           power of two s so that its inf-norm lies in [2^(k-1), 2^k), k the
+                           sigma_log2 in effect (14 with FP16 levels); the correction
+                           prolongated back from that level is multiplied by s.  0: off */
+    int32_t base_solver;/* 0 (default): exact base solve with the dense FP64 inverse;
+                           1: conjugate gradients in the base level's precision (Sec. 6:
+                           x, r, p stored in the level's type, A p and dot products in its
+                           arithmetic type), from x = 0, until ||r||_2 <= base_tol ||g||_2
+                           or base_maxit steps */
+    int32_t base_maxit; /* CG step limit, at most 100000; 0 = the number of base-level unknowns */
+    double base_tol;    /* CG relative tolerance; default 1e-4 */
+    int32_t reserved[2];/* must be 0 */
 } mg_params;
 
 /* Outcome of one solve. */
@@ -245,7 +257,9 @@ mg_status mg_residual_norms_noalloc(int32_t dim, int32_t n, const double* b, con
 typedef struct mg_kernel_time {
     int32_t kind;        /* 0 stencil sweep, 1 base solve, 2 prolongation, 3 zero fill, 4 norm
                             finalise, 5 FP64 IR update, 6 scale and cast of the residual,
-                            7 coarse tail (the cycle below `level` in one cluster kernel) */
+                            7 coarse tail (the cycle below `level` in one CTA),
+                            8 rescale of a restricted residual into an FP16 level (max-norm
+                            and scaled cast; two kernels) */
     int32_t level;       /* level index (0 = coarsest) */
     int32_t mode;        /* sweep mode: 0 Jacobi, 1 two sweeps from zero, 2 one sweep from zero,
                             3 residual + restriction */
@@ -285,9 +299,10 @@ mg_status mg_level_info_get(const mg_hierarchy* h, int32_t level, mg_level_info*
  *   MG_STAGE_JACOBI        C <- C + omega D^-1 (G - A C)          (Sec. 4.2)
  *   MG_STAGE_JACOBI_ZERO2  C <- two damped Jacobi sweeps from C = 0 on G
  *   MG_STAGE_RESTRICT      G_{l-1} <- cast(R (G_l - A_l C_l))     (Alg. 1 step 2)
- *   MG_STAGE_PROLONG       C_l <- C_l + cast(P C_{l-1})           (Alg. 1 step 4)
+ *   MG_STAGE_PROLONG       C_l <- C_l + cast(s P C_{l-1})         (Alg. 1 step 4);
+ *                          s = arg[0] when arg is not NULL (a rescaled coarse level), else 1
  *   MG_STAGE_JACOBI_PROLONG  C_l <- C_l + P C_{l-1}, then one Jacobi sweep
- *   MG_STAGE_COARSE        C_0 <- A_0^-1 G_0 (level 0 only)
+ *   MG_STAGE_COARSE        C_0 <- A_0^-1 G_0 (level 0 only; the base_solver in effect)
  *   MG_STAGE_SCALE_ZERO2   G_L <- cast(R * s) (Alg. 2 line 4), then JACOBI_ZERO2 on
  *                          level L; s = arg[0]
  *   MG_STAGE_IR_UPDATE     U <- U + a C_L;  R <- R - a A C_L;  a = arg[0]  (Alg. 2 l. 6-7)
@@ -295,12 +310,15 @@ mg_status mg_level_info_get(const mg_hierarchy* h, int32_t level, mg_level_info*
  *   MG_STAGE_CYCLE         C_L <- one full cycle on G_L (Alg. 1, recursive)
  *   MG_STAGE_PRE_RESTRICT  C <- two damped Jacobi sweeps from C = 0 on G, then
  *                          G_{l-1} <- cast(R (G_l - A_l C_l)): one pass (3D)
+ *   MG_STAGE_RESTRICT_RESCALE  G_{l-1} <- cast(R (G_l - A_l C_l) / s), level l-1 FP16,
+ *                          s the power of two of the rescale16 rule; out[0] = s
  * out (may be NULL) receives, where the stage computes them, ||R||_2 and
- * ||R||_inf (IR_UPDATE, RESIDUAL).  Synchronous. */
+ * ||R||_inf (IR_UPDATE, RESIDUAL) or the scale s (RESTRICT_RESCALE).  Synchronous. */
 typedef enum {
     MG_STAGE_JACOBI = 0, MG_STAGE_JACOBI_ZERO2 = 1, MG_STAGE_RESTRICT = 2, MG_STAGE_PROLONG = 3,
     MG_STAGE_JACOBI_PROLONG = 4, MG_STAGE_COARSE = 5, MG_STAGE_SCALE_ZERO2 = 6,
-    MG_STAGE_IR_UPDATE = 7, MG_STAGE_RESIDUAL = 8, MG_STAGE_CYCLE = 9, MG_STAGE_PRE_RESTRICT = 10
+    MG_STAGE_IR_UPDATE = 7, MG_STAGE_RESIDUAL = 8, MG_STAGE_CYCLE = 9, MG_STAGE_PRE_RESTRICT = 10,
+    MG_STAGE_RESTRICT_RESCALE = 11
 } mg_stage;
 mg_status mg_run_stage(mg_hierarchy* h, int32_t stage, int32_t level, const double* arg,
                        const void* ptr_arg, double* out);

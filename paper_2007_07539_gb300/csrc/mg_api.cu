@@ -175,6 +175,28 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
             rc = mgi_run_op(*h, op, s);
             break;
         }
+        case MG_STAGE_RESTRICT_RESCALE: {
+            if (level < 1 || !h->rescaled(level - 1))
+                SFAIL(MG_ERR_INVALID, "rescaled restriction needs an FP16 level below a non-FP16 level, rescale16 = 1");
+            Op op = mgi_kernel_op(*h, level, K_SWEEP, M_RESTRICT, lv.c, h->rsc_alloc + h->lv[level - 1].geo.base,
+                                  lv.g, 0, nullptr);
+            op.prec_c = MG_FP32;
+            rc = mgi_run_op(*h, op, s);
+            if (!rc) {
+                Op r{};
+                r.kind = OP_RESCALE;
+                r.level = level - 1;
+                r.prec = r.prec_c = MG_FP16;
+                r.ptr = h->lv[level - 1].g;
+                rc = mgi_run_op(*h, r, s);
+            }
+            if (rc) SFAIL(MG_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString((cudaError_t)rc));
+            double sc = 0.0;
+            SCK(cudaMemcpyAsync(&sc, &h->st->lscale[level - 1], sizeof(double), cudaMemcpyDeviceToHost, s));
+            SCK(cudaStreamSynchronize(s));
+            if (out) { out[0] = sc; out[1] = 0.0; }
+            return MG_OK;
+        }
         case MG_STAGE_RESTRICT: {
             if (level < 1) SFAIL(MG_ERR_INVALID, "restriction needs level >= 1");
             Op op = mgi_kernel_op(*h, level, K_SWEEP, M_RESTRICT, lv.c, h->lv[level - 1].g, lv.g, 0, nullptr);
@@ -186,6 +208,11 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
             if (level < 1) SFAIL(MG_ERR_INVALID, "prolongation needs level >= 1");
             Op op = mgi_kernel_op(*h, level, K_PROLONG, 0, nullptr, lv.c, nullptr, 0, nullptr);
             op.a.coarse = h->lv[level - 1].c;
+            if (arg) {  // the coarse correction's scale, staged in the level's scale slot
+                double* slot = &h->st->lscale[level - 1];
+                SCK(cudaMemcpyAsync(slot, arg, sizeof(double), cudaMemcpyHostToDevice, s));
+                op.a.cscale = slot;
+            }
             rc = mgi_run_op(*h, op, s);
             if (!rc && stage == MG_STAGE_JACOBI_PROLONG) {
                 Op sw = mgi_kernel_op(*h, level, K_SWEEP, M_JACOBI, lv.c, lv.t, lv.g, 0, nullptr);

@@ -60,6 +60,10 @@ extern "C" void mg_params_init(mg_params* p, int32_t dim, int32_t n) {
     p->zero_guess = 0;
     p->guard = 1;
     p->graph = 1;
+    p->rescale16 = 1;
+    p->base_solver = 0;
+    p->base_maxit = 0;
+    p->base_tol = 1e-4;
 }
 
 extern "C" int32_t mg_level_count(int32_t n, int32_t levels_req, int32_t* sizes) {
@@ -103,7 +107,13 @@ int mgi_validate(const mg_params* p, std::string& why) {
         why = "no_tail, tune and fuse_pre must be 0 or 1";
         return 0;
     }
-    for (int i = 0; i < 5; ++i)
+    if ((p->rescale16 != 0 && p->rescale16 != 1) || (p->base_solver != 0 && p->base_solver != 1)) {
+        why = "rescale16 and base_solver must be 0 or 1";
+        return 0;
+    }
+    if (p->base_maxit < 0 || p->base_maxit > 100000) { why = "base_maxit out of range (0..100000)"; return 0; }
+    if (!(p->base_tol >= 0.0) || !std::isfinite(p->base_tol)) { why = "base_tol must be finite and >= 0"; return 0; }
+    for (int i = 0; i < 2; ++i)
         if (p->reserved[i] != 0) { why = "reserved fields must be 0"; return 0; }
     return L;
 }
@@ -113,7 +123,7 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
     size_t level_off[MG_MAX_LEVELS][3];
-    size_t u_off, r_off, part_off, st_off, minv_off, tprog_off, total;
+    size_t u_off, r_off, part_off, st_off, minv_off, tprog_off, rsc_off, rpart_off, total;
     size_t part_cap;
 };
 
@@ -136,6 +146,16 @@ static void compute_layout(mgi_hier& h, Layout& lay) {
     lay.minv_off = off; off += align_up((size_t)h.m0 * h.m0 * 8, 256);
     lay.tprog_off = off;
     if (h.tail_level >= 0) off += align_up(sizeof(TailOp) * kTailMaxOps, 256);
+    // FP32 restriction into a rescaled FP16 level run as plain kernels (any
+    // rescaled level: a W-cycle beyond the tail's program capacity drops the tail)
+    size_t rsc = 0;
+    for (int l = 0; l < h.nlev; ++l)
+        if (h.rescaled(l)) rsc = std::max(rsc, (size_t)h.lv[l].geo.total * 4);
+    lay.rsc_off = lay.rpart_off = 0;
+    if (rsc) {
+        lay.rsc_off = off; off += align_up(rsc, 256);
+        lay.rpart_off = off; off += align_up(kRescaleCtas * sizeof(float), 256);
+    }
     lay.total = off;
 }
 
@@ -235,6 +255,17 @@ struct Gen {
         return op;
     }
 
+    Op rescale_op(int l) {  // max-norm and scaled cast of the FP32 restriction into FP16 level l
+        Op op{};
+        op.kind = OP_RESCALE;
+        op.level = l;
+        op.prec = op.prec_c = h->lv[l].prec;
+        op.ptr = h->lv[l].g;
+        op.a.gate = gate;
+        op.a.st = st;
+        return op;
+    }
+
     void sweep(int l) {  // one Jacobi sweep on level l, ping-pong
         out->push_back(kernel(l, K_SWEEP, M_JACOBI, cbuf(l), obuf(l), gbuf(l)));
         cur[l] ^= 1;
@@ -257,6 +288,11 @@ struct Gen {
         t.h2inv = (double)(f.n + 1) * (double)(f.n + 1);
         t.omega = h->p.omega;
         t.cf = make_sweep_coef(h->dim, t.omega, t.h2inv);
+        t.sslot = -1;
+        t.scr2 = -1;
+        t.rsig = h->rsig;
+        t.cgmax = h->cg_maxit();
+        t.cgtol = h->p.base_tol;
         return t;
     }
     void tpush(const TailOp& t) { h->tail_host.push_back(t); }
@@ -269,6 +305,8 @@ struct Gen {
     void tcycle(int l, bool first) {
         if (l == 0) {
             TailOp t = tbase(0, TK_COARSE);
+            t.mode = h->p.base_solver;
+            t.src = h->tail_cg;
             t.g = sg(0);
             t.dst = sc(0);
             tpush(t);
@@ -293,11 +331,15 @@ struct Gen {
         tpush(r);
         TailOp rs = tbase(l, TK_RESTRICT);
         rs.src = h->tail_rscr; rs.dst = sg(l - 1);
+        const int slot = h->rescaled(l - 1) ? h->tail_sslot + 8 * (l - 1) : -1;
+        rs.sslot = slot;
+        rs.scr2 = h->tail_scr2;
         tpush(rs);
         cur[l - 1] = 0;
         for (int k = 0; k < h->p.gamma; ++k) tcycle(l - 1, k == 0);
         TailOp pr = tbase(l, TK_PROLONG);
         pr.dst = sc(l); pr.coarse = sc(l - 1);
+        pr.sslot = slot;
         tpush(pr);
         for (int k = 0; k < h->p.nu2; ++k) tjacobi(l);
     }
@@ -351,7 +393,8 @@ struct Gen {
             return;
         }
         // one pass for the two sweeps from zero and the residual-restriction
-        const bool fused = first && h->p.nu1 == 2 && h->dim == 3 && h->p.fuse_pre == 1;
+        const bool resc = h->rescaled(l - 1);
+        const bool fused = first && h->p.nu1 == 2 && h->dim == 3 && h->p.fuse_pre == 1 && !resc;
         if (fused) {
             Op op = kernel(l, K_SWEEP, M_PRE, gbuf(l), h->lv[l - 1].g, gbuf(l));
             op.a.dst2 = cbuf(l);
@@ -375,11 +418,19 @@ struct Gen {
         } else {
             for (int s = 0; s < h->p.nu1; ++s) sweep(l);
         }
-        if (!fused) out->push_back(kernel(l, K_SWEEP, M_RESTRICT, cbuf(l), h->lv[l - 1].g, gbuf(l)));
+        if (resc) {  // restriction into a rescaled FP16 level: FP32 scratch, then max-norm and scaled cast
+            Op op = kernel(l, K_SWEEP, M_RESTRICT, cbuf(l), h->rsc_alloc + h->lv[l - 1].geo.base, gbuf(l));
+            op.prec_c = MG_FP32;
+            out->push_back(op);
+            out->push_back(rescale_op(l - 1));
+        } else if (!fused) {
+            out->push_back(kernel(l, K_SWEEP, M_RESTRICT, cbuf(l), h->lv[l - 1].g, gbuf(l)));
+        }
         cur[l - 1] = 0;
         for (int k = 0; k < h->p.gamma; ++k) cycle(l - 1, k == 0);
         Op pr = kernel(l, K_PROLONG, 0, nullptr, cbuf(l), nullptr);
         pr.a.coarse = cbuf(l - 1);
+        if (resc) pr.a.cscale = &h->st->lscale[l - 1];
         out->push_back(pr);
         for (int s = 0; s < h->p.nu2; ++s) sweep(l);
     }
@@ -452,7 +503,7 @@ static void build_step(mgi_hier& h) {
     fin.nblocks = up.sh.nblocks();
     h.step.push_back(fin);
     h.step_kernels = 0;
-    for (const Op& op : h.step) h.step_kernels += op.kind != OP_ZERO;
+    for (const Op& op : h.step) h.step_kernels += op.kind == OP_ZERO ? 0 : op.kind == OP_RESCALE ? 2 : 1;
 }
 
 int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
@@ -462,7 +513,14 @@ int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
             return launch_kernel(h.dim, op.kkind, op.mode, op.prec, op.prec_c, op.a, op.sh,
                                  op.has_maps ? &op.maps : nullptr, s);
         case OP_COARSE:
+            if (h.p.base_solver == 1)
+                return launch_coarse_cg(op.prec, op.g, op.c, h.lv[0].geo, h.p.base_tol, h.cg_maxit(), op.a.st,
+                                        op.a.gate, s);
             return launch_coarse_solve(op.prec, h.minv, h.m0, op.g, op.c, h.lv[0].geo, op.a.st, op.a.gate, s);
+        case OP_RESCALE:
+            if (!h.rsc_alloc) return (int)cudaErrorInvalidValue;
+            return launch_rescale(h.rsc_alloc + h.lv[op.level].geo.base, op.ptr, h.lv[op.level].geo, h.rsc_part,
+                                  h.rsig, &h.st->lscale[op.level], op.a.st, op.a.gate, s);
         case OP_ZERO:
             return (int)cudaMemsetAsync((char*)op.ptr - op.zero_base, 0, op.bytes, s);
         case OP_FINALIZE:
@@ -499,8 +557,10 @@ static void free_hier(mgi_hier* h) {
 
 // Shared-memory plan of the coarse tail: the deepest level T >= 1 with at
 // most kTailMaxPoints points whose arrays (c, t, g of levels 0..T in their
-// storage types, plus one residual scratch in the arithmetic type) fit in
-// kTailMaxSmem bytes; tail_level = -1 when no level qualifies.
+// storage types, plus one residual scratch in the arithmetic type, the
+// scale slots and coarse scratch of rescaled FP16 levels, and the CG vectors
+// of the base level) fit in kTailMaxSmem bytes; tail_level = -1 when no level
+// qualifies.
 static void plan_tail(mgi_hier& h, bool disabled) {
     h.tail_level = -1;
     h.tail_smem = 0;
@@ -521,6 +581,24 @@ static void plan_tail(mgi_hier& h, bool disabled) {
         if (!ok) continue;
         h.tail_rscr = (int)off;
         off = align_up(off + rmax, 16);
+        h.tail_sslot = h.tail_scr2 = h.tail_cg = -1;
+        size_t smax = 0;  // rescaled restrictions inside the tail: coarse values in the arithmetic type
+        for (int l = 0; l < T; ++l)
+            if (h.rescaled(l)) {
+                const long long n = h.lv[l].geo.n;
+                smax = std::max(smax, (size_t)(h.dim == 3 ? n * n * n : n * n) * 8);
+            }
+        if (smax) {
+            h.tail_sslot = (int)off;
+            off = align_up(off + 8 * MG_MAX_LEVELS, 16);
+            h.tail_scr2 = (int)off;
+            off = align_up(off + smax, 16);
+        }
+        if (h.p.base_solver == 1) {  // r, p, A p of the base level: 16-byte aligned slots of m0 * 8 bytes
+            const long long n = h.lv[0].geo.n;
+            h.tail_cg = (int)off;
+            off += 3 * align_up((size_t)(h.dim == 3 ? n * n * n : n * n) * 8, 16);
+        }
         if (off > kTailMaxSmem) continue;
         h.tail_level = T;
         h.tail_smem = off;
@@ -640,6 +718,7 @@ static mg_status plan_hier(const mg_params* p, mgi_hier& h) {
     int sl = p->sigma_log2 >= 0 ? p->sigma_log2 : (any16 ? 14 : 0);
     h.sigma = p->scaling == 0 ? 1.0 : std::ldexp(1.0, sl);
     h.g_alias_r = (p->prec[L - 1] == MG_FP64 && p->scaling == 0);
+    h.rsig = sl;
     plan_tail(h, p->no_tail == 1);
     h.m0 = 1;
     for (int a = 0; a < p->dim; ++a) h.m0 *= sizes[0];
@@ -694,6 +773,10 @@ extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, 
     if (h->tail_level >= 0) h->tail_prog = (TailOp*)(base + lay.tprog_off);
     h->st = (DevState*)(base + lay.st_off);
     h->minv = (double*)(base + lay.minv_off);
+    if (lay.rsc_off) {
+        h->rsc_alloc = (float*)(base + lay.rsc_off);
+        h->rsc_part = (float*)(base + lay.rpart_off);
+    }
     std::vector<double> inv;
     if (!coarse_inverse(h->dim, h->lv[0].geo.n, inv)) { free_hier(h); FAIL(MG_ERR_INVALID, "singular base-level operator"); }
 #define CK_CREATE(call)                                                                       \
@@ -1099,7 +1182,8 @@ static double op_bytes(const mgi_hier& h, const Op& op) {
                 case K_PROLONG: return 2 * s * N + sc * Nc;         // read+write c; read c_coarse
             }
             return 0.0;
-        case OP_COARSE: return 2 * s * N + 8.0 * h.m0 * h.m0;
+        case OP_COARSE: return 2 * s * N + (h.p.base_solver == 1 ? 0.0 : 8.0 * h.m0 * h.m0);
+        case OP_RESCALE: return 10.0 * N;  // read the FP32 restriction twice; write g (FP16)
         case OP_ZERO: return (double)op.bytes;
         case OP_FINALIZE: return 16.0 * op.nblocks;
         case OP_TAIL: {
@@ -1108,7 +1192,7 @@ static double op_bytes(const mgi_hier& h, const Op& op) {
                 const TailOp& t = h.tail_host[i];
                 const double tn = h.dim == 3 ? (double)t.n * t.n * t.n : (double)t.n * t.n;
                 if (t.kind == TK_LOAD || t.kind == TK_STORE) b += (double)elem_size(t.prec) * tn;
-                if (t.kind == TK_COARSE) b += 8.0 * h.m0 * h.m0;
+                if (t.kind == TK_COARSE && t.mode == 0) b += 8.0 * h.m0 * h.m0;
             }
             return b;
         }
@@ -1142,7 +1226,7 @@ extern "C" mg_status mg_profile_solve(mg_hierarchy* hh, const double* b, double*
         std::memset(&k, 0, sizeof(k));
         k.kind = op.kind == OP_KERNEL ? (op.kkind == K_SWEEP ? 0 : op.kkind == K_PROLONG ? 2
                                          : op.kkind == K_UPDATE ? 5 : 6)
-                                      : op.kind;  // OP_TAIL = 7
+                                      : op.kind;  // OP_TAIL = 7, OP_RESCALE = 8
         k.level = op.level;
         k.mode = op.mode;
         k.loader = 0;

@@ -24,7 +24,7 @@ struct Level {
 // OP_KERNEL covers the fine-level kernels (kernel kind in kkind: sweep,
 // IR update, scale-cast, prolongation); the values of `kind` follow
 // mg_kernel_time.kind of mg.h.
-enum OpKind : int { OP_KERNEL = 0, OP_COARSE = 1, OP_ZERO = 3, OP_FINALIZE = 4, OP_TAIL = 7 };
+enum OpKind : int { OP_KERNEL = 0, OP_COARSE = 1, OP_ZERO = 3, OP_FINALIZE = 4, OP_TAIL = 7, OP_RESCALE = 8 };
 
 struct Op {
     int kind = 0, level = 0;
@@ -33,7 +33,7 @@ struct Op {
     MarchShape sh{};
     const void* g = nullptr;  // OP_COARSE
     void* c = nullptr;
-    void* ptr = nullptr;      // OP_ZERO: padded base pointer
+    void* ptr = nullptr;      // OP_ZERO: padded base pointer; OP_RESCALE: the FP16 level's g
     size_t bytes = 0;
     size_t zero_base = 0;     // bytes between allocation start and ptr
     int fin_kind = 0, nblocks = 0;
@@ -92,6 +92,17 @@ struct mgi_hier {
     int tail_rscr = 0;                     // shared-memory byte offset of the tail's residual scratch
     size_t tail_smem = 0;                  // dynamic shared memory of the tail kernel
     int tail_prec = -1;                    // storage type of every tail level, -1 if they differ
+    int tail_sslot = -1;                   // shared-memory byte offset of the rescale slots (8 B per level)
+    int tail_scr2 = -1;                    // ... of the coarse scratch of rescaled restrictions
+    int tail_cg = -1;                      // ... of the CG scratch of the base level
+    int rsig = 0;                          // rescaled FP16 levels: target max-norm 2^rsig
+    float* rsc_alloc = nullptr;            // FP32 restriction into a rescaled level above the tail (padded)
+    float* rsc_part = nullptr;             // kRescaleCtas partial maxima
+    // level l is an FP16 level whose restricted residual is rescaled (rescale16)
+    bool rescaled(int l) const {
+        return p.rescale16 == 1 && l >= 0 && l + 1 < nlev && lv[l].prec == MG_FP16 && lv[l + 1].prec != MG_FP16;
+    }
+    int cg_maxit() const { return p.base_maxit > 0 ? p.base_maxit : m0; }
     void* arena = nullptr;
     size_t arena_bytes = 0;
     size_t footprint = 0;

@@ -73,6 +73,7 @@ struct DevState {
     int dirty;        // u changed since it was last copied to the caller's array
     int loops;        // body iterations of the device-side IR loop (bounded)
     int kerr;         // non-zero: a kernel's bounded wait for its tile copies ran out
+    double lscale[MG_MAX_LEVELS];  // power-of-two scale of each rescaled FP16 level's residual
     const double* b;  // caller's right-hand side (device, contiguous)
     double* uout;     // caller's solution (device, contiguous): u0 in, u out
     double hist[kMaxHist + 2];
@@ -121,6 +122,7 @@ struct KArgs {
     void* dst;           // output (T, or TC for M_RESTRICT / M_PRE)
     void* dst2;          // M_PRE: the smoothed correction (T)
     const void* coarse;  // coarse correction (TC) for K_PROLONG
+    const double* cscale;// K_PROLONG: scale of the coarse correction (a rescaled level), null = 1
     const double* r64;   // FP64 residual for K_SCALE (padded, finest geometry)
     double* u64;         // K_UPDATE: FP64 solution (padded)
     double* rw64;        // K_UPDATE: FP64 residual (padded)
@@ -257,6 +259,16 @@ int launch_kernel(int dim, int kind, int mode, int prec, int prec_c, const KArgs
                   const SweepMaps* maps, void* stream);
 
 // Misc kernels (mg_misc.cu).
+// Rescale of a restricted residual into an FP16 level: x is the FP32
+// restriction (padded, geometry geo), g the FP16 level vector; s = 2^-k with
+// max|x| 2^k in [2^(sig-1), 2^sig) is written to *scale and g = cast(x 2^k).
+// part holds kRescaleCtas floats.
+constexpr int kRescaleCtas = 304;
+int launch_rescale(const float* x, void* g, const Geom& geo, float* part, int sig, double* scale,
+                   const DevState* st, int gate, void* stream);
+// Conjugate gradients on the base level (one CTA; Sec. 6), in the level's type.
+int launch_coarse_cg(int prec, const void* g, void* c, const Geom& geo, double tol, int maxit,
+                     const DevState* st, int gate, void* stream);
 int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void* c, const Geom& geo,
                         const DevState* st, int gate, void* stream);
 int launch_residual64(int dim, const RArgs& a, int* nblocks, void* stream);

@@ -1197,6 +1197,8 @@ __device__ __forceinline__ void prolong_body(const KArgs& a, int cta) {
 #pragma unroll
             for (int i = 0; i < V; ++i) X[b][c][i] = (i & 1) ? sv[(i + 1) >> 1] : (C)0.5 * (sv[i >> 1] + sv[(i >> 1) + 1]);
         }
+    // a rescaled coarse level holds its values times 2^k (sc = 2^-k; exact)
+    const C sc = a.cscale ? (C)__ldg(a.cscale) : (C)1;
     // all fine rows of the block are loaded before any is stored (no
     // load-after-store ordering between them)
     T* f0 = reinterpret_cast<T*>(a.dst) + x;
@@ -1226,7 +1228,7 @@ __device__ __forceinline__ void prolong_body(const KArgs& a, int cta) {
                     const C pz1 = dy ? (C)0.5 * (X[0][NZ - 1][i] + X[1][NZ - 1][i]) : X[0][NZ - 1][i];
                     p = dz ? (C)0.5 * (pz0 + pz1) : pz0;
                 }
-                v[dz][dy][i] = x + i < a.n ? v[dz][dy][i] + p : (C)0;
+                v[dz][dy][i] = x + i < a.n ? v[dz][dy][i] + sc * p : (C)0;
             }
             stv(fr[dz][dy], v[dz][dy]);
         }

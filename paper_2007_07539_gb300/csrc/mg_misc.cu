@@ -9,6 +9,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "mg_compact.cuh"
 #include "mg_march.cuh"
 
 namespace mgi {
@@ -304,6 +305,128 @@ int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void*
             k_coarse_solve<__nv_bfloat16><<<grid, block, sm, s>>>(inv, m, (const __nv_bfloat16*)g, (__nv_bfloat16*)c, geo.n, geo.P, geo.S, geo.dim, st, gate);
             break;
         default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- base solve by CG
+// One CTA: g is gathered from its padded array into compact shared arrays,
+// cg_base runs there, and x is scattered to c.  Shared memory: A p in the
+// arithmetic type, then x, g, r, p in the level type (m <= 4096 points).
+template <int DIM, class T>
+__global__ void __launch_bounds__(1024) k_coarse_cg(const T* __restrict__ g, T* __restrict__ c, int n, int P,
+                                                    long long S, double tol, int maxit, const DevState* st,
+                                                    int gate) {
+    using C = typename Tr<T>::C;
+    if (gate && st->phase != 0) return;
+    extern __shared__ __align__(16) unsigned char smc[];
+    const int m = DIM == 3 ? n * n * n : n * n;
+    C* q = reinterpret_cast<C*>(smc);
+    T* x = reinterpret_cast<T*>(q + m);
+    T* gs = x + m;
+    T* r = gs + m;
+    T* p = r + m;
+    const unsigned long long mn = ((1ull << 40) + (unsigned long long)n - 1) / (unsigned long long)n;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        int i, j, k;
+        decode<DIM>(t, n, mn, i, j, k);
+        gs[t] = g[(DIM == 3 ? (long long)k * S : 0LL) + (long long)j * P + i];
+    }
+    __syncthreads();
+    cg_base<DIM, T>(n, mn, (C)((double)(n + 1) * (double)(n + 1)), gs, x, r, p, q, tol, maxit);
+    __syncthreads();
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        int i, j, k;
+        decode<DIM>(t, n, mn, i, j, k);
+        c[(DIM == 3 ? (long long)k * S : 0LL) + (long long)j * P + i] = x[t];
+    }
+}
+
+template <int DIM, class T>
+static int launch_coarse_cg_t(const void* g, void* c, const Geom& geo, double tol, int maxit, const DevState* st,
+                              int gate, cudaStream_t s) {
+    using C = typename Tr<T>::C;
+    const int m = DIM == 3 ? geo.n * geo.n * geo.n : geo.n * geo.n;
+    const size_t smem = (size_t)m * (sizeof(C) + 4 * sizeof(T));
+    auto f = &k_coarse_cg<DIM, T>;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
+    f<<<1, 1024, smem, s>>>((const T*)g, (T*)c, geo.n, geo.P, geo.S, tol, maxit, st, gate);
+    return (int)cudaGetLastError();
+}
+
+int launch_coarse_cg(int prec, const void* g, void* c, const Geom& geo, double tol, int maxit, const DevState* st,
+                     int gate, void* stream) {
+    const cudaStream_t s = (cudaStream_t)stream;
+    const bool d3 = geo.dim == 3;
+    switch (prec) {
+        case MG_FP64: return d3 ? launch_coarse_cg_t<3, double>(g, c, geo, tol, maxit, st, gate, s)
+                                : launch_coarse_cg_t<2, double>(g, c, geo, tol, maxit, st, gate, s);
+        case MG_FP32: return d3 ? launch_coarse_cg_t<3, float>(g, c, geo, tol, maxit, st, gate, s)
+                                : launch_coarse_cg_t<2, float>(g, c, geo, tol, maxit, st, gate, s);
+        case MG_FP16: return d3 ? launch_coarse_cg_t<3, __half>(g, c, geo, tol, maxit, st, gate, s)
+                                : launch_coarse_cg_t<2, __half>(g, c, geo, tol, maxit, st, gate, s);
+        case MG_BF16: return d3 ? launch_coarse_cg_t<3, __nv_bfloat16>(g, c, geo, tol, maxit, st, gate, s)
+                                : launch_coarse_cg_t<2, __nv_bfloat16>(g, c, geo, tol, maxit, st, gate, s);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- FP16 level rescale
+// Restriction into a rescaled FP16 level (DSH_MG, Sec. 6), after the
+// restriction kernel has written the coarse residual x in FP32: (1) per-CTA
+// max |x| over the interior; (2) every CTA reduces those kRescaleCtas
+// partials in the same order, takes the shift k of rescale_shift, and casts
+// g = fp16(x 2^k) (one rounding: the product is exact); CTA 0 stores 2^-k.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_absmax(const float* __restrict__ x, int n, int P, long long S,
+                                                float* __restrict__ part, const DevState* st, int gate) {
+    if (gate && st->phase != 0) return;
+    const int npts = DIM == 3 ? n * n * n : n * n;
+    float m = 0.0f;
+    for (int oc = blockIdx.x * blockDim.x + threadIdx.x; oc < npts; oc += gridDim.x * blockDim.x) {
+        const int q = oc / n;
+        const int i = oc - q * n;
+        const int k = DIM == 3 ? q / n : 0;
+        const int j = q - k * n;
+        m = fmaxf(m, fabsf(x[offs<DIM>(i, j, k, P, S)]));
+    }
+    m = block_max<float>(m);
+    if (threadIdx.x == 0) part[blockIdx.x] = m;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_rescale_cast(const float* __restrict__ x, __half* __restrict__ g, int n,
+                                                      int P, long long S, const float* __restrict__ part, int sig,
+                                                      double* __restrict__ scale, const DevState* st, int gate) {
+    if (gate && st->phase != 0) return;
+    float m = 0.0f;
+    for (int t = threadIdx.x; t < kRescaleCtas; t += blockDim.x) m = fmaxf(m, part[t]);
+    const int k = rescale_shift<float>(block_max<float>(m), sig);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *scale = pow2d(-k);
+    const float f = pow2f(k);
+    const int npts = DIM == 3 ? n * n * n : n * n;
+    for (int oc = blockIdx.x * blockDim.x + threadIdx.x; oc < npts; oc += gridDim.x * blockDim.x) {
+        const int q = oc / n;
+        const int i = oc - q * n;
+        const int kz = DIM == 3 ? q / n : 0;
+        const int j = q - kz * n;
+        const long long o = offs<DIM>(i, j, kz, P, S);
+        g[o] = __float2half_rn(x[o] * f);
+    }
+}
+
+int launch_rescale(const float* x, void* g, const Geom& geo, float* part, int sig, double* scale,
+                   const DevState* st, int gate, void* stream) {
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (geo.dim == 3) {
+        k_absmax<3><<<kRescaleCtas, 256, 0, s>>>(x, geo.n, geo.P, geo.S, part, st, gate);
+        k_rescale_cast<3><<<kRescaleCtas, 256, 0, s>>>(x, (__half*)g, geo.n, geo.P, geo.S, part, sig, scale, st, gate);
+    } else {
+        k_absmax<2><<<kRescaleCtas, 256, 0, s>>>(x, geo.n, geo.P, geo.S, part, st, gate);
+        k_rescale_cast<2><<<kRescaleCtas, 256, 0, s>>>(x, (__half*)g, geo.n, geo.P, geo.S, part, sig, scale, st, gate);
     }
     return (int)cudaGetLastError();
 }

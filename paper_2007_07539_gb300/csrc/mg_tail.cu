@@ -16,6 +16,7 @@
 // Arithmetic per level: FP32 for FP16/BF16/FP32 storage, FP64 for FP64.
 #include <cuda_runtime.h>
 
+#include "mg_compact.cuh"
 #include "mg_march.cuh"
 #include "mg_tail.h"
 
@@ -23,48 +24,17 @@ namespace mgi {
 
 template <class T>
 __device__ __forceinline__ typename Tr<T>::C sget(const unsigned char* sm, int off, int p) {
-    const T* a = reinterpret_cast<const T*>(sm + off);
-    if constexpr (std::is_same<T, __half>::value) return __half2float(a[p]);
-    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __bfloat162float(a[p]);
-    else return a[p];
+    return cget(reinterpret_cast<const T*>(sm + off), p);
 }
 template <class T, class V>
 __device__ __forceinline__ void sput(unsigned char* sm, int off, int p, V v) {
     st1(reinterpret_cast<T*>(sm + off) + p, v);
 }
-
-// (i, j, k) of compact point p (x fastest); mn = ceil(2^40 / n), p < 2^13
-__device__ __forceinline__ int divn(int p, unsigned long long mn) {
-    return (int)(((unsigned long long)(unsigned)p * mn) >> 40);
-}
-template <int DIM>
-__device__ __forceinline__ void decode(int p, int n, unsigned long long mn, int& i, int& j, int& k) {
-    const int q = divn(p, mn);
-    i = p - q * n;
-    if (DIM == 3) {
-        k = divn(q, mn);
-        j = q - k * n;
-    } else {
-        j = q;
-        k = 0;
-    }
-}
-
-// sum of the 2*DIM axis neighbours of point p; zero outside the grid
+// sum of the 2*DIM axis neighbours of point p of the array at byte offset off
 template <int DIM, class T>
 __device__ __forceinline__ typename Tr<T>::C nbsum(const unsigned char* sm, int off, int p, int n, int i, int j,
                                                    int k) {
-    using C = typename Tr<T>::C;
-    C s = 0;
-    if (i > 0) s += sget<T>(sm, off, p - 1);
-    if (i < n - 1) s += sget<T>(sm, off, p + 1);
-    if (j > 0) s += sget<T>(sm, off, p - n);
-    if (j < n - 1) s += sget<T>(sm, off, p + n);
-    if (DIM == 3) {
-        if (k > 0) s += sget<T>(sm, off, p - n * n);
-        if (k < n - 1) s += sget<T>(sm, off, p + n * n);
-    }
-    return s;
+    return cnbsum<DIM, T>(reinterpret_cast<const T*>(sm + off), p, n, i, j, k);
 }
 
 // ---- Jacobi family (Alg. 1 smoother; M_ZERO2 / M_ZERO1 start from c = 0)
@@ -126,7 +96,20 @@ __device__ void t_restrict(const TailOp& op, unsigned char* sm) {
             }
             s += (DIM == 3 ? (dk == 1 ? (C)0.5 : (C)0.25) : (C)1) * sj;
         }
-        sput<TC>(sm, op.dst, p, s);
+        if (op.sslot >= 0) reinterpret_cast<C*>(sm + op.scr2)[p] = s;
+        else sput<TC>(sm, op.dst, p, s);
+    }
+    if (op.sslot >= 0) {
+        // restriction into a rescaled FP16 level (DSH_MG, Sec. 6): the coarse
+        // residual times 2^k, max-norm in [2^(rsig-1), 2^rsig), then the cast;
+        // the matching prolongation multiplies by the stored 2^-k
+        const C* v = reinterpret_cast<const C*>(sm + op.scr2);
+        C m = 0;
+        for (int p = threadIdx.x; p < Nc; p += blockDim.x) m = max(m, fabs(v[p]));
+        const int k = rescale_shift<C>(block_max<C>(m), op.rsig);
+        if (threadIdx.x == 0) *reinterpret_cast<double*>(sm + op.sslot) = pow2d(-k);
+        const C f = std::is_same<C, double>::value ? (C)pow2d(k) : (C)pow2f(k);
+        for (int p = threadIdx.x; p < Nc; p += blockDim.x) sput<TC>(sm, op.dst, p, v[p] * f);
     }
 }
 
@@ -136,6 +119,8 @@ __device__ void t_prolong(const TailOp& op, unsigned char* sm) {
     using C = typename Tr<T>::C;
     const int n = op.n, nc = op.nc;
     const int N = DIM == 3 ? n * n * n : n * n;
+    // a rescaled coarse level holds its values times 2^k: the weights carry 2^-k
+    const C sc = op.sslot >= 0 ? (C)*reinterpret_cast<const double*>(sm + op.sslot) : (C)1;
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
         int i, j, k;
         decode<DIM>(p, n, op.mn, i, j, k);
@@ -143,7 +128,7 @@ __device__ void t_prolong(const TailOp& op, unsigned char* sm) {
         const int il = (i - 1) >> 1, ih = i >> 1;  // equal for odd i
         const int jl = (j - 1) >> 1, jh = j >> 1;
         const int kl = DIM == 3 ? (k - 1) >> 1 : 0, kh = DIM == 3 ? k >> 1 : 0;
-        C w = 1;
+        C w = sc;
         if (!(i & 1)) w *= (C)0.5;
         if (!(j & 1)) w *= (C)0.5;
         if (DIM == 3 && !(k & 1)) w *= (C)0.5;
@@ -184,6 +169,21 @@ __device__ void t_coarse(const TailOp& op, unsigned char* sm, const double* minv
     }
 }
 
+// ---- base solve by conjugate gradients in the level's type (op.mode == 1);
+// scratch at op.src: r and p (T), then A p (arithmetic type), 16-byte aligned
+// slots of n^d * 8 bytes each
+template <int DIM, class T>
+__device__ void t_cg(const TailOp& op, unsigned char* sm) {
+    using C = typename Tr<T>::C;
+    const int N = DIM == 3 ? op.n * op.n * op.n : op.n * op.n;
+    const int slot = ((N * 8 + 15) / 16) * 16;
+    T* r = reinterpret_cast<T*>(sm + op.src);
+    T* p = reinterpret_cast<T*>(sm + op.src + slot);
+    C* q = reinterpret_cast<C*>(sm + op.src + 2 * slot);
+    cg_base<DIM, T>(op.n, op.mn, coef<C>(op.cf, 4), reinterpret_cast<const T*>(sm + op.g),
+                    reinterpret_cast<T*>(sm + op.dst), r, p, q, op.cgtol, op.cgmax);
+}
+
 template <int DIM, class T>
 __device__ void t_zero(const TailOp& op, unsigned char* sm) {
     const int N = DIM == 3 ? op.n * op.n * op.n : op.n * op.n;
@@ -214,7 +214,10 @@ __device__ void run_tail_op_t(const TailOp& op, unsigned char* sm, const double*
     switch (op.kind) {
         case TK_SWEEP: t_sweep<DIM, T>(op, sm); return;
         case TK_RESID: t_resid<DIM, T>(op, sm); return;
-        case TK_COARSE: t_coarse<DIM, T>(op, sm, minv, m0); return;
+        case TK_COARSE:
+            if (op.mode == 1) t_cg<DIM, T>(op, sm);
+            else t_coarse<DIM, T>(op, sm, minv, m0);
+            return;
         case TK_ZERO: t_zero<DIM, T>(op, sm); return;
         case TK_LOAD: t_copy<DIM, T>(op, sm, true); return;
         case TK_STORE: t_copy<DIM, T>(op, sm, false); return;

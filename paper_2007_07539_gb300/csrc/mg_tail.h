@@ -16,7 +16,7 @@ enum TailKind : int {
     TK_RESID = 1,     // scratch r = g - A c (arithmetic type)
     TK_RESTRICT = 2,  // coarse g = R r (cast to the coarse storage type)
     TK_PROLONG = 3,   // c += P c_coarse
-    TK_COARSE = 4,    // c = A0^-1 g
+    TK_COARSE = 4,    // c = A0^-1 g (mode 0: dense inverse; mode 1: CG, scratch at src)
     TK_ZERO = 5,      // c = 0
     TK_LOAD = 6,      // shared array <- padded global array
     TK_STORE = 7      // padded global array <- shared array
@@ -33,9 +33,14 @@ struct TailOp {
     int n, nc, P, S;
     int src, g, dst, coarse;
     unsigned long long mn, mnc;
+    int sslot;  // TK_RESTRICT / TK_PROLONG into / from a rescaled FP16 level: byte offset of its scale, else -1
+    int scr2;   // TK_RESTRICT with sslot >= 0: byte offset of the coarse-value scratch
+    int rsig;   // TK_RESTRICT with sslot >= 0: target max-norm 2^rsig (power-of-two range)
+    int cgmax;  // TK_COARSE mode 1 (CG): step limit
     void* gptr;
     double h2inv;
     double omega;
+    double cgtol;  // TK_COARSE mode 1: relative residual tolerance
     SweepCoef cf;  // host-computed sweep coefficients of level n
 };
 static_assert(sizeof(TailOp) % 8 == 0, "TailOp is copied as 8-byte words");

@@ -24,7 +24,8 @@ STATUS = {0: "MG_OK", 1: "MG_BUSY", 2: "MG_ERR_INVALID", 3: "MG_ERR_OOM", 4: "MG
 MG_OK, MG_BUSY = 0, 1
 VEC_C, VEC_G, VEC_T, VEC_U, VEC_R = range(5)
 (STAGE_JACOBI, STAGE_JACOBI_ZERO2, STAGE_RESTRICT, STAGE_PROLONG, STAGE_JACOBI_PROLONG, STAGE_COARSE,
- STAGE_SCALE_ZERO2, STAGE_IR_UPDATE, STAGE_RESIDUAL, STAGE_CYCLE, STAGE_PRE_RESTRICT) = range(11)
+ STAGE_SCALE_ZERO2, STAGE_IR_UPDATE, STAGE_RESIDUAL, STAGE_CYCLE, STAGE_PRE_RESTRICT,
+ STAGE_RESTRICT_RESCALE) = range(12)
 
 # Every symbol declared in include/mg.h.
 EXPORTS = ["mg_params_init", "mg_level_count", "mg_last_error", "mg_footprint_bytes",
@@ -40,7 +41,8 @@ class Params(ctypes.Structure):
                 ("sigma_log2", ctypes.c_int32), ("tol_mode", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("zero_guess", ctypes.c_int32), ("guard", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("no_tail", ctypes.c_int32), ("tune", ctypes.c_int32),
-                ("fuse_pre", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("fuse_pre", ctypes.c_int32), ("rescale16", ctypes.c_int32), ("base_solver", ctypes.c_int32),
+                ("base_maxit", ctypes.c_int32), ("base_tol", ctypes.c_double), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Result(ctypes.Structure):
@@ -64,7 +66,8 @@ class KernelTime(ctypes.Structure):
                 ("launches", ctypes.c_int32), ("threads", ctypes.c_int32), ("grid", ctypes.c_int32 * 3),
                 ("reserved", ctypes.c_int32), ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
-    KIND = ["sweep", "base_solve", "prolong", "zero", "finalize", "ir_update", "scale_cast", "coarse_tail"]
+    KIND = ["sweep", "base_solve", "prolong", "zero", "finalize", "ir_update", "scale_cast", "coarse_tail",
+            "rescale16"]
     MODE = ["jacobi", "jacobi_x2_from_zero", "jacobi_from_zero", "residual_restrict", "pre_smooth_restrict"]
 
     def name(self) -> str:
