@@ -11,9 +11,12 @@
  * Every routine is written directly from the paper's text, in FP64 (double),
  * with no blocking, fusion or reordering beyond what the cited definition says:
  *
- *   or_apply_A        Poisson's equation (Sec. 5, Eq. 1) discretised by the
- *                     finite-difference 5-point (2D) / 7-point (3D) stencil on
- *                     the unit square/cube, zero Dirichlet boundary, h = 1/(n+1)
+ *   or_apply_A_op     Poisson's equation (Sec. 5, Eq. 1) on the unit
+ *                     square/cube, zero Dirichlet boundary, h = 1/(n+1),
+ *                     discretised either by the finite-difference 5-point (2D) /
+ *                     7-point (3D) stencil (op 0) or by bilinear / trilinear Q1
+ *                     finite elements (op 1, Sec. 5), the element matrix
+ *                     assembled from the 1-D element integrals, divided by h^d
  *   or_residual       IR step 1, r = b - A u (Sec. 4.1)
  *   or_jacobi         damped Jacobi smoothing step (Sec. 4.2, smoother paragraph)
  *   or_restrict       restriction of a residual to the next coarser grid
@@ -58,6 +61,7 @@ typedef struct {
     int max_iter;
     int true_residual_guard; /* 1: confirm convergence with b - A u */
     int nthreads;         /* OpenMP threads for stencil loops (<= 0: 1) */
+    int op;               /* 0: finite differences; 1: Q1 finite elements */
 } or_params;
 
 typedef struct {
@@ -88,7 +92,7 @@ static double at(const double *v, int d, int n, int i, int j, int k) {
  * With absmode != 0 the neighbour coefficients are taken as +1: this gives
  * |A| |v|, the magnitude used to scale rounding tolerances.
  */
-void or_apply_A_mode(int d, int n, const double *v, double *out, int absmode) {
+static void apply_fd(int d, int n, const double *v, double *out, int absmode) {
     const double h = 1.0 / (n + 1);
     const double ih2 = 1.0 / (h * h);
     const double sgn = absmode ? 1.0 : -1.0;
@@ -110,29 +114,103 @@ void or_apply_A_mode(int d, int n, const double *v, double *out, int absmode) {
             }
 }
 
-void or_apply_A(int d, int n, const double *v, double *out) { or_apply_A_mode(d, n, v, out, 0); }
-
-/* IR step 1 (Sec. 4.1): r = b - A u. */
-void or_residual(int d, int n, const double *b, const double *u, double *r) {
-    size_t N = npts(d, n);
-    double *au = (double *)malloc(N * sizeof(double));
-    or_apply_A(d, n, u, au);
-    for (size_t p = 0; p < N; ++p) r[p] = b[p] - au[p];
-    free(au);
+/*
+ * Q1 finite elements (Sec. 5: bilinear quadrilaterals in 2D, trilinear
+ * hexahedra in 3D) on the uniform grid.  The basis function of node p is the
+ * product of 1-D hat functions, so the Galerkin entry between nodes p and
+ * p + o (o in {-1, 0, 1}^d) is
+ *     int grad phi_p . grad phi_{p+o} = sum_a K1(o_a) prod_{b != a} M1(o_b)
+ * with K1, M1 the 1-D stiffness and mass integrals of two hats at offset o,
+ * assembled from the element matrices of a linear element of length h.
+ */
+static double q1_stiff1(int o, double h) {
+    const double ke[2][2] = {{1.0 / h, -1.0 / h}, {-1.0 / h, 1.0 / h}};  /* int phi_a' phi_b' over one element */
+    return o == 0 ? ke[0][0] + ke[1][1] : ke[0][1];  /* a node's hat spans two elements */
+}
+static double q1_mass1(int o, double h) {
+    const double me[2][2] = {{h / 3.0, h / 6.0}, {h / 6.0, h / 3.0}};      /* int phi_a phi_b over one element */
+    return o == 0 ? me[0][0] + me[1][1] : me[0][1];
+}
+static double q1_entry(int d, double h, const int *o) {
+    double s = 0.0;
+    for (int a = 0; a < d; ++a) {
+        double t = q1_stiff1(o[a], h);
+        for (int b = 0; b < d; ++b)
+            if (b != a) t *= q1_mass1(o[b], h);
+        s += t;
+    }
+    return s;
 }
 
 /*
- * One damped Jacobi step (Sec. 4.2): out = v + omega D^-1 (g - A v), with
- * D = diag(A) = 2d/h^2.  The update is simultaneous: out must not alias v.
+ * (A v)_p = h^-d sum_o q1_entry(o) v_{p+o}: the Q1 stiffness matrix divided
+ * by the element measure h^d, so that, like the finite-difference operator, it
+ * approximates -Laplace pointwise and its coarse-grid counterpart at 2h equals
+ * the Galerkin product of full weighting, A and interpolation.  absmode: the
+ * absolute values of the entries (|A| |v|).
  */
-void or_jacobi(int d, int n, double omega, const double *g, const double *v, double *out) {
+static void apply_q1(int d, int n, const double *v, double *out, int absmode) {
     const double h = 1.0 / (n + 1);
-    const double dinv = h * h / (2.0 * d);
+    const double scale = 1.0 / pow(h, d);
+    const int nk = d == 3 ? n : 1;
+    const int ok0 = d == 3 ? -1 : 0, ok1 = d == 3 ? 1 : 0;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double s = 0.0;
+                for (int ok = ok0; ok <= ok1; ++ok)
+                    for (int oj = -1; oj <= 1; ++oj)
+                        for (int oi = -1; oi <= 1; ++oi) {
+                            const int o[3] = {oi, oj, ok};
+                            double w = q1_entry(d, h, o);
+                            double x = at(v, d, n, i + oi, j + oj, k + ok);
+                            s += absmode ? fabs(w) * fabs(x) : w * x;
+                        }
+                size_t p = d == 2 ? (size_t)j * n + i : ((size_t)k * n + j) * n + i;
+                out[p] = scale * s;
+            }
+}
+
+/* Diagonal entry of A (the Jacobi D): 2d/h^2 (op 0) or h^-d q1_entry(0). */
+static double diag_A(int op, int d, int n) {
+    const double h = 1.0 / (n + 1);
+    if (op == 0) return 2.0 * d / (h * h);
+    const int o[3] = {0, 0, 0};
+    return q1_entry(d, h, o) / pow(h, d);
+}
+
+void or_apply_A_op(int op, int d, int n, const double *v, double *out, int absmode) {
+    if (op == 1) apply_q1(d, n, v, out, absmode);
+    else apply_fd(d, n, v, out, absmode);
+}
+void or_apply_A_mode(int d, int n, const double *v, double *out, int absmode) { or_apply_A_op(0, d, n, v, out, absmode); }
+void or_apply_A(int d, int n, const double *v, double *out) { or_apply_A_op(0, d, n, v, out, 0); }
+
+/* IR step 1 (Sec. 4.1): r = b - A u. */
+void or_residual_op(int op, int d, int n, const double *b, const double *u, double *r) {
+    size_t N = npts(d, n);
+    double *au = (double *)malloc(N * sizeof(double));
+    or_apply_A_op(op, d, n, u, au, 0);
+    for (size_t p = 0; p < N; ++p) r[p] = b[p] - au[p];
+    free(au);
+}
+void or_residual(int d, int n, const double *b, const double *u, double *r) { or_residual_op(0, d, n, b, u, r); }
+
+/*
+ * One damped Jacobi step (Sec. 4.2): out = v + omega D^-1 (g - A v), with
+ * D = diag(A).  The update is simultaneous: out must not alias v.
+ */
+void or_jacobi_op(int op, int d, int n, double omega, const double *g, const double *v, double *out) {
+    const double dinv = 1.0 / diag_A(op, d, n);
     size_t N = npts(d, n);
     double *av = (double *)malloc(N * sizeof(double));
-    or_apply_A(d, n, v, av);
+    or_apply_A_op(op, d, n, v, av, 0);
     for (size_t p = 0; p < N; ++p) out[p] = v[p] + omega * dinv * (g[p] - av[p]);
     free(av);
+}
+void or_jacobi(int d, int n, double omega, const double *g, const double *v, double *out) {
+    or_jacobi_op(0, d, n, omega, g, v, out);
 }
 
 /* 1-D full-weighting weight of fine offset o in {-1, 0, 1}: [1/4, 1/2, 1/4]. */
@@ -207,7 +285,7 @@ void or_prolong_add(int d, int nc, const double *cc, double *cf) {
  * Cholesky (A is symmetric positive definite) and solve.  Returns 0 on
  * success, -1 if the factorisation breaks down or n^d is too large.
  */
-int or_coarse_solve(int d, int n, const double *g, double *c) {
+int or_coarse_solve_op(int op, int d, int n, const double *g, double *c) {
     size_t m = npts(d, n);
     if (m > 4096) return -1;
     double *A = (double *)calloc(m * m, sizeof(double));
@@ -218,7 +296,7 @@ int or_coarse_solve(int d, int n, const double *g, double *c) {
     g_threads = 1;
     for (size_t q = 0; q < m; ++q) {
         e[q] = 1.0;
-        or_apply_A(d, n, e, col);
+        or_apply_A_op(op, d, n, e, col, 0);
         for (size_t p = 0; p < m; ++p) A[p * m + q] = col[p];
         e[q] = 0.0;
     }
@@ -252,6 +330,7 @@ int or_coarse_solve(int d, int n, const double *g, double *c) {
     free(A); free(e); free(col); free(y);
     return rc;
 }
+int or_coarse_solve(int d, int n, const double *g, double *c) { return or_coarse_solve_op(0, d, n, g, c); }
 
 /* Coarsening rule: n_{l-1} = (n_l - 1)/2 while n_l is odd and > 3.
  * Fills sizes[0..L] with sizes[L] = n (finest) and returns the level count. */
@@ -286,14 +365,15 @@ static int cycle(or_hier *H, const or_params *P, int l) {
     int d = H->d, n = H->n[l];
     size_t N = npts(d, n);
     double *c = H->c[l], *g = H->g[l], *t = H->t[l];
-    if (l == 0) return or_coarse_solve(d, n, g, c);
-    for (int s = 0; s < P->nu1; ++s) { or_jacobi(d, n, P->omega, g, c, t); memcpy(c, t, N * sizeof(double)); }
-    or_residual(d, n, g, c, t);
+    const int op = P->op;
+    if (l == 0) return or_coarse_solve_op(op, d, n, g, c);
+    for (int s = 0; s < P->nu1; ++s) { or_jacobi_op(op, d, n, P->omega, g, c, t); memcpy(c, t, N * sizeof(double)); }
+    or_residual_op(op, d, n, g, c, t);
     or_restrict(d, n, t, H->g[l - 1]);
     memset(H->c[l - 1], 0, npts(d, H->n[l - 1]) * sizeof(double));
     for (int k = 0; k < P->gamma; ++k) { int rc = cycle(H, P, l - 1); if (rc) return rc; }
     or_prolong_add(d, H->n[l - 1], H->c[l - 1], c);
-    for (int s = 0; s < P->nu2; ++s) { or_jacobi(d, n, P->omega, g, c, t); memcpy(c, t, N * sizeof(double)); }
+    for (int s = 0; s < P->nu2; ++s) { or_jacobi_op(op, d, n, P->omega, g, c, t); memcpy(c, t, N * sizeof(double)); }
     return 0;
 }
 
@@ -374,7 +454,8 @@ int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, 
     double *r = (double *)malloc(N * sizeof(double));
     double *ac = (double *)malloc(N * sizeof(double));
     int status = 1;
-    or_residual(d, n, b, u, r);
+    const int op = P->op;
+    or_residual_op(op, d, n, b, u, r);
     double bnorm = or_norm2(N, b);
     res->bnorm = bnorm;
     double scale = P->tol_mode == 0 ? bnorm : 1.0;
@@ -386,7 +467,7 @@ int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, 
         res->rel_res = bnorm > 0 ? rn / bnorm : rn;
         if (rn <= P->tol * scale) {
             if (!P->true_residual_guard) { status = 0; break; }
-            or_residual(d, n, b, u, ac);
+            or_residual_op(op, d, n, b, u, ac);
             double tn = or_norm2(N, ac);
             if (tn <= P->tol * scale) { status = 0; break; }
             memcpy(r, ac, N * sizeof(double));
@@ -406,13 +487,13 @@ int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, 
         memset(c, 0, N * sizeof(double));
         if (cycle(&H, P, H.L)) { status = -1; break; }
         for (size_t p = 0; p < N; ++p) u[p] = u[p] + alpha * c[p];
-        or_apply_A(d, n, c, ac);
+        or_apply_A_op(op, d, n, c, ac, 0);
         for (size_t p = 0; p < N; ++p) r[p] = r[p] - alpha * ac[p];
         ++it;
     }
     res->iters = it;
     res->converged = status == 0;
-    or_residual(d, n, b, u, ac);
+    or_residual_op(op, d, n, b, u, ac);
     res->rel_res_true = bnorm > 0 ? or_norm2(N, ac) / bnorm : or_norm2(N, ac);
     free(r); free(ac);
     hier_free(&H);

@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("scaling", ctypes.c_int),
                 ("tol_mode", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("true_residual_guard", ctypes.c_int),
-                ("nthreads", ctypes.c_int)]
+                ("nthreads", ctypes.c_int), ("op", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -61,13 +61,13 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             i, d = ctypes.c_int, ctypes.c_double
-            lib.or_apply_A_mode.argtypes = [i, i, _D, _D, i]
-            lib.or_residual.argtypes = [i, i, _D, _D, _D]
-            lib.or_jacobi.argtypes = [i, i, d, _D, _D, _D]
+            lib.or_apply_A_op.argtypes = [i, i, i, _D, _D, i]
+            lib.or_residual_op.argtypes = [i, i, i, _D, _D, _D]
+            lib.or_jacobi_op.argtypes = [i, i, i, d, _D, _D, _D]
             lib.or_restrict.argtypes = [i, i, _D, _D]
             lib.or_prolong_add.argtypes = [i, i, _D, _D]
-            lib.or_coarse_solve.argtypes = [i, i, _D, _D]
-            lib.or_coarse_solve.restype = i
+            lib.or_coarse_solve_op.argtypes = [i, i, i, _D, _D]
+            lib.or_coarse_solve_op.restype = i
             lib.or_level_sizes.argtypes = [i, i, ctypes.POINTER(ctypes.c_int)]
             lib.or_level_sizes.restype = i
             lib.or_mg_cycle.argtypes = [ctypes.POINTER(Params), _D, _D]
@@ -94,30 +94,31 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
-def apply_A(v, absmode: bool = False) -> np.ndarray:
-    """A v, the 5/7-point finite-difference -Laplacian (Sec. 5), or |A||v|."""
+def apply_A(v, absmode: bool = False, op: int = 0) -> np.ndarray:
+    """A v, or |A||v|: the 5/7-point finite-difference -Laplacian (op 0) or the
+    Q1 finite-element operator divided by h^d (op 1) (Sec. 5)."""
     v = _f64(v)
     d, n = _dn(v)
     out = np.empty_like(v)
-    _load().or_apply_A_mode(d, n, _p(v), _p(out), 1 if absmode else 0)
+    _load().or_apply_A_op(int(op), d, n, _p(v), _p(out), 1 if absmode else 0)
     return out
 
 
-def residual(b, u) -> np.ndarray:
+def residual(b, u, op: int = 0) -> np.ndarray:
     """r = b - A u (Sec. 4.1, IR step 1)."""
     b, u = _f64(b), _f64(u)
     d, n = _dn(u)
     r = np.empty_like(u)
-    _load().or_residual(d, n, _p(b), _p(u), _p(r))
+    _load().or_residual_op(int(op), d, n, _p(b), _p(u), _p(r))
     return r
 
 
-def jacobi(g, v, omega: float) -> np.ndarray:
+def jacobi(g, v, omega: float, op: int = 0) -> np.ndarray:
     """One damped Jacobi step v + omega D^-1 (g - A v) (Sec. 4.2)."""
     g, v = _f64(g), _f64(v)
     d, n = _dn(v)
     out = np.empty_like(v)
-    _load().or_jacobi(d, n, float(omega), _p(g), _p(v), _p(out))
+    _load().or_jacobi_op(int(op), d, n, float(omega), _p(g), _p(v), _p(out))
     return out
 
 
@@ -141,12 +142,12 @@ def prolong_add(cc, cf) -> np.ndarray:
     return out
 
 
-def coarse_solve(g) -> np.ndarray:
+def coarse_solve(g, op: int = 0) -> np.ndarray:
     """Exact base-level solve A c = g by dense Cholesky (Sec. 4.2)."""
     g = _f64(g)
     d, n = _dn(g)
     c = np.empty_like(g)
-    rc = _load().or_coarse_solve(d, n, _p(g), _p(c))
+    rc = _load().or_coarse_solve_op(int(op), d, n, _p(g), _p(c))
     if rc != 0:
         raise RuntimeError("oracle coarse solve failed")
     return c
@@ -162,9 +163,9 @@ def level_sizes(n: int, levels: int = 0) -> list[int]:
 def make_params(dim: int, n: int, *, levels: int = 0, nu1: int = 2, nu2: int = 2,
                 gamma: int = 1, omega: float = 0.8, scaling: int = 1, tol_mode: int = 0,
                 tol: float = 1e-10, max_iter: int = 100, guard: bool = True,
-                nthreads: int = 1) -> Params:
+                nthreads: int = 1, op: int = 0) -> Params:
     return Params(dim, n, levels, nu1, nu2, gamma, omega, scaling, tol_mode, tol,
-                  max_iter, 1 if guard else 0, nthreads)
+                  max_iter, 1 if guard else 0, nthreads, op)
 
 
 def mg_cycle(g, c0=None, **kw) -> np.ndarray:

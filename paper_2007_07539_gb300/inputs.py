@@ -14,6 +14,10 @@ Recipes (all FP64 on the host, so the oracle and the GPU see identical bits):
   right-hand side of -Laplace(u) = f for u = prod_a sin(k pi x_a) (Sec. 5,
   Eq. 2 of the paper and its 3-D analogue), sampled at the interior grid
   points x = (i+1) h, h = 1/(n+1).
+* ``manufactured_load(dim, n, k)``: the same f integrated against the Q1
+  finite-element basis (the load vector of the paper's FEM discretisation,
+  Sec. 5), divided by h^d, in closed form.
+* ``random_guess``: initial guesses in [0, 1), the paper's choice (Sec. 8.1).
 * batched and serving workloads: log-uniform grid sizes snapped to sizes
   n with n+1 in {2^a, 3*2^a}, the shapes of the paper's grids (Sec. 8.1).
 """
@@ -67,6 +71,16 @@ def sine_product(dim: int, n: int, k: int = 1) -> np.ndarray:
 def manufactured_rhs(dim: int, n: int, k: int = 1) -> np.ndarray:
     """f = -Laplace(u) for u = prod_a sin(k pi x_a): f = dim (k pi)^2 u."""
     return dim * (k * math.pi) ** 2 * sine_product(dim, n, k)
+
+
+def manufactured_load(dim: int, n: int, k: int = 1) -> np.ndarray:
+    """The finite-element load vector of the same f, h^-d times the integral of
+    f against each node's Q1 basis function (a product of 1-D hats), in closed
+    form: a hat of half-width h centred at x_i integrates sin(k pi x) to
+    sin(k pi x_i) * 2 (1 - cos t) / ((k pi)^2 h) with t = k pi h, so
+    b = dim (k pi)^2 prod_a sin(k pi x_a) (2 (1 - cos t) / t^2)^dim."""
+    t = k * math.pi / (n + 1)
+    return manufactured_rhs(dim, n, k) * (2.0 * (1.0 - math.cos(t)) / t ** 2) ** dim
 
 
 def random_rhs(dim: int, n: int, seed: int) -> np.ndarray:

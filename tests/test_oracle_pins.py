@@ -338,3 +338,154 @@ def test_ir_max_iter_reports_not_converged(oracle):
     b = I.random_rhs(2, 31, 26)
     _, info, hist = oracle.ir_solve(b, max_iter=2)
     assert info["status"] == 1 and not info["converged"] and info["iters"] == 2 and len(hist) == 3
+
+
+# ----------------------------------------------------------------------------- Q1 finite elements (op 1)
+def q1_assembled(dim, n):
+    """The Q1 stiffness matrix assembled element by element, each element matrix
+    integrated by 2^d-point Gauss quadrature of grad(phi_i) . grad(phi_j) over the
+    bilinear / trilinear shape functions of the reference cell mapped to an h-cube;
+    Dirichlet nodes dropped; divided by h^d.  A route independent of the 1-D
+    product form the oracle uses."""
+    h = 1.0 / (n + 1)
+    gp = np.array([-1.0, 1.0]) / math.sqrt(3.0)  # Gauss points on [-1, 1], weights 1
+    corners = [tuple((c >> a) & 1 for a in range(dim)) for c in range(2 ** dim)]
+    Ke = np.zeros((2 ** dim, 2 ** dim))
+    for q in np.array(np.meshgrid(*([gp] * dim), indexing="ij")).reshape(dim, -1).T:
+        grads = []
+        for c in corners:  # shape function prod_a (1 + s_a xi_a)/2, s = +-1
+            s = [2 * ca - 1 for ca in c]
+            g = []
+            for a in range(dim):
+                t = s[a] / 2.0
+                for b in range(dim):
+                    if b != a:
+                        t *= (1 + s[b] * q[b]) / 2.0
+                g.append(t * 2.0 / h)  # d xi / d x = 2 / h
+            grads.append(g)
+        G = np.array(grads)
+        Ke += (G @ G.T) * (h / 2.0) ** dim  # Jacobian of the map
+    N = n ** dim
+    A = np.zeros((N, N))
+    for e in np.ndindex(*([n + 1] * dim)):  # element e spans nodes e .. e+1 (node 0 = boundary)
+        idx = []
+        for c in corners:
+            node = [e[a] + c[a] - 1 for a in range(dim)]  # interior index, -1 / n are boundary
+            idx.append(None if any(v < 0 or v >= n for v in node) else
+                       sum(node[a] * n ** a for a in range(dim)))
+        for i, p in enumerate(idx):
+            if p is None:
+                continue
+            for j, q in enumerate(idx):
+                if q is not None:
+                    A[p, q] += Ke[i, j]
+    return A / h ** dim
+
+
+def q1_symbol(dim, n, ms):
+    """Eigenvalue of the h^-d-scaled Q1 operator on the sampled sine mode ms:
+    h^-d sum_a k(t_a) prod_{b != a} m(t_b), k(t) = (2 - 2 cos t)/h, m(t) = h (4 + 2 cos t)/6,
+    t = m pi h (the Fourier symbols of the 1-D stiffness and mass stencils)."""
+    h = 1.0 / (n + 1)
+    t = [m * math.pi * h for m in ms]
+    k = [(2 - 2 * math.cos(x)) / h for x in t]
+    mm = [h * (4 + 2 * math.cos(x)) / 6 for x in t]
+    lam = 0.0
+    for a in range(dim):
+        v = k[a]
+        for b in range(dim):
+            if b != a:
+                v *= mm[b]
+        lam += v
+    return lam / h ** dim
+
+
+@pytest.mark.parametrize("dim,n", [(2, 5), (2, 8), (3, 3), (3, 5)])
+def test_q1_matches_quadrature_assembly(oracle, dim, n):
+    A = q1_assembled(dim, n)
+    v = I.uniform(71, (n,) * dim)
+    ref = (A @ v.ravel()).reshape(v.shape)
+    assert np.abs(oracle.apply_A(v, op=1) - ref).max() <= 1e-12 * np.abs(ref).max()
+    absref = (np.abs(A) @ np.abs(v).ravel()).reshape(v.shape)
+    assert np.abs(oracle.apply_A(v, absmode=True, op=1) - absref).max() <= 1e-12 * absref.max()
+    g = I.uniform(72, (n,) * dim)
+    ref = np.linalg.solve(A, g.ravel()).reshape(g.shape)
+    assert np.abs(oracle.coarse_solve(g, op=1) - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_q1_stencil_weights(oracle):
+    """The interior rows: 2D h^-2 [8/3 centre, -1/3 x 8]; 3D h^-2 [8/3 centre, 0 faces,
+    -1/6 edges, -1/12 corners] (row sums zero)."""
+    for dim, n in ((2, 5), (3, 5)):
+        h = 1.0 / (n + 1)
+        e = np.zeros((n,) * dim)
+        e[(2,) * dim] = 1.0
+        col = oracle.apply_A(e, op=1) * h * h
+        c = (2,) * dim
+        assert col[c] == pytest.approx(8 / 3, rel=1e-14)
+        for off in np.ndindex(*([3] * dim)):
+            o = tuple(x - 1 for x in off)
+            nz = sum(1 for x in o if x)
+            if nz == 0:
+                continue
+            want = -1 / 3 if dim == 2 else {1: 0.0, 2: -1 / 6, 3: -1 / 12}[nz]
+            assert col[tuple(ci + oi for ci, oi in zip(c, o))] == pytest.approx(want, abs=1e-14)
+        assert abs(col.sum()) <= 1e-13
+
+
+@pytest.mark.parametrize("dim,n,ms", [(2, 7, (1, 1)), (2, 16, (3, 5)), (3, 7, (1, 2, 3)), (3, 12, (11, 1, 5))])
+def test_q1_eigenvector_closed_form(oracle, dim, n, ms):
+    v = mode(dim, n, ms)
+    lam = q1_symbol(dim, n, ms)
+    assert np.abs(oracle.apply_A(v, op=1) - lam * v).max() <= 1e-13 * lam * np.abs(v).max()
+
+
+@pytest.mark.parametrize("dim,nc", [(2, 3), (2, 7), (3, 3)])
+def test_q1_coarse_operator_is_galerkin(oracle, dim, nc):
+    """With the h^-d scaling, full weighting R and interpolation P = 2^d R^T, the
+    re-discretised coarse operator equals R A_h P exactly."""
+    nf = 2 * nc + 1
+
+    def dense(n):
+        N = n ** dim
+        M = np.zeros((N, N))
+        for q in range(N):
+            e = np.zeros(N)
+            e[q] = 1.0
+            M[:, q] = oracle.apply_A(e.reshape((n,) * dim), op=1).ravel()
+        return M
+    R = fw(dim, nf).toarray()
+    RAP = R @ dense(nf) @ (2 ** dim * R.T)
+    A2h = dense(nc)
+    assert np.abs(RAP - A2h).max() <= 1e-12 * np.abs(A2h).max()
+
+
+def test_q1_jacobi_eigen_factor(oracle):
+    """Damped Jacobi with D = 8/3 h^-2 (both dimensions) multiplies a mode by 1 - omega lambda / D."""
+    for dim, n, ms in ((2, 15, (3, 7)), (3, 7, (7, 1, 4))):
+        h = 1.0 / (n + 1)
+        v = mode(dim, n, ms)
+        fac = 1.0 - 0.8 * q1_symbol(dim, n, ms) / (8.0 / 3.0 / h ** 2)
+        assert np.abs(oracle.jacobi(np.zeros_like(v), v, 0.8, op=1) - fac * v).max() <= 1e-13
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, 31, 1), (2, 63, 3), (3, 15, 1), (3, 31, 2)])
+def test_q1_ir_manufactured_discrete_solution_exact(oracle, dim, n, k):
+    """The Q1 load vector of f = d (k pi)^2 prod sin(k pi x) is a multiple of the
+    sampled mode, so the discrete solution is b / lambda in closed form."""
+    b = I.manufactured_load(dim, n, k)
+    lam = q1_symbol(dim, n, (k,) * dim)
+    uh = b / lam
+    u, info, _ = oracle.ir_solve(b, op=1)
+    assert info["converged"] and info["rel_res_true"] <= 1e-10
+    assert np.abs(u - uh).max() <= 1e-9 * np.abs(uh).max()
+    ustar = I.sine_product(dim, n, k)
+    err = np.abs(u - ustar).max() / np.abs(ustar).max()
+    assert err <= (k * math.pi / (n + 1)) ** 2  # O(h^2) nodal error
+
+
+def test_q1_ir_iteration_count_grid_independent(oracle):
+    its = [oracle.ir_solve(I.random_rhs(3, n, 73), op=1)[1]["iters"] for n in (15, 31)]
+    assert max(its) <= 25 and max(its) - min(its) <= 2
+    its2 = [oracle.ir_solve(I.random_rhs(2, n, 74), op=1)[1]["iters"] for n in (31, 63, 127)]
+    assert max(its2) <= 25 and max(its2) - min(its2) <= 2
