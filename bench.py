@@ -271,6 +271,35 @@ def extra_workloads(mg, I, torch, flush, quick=False):
     del b, u
     torch.cuda.empty_cache()
 
+    # ---- the paper's discretisation (Sec. 5): Q1 finite elements (27-point), 255^3.
+    # (a) Table 2's variants on the random right-hand side from u0 = 0; (b) Table 3's
+    # setting: manufactured load with k = 1 and 20, initial guess uniform in [0, 1),
+    # IR steps to ||r||_2 <= 1e-10 ||b||_2 per variant
+    n = 255
+    b = torch.from_numpy(I.random_rhs(3, n, 2)).cuda()
+    u = torch.zeros_like(b)
+    q1 = {}
+    for name, (lad, kw) in variants.items():
+        with mg.Hierarchy(mg.make_params(3, n, lad, zero_guess=1, tune=1, op=1, **kw)) as h:
+            solve_ms(h, b, u, 1)
+            t, r = solve_ms(h, b, u, 1 if quick else 3)
+        q1[name] = {"ms": t, "iters": r["iters"], "dofs": n ** 3 / (t * 1e-3), "rel_res_true": r["rel_res_true"]}
+    for name in q1:
+        q1[name]["speedup_vs_D_MG"] = q1["D_MG"]["ms"] / q1[name]["ms"]
+    iters = {}
+    u0 = torch.from_numpy(I.random_guess(3, n, 3)).cuda()
+    for k in (1, 20):
+        bk = torch.from_numpy(I.manufactured_load(3, n, k)).cuda()
+        for name, (lad, kw) in variants.items():
+            with mg.Hierarchy(mg.make_params(3, n, lad, op=1, **kw)) as h:
+                u.copy_(u0)
+                r = h.solve(bk, u)
+            iters[f"k{k}_{name}"] = r["iters"]
+    out["q1_fem_255"] = {"operator": "trilinear Q1 elements, 27-point, stiffness / h^3", "variants": q1,
+                         "iters_manufactured_random_u0": iters}
+    del b, u, u0
+    torch.cuda.empty_cache()
+
     # ---- batched: 64 independent instances in one mg_solve_batch call
     work = I.batched_workload(count=16 if quick else 64)
     hs = [mg.Hierarchy(mg.make_params(3, nn, "H", zero_guess=1, tune=1)) for nn, _ in work]

@@ -16,9 +16,11 @@
  *     alpha = ||r||; r_low = (1/alpha) r_high; one cycle gives c_low;
  *     u += alpha c_low; r -= alpha A c_low, with r, u and the stopping test in FP64.
  *   - Model problem, Sec. 5 (Eq. 1): -Laplace(u) = f on the unit square/cube,
- *     u = 0 on the boundary.  Here discretised by the 5-point (2D) / 7-point
- *     (3D) finite-difference stencil on n interior points per dimension,
- *     h = 1/(n+1):  (A u)_p = h^-2 (2d u_p - sum of the 2d axis neighbours).
+ *     u = 0 on the boundary, on n interior points per dimension, h = 1/(n+1).
+ *     Discretised by the 5-point (2D) / 7-point (3D) finite-difference stencil,
+ *     (A u)_p = h^-2 (2d u_p - sum of the 2d axis neighbours) (op = 0), or by
+ *     the paper's bilinear / trilinear Q1 finite elements (op = 1, 9/27-point,
+ *     the stiffness matrix divided by h^d; see mg_params.op).
  *
  * Conventions for every entry point:
  *   - Grid vectors passed by the caller (b, u) are interior-only, contiguous,
@@ -113,7 +115,16 @@ typedef struct mg_params {
                            or base_maxit steps */
     int32_t base_maxit; /* CG step limit, at most 100000; 0 = the number of base-level unknowns */
     double base_tol;    /* CG relative tolerance; default 1e-4 */
-    int32_t reserved[2];/* must be 0 */
+    int32_t op;         /* discretisation of -Laplace (Sec. 5): 0 (default) finite differences,
+                           5-point (2D) / 7-point (3D), A = h^-2 (2d I - axis neighbours);
+                           1 bilinear / trilinear Q1 finite elements, the stiffness matrix
+                           divided by h^d: 2D A = h^-2/3 (8 I - the 8 neighbours), 3D
+                           A = h^-2/12 (32 I - 2 x the 12 edge - the 8 corner neighbours).
+                           b is then the load vector divided by h^d.  Coarse levels use the
+                           same operator at their h (for Q1 this equals the Galerkin
+                           product of full weighting, A and interpolation).  op = 1
+                           requires fuse_pre = 0 */
+    int32_t reserved[1];/* must be 0 */
 } mg_params;
 
 /* Outcome of one solve. */
@@ -234,7 +245,7 @@ mg_status mg_axpy(int32_t prec, int64_t n, double a, const void* x, void* y, voi
  * synchronise the device and stall other streams.  mg_solve and the stage
  * calls allocate (hierarchy buffers, staging); this call does not.
  *
- * Computes, for the operator A of this library (5/7-point, h = 1/(n+1)):
+ * Computes, for the finite-difference operator A (op = 0: 5/7-point, h = 1/(n+1)):
  *   norms[0] = ||b - A u||_2,  norms[1] = ||b - A u||_inf,  norms[2] = ||b||_2
  * b, u: n^d FP64 values, contiguous, x fastest, device memory, read only.
  * norms: 3 doubles of device memory, written.  All three must be device

@@ -169,7 +169,8 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
             break;
         }
         case MG_STAGE_PRE_RESTRICT: {
-            if (level < 1 || h->dim != 3) SFAIL(MG_ERR_INVALID, "the one-pass pre-smoothing needs 3D and level >= 1");
+            if (level < 1 || h->dim != 3 || h->p.op != 0)
+                SFAIL(MG_ERR_INVALID, "the one-pass pre-smoothing needs 3D, level >= 1 and the finite-difference operator");
             Op op = mgi_kernel_op(*h, level, K_SWEEP, M_PRE, lv.g, h->lv[level - 1].g, lv.g, 0, nullptr);
             op.a.dst2 = lv.c;
             rc = mgi_run_op(*h, op, s);
@@ -263,7 +264,8 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
             a.n = g.n; a.P = g.P; a.S = g.S;
             a.u = h->u; a.b = (const double*)ptr_arg; a.r = h->r; a.partials = h->partials;
             a.need_b = 1;
-            a.h2inv = (double)(g.n + 1) * (double)(g.n + 1);
+            a.h2inv = op_alpha(h->p.op, h->dim, g.n);
+            a.op = h->p.op;
             int nb = 0;
             rc = launch_residual64(h->dim, a, &nb, s);
             if (!rc) {

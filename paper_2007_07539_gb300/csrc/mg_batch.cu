@@ -206,7 +206,8 @@ void residual_ops(const std::vector<mgi_hier*>& hs, Image& img, int gate, bool c
             it.a.use_st_uout = copy_u ? 1 : 0;
             it.a.need_b = fin_kind == FIN_INIT;
             it.a.gate = gate;
-            it.a.h2inv = (double)(g.n + 1) * (double)(g.n + 1);
+            it.a.h2inv = op_alpha(h.p.op, h.dim, g.n);
+            it.a.op = h.p.op;
             it.ncta = residual64_ctas(h.dim, g.n);
             it.cta_begin = (int)table.size();
             for (int c = 0; c < it.ncta; ++c) table.push_back((int)items.size());

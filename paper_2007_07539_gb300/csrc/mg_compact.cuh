@@ -52,6 +52,37 @@ __device__ __forceinline__ typename Tr<T>::C cnbsum(const T* a, int p, int n, in
     return s;
 }
 
+// W of the Q1 operator at compact point p: weight 1 on the 8 neighbours (2D);
+// 2 on the 12 edge and 1 on the 8 corner neighbours, 0 on the 6 faces (3D)
+template <int DIM, class T>
+__device__ __forceinline__ typename Tr<T>::C cwsum_q1(const T* a, int p, int n, int i, int j, int k) {
+    using C = typename Tr<T>::C;
+    C s1 = 0, s2 = 0;  // weight-1 and weight-2 sums
+#pragma unroll
+    for (int dk = (DIM == 3 ? -1 : 0); dk <= (DIM == 3 ? 1 : 0); ++dk)
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) {
+                const int nz = (di != 0) + (dj != 0) + (dk != 0);
+                if (nz == 0 || (DIM == 3 && nz == 1)) continue;
+                if (i + di < 0 || i + di >= n || j + dj < 0 || j + dj >= n || k + dk < 0 || k + dk >= (DIM == 3 ? n : 1))
+                    continue;
+                const C v = cget(a, p + di + dj * n + dk * n * n);
+                if (DIM == 3 && nz == 2) s2 += v;
+                else s1 += v;
+            }
+    return (C)2 * s2 + s1;
+}
+// beta of operator op (the centre weight of beta I - W)
+template <int DIM>
+__device__ __forceinline__ int op_beta_d(int op) { return op == 1 ? (DIM == 3 ? 32 : 8) : 2 * DIM; }
+// W of operator op (0: the 2d axis neighbours, 1: Q1)
+template <int DIM, class T>
+__device__ __forceinline__ typename Tr<T>::C cwsum(int op, const T* a, int p, int n, int i, int j, int k) {
+    return op == 1 ? cwsum_q1<DIM, T>(a, p, n, i, j, k) : cnbsum<DIM, T>(a, p, n, i, j, k);
+}
+
 // Block-wide sum / max; every thread receives the result.  Fixed reduction
 // tree (lane shuffles, then the warps' values in warp order): the same inputs
 // give the same bits on every run.  All threads of the CTA must call.
@@ -101,19 +132,18 @@ __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) 
 __device__ __forceinline__ double pow2d(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
 
 // ---- conjugate gradients on the base level (Sec. 6: CG base solver)
-// A = h^-2 (2 DIM on the centre, -1 per axis neighbour) on n^DIM compact
-// points, from x = 0: x, r, p are stored in the level type T, A p (q) and the
-// dot products are taken in the arithmetic type C.  Stops when
+// A = alpha (beta I - W) of operator op on n^DIM compact points, from x = 0:
+// x, r, p are stored in the level type T, A p (q) and the dot products are
+// taken in the arithmetic type C.  Stops when
 // ||r||_2 <= tol ||g||_2 (recursively updated r) or after maxit steps, or when
 // p^T A p is not positive (breakdown, also for g = 0).  Called by every thread
 // of one CTA; returns the steps taken.
 template <int DIM, class T>
-__device__ int cg_base(int n, unsigned long long mn, typename Tr<T>::C h2inv, const T* __restrict__ g,
-                       T* __restrict__ x, T* __restrict__ r, T* __restrict__ p, typename Tr<T>::C* __restrict__ q,
-                       double tol, int maxit) {
+__device__ int cg_base(int n, unsigned long long mn, int op, typename Tr<T>::C alpha, typename Tr<T>::C beta,
+                       const T* __restrict__ g, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p,
+                       typename Tr<T>::C* __restrict__ q, double tol, int maxit) {
     using C = typename Tr<T>::C;
     const int N = DIM == 3 ? n * n * n : n * n;
-    const C twod = (C)(2 * DIM);
     C rr = 0;
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
         x[t] = T(0.0f);
@@ -131,7 +161,7 @@ __device__ int cg_base(int n, unsigned long long mn, typename Tr<T>::C h2inv, co
             int i, j, k;
             decode<DIM>(t, n, mn, i, j, k);
             const C pv = cget(p, t);
-            const C qv = h2inv * (twod * pv - cnbsum<DIM, T>(p, t, n, i, j, k));
+            const C qv = alpha * (beta * pv - cwsum<DIM, T>(op, p, t, n, i, j, k));
             q[t] = qv;
             pq += pv * qv;
         }

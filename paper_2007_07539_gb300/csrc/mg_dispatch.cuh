@@ -8,8 +8,29 @@ namespace mgi {
 using KFn = void (*)(KArgs);
 using KFn3 = void (*)(KArgs, SweepMaps);  // 3D sweeps (TMA descriptors by value)
 
+// Q1 variants (mode | M_FEM): one row per warp; M_ZERO1 (c = w D^-1 g) does
+// not apply the operator and shares the finite-difference kernel.
+template <class T>
+KFn3 pick_sweep3_q1(int mode, int prec_c, int rpw) {
+    if (rpw != 1) return nullptr;
+    switch (mode & M_BASE) {
+        case M_JACOBI: return &k_sweep3<M_JACOBI, T, T, 1, 1>;
+        case M_ZERO2: return &k_sweep3<M_ZERO2, T, T, 1, 1>;
+        case M_ZERO1: return &k_sweep3<M_ZERO1, T, T, 1>;
+        case M_RESTRICT:
+            switch (prec_c) {
+                case MG_FP64: return &k_sweep3<M_RESTRICT, T, double, 1, 1>;
+                case MG_FP32: return &k_sweep3<M_RESTRICT, T, float, 1, 1>;
+                case MG_FP16: return &k_sweep3<M_RESTRICT, T, __half, 1, 1>;
+                case MG_BF16: return &k_sweep3<M_RESTRICT, T, __nv_bfloat16, 1, 1>;
+            }
+    }
+    return nullptr;
+}
+
 template <class T>
 KFn3 pick_sweep3(int mode, int prec_c, int rpw) {
+    if (mode & M_FEM) return pick_sweep3_q1<T>(mode, prec_c, rpw);
     switch (mode) {
         case M_JACOBI: return rpw == 2 ? &k_sweep3<M_JACOBI, T, T, 2> : &k_sweep3<M_JACOBI, T, T, 1>;
         case M_ZERO2: return rpw == 2 ? &k_sweep3<M_ZERO2, T, T, 2> : &k_sweep3<M_ZERO2, T, T, 1>;
@@ -37,22 +58,24 @@ KFn3 pick_sweep3(int mode, int prec_c, int rpw) {
 
 template <int DIM, class T, class TC>
 KFn pick_tc(int kind, int mode) {
-    if (kind == K_SWEEP && mode == M_RESTRICT && DIM == 2) return &k_sweep2<M_RESTRICT, T, TC>;
+    if (kind == K_SWEEP && (mode & M_BASE) == M_RESTRICT && DIM == 2)
+        return (mode & M_FEM) ? &k_sweep2<M_RESTRICT, T, TC, 1> : &k_sweep2<M_RESTRICT, T, TC, 0>;
     if (kind == K_PROLONG) return &k_prolong<DIM, T, TC>;
     return nullptr;
 }
 
 template <int DIM, class T>
 KFn pick(int kind, int mode, int prec_c) {
+    const bool q1 = (mode & M_FEM) != 0;
     if (kind == K_SWEEP && DIM == 2) {
-        switch (mode) {
-            case M_JACOBI: return &k_sweep2<M_JACOBI, T, T>;
-            case M_ZERO2: return &k_sweep2<M_ZERO2, T, T>;
-            case M_ZERO1: return &k_sweep2<M_ZERO1, T, T>;
+        switch (mode & M_BASE) {
+            case M_JACOBI: return q1 ? &k_sweep2<M_JACOBI, T, T, 1> : &k_sweep2<M_JACOBI, T, T, 0>;
+            case M_ZERO2: return q1 ? &k_sweep2<M_ZERO2, T, T, 1> : &k_sweep2<M_ZERO2, T, T, 0>;
+            case M_ZERO1: return &k_sweep2<M_ZERO1, T, T, 0>;
             default: break;
         }
     }
-    if (kind == K_UPDATE) return &k_update<DIM, T>;
+    if (kind == K_UPDATE) return q1 ? &k_update<DIM, T, 1> : &k_update<DIM, T, 0>;
     if (kind == K_SCALE) return &k_scale_cast<DIM, T>;
     switch (prec_c) {
         case MG_FP64: return pick_tc<DIM, T, double>(kind, mode);
@@ -95,6 +118,22 @@ int launch_batch_t(int kind, int mode, int prec_c, int rpw, const void* items, c
     if (kind == K_SWEEP) {
         using FB = void (*)(const SweepItem*, const int*);
         FB f = nullptr;
+        if (mode & M_FEM) {  // Q1: one row per warp
+            if (rpw != 1) return (int)cudaErrorInvalidValue;
+            switch (mode & M_BASE) {
+                case M_JACOBI: f = &k_sweep3_batch<M_JACOBI, T, T, 1, 1>; break;
+                case M_ZERO2: f = &k_sweep3_batch<M_ZERO2, T, T, 1, 1>; break;
+                case M_ZERO1: f = &k_sweep3_batch<M_ZERO1, T, T, 1>; break;
+                case M_RESTRICT:
+                    switch (prec_c) {
+                        case MG_FP64: f = &k_sweep3_batch<M_RESTRICT, T, double, 1, 1>; break;
+                        case MG_FP32: f = &k_sweep3_batch<M_RESTRICT, T, float, 1, 1>; break;
+                        case MG_FP16: f = &k_sweep3_batch<M_RESTRICT, T, __half, 1, 1>; break;
+                        case MG_BF16: f = &k_sweep3_batch<M_RESTRICT, T, __nv_bfloat16, 1, 1>; break;
+                    }
+                    break;
+            }
+        } else
         switch (mode) {
             case M_JACOBI: f = rpw == 2 ? &k_sweep3_batch<M_JACOBI, T, T, 2> : &k_sweep3_batch<M_JACOBI, T, T, 1>; break;
             case M_ZERO2: f = rpw == 2 ? &k_sweep3_batch<M_ZERO2, T, T, 2> : &k_sweep3_batch<M_ZERO2, T, T, 1>; break;
@@ -127,7 +166,7 @@ int launch_batch_t(int kind, int mode, int prec_c, int rpw, const void* items, c
     }
     using FK = void (*)(const KItem*, const int*);
     FK f = nullptr;
-    if (kind == K_UPDATE) f = &k_update_batch<3, T>;
+    if (kind == K_UPDATE) f = (mode & M_FEM) ? &k_update_batch<3, T, 1> : &k_update_batch<3, T, 0>;
     else if (kind == K_SCALE) f = &k_scale_cast_batch<3, T>;
     else if (kind == K_PROLONG) {
         switch (prec_c) {

@@ -113,8 +113,9 @@ int mgi_validate(const mg_params* p, std::string& why) {
     }
     if (p->base_maxit < 0 || p->base_maxit > 100000) { why = "base_maxit out of range (0..100000)"; return 0; }
     if (!(p->base_tol >= 0.0) || !std::isfinite(p->base_tol)) { why = "base_tol must be finite and >= 0"; return 0; }
-    for (int i = 0; i < 2; ++i)
-        if (p->reserved[i] != 0) { why = "reserved fields must be 0"; return 0; }
+    if (p->op != 0 && p->op != 1) { why = "op must be 0 (finite differences) or 1 (Q1 finite elements)"; return 0; }
+    if (p->op == 1 && p->fuse_pre == 1) { why = "fuse_pre is for the finite-difference operator (op = 0)"; return 0; }
+    if (p->reserved[0] != 0) { why = "reserved fields must be 0"; return 0; }
     return L;
 }
 
@@ -160,23 +161,30 @@ static void compute_layout(mgi_hier& h, Layout& lay) {
 }
 
 // ---------------------------------------------------------------- base-level operator inverse
-// Dense A0 of the 5/7-point operator on the coarsest grid, inverted by
-// Gauss-Jordan elimination with partial pivoting in FP64 (host, at setup).
-static bool coarse_inverse(int dim, int n, std::vector<double>& inv) {
+// Dense A0 = alpha (beta I - W) of the base level's operator (op 0: 5/7-point
+// finite differences; op 1: Q1, weights 1 on the 8 neighbours in 2D, 2 on
+// edges and 1 on corners in 3D), inverted by Gauss-Jordan elimination with
+// partial pivoting in FP64 (host, at setup).
+static bool coarse_inverse(int dim, int op, int n, std::vector<double>& inv) {
     int m = 1;
     for (int a = 0; a < dim; ++a) m *= n;
-    const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+    const double alpha = op_alpha(op, dim, n);
     std::vector<double> A((size_t)m * m, 0.0);
     for (int p = 0; p < m; ++p) {
-        int i = p % n, j = (p / n) % n, k = p / (n * n);
-        A[(size_t)p * m + p] = 2.0 * dim * ih2;
-        int c[3] = {i, j, k};
-        int stride[3] = {1, n, n * n};
-        for (int a = 0; a < dim; ++a)
-            for (int s = -1; s <= 1; s += 2) {
-                int v = c[a] + s;
-                if (v >= 0 && v < n) A[(size_t)p * m + p + s * stride[a]] = -ih2;
-            }
+        const int i = p % n, j = (p / n) % n, k = p / (n * n);
+        for (int dk = (dim == 3 ? -1 : 0); dk <= (dim == 3 ? 1 : 0); ++dk)
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    const int nz = (di != 0) + (dj != 0) + (dk != 0);
+                    int w;  // the weight of the offset in beta I - W
+                    if (nz == 0) w = op_beta(op, dim);
+                    else if (op == 0) w = nz == 1 ? -1 : 0;
+                    else w = dim == 2 ? -1 : (nz == 2 ? -2 : nz == 3 ? -1 : 0);
+                    if (w == 0) continue;
+                    const int ii = i + di, jj = j + dj, kk = k + dk;
+                    if (ii < 0 || ii >= n || jj < 0 || jj >= n || kk < 0 || kk >= (dim == 3 ? n : 1)) continue;
+                    A[(size_t)p * m + (size_t)(ii + n * jj + n * n * kk)] = alpha * w;
+                }
     }
     inv.assign((size_t)m * m, 0.0);
     for (int i = 0; i < m; ++i) inv[(size_t)i * m + i] = 1.0;
@@ -227,6 +235,8 @@ struct Gen {
         op.kind = OP_KERNEL;
         op.level = l;
         op.kkind = kkind;
+        // stencil kernels of a Q1 hierarchy: the Q1 variants
+        if (h->p.op == 1 && (kkind == K_SWEEP || kkind == K_UPDATE)) mode |= M_FEM;
         op.mode = mode;
         op.prec = h->lv[l].prec;
         op.prec_c = l > 0 ? h->lv[l - 1].prec : op.prec;
@@ -239,8 +249,8 @@ struct Gen {
         a.u64 = h->u; a.rw64 = h->r; a.partials = h->partials;
         a.st = st; a.gate = gate;
         a.omega = h->p.omega;
-        a.h2inv = (double)(f.n + 1) * (double)(f.n + 1);
-        a.cf = make_sweep_coef(h->dim, a.omega, a.h2inv);
+        a.h2inv = op_alpha(h->p.op, h->dim, f.n);
+        a.cf = make_sweep_coef(h->dim, h->p.op, a.omega, a.h2inv);
         op.sh = kernel_shape(h->dim, kkind, mode, op.prec, f.n, f.P, 0);
         a.xstep = op.sh.xstep; a.ystep = op.sh.ystep; a.zstep = op.sh.zstep; a.zlen = op.sh.zlen;
         a.err = &h->st->kerr;
@@ -285,9 +295,10 @@ struct Gen {
         t.n = f.n; t.P = f.P; t.S = (int)f.S;
         t.mn = tail_magic(f.n);
         if (l > 0) { t.nc = h->lv[l - 1].geo.n; t.mnc = tail_magic(t.nc); }
-        t.h2inv = (double)(f.n + 1) * (double)(f.n + 1);
+        t.h2inv = op_alpha(h->p.op, h->dim, f.n);
         t.omega = h->p.omega;
-        t.cf = make_sweep_coef(h->dim, t.omega, t.h2inv);
+        t.cf = make_sweep_coef(h->dim, h->p.op, t.omega, t.h2inv);
+        t.op = h->p.op;
         t.sslot = -1;
         t.scr2 = -1;
         t.rsig = h->rsig;
@@ -514,8 +525,8 @@ int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
                                  op.has_maps ? &op.maps : nullptr, s);
         case OP_COARSE:
             if (h.p.base_solver == 1)
-                return launch_coarse_cg(op.prec, op.g, op.c, h.lv[0].geo, h.p.base_tol, h.cg_maxit(), op.a.st,
-                                        op.a.gate, s);
+                return launch_coarse_cg(op.prec, h.p.op, op.g, op.c, h.lv[0].geo, h.p.base_tol, h.cg_maxit(),
+                                        op.a.st, op.a.gate, s);
             return launch_coarse_solve(op.prec, h.minv, h.m0, op.g, op.c, h.lv[0].geo, op.a.st, op.a.gate, s);
         case OP_RESCALE:
             if (!h.rsc_alloc) return (int)cudaErrorInvalidValue;
@@ -659,8 +670,9 @@ static void autotune(mgi_hier& h) {
         cold = 3.0 * (double)lv.geo.total * (double)lv.esz > 32.0 * 1048576.0;
         for (int mode : {M_PRE, M_ZERO2, M_RESTRICT, M_JACOBI}) {
             if (mode == M_PRE && h.p.fuse_pre != 1) continue;
+            const int kmode = mode | (h.p.op == 1 ? M_FEM : 0);  // the key of the kernel's shapes
             TileChoice have;
-            if (tile_choice_get(3, K_SWEEP, mode, lv.prec, n, &have)) continue;
+            if (tile_choice_get(3, K_SWEEP, kmode, lv.prec, n, &have)) continue;
             const bool coarse_out = mode == M_RESTRICT || mode == M_PRE;
             const void* src = mode == M_ZERO2 || mode == M_PRE ? lv.g : lv.c;
             void* dst = coarse_out ? h.lv[l - 1].g : (mode == M_ZERO2 ? lv.c : lv.t);
@@ -679,17 +691,17 @@ static void autotune(mgi_hier& h) {
             // (timing noise of short kernels is a few percent)
             tbest *= 0.97f;
             for (int rpw = 1; rpw <= 2; ++rpw) {
-                if (rpw == 2 && (coarse_out || n < 16)) continue;
+                if (rpw == 2 && (coarse_out || n < 16 || h.p.op == 1)) continue;
                 for (int z : {z0 / 2, z0, z0 * 2}) {
                     z = std::max(1, std::min(z, zmax));
                     if (rpw == base.sh.rpw && z == z0) continue;  // the model's shape, timed above
                     const TileChoice c{rpw, z};
-                    tile_choice_set(3, K_SWEEP, mode, lv.prec, n, &c);
+                    tile_choice_set(3, K_SWEEP, kmode, lv.prec, n, &c);
                     const float t = time_op(make());
                     if (t < tbest) { tbest = t; best = c; }
                 }
             }
-            tile_choice_set(3, K_SWEEP, mode, lv.prec, n, &best);
+            tile_choice_set(3, K_SWEEP, kmode, lv.prec, n, &best);
         }
     }
     cudaStreamSynchronize(s);
@@ -778,7 +790,7 @@ extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, 
         h->rsc_part = (float*)(base + lay.rpart_off);
     }
     std::vector<double> inv;
-    if (!coarse_inverse(h->dim, h->lv[0].geo.n, inv)) { free_hier(h); FAIL(MG_ERR_INVALID, "singular base-level operator"); }
+    if (!coarse_inverse(h->dim, h->p.op, h->lv[0].geo.n, inv)) { free_hier(h); FAIL(MG_ERR_INVALID, "singular base-level operator"); }
 #define CK_CREATE(call)                                                                       \
     do {                                                                                      \
         cudaError_t e2 = (call);                                                              \
@@ -895,7 +907,8 @@ static int launch_residual(mgi_hier& h, cudaStream_t s, double* r, int copy_u, i
     a.use_st_uout = copy_u;
     a.need_b = fin_kind == FIN_INIT;
     a.gate = gate;
-    a.h2inv = (double)(g.n + 1) * (double)(g.n + 1);
+    a.h2inv = op_alpha(h.p.op, h.dim, g.n);
+    a.op = h.p.op;
     int nb = 0;
     int rc = launch_residual64(h.dim, a, &nb, s);
     if (rc) return rc;
@@ -1173,9 +1186,9 @@ static double op_bytes(const mgi_hier& h, const Op& op) {
         case OP_KERNEL:
             switch (op.kkind) {
                 case K_SWEEP:
-                    if (op.mode == M_JACOBI) return 3 * s * N;      // read c, g; write c'
-                    if (op.mode == M_RESTRICT) return 2 * s * N + sc * Nc;  // read c, g; write g_coarse
-                    if (op.mode == M_PRE) return 2 * s * N + sc * Nc;       // read g; write c, g_coarse
+                    if ((op.mode & M_BASE) == M_JACOBI) return 3 * s * N;      // read c, g; write c'
+                    if ((op.mode & M_BASE) == M_RESTRICT) return 2 * s * N + sc * Nc;  // read c, g; write g_coarse
+                    if ((op.mode & M_BASE) == M_PRE) return 2 * s * N + sc * Nc;       // read g; write c, g_coarse
                     return 2 * s * N;                               // read g; write c
                 case K_UPDATE: return (32 + s) * N;                 // read c; read+write u, r (FP64)
                 case K_SCALE: return (8 + s) * N;                   // read r (FP64); write g
@@ -1228,7 +1241,7 @@ extern "C" mg_status mg_profile_solve(mg_hierarchy* hh, const double* b, double*
                                          : op.kkind == K_UPDATE ? 5 : 6)
                                       : op.kind;  // OP_TAIL = 7, OP_RESCALE = 8
         k.level = op.level;
-        k.mode = op.mode;
+        k.mode = op.mode & M_BASE;
         k.loader = 0;
         k.prec = op.prec;
         k.prec_coarse = op.prec_c;

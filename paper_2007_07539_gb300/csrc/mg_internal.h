@@ -94,20 +94,38 @@ enum Mode : int {
     M_RESTRICT = 3, // coarse dst = R (g - A c)
     M_PRE = 4,      // dst2 = two sweeps from zero of g (src = g); coarse dst = R (g - A dst2): one pass
 };
+// Flag or'ed into the mode of the stencil kernels (sweeps, IR update) of a
+// hierarchy with the Q1 finite-element operator (op = 1); M_BASE masks it off.
+constexpr int M_FEM = 16;
+constexpr int M_BASE = 15;
+
+// The operator of a level, A = alpha (beta I - W), W the sum of neighbour
+// values with positive integer weights (Sec. 5):
+//   op 0, finite differences: alpha = h^-2, beta = 2d, weight 1 on the 2d axis neighbours;
+//   op 1, Q1 elements (stiffness / h^d): 2D alpha = h^-2/3, beta = 8, weight 1 on the 8
+//     neighbours; 3D alpha = h^-2/12, beta = 32, weight 2 on the 12 edge neighbours, 1 on
+//     the 8 corners, 0 on the 6 faces.
+inline double op_alpha(int op, int dim, int n) {
+    const double h2inv = (double)(n + 1) * (double)(n + 1);
+    return op == 1 ? h2inv / (dim == 3 ? 12.0 : 3.0) : h2inv;
+}
+inline int op_beta(int op, int dim) { return op == 1 ? (dim == 3 ? 32 : 8) : 2 * dim; }
 
 // Arguments of the fine-level kernels (passed by value).
-// Sweep coefficients, computed once on the host in the arithmetic type (the
-// same IEEE operations the kernels would do): c1 = 1 - w, c2 = w/2d,
-// c3 = w/(2d h^-2), k2 = 2 - w, h^-2, -2d h^-2.
+// Sweep coefficients of A = alpha (beta I - W), computed once on the host in
+// the arithmetic type (the same IEEE operations the kernels would do):
+// c1 = 1 - w, c2 = w/beta, c3 = w/(beta alpha) = w D^-1, k2 = 2 - w, alpha,
+// -beta alpha.  Jacobi: c1 c + c2 W c + c3 g; two sweeps from zero:
+// c3 (k2 g + c2 W g); residual: g + alpha W c - beta alpha c.
 struct SweepCoef {
     float f[6];
     double d[6];
 };
-inline SweepCoef make_sweep_coef(int dim, double omega, double h2inv) {
+inline SweepCoef make_sweep_coef(int dim, int op, double omega, double alpha) {
     SweepCoef c;
-    const float om = (float)omega, h2 = (float)h2inv, twod = (float)(2 * dim);
+    const float om = (float)omega, h2 = (float)alpha, twod = (float)op_beta(op, dim);
     c.f[0] = 1.0f - om; c.f[1] = om / twod; c.f[2] = om / (twod * h2); c.f[3] = 2.0f - om; c.f[4] = h2; c.f[5] = -twod * h2;
-    const double dom = omega, dh2 = h2inv, dtwod = (double)(2 * dim);
+    const double dom = omega, dh2 = alpha, dtwod = (double)op_beta(op, dim);
     c.d[0] = 1.0 - dom; c.d[1] = dom / dtwod; c.d[2] = dom / (dtwod * dh2); c.d[3] = 2.0 - dom; c.d[4] = dh2; c.d[5] = -dtwod * dh2;
     return c;
 }
@@ -131,7 +149,7 @@ struct KArgs {
     double a_step;       // K_UPDATE explicit alpha when st == nullptr
     double inv_explicit; // K_SCALE explicit scale when st == nullptr
     double omega;
-    double h2inv;        // 1/h^2 of this level
+    double h2inv;        // alpha of this level's operator (h^-2 for finite differences)
     int xstep, ystep, zstep, zlen;  // tile strides / march length
     int gate;            // 1: return at once unless st->phase == 0
     int* err;            // set to 1 when a bounded copy wait runs out (3D sweeps)
@@ -148,7 +166,8 @@ struct RArgs {
     double* uout;         // contiguous interior copy of u (may be null; st->uout with use_st_uout)
     double* partials;     // 4 doubles per CTA: sum r^2, max |r|, sum b^2, unused
     const DevState* st;   // control state (gating, caller pointers); may be null
-    double h2inv;
+    double h2inv;         // alpha of the operator (op_alpha)
+    int op;               // 0 finite differences, 1 Q1 elements
     int gate;             // 0 always run; 1 only when st->phase == 1; 2 only when st->dirty
     int use_st_uout;      // 1: copy u to st->uout
     int need_b;           // 1: also the partial sums of b^2 (initial residual, stage calls)
@@ -267,7 +286,7 @@ constexpr int kRescaleCtas = 304;
 int launch_rescale(const float* x, void* g, const Geom& geo, float* part, int sig, double* scale,
                    const DevState* st, int gate, void* stream);
 // Conjugate gradients on the base level (one CTA; Sec. 6), in the level's type.
-int launch_coarse_cg(int prec, const void* g, void* c, const Geom& geo, double tol, int maxit,
+int launch_coarse_cg(int prec, int op, const void* g, void* c, const Geom& geo, double tol, int maxit,
                      const DevState* st, int gate, void* stream);
 int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void* c, const Geom& geo,
                         const DevState* st, int gate, void* stream);

@@ -279,18 +279,25 @@ constexpr unsigned kDrainTries = 1u << 10; // every wait after one ran out
 // swap roles each plane: the loop body is unrolled three times).
 // Launch bounds: 8 warps (9 for the residual-restriction tiles).  One row per
 // warp: 4 CTAs per SM (3 for restriction); two rows per warp: 2 CTAs per SM.
-template <int MODE, int RPW>
+template <int MODE, int RPW, int OP = 0>
 struct SweepLB {
     static constexpr int kThreads = MODE == M_RESTRICT ? 288 : 256;
-    static constexpr int kMinBlocks = RPW == 2 ? 2 : (MODE == M_RESTRICT ? 3 : 4);
+    // Q1 keeps three in-plane sums per plane in registers: 2 CTAs per SM
+    static constexpr int kMinBlocks = (RPW == 2 || OP == 1) ? 2 : (MODE == M_RESTRICT ? 3 : 4);
 };
 // The body takes the CTA's tile coordinates (bx, by, bz) explicitly: the
 // single-grid kernel passes blockIdx, the batched kernel the coordinates of
 // its (instance, tile) work item.  maps may live in parameter space or in
 // global memory (64-byte aligned; written before the launch).
-template <int MODE, class T, class TC, int RPW>
+// OP = 1: the Q1 operator (27-point, Sec. 5).  W(z) = 2 (D(z) + X(z-1) + X(z+1))
+// + D(z-1) + D(z+1) with X(p) the in-plane cross sum (x +- 1, y +- 1) and D(p)
+// the in-plane diagonal sum of plane p at the row: X and D of a plane are
+// formed once, when it arrives, and kept in registers with the plane's row.
+template <int MODE, class T, class TC, int RPW, int OP>
 __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& maps, int bx, int by, int bz) {
     using C = typename Tr<T>::C;
+    constexpr bool Q1 = OP == 1;
+    static_assert(!Q1 || RPW == 1, "the Q1 sweep keeps one row per warp");
     using PR = typename std::conditional<MODE == M_RESTRICT, ScalarPair<C>, Pair<C>>::type;
     using P2 = typename PR::t;
     constexpr int V = Tr<T>::V;
@@ -376,18 +383,46 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
         gown[r] = CB + (w + r * TY) * 512 - 16;
     }
 
+    // the row and, for Q1, its in-plane cross (X) and diagonal (D) sums of the
+    // plane in stage st
+    auto xsum = [&](const P2 (&v)[NP], C l, C rgt, int k) {  // x-1 + x+1 of pair k
+        const C xl = k ? v[k - 1].y : l;
+        const C xr = k < NP - 1 ? v[k + 1].x : rgt;
+        return PR::mk(xl + v[k].y, v[k].x + xr);
+    };
+    auto plane_in = [&](const unsigned char* st, int r, P2 (&c)[NP], P2 (&X)[NP], P2 (&D)[NP]) {
+        lds_pairs<T>(st + own[r], lane, c);
+        if constexpr (Q1) {
+            P2 ym[NP], yp[NP];
+            lds_pairs<T>(st + own[r] - RB, lane, ym);
+            lds_pairs<T>(st + own[r] + RB, lane, yp);
+            const C l0 = lds_one<T>(st + own[r], lane * V - 1), r0 = lds_one<T>(st + own[r], lane * V + V);
+            const C lm = lds_one<T>(st + own[r] - RB, lane * V - 1), rm = lds_one<T>(st + own[r] - RB, lane * V + V);
+            const C lp = lds_one<T>(st + own[r] + RB, lane * V - 1), rp = lds_one<T>(st + own[r] + RB, lane * V + V);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                X[k] = PR::add(xsum(c, l0, r0, k), PR::add(ym[k], yp[k]));
+                D[k] = PR::add(xsum(ym, lm, rm, k), xsum(yp, lp, rp, k));
+            }
+        }
+    };
     P2 pa[RPW][NP], pb[RPW][NP], pc[RPW][NP];
+    P2 qa[RPW][NP], qb[RPW][NP], qc[RPW][NP];  // Q1: X of the three planes
+    P2 da[RPW][NP], db[RPW][NP], dc[RPW][NP];  // Q1: D of the three planes
     wait_next();  // plane zb-1
     wait_next();  // plane zb
 #pragma unroll
     for (int r = 0; r < RPW; ++r) {
-        lds_pairs<T>(base + own[r], lane, pa[r]);
-        lds_pairs<T>(base + SB + own[r], lane, pb[r]);
+        plane_in(base, r, pa[r], qa[r], da[r]);
+        plane_in(base + SB, r, pb[r], qb[r], db[r]);
     }
     int so = SB;  // stage of plane z
 
-    // One plane: cm / c0 hold planes z-1 / z, cp receives plane z+1.
-    auto step = [&](int z, const P2 (&cm)[RPW][NP], const P2 (&c0)[RPW][NP], P2 (&cp)[RPW][NP]) {
+    // One plane: cm / c0 hold planes z-1 / z, cp receives plane z+1 (and the
+    // X / D sums of the same planes for Q1).
+    auto step = [&](int z, const P2 (&cm)[RPW][NP], const P2 (&c0)[RPW][NP], P2 (&cp)[RPW][NP],
+                    const P2 (&Xm)[RPW][NP], const P2 (&X0)[RPW][NP], P2 (&Xp)[RPW][NP],
+                    const P2 (&dm)[RPW][NP], const P2 (&d0)[RPW][NP], P2 (&dp)[RPW][NP]) {
         __syncthreads();  // every warp is done with plane z-2's stage
         if (leader) issue(z + S - 2);
         wait_next();      // plane z+1
@@ -398,20 +433,29 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
 #pragma unroll
         for (int r = 0; r < RPW; ++r) {
             P2 ym[NP], yp[NP], g[NP];
-            lds_pairs<T>(base + s1 + own[r], lane, cp[r]);
-            lds_pairs<T>(st0 + own[r] - RB, lane, ym);
-            lds_pairs<T>(st0 + own[r] + RB, lane, yp);
-            const C left = lds_one<T>(st0 + own[r], lane * V - 1);
-            const C right = lds_one<T>(st0 + own[r], lane * V + V);
+            plane_in(base + s1, r, cp[r], Xp[r], dp[r]);
+            C left = 0, right = 0;
+            if constexpr (!Q1) {
+                lds_pairs<T>(st0 + own[r] - RB, lane, ym);
+                lds_pairs<T>(st0 + own[r] + RB, lane, yp);
+                left = lds_one<T>(st0 + own[r], lane * V - 1);
+                right = lds_one<T>(st0 + own[r], lane * V + V);
+            }
             if (NEED_G) lds_pairs<T>(st0 + gown[r], lane, g);
             P2 out[NP];
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
-                // x-neighbour sums: element 2k has 2k-1 and 2k+1, element 2k+1 has 2k and 2k+2
-                const C xl = k ? c0[r][k - 1].y : left;
-                const C xr = k < NP - 1 ? c0[r][k + 1].x : right;
-                const P2 xs = PR::mk(xl + c0[r][k].y, c0[r][k].x + xr);
-                const P2 nb = PR::add(PR::add(xs, PR::add(ym[k], yp[k])), PR::add(cm[r][k], cp[r][k]));
+                P2 nb;
+                if constexpr (Q1) {
+                    // edges (weight 2): D(z), X(z-1), X(z+1); corners (weight 1): D(z-1), D(z+1)
+                    const P2 e = PR::add(d0[r][k], PR::add(Xm[r][k], Xp[r][k]));
+                    (void)X0;
+                    nb = PR::fma(PR::splat((C)2), e, PR::add(dm[r][k], dp[r][k]));
+                } else {
+                    // x-neighbour sums: element 2k has 2k-1 and 2k+1, element 2k+1 has 2k and 2k+2
+                    const P2 xs = xsum(c0[r], left, right, k);
+                    nb = PR::add(PR::add(xs, PR::add(ym[k], yp[k])), PR::add(cm[r][k], cp[r][k]));
+                }
                 P2 v;
                 if (MODE == M_JACOBI) v = PR::fma(c2, nb, PR::fma(c1, c0[r][k], PR::mul(c3, g[k])));  // c + w D^-1 (g - A c)
                 else if (MODE == M_ZERO2) v = PR::mul(c3, PR::fma(c2, nb, PR::mul(k2, c0[r][k])));     // two sweeps from 0, c0 = g
@@ -473,29 +517,29 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
         so = s1;
     };
     for (int z = zb; z < ze;) {
-        step(z, pa, pb, pc);
+        step(z, pa, pb, pc, qa, qb, qc, da, db, dc);
         if (++z >= ze) break;
-        step(z, pb, pc, pa);
+        step(z, pb, pc, pa, qb, qc, qa, db, dc, da);
         if (++z >= ze) break;
-        step(z, pc, pa, pb);
+        step(z, pc, pa, pb, qc, qa, qb, dc, da, db);
         ++z;
     }
 }
 
-template <int MODE, class T, class TC, int RPW>
-__global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RPW>::kMinBlocks)
+template <int MODE, class T, class TC, int RPW, int OP = 0>
+__global__ void __launch_bounds__(SweepLB<MODE, RPW, OP>::kThreads, SweepLB<MODE, RPW, OP>::kMinBlocks)
     k_sweep3(const KArgs a, const __grid_constant__ SweepMaps maps) {
-    sweep3_body<MODE, T, TC, RPW>(a, maps, blockIdx.x, blockIdx.y, blockIdx.z);
+    sweep3_body<MODE, T, TC, RPW, OP>(a, maps, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 // Batched: CTA -> work item through a table; the item's grid (gx, gy, gz)
 // decodes the CTA's tile.
-template <int MODE, class T, class TC, int RPW>
-__global__ void __launch_bounds__(SweepLB<MODE, RPW>::kThreads, SweepLB<MODE, RPW>::kMinBlocks)
+template <int MODE, class T, class TC, int RPW, int OP = 0>
+__global__ void __launch_bounds__(SweepLB<MODE, RPW, OP>::kThreads, SweepLB<MODE, RPW, OP>::kMinBlocks)
     k_sweep3_batch(const SweepItem* __restrict__ items, const int* __restrict__ cta_item) {
     const SweepItem& it = items[cta_item[blockIdx.x]];
     const int local = blockIdx.x - it.cta_begin;
     const int bx = local % it.gx, rest = local / it.gx;
-    sweep3_body<MODE, T, TC, RPW>(it.a, it.maps, bx, rest % it.gy, rest / it.gy);
+    sweep3_body<MODE, T, TC, RPW, OP>(it.a, it.maps, bx, rest % it.gy, rest / it.gy);
 }
 
 // ---------------------------------------------------------------- 3D one-pass pre-smoothing + restriction
@@ -720,7 +764,8 @@ __global__ void __launch_bounds__(288, 3) k_pre3_batch(const SweepItem* __restri
 }
 
 // ---------------------------------------------------------------- 2D sweep
-template <int MODE, class T, class TC>
+// OP = 1: the Q1 operator, W = the 8 neighbours (rows y-1, y+1 with their halos)
+template <int MODE, class T, class TC, int OP>
 __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
     using C = typename Tr<T>::C;
     constexpr int V = Tr<T>::V;
@@ -756,7 +801,7 @@ __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
 #pragma unroll
     for (int k = 0; k < S - 1; ++k) issue(yb - 1 + k);
     const C c1 = coef<C>(a.cf, 0), c2 = coef<C>(a.cf, 1), c3 = coef<C>(a.cf, 2), k2 = coef<C>(a.cf, 3);
-    const C h2inv = coef<C>(a.cf, 4), twod = (C)4;
+    const C h2inv = coef<C>(a.cf, 4), twod = (C)(OP == 1 ? 8 : 4);
     C acc[VH];
 #pragma unroll
     for (int k = 0; k < VH; ++k) acc[k] = 0;
@@ -775,11 +820,21 @@ __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
         lds_vec<T>(crow(slot(y + 1)), lane, cp);
         const C left = lds_one<T>(crow(s0), lane * V - 1);
         const C right = lds_one<T>(crow(s0), lane * V + V);
+        C lm = 0, rm = 0, lp = 0, rp = 0;  // halos of rows y-1, y+1 (Q1 only)
+        if constexpr (OP == 1) {
+            lm = lds_one<T>(crow(slot(y - 1)), lane * V - 1);
+            rm = lds_one<T>(crow(slot(y - 1)), lane * V + V);
+            lp = lds_one<T>(crow(slot(y + 1)), lane * V - 1);
+            rp = lds_one<T>(crow(slot(y + 1)), lane * V + V);
+        }
         if (NEED_G) lds_vec<T>(grow(s0), lane, g);
         C out[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            const C nb = (i ? c0[i - 1] : left) + (i < V - 1 ? c0[i + 1] : right) + cm[i] + cp[i];
+            C nb = (i ? c0[i - 1] : left) + (i < V - 1 ? c0[i + 1] : right) + cm[i] + cp[i];
+            if constexpr (OP == 1)
+                nb += ((i ? cm[i - 1] : lm) + (i < V - 1 ? cm[i + 1] : rm)) +
+                      ((i ? cp[i - 1] : lp) + (i < V - 1 ? cp[i + 1] : rp));
             const C v = point_value<MODE, C>(c0[i], nb, NEED_G ? g[i] : (C)0, c1, c2, c3, h2inv, twod, k2);
             out[i] = (x + i < a.n) ? v : (C)0;
         }
@@ -906,11 +961,12 @@ template <> struct ExactStencil<__half> {
 };
 template <class T> struct ExactStencil {
     static constexpr bool kTwoTerm = true;
-    // FP32/BF16 values: double-float sum with error-free transformations.
-    template <int NB>
+    // FP32/BF16 values: double-float sum with error-free transformations of
+    // S = BETA c0 - sum of nb (nb already multiplied by their weights, exactly).
+    template <int NB, int BETA = NB>
     __device__ static void sum(float c0, const float (&nb)[NB], double& s, double& s2) {
-        float p = __fmul_rn((float)NB, c0);
-        float e = __fmaf_rn((float)NB, c0, -p);
+        float p = __fmul_rn((float)BETA, c0);
+        float e = __fmaf_rn((float)BETA, c0, -p);
         float acc = p;
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
@@ -925,15 +981,22 @@ template <class T> struct ExactStencil {
 };
 template <> struct ExactStencil<double> {
     static constexpr bool kTwoTerm = false;
-    template <int NB>
+    template <int NB, int BETA = NB>
     __device__ static void sum(double c0, const double (&nb)[NB], double& s, double& s2) {
         double t = 0.0;
 #pragma unroll
         for (int j = 0; j < NB; ++j) t += nb[j];
-        s = fma((double)NB, c0, -t);
+        s = fma((double)BETA, c0, -t);
         s2 = 0.0;
     }
 };
+
+// Q1 weight of neighbour offset (dx, dy, dz): 2D all 8 neighbours 1; 3D edges
+// (two non-zero offsets) 2, corners 1, faces 0.  The centre is beta.
+template <int DIM>
+__host__ __device__ constexpr int q1_weight(int dx, int dy, int dz) {
+    return (DIM == 2) ? 1 : ((dx != 0) + (dy != 0) + (dz != 0) == 2 ? 2 : ((dx != 0) + (dy != 0) + (dz != 0) == 3 ? 1 : 0));
+}
 
 __device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
@@ -1049,11 +1112,13 @@ __device__ __forceinline__ void ld4(const T* p, typename Tr<T>::C (&v)[4]) {
 // the stencil of c comes through the read-only cache as vector loads.  FP64
 // instructions: the two fused multiply-adds of Alg. 2 lines 6-7 per point
 // (three for FP32/BF16 corrections), nothing else.
+// OP = 1: the Q1 operator (3x3(x3) neighbourhood, integer weights).
 constexpr int kUpdQ = 4;
-template <int DIM, class T>
+template <int DIM, class T, int OP>
 __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
     using C = typename Tr<T>::C;
     constexpr int Q = kUpdQ;
+    constexpr bool Q1 = OP == 1;
     if (a.gate && a.st->phase != 0) return;
     const int vpr = a.P / Q;
     const int rows = DIM == 3 ? a.n * a.n : a.n;
@@ -1080,6 +1145,76 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
         const double2 r01 = *reinterpret_cast<const double2*>(rp);
         const double2 r23 = *reinterpret_cast<const double2*>(rp + 2);
         C c0[Q], ym[Q], yp[Q], zm[Q], zp[Q];
+        double uu[Q] = {u01.x, u01.y, u23.x, u23.y};
+        double rr[Q] = {r01.x, r01.y, r23.x, r23.y};
+        if constexpr (Q1) {
+            // Q1: S = beta c0 - sum_o w_o c_o over the 3x3(x3) neighbourhood, rows
+            // (dy, dz) loaded with one halo value on each side
+            constexpr int NR = DIM == 3 ? 9 : 3;
+            constexpr int BETA = DIM == 3 ? 32 : 8;
+            C rv[NR][Q + 2];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                const T* rp = c + (q % 3 - 1) * (long long)a.P + (DIM == 3 ? (q / 3 - 1) * a.S : 0LL);
+                C mid[Q];
+                ld4(rp, mid);
+                rv[q][0] = ld1(rp - 1);
+                rv[q][Q + 1] = ld1(rp + Q);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) rv[q][i + 1] = mid[i];
+            }
+            constexpr int CR = DIM == 3 ? 4 : 1;  // the centre row (dy = dz = 0)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (x + i < a.n) {
+                    const C cc = rv[CR][i + 1];
+                    double s, s2 = 0.0;
+                    if constexpr (std::is_same<T, __half>::value) {
+                        // FP16 values as integers in units of 2^-24 (h_split): the
+                        // weighted sum of the hi parts in int32 (|.| <= 64 * 2^22),
+                        // of the lo parts in FP32 (integers, |.| <= 64 * 2^17 < 2^24)
+                        HSplit m = h_split(cc);
+                        int H = BETA * m.hi;
+                        float L = __fmul_rn((float)BETA, m.lo);
+#pragma unroll
+                        for (int q = 0; q < NR; ++q)
+#pragma unroll
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const int dy = q % 3 - 1, dz = DIM == 3 ? q / 3 - 1 : 0;
+                                if (dx == 0 && dy == 0 && dz == 0) continue;
+                                const int w = q1_weight<DIM>(dx, dy, dz);
+                                if (w == 0) continue;
+                                const HSplit t = h_split(rv[q][i + 1 + dx]);
+                                H -= w * t.hi;
+                                L = __fmaf_rn(-(float)w, t.lo, L);
+                            }
+                        const int Li = __float2int_rn(L);
+                        s = i64_to_f64(((long long)H << 18) + (long long)Li, -24);
+                    } else {
+                        constexpr int NB = DIM == 3 ? 20 : 8;
+                        C nb[NB];
+                        int j = 0;
+#pragma unroll
+                        for (int q = 0; q < NR; ++q)
+#pragma unroll
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const int dy = q % 3 - 1, dz = DIM == 3 ? q / 3 - 1 : 0;
+                                if (dx == 0 && dy == 0 && dz == 0) continue;
+                                const int w = q1_weight<DIM>(dx, dy, dz);
+                                if (w == 0) continue;
+                                nb[j++] = (C)w * rv[q][i + 1 + dx];  // exact: w is 1 or 2
+                            }
+                        ExactStencil<T>::template sum<NB, BETA>(cc, nb, s, s2);
+                    }
+                    double r = fma(-beta, s, rr[i]);
+                    if (ExactStencil<T>::kTwoTerm && !std::is_same<T, __half>::value) r = fma(-beta, s2, r);
+                    rr[i] = r;
+                    uu[i] = fma(alpha, to_f64(cc), uu[i]);
+                    sq.add(r, E);
+                    nmax = key_max(nmax, abs_key(r));
+                }
+            }
+        } else {
         ld4(c, c0);
         ld4(c - a.P, ym);
         ld4(c + a.P, yp);
@@ -1088,8 +1223,6 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
             ld4(c + a.S, zp);
         }
         const C left = ld1(c - 1), right = ld1(c + Q);
-        double uu[Q] = {u01.x, u01.y, u23.x, u23.y};
-        double rr[Q] = {r01.x, r01.y, r23.x, r23.y};
         if constexpr (DIM == 3 && std::is_same<T, __half>::value) {
             // FP16 corrections: every loaded value is split once (22 splits
             // for 4 points), the exact stencil sum S = 6 c0 - sum of neighbours
@@ -1145,6 +1278,7 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
             }
         }
         }
+        }
         *reinterpret_cast<double2*>(up) = make_double2(uu[0], uu[1]);
         *reinterpret_cast<double2*>(up + 2) = make_double2(uu[2], uu[3]);
         *reinterpret_cast<double2*>(rp) = make_double2(rr[0], rr[1]);
@@ -1152,12 +1286,12 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
     }
     write_partials(sq, nmax, E, a.partials, cta);
 }
-template <int DIM, class T>
-__global__ void __launch_bounds__(256) k_update(const KArgs a) { update_body<DIM, T>(a, blockIdx.x, gridDim.x); }
-template <int DIM, class T>
+template <int DIM, class T, int OP>
+__global__ void __launch_bounds__(256) k_update(const KArgs a) { update_body<DIM, T, OP>(a, blockIdx.x, gridDim.x); }
+template <int DIM, class T, int OP>
 __global__ void __launch_bounds__(256) k_update_batch(const KItem* __restrict__ items, const int* __restrict__ cta_item) {
     const KItem& it = items[cta_item[blockIdx.x]];
-    update_body<DIM, T>(it.a, blockIdx.x - it.cta_begin, it.ncta);
+    update_body<DIM, T, OP>(it.a, blockIdx.x - it.cta_begin, it.ncta);
 }
 
 // ---------------------------------------------------------------- prolongation (Alg. 1 step 4)

@@ -186,8 +186,10 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
         s.smem = 0;
         return s;
     }
-    const bool need_g = mode == M_JACOBI || mode == M_RESTRICT;
-    if (mode == M_RESTRICT || mode == M_PRE) {
+    const int bmode = mode & M_BASE;
+    const bool q1 = (mode & M_FEM) != 0;  // Q1 sweeps keep one row per warp
+    const bool need_g = bmode == M_JACOBI || bmode == M_RESTRICT;
+    if (bmode == M_RESTRICT || bmode == M_PRE) {
         const int nc = (n - 1) / 2;
         s.xstep = P > CW ? CW - V : CW;
         const int nchunks = P > CW ? 1 + cdiv(P - CW, CW - V) : 1;
@@ -200,7 +202,7 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
             s.ystep = 2 * TJ;
             s.gx = nchunks;
             s.gy = cdiv(nc, TJ);
-            s.smem = mode == M_PRE ? (size_t)pre3_smem(rows, rows * 32 * VH * (int)cs)
+            s.smem = bmode == M_PRE ? (size_t)pre3_smem(rows, rows * 32 * VH * (int)cs)
                                    : (size_t)sweep3_smem(rows, true, rows * 32 * VH * (int)cs, sweep3_stages(M_RESTRICT, s.rpw));
             const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem, s.rpw);
             TileChoice tc;
@@ -230,11 +232,11 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
         // per-plane work of a warp (waits, barrier, copy issue, addressing)
         // is shared by twice the points
         s.ty = clampi(n, 1, 8);
-        s.rpw = n >= 16 ? 2 : 1;
+        s.rpw = n >= 16 && !q1 ? 2 : 1;
         TileChoice tc;
         const bool tuned = tile_choice_get(dim, kind, mode, prec, n, &tc);
         if (tuned) {
-            s.rpw = n >= 16 ? clampi(tc.rpw, 1, 2) : 1;
+            s.rpw = n >= 16 && !q1 ? clampi(tc.rpw, 1, 2) : 1;
             if (tz_hint <= 0) tz_hint = tc.zlen;
         }
         s.ystep = s.ty * s.rpw;
@@ -315,8 +317,8 @@ int launch_coarse_solve(int prec, const double* inv, int m, const void* g, void*
 // arithmetic type, then x, g, r, p in the level type (m <= 4096 points).
 template <int DIM, class T>
 __global__ void __launch_bounds__(1024) k_coarse_cg(const T* __restrict__ g, T* __restrict__ c, int n, int P,
-                                                    long long S, double tol, int maxit, const DevState* st,
-                                                    int gate) {
+                                                    long long S, int op, double alpha, double tol, int maxit,
+                                                    const DevState* st, int gate) {
     using C = typename Tr<T>::C;
     if (gate && st->phase != 0) return;
     extern __shared__ __align__(16) unsigned char smc[];
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(const T* __restrict__ g, T* 
         gs[t] = g[(DIM == 3 ? (long long)k * S : 0LL) + (long long)j * P + i];
     }
     __syncthreads();
-    cg_base<DIM, T>(n, mn, (C)((double)(n + 1) * (double)(n + 1)), gs, x, r, p, q, tol, maxit);
+    cg_base<DIM, T>(n, mn, op, (C)alpha, (C)op_beta_d<DIM>(op), gs, x, r, p, q, tol, maxit);
     __syncthreads();
     for (int t = threadIdx.x; t < m; t += blockDim.x) {
         int i, j, k;
@@ -343,8 +345,8 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(const T* __restrict__ g, T* 
 }
 
 template <int DIM, class T>
-static int launch_coarse_cg_t(const void* g, void* c, const Geom& geo, double tol, int maxit, const DevState* st,
-                              int gate, cudaStream_t s) {
+static int launch_coarse_cg_t(const void* g, void* c, const Geom& geo, int op, double tol, int maxit,
+                              const DevState* st, int gate, cudaStream_t s) {
     using C = typename Tr<T>::C;
     const int m = DIM == 3 ? geo.n * geo.n * geo.n : geo.n * geo.n;
     const size_t smem = (size_t)m * (sizeof(C) + 4 * sizeof(T));
@@ -353,23 +355,24 @@ static int launch_coarse_cg_t(const void* g, void* c, const Geom& geo, double to
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
     }
-    f<<<1, 1024, smem, s>>>((const T*)g, (T*)c, geo.n, geo.P, geo.S, tol, maxit, st, gate);
+    f<<<1, 1024, smem, s>>>((const T*)g, (T*)c, geo.n, geo.P, geo.S, op, op_alpha(op, DIM, geo.n), tol, maxit, st,
+                            gate);
     return (int)cudaGetLastError();
 }
 
-int launch_coarse_cg(int prec, const void* g, void* c, const Geom& geo, double tol, int maxit, const DevState* st,
-                     int gate, void* stream) {
+int launch_coarse_cg(int prec, int op, const void* g, void* c, const Geom& geo, double tol, int maxit,
+                     const DevState* st, int gate, void* stream) {
     const cudaStream_t s = (cudaStream_t)stream;
     const bool d3 = geo.dim == 3;
     switch (prec) {
-        case MG_FP64: return d3 ? launch_coarse_cg_t<3, double>(g, c, geo, tol, maxit, st, gate, s)
-                                : launch_coarse_cg_t<2, double>(g, c, geo, tol, maxit, st, gate, s);
-        case MG_FP32: return d3 ? launch_coarse_cg_t<3, float>(g, c, geo, tol, maxit, st, gate, s)
-                                : launch_coarse_cg_t<2, float>(g, c, geo, tol, maxit, st, gate, s);
-        case MG_FP16: return d3 ? launch_coarse_cg_t<3, __half>(g, c, geo, tol, maxit, st, gate, s)
-                                : launch_coarse_cg_t<2, __half>(g, c, geo, tol, maxit, st, gate, s);
-        case MG_BF16: return d3 ? launch_coarse_cg_t<3, __nv_bfloat16>(g, c, geo, tol, maxit, st, gate, s)
-                                : launch_coarse_cg_t<2, __nv_bfloat16>(g, c, geo, tol, maxit, st, gate, s);
+        case MG_FP64: return d3 ? launch_coarse_cg_t<3, double>(g, c, geo, op, tol, maxit, st, gate, s)
+                                : launch_coarse_cg_t<2, double>(g, c, geo, op, tol, maxit, st, gate, s);
+        case MG_FP32: return d3 ? launch_coarse_cg_t<3, float>(g, c, geo, op, tol, maxit, st, gate, s)
+                                : launch_coarse_cg_t<2, float>(g, c, geo, op, tol, maxit, st, gate, s);
+        case MG_FP16: return d3 ? launch_coarse_cg_t<3, __half>(g, c, geo, op, tol, maxit, st, gate, s)
+                                : launch_coarse_cg_t<2, __half>(g, c, geo, op, tol, maxit, st, gate, s);
+        case MG_BF16: return d3 ? launch_coarse_cg_t<3, __nv_bfloat16>(g, c, geo, op, tol, maxit, st, gate, s)
+                                : launch_coarse_cg_t<2, __nv_bfloat16>(g, c, geo, op, tol, maxit, st, gate, s);
     }
     return (int)cudaErrorInvalidValue;
 }
@@ -457,10 +460,28 @@ __device__ __forceinline__ void residual64_body(const RArgs& a, int cta, int nct
             r = bv;  // u = 0: r = b
         } else {
             const double* u = a.u + o;
-            double nb = __ldg(u - 1) + __ldg(u + 1) + __ldg(u - a.P) + __ldg(u + a.P);
-            if (DIM == 3) nb += __ldg(u - a.S) + __ldg(u + a.S);
             const double uc = __ldg(u);
-            r = fma(-a.h2inv, fma(2.0 * DIM, uc, -nb), bv);
+            if (a.op == 1) {  // Q1: r = b - alpha (beta u - W) (the pads and ghost planes are zero)
+                double s1 = 0.0, s2 = 0.0;  // weight-1 and weight-2 neighbour sums
+#pragma unroll
+                for (int dk = (DIM == 3 ? -1 : 0); dk <= (DIM == 3 ? 1 : 0); ++dk)
+#pragma unroll
+                    for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+                        for (int di = -1; di <= 1; ++di) {
+                            const int nz = (di != 0) + (dj != 0) + (dk != 0);
+                            if (nz == 0 || (DIM == 3 && nz == 1)) continue;
+                            const double v = __ldg(u + di + (long long)dj * a.P + (DIM == 3 ? (long long)dk * a.S : 0LL));
+                            if (DIM == 3 && nz == 2) s2 += v;
+                            else s1 += v;
+                        }
+                const double W = fma(2.0, s2, s1);
+                r = fma(-a.h2inv, fma(DIM == 3 ? 32.0 : 8.0, uc, -W), bv);
+            } else {
+                double nb = __ldg(u - 1) + __ldg(u + 1) + __ldg(u - a.P) + __ldg(u + a.P);
+                if (DIM == 3) nb += __ldg(u - a.S) + __ldg(u + a.S);
+                r = fma(-a.h2inv, fma(2.0 * DIM, uc, -nb), bv);
+            }
             if (uout) uout[oc] = uc;
         }
         if (a.r) a.r[o] = r;

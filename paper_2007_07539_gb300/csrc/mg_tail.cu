@@ -30,11 +30,12 @@ template <class T, class V>
 __device__ __forceinline__ void sput(unsigned char* sm, int off, int p, V v) {
     st1(reinterpret_cast<T*>(sm + off) + p, v);
 }
-// sum of the 2*DIM axis neighbours of point p of the array at byte offset off
+// W of the operator (op 0: the 2d axis neighbours; 1: Q1) at point p of the
+// array at byte offset off
 template <int DIM, class T>
-__device__ __forceinline__ typename Tr<T>::C nbsum(const unsigned char* sm, int off, int p, int n, int i, int j,
-                                                   int k) {
-    return cnbsum<DIM, T>(reinterpret_cast<const T*>(sm + off), p, n, i, j, k);
+__device__ __forceinline__ typename Tr<T>::C nbsum(int op, const unsigned char* sm, int off, int p, int n, int i,
+                                                   int j, int k) {
+    return cwsum<DIM, T>(op, reinterpret_cast<const T*>(sm + off), p, n, i, j, k);
 }
 
 // ---- Jacobi family (Alg. 1 smoother; M_ZERO2 / M_ZERO1 start from c = 0)
@@ -48,7 +49,7 @@ __device__ void t_sweep(const TailOp& op, unsigned char* sm) {
         int i, j, k;
         decode<DIM>(p, n, op.mn, i, j, k);
         const C c0 = sget<T>(sm, op.src, p);
-        const C nb = nbsum<DIM, T>(sm, op.src, p, n, i, j, k);
+        const C nb = nbsum<DIM, T>(op.op, sm, op.src, p, n, i, j, k);
         C v;
         if (op.mode == M_JACOBI) v = c1 * c0 + c2 * nb + c3 * sget<T>(sm, op.g, p);
         else if (op.mode == M_ZERO2) v = c3 * (k2 * c0 + c2 * nb);
@@ -63,13 +64,13 @@ __device__ void t_resid(const TailOp& op, unsigned char* sm) {
     using C = typename Tr<T>::C;
     const int n = op.n;
     const int N = DIM == 3 ? n * n * n : n * n;
-    const C h2inv = coef<C>(op.cf, 4), twod = (C)(2 * DIM);
+    const C alpha = coef<C>(op.cf, 4), beta = (C)op_beta_d<DIM>(op.op);
     C* r = reinterpret_cast<C*>(sm + op.dst);
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
         int i, j, k;
         decode<DIM>(p, n, op.mn, i, j, k);
-        const C nb = nbsum<DIM, T>(sm, op.src, p, n, i, j, k);
-        r[p] = sget<T>(sm, op.g, p) - h2inv * (twod * sget<T>(sm, op.src, p) - nb);
+        const C nb = nbsum<DIM, T>(op.op, sm, op.src, p, n, i, j, k);
+        r[p] = sget<T>(sm, op.g, p) - alpha * (beta * sget<T>(sm, op.src, p) - nb);  // g - alpha (beta c - W)
     }
 }
 
@@ -180,8 +181,9 @@ __device__ void t_cg(const TailOp& op, unsigned char* sm) {
     T* r = reinterpret_cast<T*>(sm + op.src);
     T* p = reinterpret_cast<T*>(sm + op.src + slot);
     C* q = reinterpret_cast<C*>(sm + op.src + 2 * slot);
-    cg_base<DIM, T>(op.n, op.mn, coef<C>(op.cf, 4), reinterpret_cast<const T*>(sm + op.g),
-                    reinterpret_cast<T*>(sm + op.dst), r, p, q, op.cgtol, op.cgmax);
+    cg_base<DIM, T>(op.n, op.mn, op.op, coef<C>(op.cf, 4), (C)op_beta_d<DIM>(op.op),
+                    reinterpret_cast<const T*>(sm + op.g), reinterpret_cast<T*>(sm + op.dst), r, p, q, op.cgtol,
+                    op.cgmax);
 }
 
 template <int DIM, class T>

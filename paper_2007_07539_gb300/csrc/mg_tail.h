@@ -37,6 +37,8 @@ struct TailOp {
     int scr2;   // TK_RESTRICT with sslot >= 0: byte offset of the coarse-value scratch
     int rsig;   // TK_RESTRICT with sslot >= 0: target max-norm 2^rsig (power-of-two range)
     int cgmax;  // TK_COARSE mode 1 (CG): step limit
+    int op;     // operator: 0 finite differences, 1 Q1 elements
+    int pad_;
     void* gptr;
     double h2inv;
     double omega;

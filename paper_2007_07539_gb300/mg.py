@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("zero_guess", ctypes.c_int32), ("guard", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("no_tail", ctypes.c_int32), ("tune", ctypes.c_int32),
                 ("fuse_pre", ctypes.c_int32), ("rescale16", ctypes.c_int32), ("base_solver", ctypes.c_int32),
-                ("base_maxit", ctypes.c_int32), ("base_tol", ctypes.c_double), ("reserved", ctypes.c_int32 * 2)]
+                ("base_maxit", ctypes.c_int32), ("base_tol", ctypes.c_double), ("op", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class Result(ctypes.Structure):

@@ -40,7 +40,7 @@ def test_params_defaults():
     assert (p.nu1, p.nu2, p.gamma, p.scaling, p.tol_mode, p.max_iter) == (2, 2, 1, 1, 0, 100)
     assert p.omega == 0.8 and p.tol == 1e-10
     assert list(p.prec)[:7] == [mg.FP64] * 7
-    assert (p.rescale16, p.base_solver, p.base_maxit, p.base_tol) == (1, 0, 0, 1e-4)
+    assert (p.rescale16, p.base_solver, p.base_maxit, p.base_tol, p.op) == (1, 0, 0, 1e-4, 0)
 
 
 def test_ladders():
@@ -53,7 +53,8 @@ def test_ladders():
 @pytest.mark.parametrize("bad", [dict(dim=4), dict(n=0), dict(omega=2.5), dict(gamma=3), dict(scaling=7),
                                  dict(max_iter=5000), dict(nu1=-1), dict(levels=9), dict(tol=-1.0), dict(tune=2),
                                  dict(no_tail=5), dict(fuse_pre=3), dict(rescale16=2), dict(base_solver=2),
-                                 dict(base_maxit=-1), dict(base_tol=-1.0), dict(base_tol=float("nan"))])
+                                 dict(base_maxit=-1), dict(base_tol=-1.0), dict(base_tol=float("nan")),
+                                 dict(op=2), dict(op=1, fuse_pre=1)])
 def test_invalid_params_rejected_without_gpu(bad):
     p = mg.make_params(3, 63)
     for k, v in bad.items():
