@@ -45,6 +45,9 @@ WORKLOAD = ("3D Poisson 7-point FDM, zero Dirichlet, 255^3 interior (16,581,375 
             "H_MG: V(2,2) damped-Jacobi (omega 0.8) MG preconditioner with all 7 levels in FP16 "
             "(FP32 in-sweep accumulation), residual scaled by 2^14/||r||_inf before the FP16 cast, "
             "FP64 iterative refinement to rel. residual 1e-10; compared with all-FP64 MG (D_MG)")
+# --op 1: the same line for the paper's trilinear Q1 finite-element operator (27-point)
+WORKLOAD_Q1 = WORKLOAD.replace("3D Poisson 7-point FDM", "3D Poisson trilinear Q1 FEM (27-point, stiffness / h^3)")
+GOLDEN_KEY = {0: "3d_n255_random_seed2", 1: "3d_n255_random_seed2_q1"}
 
 
 def env_int(k, d):
@@ -109,7 +112,7 @@ def oracle_iters(name: str) -> int:
         return int(json.load(f)[name]["iters"])
 
 
-def cpu_oracle_sample(b, steps: int = 1):
+def cpu_oracle_sample(b, steps: int = 1, op: int = 0):
     """The FP64 oracle on the same 255^3 workload, bounded: solves with max_iter = 0
     (initial and final residual) and max_iter = 1 are timed; the per-step cost is their
     difference and DOF/s to 1e-10 is extrapolated with the oracle's own iteration count
@@ -117,14 +120,14 @@ def cpu_oracle_sample(b, steps: int = 1):
     from oracle import oracle as O
     O.build()
     cores = os.cpu_count() or 1
-    iters = oracle_iters("3d_n255_random_seed2")
+    iters = oracle_iters(GOLDEN_KEY[op])
     t0s, t1s = [], []
     for _ in range(steps):
         t = time.perf_counter()
-        O.ir_solve(b, max_iter=0, nthreads=cores)
+        O.ir_solve(b, max_iter=0, nthreads=cores, op=op)
         t0s.append(time.perf_counter() - t)
         t = time.perf_counter()
-        O.ir_solve(b, max_iter=1, nthreads=cores)
+        O.ir_solve(b, max_iter=1, nthreads=cores, op=op)
         t1s.append(time.perf_counter() - t)
     t0, t1 = min(t0s), min(t1s)
     t_solve = t0 + iters * max(t1 - t0, 0.0)
@@ -413,6 +416,9 @@ def main():
     ap.add_argument("--kernel-dump", default=None, help="write every kernel's profiled time to this JSON file")
     ap.add_argument("--ncu-case", action="store_true",
                     help="only two FP16 solves of the workload (a small launch list for ncu captures)")
+    ap.add_argument("--op", type=int, default=0, choices=[0, 1],
+                    help="operator: 0 the 7-point finite-difference stencil (the headline workload), "
+                         "1 the trilinear Q1 finite elements of Sec. 5")
     ap.add_argument("--graph", type=int, default=1,
                     help="1: each solve is one CUDA graph with a device-side IR loop; 0: kernels launched one "
                          "by one from the host loop (ncu cannot profile kernels inside conditional graphs)")
@@ -448,8 +454,8 @@ def main():
     graph = 0 if args.ncu_case else args.graph
     # tile shapes of the stencil kernels autotuned at creation (results do not depend on them)
     tune = 0 if args.no_tune else 1
-    hH = mg.Hierarchy(mg.make_params(DIM, N, "H", zero_guess=1, graph=graph, tune=tune))
-    hD = mg.Hierarchy(mg.make_params(DIM, N, "D", zero_guess=1, scaling=0, graph=graph, tune=tune))
+    hH = mg.Hierarchy(mg.make_params(DIM, N, "H", zero_guess=1, graph=graph, tune=tune, op=args.op))
+    hD = mg.Hierarchy(mg.make_params(DIM, N, "D", zero_guess=1, scaling=0, graph=graph, tune=tune, op=args.op))
 
     def run(h, bb, uu, k):
         secs, res = [], None
@@ -505,7 +511,10 @@ def main():
         with open(args.kernel_dump, "w") as f:
             json.dump({"result": resP, "kernels": ktimes}, f, indent=1)
     top = max(ktimes, key=lambda k: k["total_ms"])
-    traffic, traffic_note = profiled_traffic() if top["kind"] == 5 else (None, "dominant kernel is not the update")
+    if args.op != 0:
+        traffic, traffic_note = None, "the ncu summary covers the finite-difference workload"
+    else:
+        traffic, traffic_note = profiled_traffic() if top["kind"] == 5 else (None, "dominant kernel is not the update")
     tot_ms = sum(k["total_ms"] for k in ktimes)
     peak, peak_kind = measured_peaks()
     ach = top["bytes"] * top["launches"] / (top["total_ms"] * 1e-3) / 1e9
@@ -520,8 +529,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16 storage / f32 sweeps / f64 refinement",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "dof": ndof, "iters_fp16": resH["iters"], "iters_fp64": resD["iters"],
-                   "oracle_iters": oracle_iters("3d_n255_random_seed2"),
+        "config": {"workload": WORKLOAD_Q1 if args.op == 1 else WORKLOAD, "dof": ndof,
+                   "iters_fp16": resH["iters"], "iters_fp64": resD["iters"],
+                   "oracle_iters": oracle_iters(GOLDEN_KEY[args.op]),
                    "rel_res_true_fp16": resH["rel_res_true"], "rel_res_true_fp64": resD["rel_res_true"],
                    "fp64_mg_dofs": valueD, "fp64_mg_ms": 1e3 * tD, "speedup_fp16_vs_fp64": value / valueD,
                    "rel_diff_u_fp16_vs_fp64": rel_diff, "l2": "256 MiB L2 flush before every step; "
@@ -541,12 +551,12 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_extras:
+    if rank == 0 and world == 1 and not args.no_extras and args.op == 0:
         hH.close()
         hD.close()
         line["config"]["extras"] = extra_workloads(mg, I, torch, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample, _ = cpu_oracle_sample(b, 1)
+        v, cores, sample, _ = cpu_oracle_sample(b, 1, args.op)
         line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -124,6 +124,16 @@ typedef struct mg_params {
                            same operator at their h (for Q1 this equals the Galerkin
                            product of full weighting, A and interpolation).  op = 1
                            requires fuse_pre = 0 */
+    int32_t scale_ahead;/* 1 (default): with scaling = 1 and a non-FP64 finest level, the fused
+                           IR update (Alg. 2 lines 6-7) also writes the next step's g =
+                           cast(r * 2^k) (line 4), with 2^k = 2^sigma_log2 / 2^e and 2^e the
+                           power of two just above the previous ||r||_inf, so the separate
+                           scale-and-cast pass over the FP64 residual is skipped; alpha is
+                           then 2^-k, a power of two within a factor of two of the previous
+                           residual's norm instead of the current one.  When the scaled
+                           values would overflow the storage type, that step falls back to
+                           the scale-and-cast with alpha = ||r||_inf.  0: always
+                           alpha = ||r||_inf and the separate pass */
     int32_t reserved[1];/* must be 0 */
 } mg_params;
 

@@ -116,7 +116,7 @@ void merge_position(const std::vector<std::pair<int, const Op*>>& members, const
             mo.kkind = o0.kkind; mo.mode = o0.mode; mo.prec = o0.prec; mo.prec_c = o0.prec_c;
             mo.rpw = o0.sh.rpw; mo.ty = o0.sh.ty; mo.smem = o0.sh.smem;
             std::vector<int> table;
-            if (o0.kkind == K_SWEEP) {
+            if (o0.kkind == K_SWEEP && o0.sh.rpw > 0) {  // marching (TMA) sweeps
                 std::vector<SweepItem> items(g.second.size());
                 for (size_t i = 0; i < g.second.size(); ++i) {
                     const Op& o = *g.second[i].second;
@@ -460,6 +460,8 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
         sh.scaling = h.p.scaling;
         sh.tol_mode = h.p.tol_mode;
         sh.guard = h.p.guard;
+        sh.scale_ahead = h.scale_ahead_on() ? 1 : 0;
+        sh.glimit = h.g_limit();
         sh.b = b[i];
         sh.uout = u[i];
     }

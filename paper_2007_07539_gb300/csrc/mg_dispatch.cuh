@@ -7,6 +7,7 @@ namespace mgi {
 
 using KFn = void (*)(KArgs);
 using KFn3 = void (*)(KArgs, SweepMaps);  // 3D sweeps (TMA descriptors by value)
+using FKB = void (*)(const KItem*, const int*);  // batched kernels over KItem work lists
 
 // Q1 variants (mode | M_FEM): one row per warp; M_ZERO1 (c = w D^-1 g) does
 // not apply the operator and shares the finite-difference kernel.
@@ -86,9 +87,49 @@ KFn pick(int kind, int mode, int prec_c) {
     return nullptr;
 }
 
+// The direct small-level kernels (3D, finite differences): rpw 0.
+template <class T>
+KFn pick_direct3(int mode, int prec_c) {
+    switch (mode) {
+        case M_JACOBI: return &k_dsweep3<M_JACOBI, T>;
+        case M_ZERO2: return &k_dsweep3<M_ZERO2, T>;
+        case M_ZERO1: return &k_dsweep3<M_ZERO1, T>;
+        case M_RESTRICT:
+            switch (prec_c) {
+                case MG_FP64: return &k_drestrict3<T, double>;
+                case MG_FP32: return &k_drestrict3<T, float>;
+                case MG_FP16: return &k_drestrict3<T, __half>;
+                case MG_BF16: return &k_drestrict3<T, __nv_bfloat16>;
+            }
+    }
+    return nullptr;
+}
+template <class T>
+FKB pick_direct3_batch(int mode, int prec_c) {
+    switch (mode) {
+        case M_JACOBI: return &k_dsweep3_batch<M_JACOBI, T>;
+        case M_ZERO2: return &k_dsweep3_batch<M_ZERO2, T>;
+        case M_ZERO1: return &k_dsweep3_batch<M_ZERO1, T>;
+        case M_RESTRICT:
+            switch (prec_c) {
+                case MG_FP64: return &k_drestrict3_batch<T, double>;
+                case MG_FP32: return &k_drestrict3_batch<T, float>;
+                case MG_FP16: return &k_drestrict3_batch<T, __half>;
+                case MG_BF16: return &k_drestrict3_batch<T, __nv_bfloat16>;
+            }
+    }
+    return nullptr;
+}
+
 template <class T>
 int launch_kernel_t(int dim, int kind, int mode, int prec_c, const KArgs& a, const MarchShape& s,
                     const SweepMaps* maps, void* stream) {
+    if (dim == 3 && kind == K_SWEEP && s.rpw == 0) {
+        KFn f = pick_direct3<T>(mode, prec_c);
+        if (!f) return (int)cudaErrorInvalidValue;
+        f<<<s.gx, s.tx, 0, (cudaStream_t)stream>>>(a);
+        return (int)cudaGetLastError();
+    }
     if (dim == 3 && kind == K_SWEEP) {
         KFn3 f3 = pick_sweep3<T>(mode, prec_c, s.rpw);
         if (!f3 || !maps) return (int)cudaErrorInvalidValue;
@@ -115,6 +156,12 @@ template <class T>
 int launch_batch_t(int kind, int mode, int prec_c, int rpw, const void* items, const int* cta_item, int ncta, int ty,
                    size_t smem, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
+    if (kind == K_SWEEP && rpw == 0) {  // direct small-level kernels: KItem work lists
+        FKB f = pick_direct3_batch<T>(mode, prec_c);
+        if (!f) return (int)cudaErrorInvalidValue;
+        f<<<ncta, 256, 0, st>>>(static_cast<const KItem*>(items), cta_item);
+        return (int)cudaGetLastError();
+    }
     if (kind == K_SWEEP) {
         using FB = void (*)(const SweepItem*, const int*);
         FB f = nullptr;

@@ -64,6 +64,7 @@ extern "C" void mg_params_init(mg_params* p, int32_t dim, int32_t n) {
     p->base_solver = 0;
     p->base_maxit = 0;
     p->base_tol = 1e-4;
+    p->scale_ahead = 1;
 }
 
 extern "C" int32_t mg_level_count(int32_t n, int32_t levels_req, int32_t* sizes) {
@@ -115,6 +116,7 @@ int mgi_validate(const mg_params* p, std::string& why) {
     if (!(p->base_tol >= 0.0) || !std::isfinite(p->base_tol)) { why = "base_tol must be finite and >= 0"; return 0; }
     if (p->op != 0 && p->op != 1) { why = "op must be 0 (finite differences) or 1 (Q1 finite elements)"; return 0; }
     if (p->op == 1 && p->fuse_pre == 1) { why = "fuse_pre is for the finite-difference operator (op = 0)"; return 0; }
+    if (p->scale_ahead != 0 && p->scale_ahead != 1) { why = "scale_ahead must be 0 or 1"; return 0; }
     if (p->reserved[0] != 0) { why = "reserved fields must be 0"; return 0; }
     return L;
 }
@@ -254,7 +256,7 @@ struct Gen {
         op.sh = kernel_shape(h->dim, kkind, mode, op.prec, f.n, f.P, 0);
         a.xstep = op.sh.xstep; a.ystep = op.sh.ystep; a.zstep = op.sh.zstep; a.zlen = op.sh.zlen;
         a.err = &h->st->kerr;
-        if (h->dim == 3 && kkind == K_SWEEP) {  // TMA boxes: TY+2 rows of the swept vector, TY rows of g
+        if (h->dim == 3 && kkind == K_SWEEP && op.sh.rpw > 0) {  // TMA boxes: TY+2 rows of the swept vector, TY rows of g
             op.has_maps = true;
             const int rows = op.sh.ty * op.sh.rpw;
             // the one-pass pre-smoothing + restriction reads g boxes of TY+4 rows
@@ -485,7 +487,8 @@ Op mgi_update_op(mgi_hier& h, const void* cL, int gate, const DevState* st) {
     gen.gate = gate;
     gen.st = st;
     gen.top_from_r = true;
-    return gen.kernel(L, K_UPDATE, 0, cL, nullptr, nullptr);
+    // scale-ahead: the update also writes the next step's g (used only when st is set)
+    return gen.kernel(L, K_UPDATE, 0, cL, h.scale_ahead_on() ? h.lv[L].g : nullptr, nullptr);
 }
 
 static size_t update_blocks_max(const mgi_hier& h) {
@@ -520,7 +523,7 @@ static void build_step(mgi_hier& h) {
 int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
     switch (op.kind) {
         case OP_KERNEL:
-            if (h.dim == 3 && op.kkind == K_SWEEP && !op.has_maps) return (int)cudaErrorNotSupported;
+            if (h.dim == 3 && op.kkind == K_SWEEP && op.sh.rpw > 0 && !op.has_maps) return (int)cudaErrorNotSupported;
             return launch_kernel(h.dim, op.kkind, op.mode, op.prec, op.prec_c, op.a, op.sh,
                                  op.has_maps ? &op.maps : nullptr, s);
         case OP_COARSE:
@@ -683,13 +686,20 @@ static void autotune(mgi_hier& h) {
                 return op;
             };
             const Op base = make();
-            const int z0 = coarse_out ? (base.sh.zlen - 1) / 2 : base.sh.zlen;
+            const int z0 = base.sh.rpw == 0 ? std::max(1, std::min(8, coarse_out ? (n - 1) / 2 : n))
+                                             : (coarse_out ? (base.sh.zlen - 1) / 2 : base.sh.zlen);
             const int zmax = coarse_out ? (n - 1) / 2 : n;
             TileChoice best{base.sh.rpw, z0};
             float tbest = time_op(base);
             // a candidate replaces the model's shape only when clearly faster
             // (timing noise of short kernels is a few percent)
             tbest *= 0.97f;
+            if (h.p.op == 0 && mode != M_PRE && base.sh.rpw != 0 && n <= 255) {  // the direct kernel
+                const TileChoice c{0, 0};
+                tile_choice_set(3, K_SWEEP, kmode, lv.prec, n, &c);
+                const float t = time_op(make());
+                if (t < tbest) { tbest = t; best = c; }
+            }
             for (int rpw = 1; rpw <= 2; ++rpw) {
                 if (rpw == 2 && (coarse_out || n < 16 || h.p.op == 1)) continue;
                 for (int z : {z0 / 2, z0, z0 * 2}) {
@@ -1034,6 +1044,8 @@ mg_status mgi_solve_begin(mgi_hier& h, const double* b, double* u) {
     sh.scaling = h.p.scaling;
     sh.tol_mode = h.p.tol_mode;
     sh.guard = h.p.guard;
+    sh.scale_ahead = h.scale_ahead_on() ? 1 : 0;
+    sh.glimit = h.g_limit();
     sh.phase = 0;
     sh.b = c.bd;
     sh.uout = c.ud;
@@ -1190,7 +1202,7 @@ static double op_bytes(const mgi_hier& h, const Op& op) {
                     if ((op.mode & M_BASE) == M_RESTRICT) return 2 * s * N + sc * Nc;  // read c, g; write g_coarse
                     if ((op.mode & M_BASE) == M_PRE) return 2 * s * N + sc * Nc;       // read g; write c, g_coarse
                     return 2 * s * N;                               // read g; write c
-                case K_UPDATE: return (32 + s) * N;                 // read c; read+write u, r (FP64)
+                case K_UPDATE: return (32 + s + (op.a.dst ? s : 0)) * N;  // read c; read+write u, r (FP64); g
                 case K_SCALE: return (8 + s) * N;                   // read r (FP64); write g
                 case K_PROLONG: return 2 * s * N + sc * Nc;         // read+write c; read c_coarse
             }

@@ -103,6 +103,12 @@ struct mgi_hier {
         return p.rescale16 == 1 && l >= 0 && l + 1 < nlev && lv[l].prec == MG_FP16 && lv[l + 1].prec != MG_FP16;
     }
     int cg_maxit() const { return p.base_maxit > 0 ? p.base_maxit : m0; }
+    // the update writes the next step's g (mg_params.scale_ahead; max-norm scaling, non-FP64 finest level)
+    bool scale_ahead_on() const {
+        return p.scale_ahead == 1 && p.scaling == 1 && nlev > 0 && lv[nlev - 1].prec != MG_FP64 && !g_alias_r;
+    }
+    // overflow threshold of the finest storage type for scaled residual values
+    double g_limit() const { return nlev > 0 && lv[nlev - 1].prec == MG_FP16 ? 65520.0 : 3.0e38; }
     void* arena = nullptr;
     size_t arena_bytes = 0;
     size_t footprint = 0;

@@ -73,6 +73,12 @@ struct DevState {
     int dirty;        // u changed since it was last copied to the caller's array
     int loops;        // body iterations of the device-side IR loop (bounded)
     int kerr;         // non-zero: a kernel's bounded wait for its tile copies ran out
+    int scale_ahead;  // 1: the update writes the next g with inv_pred (mg_params.scale_ahead in effect)
+    int g_ready;      // 1: g of the coming step was written by the last update (the scale-cast returns)
+    int gover;        // set by the update when a scaled g value overflowed the storage type
+    double inv_pred;  // scale-ahead: sigma / 2^e, 2^e the power of two above the last ||r||_inf
+    double thr_pred;  // scale-ahead: |r| >= thr_pred overflows the finest storage type after scaling
+    double glimit;    // the finest storage type's overflow threshold (set at solve start)
     double lscale[MG_MAX_LEVELS];  // power-of-two scale of each rescaled FP16 level's residual
     const double* b;  // caller's right-hand side (device, contiguous)
     double* uout;     // caller's solution (device, contiguous): u0 in, u out
@@ -185,7 +191,8 @@ struct FinItem {
 
 struct MarchShape {
     int gx, gy, gz, tx, ty;
-    int rpw;  // 3D sweeps: rows per warp (the CTA tile has ty * rpw rows)
+    int rpw;  // 3D sweeps: rows per warp (the CTA tile has ty * rpw rows); 0: the direct
+              // small-level kernels (k_dsweep3 / k_drestrict3, one thread per vector / coarse point)
     size_t smem;
     int xstep, ystep, zstep, zlen;
     int nblocks() const { return gx * gy * gz; }
@@ -198,8 +205,11 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
 // sweeps, coarse planes per CTA for the residual-restriction).  kernel_shape
 // uses an entry when there is one, else its wave model.
 struct TileChoice {
-    int rpw, zlen;
+    int rpw, zlen;  // rpw 0: the direct kernel
 };
+// Default for levels of at most this many points per dimension (3D, finite
+// differences, untuned): the direct kernels.
+constexpr int kDirectMaxN = 63;
 void tile_choice_set(int dim, int kind, int mode, int prec, int n, const TileChoice* c);  // nullptr: erase
 bool tile_choice_get(int dim, int kind, int mode, int prec, int n, TileChoice* c);
 

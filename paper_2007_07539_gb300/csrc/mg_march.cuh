@@ -542,6 +542,118 @@ __global__ void __launch_bounds__(SweepLB<MODE, RPW, OP>::kThreads, SweepLB<MODE
     sweep3_body<MODE, T, TC, RPW, OP>(it.a, it.maps, bx, rest % it.gy, rest / it.gy);
 }
 
+// ---------------------------------------------------------------- 3D direct kernels for small levels
+// Levels that live in L2 are bound by latency, not bandwidth: a marching tile
+// pays its pipeline fill per CTA.  These kernels give every thread one V-vector
+// of a row (sweeps) or one coarse point (residual-restriction) and read the
+// operands through the read-only path.  They perform the same IEEE operations
+// in the same order as k_sweep3 (finite differences), so a level gives the same
+// bits whichever of the two runs it.
+template <class C> struct SA;
+template <> struct SA<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <> struct SA<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+
+template <int MODE, class T>
+__device__ __forceinline__ void dsweep3_body(const KArgs& a, int cta) {
+    using C = typename Tr<T>::C;
+    using A = SA<C>;
+    constexpr int V = Tr<T>::V;
+    constexpr bool NEED_G = MODE == M_JACOBI;
+    if (a.gate && a.st->phase != 0) return;
+    const int vpr = a.P / V;
+    const int idx = cta * blockDim.x + threadIdx.x;
+    if (idx >= vpr * a.n * a.n) return;
+    const int row = idx / vpr;
+    const int x = (idx - row * vpr) * V;
+    const int z = row / a.n, y = row - z * a.n;
+    const long long o = offs<3>(x, y, z, a.P, a.S);
+    const T* src = reinterpret_cast<const T*>(a.src) + o;
+    const C c1 = coef<C>(a.cf, 0), c2 = coef<C>(a.cf, 1), c3 = coef<C>(a.cf, 2), k2 = coef<C>(a.cf, 3);
+    C c0[V], out[V];
+    ldv(src, c0);
+    if constexpr (MODE == M_ZERO1) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) out[i] = x + i < a.n ? A::mul(c3, c0[i]) : (C)0;
+    } else {
+        C ym[V], yp[V], zm[V], zp[V], g[V];
+        ldv(src - a.P, ym);
+        ldv(src + a.P, yp);
+        ldv(src - a.S, zm);
+        ldv(src + a.S, zp);
+        if (NEED_G) ldv(reinterpret_cast<const T*>(a.g) + o, g);
+        const C left = ld1(src - 1), right = ld1(src + V);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const C xs = A::add(i ? c0[i - 1] : left, i < V - 1 ? c0[i + 1] : right);
+            const C nb = A::add(A::add(xs, A::add(ym[i], yp[i])), A::add(zm[i], zp[i]));
+            C v;
+            if (MODE == M_JACOBI) v = A::fma(c2, nb, A::fma(c1, c0[i], A::mul(c3, g[i])));
+            else v = A::mul(c3, A::fma(c2, nb, A::mul(k2, c0[i])));
+            out[i] = x + i < a.n ? v : (C)0;
+        }
+    }
+    stv(reinterpret_cast<T*>(a.dst) + o, out);
+}
+template <int MODE, class T>
+__global__ void __launch_bounds__(256) k_dsweep3(const KArgs a) { dsweep3_body<MODE, T>(a, blockIdx.x); }
+template <int MODE, class T>
+__global__ void __launch_bounds__(256) k_dsweep3_batch(const KItem* __restrict__ items, const int* __restrict__ cta_item) {
+    const KItem& it = items[cta_item[blockIdx.x]];
+    dsweep3_body<MODE, T>(it.a, blockIdx.x - it.cta_begin);
+}
+
+// Coarse point (I, J, K) = R (g - A c) over fine points 2I..2I+2 (x), 2J..2J+2 (y),
+// 2K..2K+2 (z): x first, then z, then y, as the marching kernel combines them.
+template <class T, class TC>
+__device__ __forceinline__ void drestrict3_body(const KArgs& a, int cta) {
+    using C = typename Tr<T>::C;
+    using A = SA<C>;
+    if (a.gate && a.st->phase != 0) return;
+    const int nc = a.nc;
+    const int idx = cta * blockDim.x + threadIdx.x;
+    if (idx >= nc * nc * nc) return;
+    const int I = idx % nc, J = (idx / nc) % nc, K = idx / (nc * nc);
+    const C h2v = coef<C>(a.cf, 4), mh6 = coef<C>(a.cf, 5);
+    const T* c = reinterpret_cast<const T*>(a.src);
+    const T* g = reinterpret_cast<const T*>(a.g);
+    auto resid = [&](int fx, int fy, int fz) {  // g - A c at a fine point, as k_sweep3 forms it
+        const long long o = offs<3>(fx, fy, fz, a.P, a.S);
+        const T* p = c + o;
+        const C xs = A::add(ld1(p - 1), ld1(p + 1));
+        const C nb = A::add(A::add(xs, A::add(ld1(p - a.P), ld1(p + a.P))), A::add(ld1(p - a.S), ld1(p + a.S)));
+        return A::fma(h2v, nb, A::fma(mh6, ld1(p), ld1(g + o)));
+    };
+    C zr[3];  // z-combined x-restrictions of the fine rows 2J, 2J+1, 2J+2
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+        C q[3];
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz) {
+            const int fy = 2 * J + dy, fz = 2 * K + dz, fx = 2 * I;
+            q[dz] = A::add(A::add(A::mul((C)0.25, resid(fx, fy, fz)), A::mul((C)0.5, resid(fx + 1, fy, fz))),
+                           A::mul((C)0.25, resid(fx + 2, fy, fz)));
+        }
+        zr[dy] = A::add(A::add(A::mul((C)0.25, q[0]), A::mul((C)0.5, q[1])), A::mul((C)0.25, q[2]));
+    }
+    const C v = A::add(A::add(A::mul((C)0.25, zr[0]), A::mul((C)0.5, zr[1])), A::mul((C)0.25, zr[2]));
+    st1(reinterpret_cast<TC*>(a.dst) + offs<3>(I, J, K, a.Pc, a.Sc), v);
+}
+template <class T, class TC>
+__global__ void __launch_bounds__(256) k_drestrict3(const KArgs a) { drestrict3_body<T, TC>(a, blockIdx.x); }
+template <class T, class TC>
+__global__ void __launch_bounds__(256) k_drestrict3_batch(const KItem* __restrict__ items, const int* __restrict__ cta_item) {
+    const KItem& it = items[cta_item[blockIdx.x]];
+    drestrict3_body<T, TC>(it.a, blockIdx.x - it.cta_begin);
+}
+
 // ---------------------------------------------------------------- 3D one-pass pre-smoothing + restriction
 // Temporal blocking of Alg. 1 steps 1-2 on one level (M_PRE): for a tile of
 // R = 2TJ+1 fine rows and 2TK+1 fine planes it computes the two damped
@@ -900,6 +1012,7 @@ __device__ __forceinline__ void scale_cast_body(const KArgs& a, int cta) {
     using C = typename Tr<T>::C;
     constexpr int V = Tr<T>::V;
     if (a.gate && a.st->phase != 0) return;
+    if (a.st && a.st->g_ready) return;  // the last update already wrote g (scale-ahead)
     const int vpr = a.P / V;  // vectors per padded row
     const int rows = DIM == 3 ? a.n * a.n : a.n;
     const int idx = cta * blockDim.x + threadIdx.x;
@@ -1112,6 +1225,20 @@ __device__ __forceinline__ void ld4(const T* p, typename Tr<T>::C (&v)[4]) {
 // the stencil of c comes through the read-only cache as vector loads.  FP64
 // instructions: the two fused multiply-adds of Alg. 2 lines 6-7 per point
 // (three for FP32/BF16 corrections), nothing else.
+// Four consecutive values rounded to T (16-byte aligned for FP32, 8 for 16-bit types).
+template <class T>
+__device__ __forceinline__ void st4(T* p, const float (&v)[4]) {
+    if constexpr (std::is_same<T, float>::value) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (std::is_same<T, __half>::value) {
+        const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+        *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const unsigned*>(&a), *reinterpret_cast<const unsigned*>(&b));
+    } else if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+        *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const unsigned*>(&a), *reinterpret_cast<const unsigned*>(&b));
+    }
+}
+
 // OP = 1: the Q1 operator (3x3(x3) neighbourhood, integer weights).
 constexpr int kUpdQ = 4;
 template <int DIM, class T, int OP>
@@ -1128,6 +1255,18 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
     const double beta = alpha * a.h2inv;
     SqAcc sq;
     unsigned long long nmax = 0ull;
+    // scale-ahead (Alg. 2 line 4 of the next step, fused): g = cast(r inv_pred),
+    // inv_pred a power of two; |r| >= thr_pred would overflow T (flagged, and the
+    // next step falls back to the separate scale-and-cast)
+    T* const gout = (!std::is_same<T, double>::value && a.st && a.st->scale_ahead && a.dst)
+                        ? reinterpret_cast<T*>(a.dst) : nullptr;
+    ScaleK gk{};
+    unsigned long long gthr = ~0ull;
+    if (gout) {
+        gk = make_scale(a.st->inv_pred);
+        gthr = abs_key(a.st->thr_pred);
+    }
+    bool gbad = false;
     // grid-stride over the row vectors: each CTA owns a fixed set, so the
     // partial sums (one per CTA) are accumulated in a fixed order
     for (int idx = cta * blockDim.x + threadIdx.x; idx < total; idx += ncta * blockDim.x) {
@@ -1164,12 +1303,45 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
                 for (int i = 0; i < Q; ++i) rv[q][i + 1] = mid[i];
             }
             constexpr int CR = DIM == 3 ? 4 : 1;  // the centre row (dy = dz = 0)
+            // FP16, 3D: every loaded value is split once (h_split); the rows with one
+            // non-zero (dy, dz) offset give edges at dx = +-1 (weight 2), the rows with
+            // two give edges at dx = 0 (2) and corners at dx = +-1 (1):
+            // W_i = 2 (A1_{i-1} + A1_{i+1}) + 2 A2_i + A2_{i-1} + A2_{i+1}, with A1 / A2 the
+            // column sums of the split values over the two row groups
+            int a1h[Q + 2], a2h[Q + 2];
+            float a1l[Q + 2], a2l[Q + 2];
+            if constexpr (DIM == 3 && std::is_same<T, __half>::value) {
+#pragma unroll
+                for (int j = 0; j < Q + 2; ++j) {
+                    a1h[j] = a2h[j] = 0;
+                    a1l[j] = a2l[j] = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) {
+                        const int nz = (q % 3 != 1) + (q / 3 != 1);
+                        if (nz == 0) continue;
+                        const HSplit t = h_split(rv[q][j]);
+                        if (nz == 1) { a1h[j] += t.hi; a1l[j] = __fadd_rn(a1l[j], t.lo); }
+                        else { a2h[j] += t.hi; a2l[j] = __fadd_rn(a2l[j], t.lo); }
+                    }
+                }
+            }
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if (x + i < a.n) {
                     const C cc = rv[CR][i + 1];
                     double s, s2 = 0.0;
-                    if constexpr (std::is_same<T, __half>::value) {
+                    if constexpr (DIM == 3 && std::is_same<T, __half>::value) {
+                        // |lo| sums: 4 values per column and group, |.| <= 2^19; the total
+                        // 32 lo_c + ... stays an integer below 2^24 (exact in FP32)
+                        const HSplit m = h_split(cc);
+                        const int H = BETA * m.hi - 2 * (a1h[i] + a1h[i + 2]) - 2 * a2h[i + 1] - (a2h[i] + a2h[i + 2]);
+                        float L = __fmul_rn((float)BETA, m.lo);
+                        L = __fmaf_rn(-2.0f, __fadd_rn(a1l[i], a1l[i + 2]), L);
+                        L = __fmaf_rn(-2.0f, a2l[i + 1], L);
+                        L = __fsub_rn(L, __fadd_rn(a2l[i], a2l[i + 2]));
+                        const int Li = __float2int_rn(L);
+                        s = i64_to_f64(((long long)H << 18) + (long long)Li, -24);
+                    } else if constexpr (std::is_same<T, __half>::value) {
                         // FP16 values as integers in units of 2^-24 (h_split): the
                         // weighted sum of the hi parts in int32 (|.| <= 64 * 2^22),
                         // of the lo parts in FP32 (integers, |.| <= 64 * 2^17 < 2^24)
@@ -1283,7 +1455,20 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
         *reinterpret_cast<double2*>(up + 2) = make_double2(uu[2], uu[3]);
         *reinterpret_cast<double2*>(rp) = make_double2(rr[0], rr[1]);
         *reinterpret_cast<double2*>(rp + 2) = make_double2(rr[2], rr[3]);
+        if constexpr (!std::is_same<T, double>::value) {
+            if (gout) {  // pads of r are 0, so pads of g stay 0
+                float gv[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    gbad |= abs_key(rr[i]) >= gthr;
+                    gv[i] = scaled_f32(rr[i], gk);
+                }
+                st4(gout + o, gv);
+            }
+        }
     }
+    if (gout && __any_sync(kFull, gbad) && (threadIdx.x & 31) == 0)
+        atomicExch(&const_cast<DevState*>(a.st)->gover, 1);
     write_partials(sq, nmax, E, a.partials, cta);
 }
 template <int DIM, class T, int OP>

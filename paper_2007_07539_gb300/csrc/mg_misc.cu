@@ -189,6 +189,21 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
     const int bmode = mode & M_BASE;
     const bool q1 = (mode & M_FEM) != 0;  // Q1 sweeps keep one row per warp
     const bool need_g = bmode == M_JACOBI || bmode == M_RESTRICT;
+    if (dim == 3 && !q1 && bmode != M_PRE) {  // small levels: the direct kernels (same results)
+        TileChoice tc;
+        const bool direct = tile_choice_get(dim, kind, mode, prec, n, &tc) ? tc.rpw == 0 : n <= kDirectMaxN;
+        if (direct) {
+            s.rpw = 0;
+            s.tx = 256;
+            s.ty = 1;
+            const long long units = bmode == M_RESTRICT ? (long long)((n - 1) / 2) * ((n - 1) / 2) * ((n - 1) / 2)
+                                                        : (long long)(P / V) * n * n;
+            s.gx = (int)std::max<long long>(1, cdiv(units, 256));
+            s.gy = 1;
+            s.smem = 0;
+            return s;
+        }
+    }
     if (bmode == M_RESTRICT || bmode == M_PRE) {
         const int nc = (n - 1) / 2;
         s.xstep = P > CW ? CW - V : CW;
@@ -590,6 +605,11 @@ __device__ __forceinline__ void finalize_body(int kind, DevState* st, const doub
     if (lane != 0) return;
     const double rn = sqrt(sr);
     const double rinf = __longlong_as_double((long long)mr);
+    // scale-ahead: did this step's update write the next g (with inv_pred, no overflow)?
+    const bool ahead_ok = kind == FIN_STEP && st->scale_ahead && !st->gover && st->inv_pred > 0.0;
+    const double inv_used = st->inv_pred;
+    st->gover = 0;
+    st->g_ready = 0;
     if (kind == FIN_INIT) {
         st->bnorm2 = sqrt(sb);
         st->tol_abs = st->tol_mode == 0 ? st->tol * st->bnorm2 : st->tol;
@@ -640,8 +660,21 @@ __device__ __forceinline__ void finalize_body(int kind, DevState* st, const doub
     double alpha = 1.0, inv = 1.0;
     if (st->scaling == 1) { alpha = rinf / st->sigma; inv = st->sigma / rinf; }
     else if (st->scaling == 2) { alpha = rn / st->sigma; inv = st->sigma / rn; }
+    if (ahead_ok) {  // g = cast(r inv_used) is in place: alpha = 1 / inv_used (powers of two, exact)
+        int e = 0;
+        (void)frexp(inv_used, &e);
+        alpha = ldexp(1.0, 1 - e);
+        inv = inv_used;
+        st->g_ready = 1;
+    }
     st->alpha = alpha;
     st->inv = inv;
+    if (st->scale_ahead && rinf > 0.0) {  // the next update's scale: sigma / 2^e, 2^e > ||r||_inf >= 2^(e-1)
+        int e = 0;
+        (void)frexp(rinf, &e);
+        st->inv_pred = ldexp(st->sigma, -e);
+        st->thr_pred = st->glimit / st->inv_pred;  // exact: inv_pred is a power of two
+    }
     st->phase = 0;
 }
 

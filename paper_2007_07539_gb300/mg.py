@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("graph", ctypes.c_int32), ("no_tail", ctypes.c_int32), ("tune", ctypes.c_int32),
                 ("fuse_pre", ctypes.c_int32), ("rescale16", ctypes.c_int32), ("base_solver", ctypes.c_int32),
                 ("base_maxit", ctypes.c_int32), ("base_tol", ctypes.c_double), ("op", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("scale_ahead", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class Result(ctypes.Structure):

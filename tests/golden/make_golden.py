@@ -2,7 +2,7 @@
 of the FP64 oracle (oracle/) on the benchmark workloads.  Calls only the oracle
 and the seeded input recipes; run it after any change to either:
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [name ...]   (only the named entries; the others are kept)
 """
 import json
 import os
@@ -20,6 +20,7 @@ WORKLOADS = {
     "2d_n127_manufactured": dict(dim=2, n=127, rhs=("manufactured", 1)),
     "3d_n63_random_seed2": dict(dim=3, n=63, rhs=("random", 2)),
     "3d_n511_manufactured": dict(dim=3, n=511, rhs=("manufactured", 1)),
+    "3d_n255_random_seed2_q1": dict(dim=3, n=255, rhs=("random", 2), op=1),
 }
 
 
@@ -30,20 +31,27 @@ def rhs(w):
     return I.manufactured_rhs(w["dim"], w["n"], arg)
 
 
-def main():
+def main(only=None):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_solves.json")
     out = {}
+    if only and os.path.exists(path):
+        with open(path) as f:
+            out = json.load(f)
     for name, w in WORKLOADS.items():
+        if only and name not in only:
+            continue
         t = time.time()
-        _, info, hist = O.ir_solve(rhs(w), scaling=1, nthreads=os.cpu_count() or 1)
+        op = w.get("op", 0)
+        _, info, hist = O.ir_solve(rhs(w), scaling=1, nthreads=os.cpu_count() or 1, op=op)
         out[name] = dict(dim=w["dim"], n=w["n"], rhs=list(w["rhs"]), iters=info["iters"],
                          rel_res_true=info["rel_res_true"], history=[float(x) for x in hist],
                          params="V(2,2), omega 0.8, damped Jacobi, FW/linear transfers, exact base solve, "
-                                "alpha = ||r||_inf, rel. tol 1e-10, u0 = 0")
+                                "alpha = ||r||_inf, rel. tol 1e-10, u0 = 0, operator "
+                                + ("Q1 finite elements / h^d" if op == 1 else "finite differences"))
         print(name, info["iters"], f"{time.time() - t:.1f}s", flush=True)
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_solves.json")
     with open(path, "w") as f:
-        json.dump(out, f, indent=1)
+        json.dump({k: out[k] for k in WORKLOADS if k in out}, f, indent=1)
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:] or None)

@@ -252,3 +252,14 @@ def test_one_pass_presmoothing_same_solve(lad):
             assert r["status"] == 0
             out.append((u.cpu().numpy(), r["iters"]))
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+@pytest.mark.parametrize("dim,n,lad", [(3, 63, "H"), (3, 127, "HSD"), (2, 255, "H"), (3, 95, "BSD"), (3, 63, "S")])
+def test_scale_ahead_on_and_off(oracle, dim, n, lad):
+    """The next step's g written by the IR update with a power-of-two scale from the
+    previous residual norm (scale_ahead = 1, default) and the separate scale-and-cast
+    with alpha = ||r||_inf (scale_ahead = 0) both reach FP64 accuracy within the oracle's
+    iteration count + 2."""
+    b = I.random_rhs(dim, n, 800 + n)
+    for sa in (0, 1):
+        check_solve(oracle, dim, n, lad, b, extra_iters=2, scale_ahead=sa)
