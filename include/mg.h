@@ -91,7 +91,12 @@ typedef struct mg_params {
                            test, recompute b - A u in FP64 and continue from it if it fails */
     int32_t graph;      /* 1 (default): run the whole solve as one CUDA graph launch with a
                            device-side IR loop; 0: one launch per kernel from a host loop */
-    int32_t no_tail;    /* 1: no coarse-tail kernel (every level as plain kernels); default 0 */
+    int32_t no_tail;    /* coarse-tail kernel (the coarsest levels' cycle in one launch with the levels
+                           in shared memory): 0 (default) in one CTA; 1: no tail (every level as
+                           plain kernels); 2: in one CTA or in a thread-block cluster of 16 or 8
+                           CTAs sharing their shared memory (levels up to 2^15 points), whichever
+                           covers more levels (same results; measured no faster on GB300 at the
+                           benchmark sizes) */
     int32_t tune;       /* 1: autotune at creation: every 3D stencil kernel of the hierarchy
                            (sweeps from zero, residual-restriction, Jacobi; per level) is timed
                            on the device with candidate tile shapes -- rows per warp and march
@@ -158,7 +163,8 @@ typedef struct mg_level_info {
     int32_t n;        /* interior points per dimension */
     int32_t prec;     /* mg_prec */
     int32_t pitch;    /* row pitch of the padded device layout, in elements */
-    int32_t reserved;
+    int32_t tail_ctas;/* 0: the level runs as level kernels; else it is in the coarse tail,
+                         held by this many CTAs (1, or a thread-block cluster of 8 / 16) */
     size_t bytes;     /* device bytes held for this level */
 } mg_level_info;
 

@@ -113,7 +113,7 @@ extern "C" mg_status mg_level_info_get(const mg_hierarchy* hh, int32_t level, mg
     out->n = L.geo.n;
     out->prec = L.prec;
     out->pitch = L.geo.P;
-    out->reserved = h->nlev;
+    out->tail_ctas = h->tail_level >= 0 && level <= h->tail_level ? h->tail_cs : 0;
     out->bytes = 3 * (size_t)L.geo.total * L.esz;
     return MG_OK;
 }

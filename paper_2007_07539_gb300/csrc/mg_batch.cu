@@ -149,6 +149,7 @@ void merge_position(const std::vector<std::pair<int, const Op*>>& members, const
             out.push_back(mo);
         } else if (o0.kind == OP_TAIL) {
             mo.type = MOp::TAIL;
+            mo.ty = o0.sh.ty;  // CTAs per instance (cluster size; grouped by it)
             std::vector<TailItem> items(g.second.size());
             int prec = hs[g.second.front().first]->tail_prec;
             for (size_t i = 0; i < g.second.size(); ++i) {
@@ -244,7 +245,7 @@ int run(Plan& p, const std::vector<MOp>& ops, cudaStream_t s) {
                 break;
             case MOp::TAIL:
                 rc = launch_tail_batch(3, m.tail_prec, reinterpret_cast<const TailItem*>(base + m.items_off), m.nitems,
-                                       m.smem, s);
+                                       m.smem, m.ty, s);
                 break;
             case MOp::FIN:
                 rc = launch_finalize_batch(m.fin_kind, reinterpret_cast<const FinItem*>(base + m.items_off), m.nitems, s);

@@ -10,8 +10,10 @@
 
 namespace mgi {
 
-// p / n for p < 2^13 through mn = ceil(2^40 / n) (division by an invariant
-// integer with a fixed-point reciprocal; exact because p (mn - 2^40/n) < 2^40/n)
+// p / n through mn = ceil(2^40 / n) (division by an invariant integer with a
+// fixed-point reciprocal): the error p (mn - 2^40/n) / 2^40 < p / 2^40 stays
+// below 1/n, so the quotient is exact, for every p < 2^40 / n (here p < 2^20,
+// n < 2^10)
 __device__ __forceinline__ int divn(int p, unsigned long long mn) {
     return (int)(((unsigned long long)(unsigned)p * mn) >> 40);
 }
@@ -36,27 +38,30 @@ __device__ __forceinline__ typename Tr<T>::C cget(const T* a, int p) {
     else return a[p];
 }
 
-// sum of the 2*DIM axis neighbours of compact point p; zero outside the grid
-template <int DIM, class T>
-__device__ __forceinline__ typename Tr<T>::C cnbsum(const T* a, int p, int n, int i, int j, int k) {
-    using C = typename Tr<T>::C;
+// sum of the 2*DIM axis neighbours of compact point p; zero outside the grid.
+// get(q) returns the value of point q in the arithmetic type C.
+template <int DIM, class C, class G>
+__device__ __forceinline__ C cnbsum_f(const G& get, int p, int n, int i, int j, int k) {
     C s = 0;
-    if (i > 0) s += cget(a, p - 1);
-    if (i < n - 1) s += cget(a, p + 1);
-    if (j > 0) s += cget(a, p - n);
-    if (j < n - 1) s += cget(a, p + n);
+    if (i > 0) s += get(p - 1);
+    if (i < n - 1) s += get(p + 1);
+    if (j > 0) s += get(p - n);
+    if (j < n - 1) s += get(p + n);
     if (DIM == 3) {
-        if (k > 0) s += cget(a, p - n * n);
-        if (k < n - 1) s += cget(a, p + n * n);
+        if (k > 0) s += get(p - n * n);
+        if (k < n - 1) s += get(p + n * n);
     }
     return s;
+}
+template <int DIM, class T>
+__device__ __forceinline__ typename Tr<T>::C cnbsum(const T* a, int p, int n, int i, int j, int k) {
+    return cnbsum_f<DIM, typename Tr<T>::C>([&](int q) { return cget(a, q); }, p, n, i, j, k);
 }
 
 // W of the Q1 operator at compact point p: weight 1 on the 8 neighbours (2D);
 // 2 on the 12 edge and 1 on the 8 corner neighbours, 0 on the 6 faces (3D)
-template <int DIM, class T>
-__device__ __forceinline__ typename Tr<T>::C cwsum_q1(const T* a, int p, int n, int i, int j, int k) {
-    using C = typename Tr<T>::C;
+template <int DIM, class C, class G>
+__device__ __forceinline__ C cwsum_q1_f(const G& get, int p, int n, int i, int j, int k) {
     C s1 = 0, s2 = 0;  // weight-1 and weight-2 sums
 #pragma unroll
     for (int dk = (DIM == 3 ? -1 : 0); dk <= (DIM == 3 ? 1 : 0); ++dk)
@@ -68,11 +73,15 @@ __device__ __forceinline__ typename Tr<T>::C cwsum_q1(const T* a, int p, int n, 
                 if (nz == 0 || (DIM == 3 && nz == 1)) continue;
                 if (i + di < 0 || i + di >= n || j + dj < 0 || j + dj >= n || k + dk < 0 || k + dk >= (DIM == 3 ? n : 1))
                     continue;
-                const C v = cget(a, p + di + dj * n + dk * n * n);
+                const C v = get(p + di + dj * n + dk * n * n);
                 if (DIM == 3 && nz == 2) s2 += v;
                 else s1 += v;
             }
     return (C)2 * s2 + s1;
+}
+template <int DIM, class T>
+__device__ __forceinline__ typename Tr<T>::C cwsum_q1(const T* a, int p, int n, int i, int j, int k) {
+    return cwsum_q1_f<DIM, typename Tr<T>::C>([&](int q) { return cget(a, q); }, p, n, i, j, k);
 }
 // beta of operator op (the centre weight of beta I - W)
 template <int DIM>
@@ -81,6 +90,10 @@ __device__ __forceinline__ int op_beta_d(int op) { return op == 1 ? (DIM == 3 ? 
 template <int DIM, class T>
 __device__ __forceinline__ typename Tr<T>::C cwsum(int op, const T* a, int p, int n, int i, int j, int k) {
     return op == 1 ? cwsum_q1<DIM, T>(a, p, n, i, j, k) : cnbsum<DIM, T>(a, p, n, i, j, k);
+}
+template <int DIM, class C, class G>
+__device__ __forceinline__ C cwsum_f(int op, const G& get, int p, int n, int i, int j, int k) {
+    return op == 1 ? cwsum_q1_f<DIM, C>(get, p, n, i, j, k) : cnbsum_f<DIM, C>(get, p, n, i, j, k);
 }
 
 // Block-wide sum / max; every thread receives the result.  Fixed reduction

@@ -104,8 +104,9 @@ int mgi_validate(const mg_params* p, std::string& why) {
     if (p->tol_mode != 0 && p->tol_mode != 1) { why = "tol_mode must be 0 or 1"; return 0; }
     if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) { why = "tol must be finite and >= 0"; return 0; }
     if (p->max_iter < 0 || p->max_iter > kMaxIter) { why = "max_iter out of range"; return 0; }
-    if ((p->no_tail != 0 && p->no_tail != 1) || (p->tune != 0 && p->tune != 1) || (p->fuse_pre != 0 && p->fuse_pre != 1)) {
-        why = "no_tail, tune and fuse_pre must be 0 or 1";
+    if (p->no_tail < 0 || p->no_tail > 2) { why = "no_tail must be 0, 1 or 2"; return 0; }
+    if ((p->tune != 0 && p->tune != 1) || (p->fuse_pre != 0 && p->fuse_pre != 1)) {
+        why = "tune and fuse_pre must be 0 or 1";
         return 0;
     }
     if ((p->rescale16 != 0 && p->rescale16 != 1) || (p->base_solver != 0 && p->base_solver != 1)) {
@@ -301,6 +302,8 @@ struct Gen {
         t.omega = h->p.omega;
         t.cf = make_sweep_coef(h->dim, h->p.op, t.omega, t.h2inv);
         t.op = h->p.op;
+        t.sh = h->tail_sh[l];
+        t.shc = l > 0 ? h->tail_sh[l - 1] : t.sh;
         t.sslot = -1;
         t.scr2 = -1;
         t.rsig = h->rsig;
@@ -387,6 +390,7 @@ struct Gen {
             op.prog_off = (int)h->tail_host.size();
             tvisit(l, first);
             op.prog_len = (int)h->tail_host.size() - op.prog_off;
+            op.sh.ty = h->tail_cs;  // tails of different cluster sizes are not merged in batches
             op.a.gate = gate;
             op.a.st = st;
             out->push_back(op);
@@ -510,12 +514,8 @@ static void build_step(mgi_hier& h) {
     }
     h.step_tail_ops = h.tail_host.size();
     Op up = mgi_update_op(h, cL, 1, h.st);
+    up.a.fin = 1;  // the update's last CTA runs the step's finalisation (FIN_STEP)
     h.step.push_back(up);
-    Op fin{};
-    fin.kind = OP_FINALIZE;
-    fin.fin_kind = FIN_STEP;
-    fin.nblocks = up.sh.nblocks();
-    h.step.push_back(fin);
     h.step_kernels = 0;
     for (const Op& op : h.step) h.step_kernels += op.kind == OP_ZERO ? 0 : op.kind == OP_RESCALE ? 2 : 1;
 }
@@ -541,7 +541,7 @@ int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
             return launch_finalize(op.fin_kind, h.st, h.partials, op.nblocks, s);
         case OP_TAIL:
             return launch_tail(h.dim, h.tail_prec, h.tail_prog + op.prog_off, op.prog_len, h.minv, h.m0, op.a.st,
-                               op.a.gate, h.tail_smem, s);
+                               op.a.gate, h.tail_smem, h.tail_cs, s);
     }
     return (int)cudaErrorInvalidValue;
 }
@@ -569,57 +569,77 @@ static void free_hier(mgi_hier* h) {
     delete h;
 }
 
-// Shared-memory plan of the coarse tail: the deepest level T >= 1 with at
-// most kTailMaxPoints points whose arrays (c, t, g of levels 0..T in their
-// storage types, plus one residual scratch in the arithmetic type, the
-// scale slots and coarse scratch of rescaled FP16 levels, and the CG vectors
-// of the base level) fit in kTailMaxSmem bytes; tail_level = -1 when no level
-// qualifies.
-static void plan_tail(mgi_hier& h, bool disabled) {
+// Shared-memory plan of the coarse tail: the deepest level T >= 1 whose
+// levels 0..T (c, t, g in their storage types, one residual scratch in the
+// arithmetic type, the scale slots and coarse scratch of rescaled FP16 levels,
+// the CG vectors of the base level) fit in kTailMaxSmem bytes per CTA, either
+// in one CTA (levels of at most kTailMaxPoints points) or distributed over a
+// thread-block cluster of 16 or 8 CTAs (chunks of 2^sh points per CTA; dense
+// base solve and no rescaled level inside, as their reductions are CTA-wide);
+// tail_level = -1 when no level qualifies.  probe = false (no device query, or
+// the cluster tail not requested): single-CTA plans only.
+static void plan_tail(mgi_hier& h, bool disabled, bool probe) {
     h.tail_level = -1;
     h.tail_smem = 0;
+    h.tail_cs = 1;
     if (disabled) return;
     for (int T = h.nlev - 1; T >= 1; --T) {
-        size_t off = 0, rmax = 0;
-        bool ok = true;
-        for (int l = 0; l <= T && ok; ++l) {
-            const long long n = h.lv[l].geo.n;
-            const long long N = h.dim == 3 ? n * n * n : n * n;
-            if (N > kTailMaxPoints) { ok = false; break; }
-            for (int v = 0; v < 3; ++v) {
-                h.tail_soff[l][v] = (int)off;
-                off = align_up(off + (size_t)N * h.lv[l].esz, 16);
-            }
-            rmax = std::max(rmax, (size_t)N * (h.lv[l].prec == MG_FP64 ? 8 : 4));
-        }
-        if (!ok) continue;
-        h.tail_rscr = (int)off;
-        off = align_up(off + rmax, 16);
-        h.tail_sslot = h.tail_scr2 = h.tail_cg = -1;
-        size_t smax = 0;  // rescaled restrictions inside the tail: coarse values in the arithmetic type
-        for (int l = 0; l < T; ++l)
-            if (h.rescaled(l)) {
-                const long long n = h.lv[l].geo.n;
-                smax = std::max(smax, (size_t)(h.dim == 3 ? n * n * n : n * n) * 8);
-            }
-        if (smax) {
-            h.tail_sslot = (int)off;
-            off = align_up(off + 8 * MG_MAX_LEVELS, 16);
-            h.tail_scr2 = (int)off;
-            off = align_up(off + smax, 16);
-        }
-        if (h.p.base_solver == 1) {  // r, p, A p of the base level: 16-byte aligned slots of m0 * 8 bytes
-            const long long n = h.lv[0].geo.n;
-            h.tail_cg = (int)off;
-            off += 3 * align_up((size_t)(h.dim == 3 ? n * n * n : n * n) * 8, 16);
-        }
-        if (off > kTailMaxSmem) continue;
-        h.tail_level = T;
-        h.tail_smem = off;
-        h.tail_prec = h.lv[0].prec;
+        bool resc = false;
+        for (int l = 0; l < T; ++l) resc = resc || h.rescaled(l);
+        int uprec = h.lv[0].prec;
         for (int l = 1; l <= T; ++l)
-            if (h.lv[l].prec != h.tail_prec) h.tail_prec = -1;
-        return;
+            if (h.lv[l].prec != uprec) uprec = -1;
+        for (int cs : {16, 8, 1}) {
+            if (cs > 1 && (!probe || resc || h.p.base_solver == 1)) continue;
+            size_t off = 0, rmax = 0;
+            bool ok = true;
+            for (int l = 0; l <= T && ok; ++l) {
+                const long long n = h.lv[l].geo.n;
+                const long long N = h.dim == 3 ? n * n * n : n * n;
+                if (N > (cs > 1 ? kTailMaxPointsCl : kTailMaxPoints)) { ok = false; break; }
+                int sh = kTailWholeShift;
+                long long chunk = N;
+                if (cs > 1) {
+                    sh = 5;
+                    while (((long long)cs << sh) < N) ++sh;
+                    chunk = 1LL << sh;
+                }
+                h.tail_sh[l] = sh;
+                for (int v = 0; v < 3; ++v) {
+                    h.tail_soff[l][v] = (int)off;
+                    off = align_up(off + (size_t)chunk * h.lv[l].esz, 16);
+                }
+                rmax = std::max(rmax, (size_t)chunk * (h.lv[l].prec == MG_FP64 ? 8 : 4));
+            }
+            if (!ok) continue;
+            h.tail_rscr = (int)off;
+            off = align_up(off + rmax, 16);
+            h.tail_sslot = h.tail_scr2 = h.tail_cg = -1;
+            size_t smax = 0;  // rescaled restrictions inside the tail: coarse values in the arithmetic type
+            for (int l = 0; l < T; ++l)
+                if (h.rescaled(l)) {
+                    const long long n = h.lv[l].geo.n;
+                    smax = std::max(smax, (size_t)(h.dim == 3 ? n * n * n : n * n) * 8);
+                }
+            if (smax) {
+                h.tail_sslot = (int)off;
+                off = align_up(off + 8 * MG_MAX_LEVELS, 16);
+                h.tail_scr2 = (int)off;
+                off = align_up(off + smax, 16);
+            }
+            if (h.p.base_solver == 1) {  // r, p, A p of the base level: 16-byte aligned slots of m0 * 8 bytes
+                const long long n = h.lv[0].geo.n;
+                h.tail_cg = (int)off;
+                off += 3 * align_up((size_t)(h.dim == 3 ? n * n * n : n * n) * 8, 16);
+            }
+            if (off > kTailMaxSmem) continue;
+            if (cs > 1 && tail_cluster_ok(h.dim, uprec, cs, off) < 1) continue;
+            h.tail_level = T;
+            h.tail_smem = off;
+            h.tail_cs = cs;
+            h.tail_prec = uprec;
+            return;
+        }
     }
 }
 
@@ -721,7 +741,7 @@ static void autotune(mgi_hier& h) {
     cudaEventDestroy(eb);
 }
 
-static mg_status plan_hier(const mg_params* p, mgi_hier& h) {
+static mg_status plan_hier(const mg_params* p, mgi_hier& h, bool probe) {
     std::string why;
     int L = mgi_validate(p, why);
     if (!L) FAIL(MG_ERR_INVALID, why);
@@ -741,7 +761,7 @@ static mg_status plan_hier(const mg_params* p, mgi_hier& h) {
     h.sigma = p->scaling == 0 ? 1.0 : std::ldexp(1.0, sl);
     h.g_alias_r = (p->prec[L - 1] == MG_FP64 && p->scaling == 0);
     h.rsig = sl;
-    plan_tail(h, p->no_tail == 1);
+    plan_tail(h, p->no_tail == 1, probe && p->no_tail == 2);
     h.m0 = 1;
     for (int a = 0; a < p->dim; ++a) h.m0 *= sizes[0];
     Layout lay;
@@ -753,7 +773,7 @@ static mg_status plan_hier(const mg_params* p, mgi_hier& h) {
 
 extern "C" size_t mg_footprint_bytes(const mg_params* p) {
     mgi_hier h;
-    if (plan_hier(p, h) != MG_OK) return 0;
+    if (plan_hier(p, h, false) != MG_OK) return 0;
     return h.footprint;
 }
 
@@ -761,7 +781,7 @@ extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, 
     if (!out) FAIL(MG_ERR_INVALID, "out is NULL");
     *out = nullptr;
     mgi_hier* h = new mgi_hier();
-    mg_status st = plan_hier(p, *h);
+    mg_status st = plan_hier(p, *h, true);
     if (st != MG_OK) { delete h; return st; }
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { delete h; FAIL(MG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)); }

@@ -92,6 +92,8 @@ struct mgi_hier {
     int tail_rscr = 0;                     // shared-memory byte offset of the tail's residual scratch
     size_t tail_smem = 0;                  // dynamic shared memory of the tail kernel
     int tail_prec = -1;                    // storage type of every tail level, -1 if they differ
+    int tail_cs = 1;                       // CTAs of the tail's thread-block cluster (1: one CTA)
+    int tail_sh[MG_MAX_LEVELS] = {};       // chunk shift per tail level (points per CTA = 2^sh)
     int tail_sslot = -1;                   // shared-memory byte offset of the rescale slots (8 B per level)
     int tail_scr2 = -1;                    // ... of the coarse scratch of rescaled restrictions
     int tail_cg = -1;                      // ... of the CG scratch of the base level

@@ -76,6 +76,7 @@ struct DevState {
     int scale_ahead;  // 1: the update writes the next g with inv_pred (mg_params.scale_ahead in effect)
     int g_ready;      // 1: g of the coming step was written by the last update (the scale-cast returns)
     int gover;        // set by the update when a scaled g value overflowed the storage type
+    int fin_count;    // IR update CTAs done in this step (the last one finalises)
     double inv_pred;  // scale-ahead: sigma / 2^e, 2^e the power of two above the last ||r||_inf
     double thr_pred;  // scale-ahead: |r| >= thr_pred overflows the finest storage type after scaling
     double glimit;    // the finest storage type's overflow threshold (set at solve start)
@@ -158,6 +159,7 @@ struct KArgs {
     double h2inv;        // alpha of this level's operator (h^-2 for finite differences)
     int xstep, ystep, zstep, zlen;  // tile strides / march length
     int gate;            // 1: return at once unless st->phase == 0
+    int fin;             // K_UPDATE: the last CTA runs the step's finalisation (FIN_STEP)
     int* err;            // set to 1 when a bounded copy wait runs out (3D sweeps)
     SweepCoef cf;        // sweep coefficients of this level (host-computed)
 };

@@ -29,6 +29,7 @@
 #include <type_traits>
 
 #include "mg_device.cuh"
+#include "mg_final.cuh"
 
 namespace mgi {
 
@@ -1006,30 +1007,22 @@ __device__ __forceinline__ float scaled_f32(double r, const ScaleK& k) {
     return __fmul_rn(f64_to_f32_trunc(__longlong_as_double(b + k.eadd)), k.mant);
 }
 
-// g = round_T(r * inv) over the padded rows of the finest level (pads stay 0).
+// One row vector of g = round_T(r * inv) (pads of r are 0, so pads of g stay 0).
 template <int DIM, class T>
-__device__ __forceinline__ void scale_cast_body(const KArgs& a, int cta) {
+__device__ __forceinline__ void scale_cast_vec(const KArgs& a, int idx, int vpr, double inv, const ScaleK& k) {
     using C = typename Tr<T>::C;
     constexpr int V = Tr<T>::V;
-    if (a.gate && a.st->phase != 0) return;
-    if (a.st && a.st->g_ready) return;  // the last update already wrote g (scale-ahead)
-    const int vpr = a.P / V;  // vectors per padded row
-    const int rows = DIM == 3 ? a.n * a.n : a.n;
-    const int idx = cta * blockDim.x + threadIdx.x;
-    if (idx >= rows * vpr) return;
     const int row = idx / vpr;
     const int x = (idx - row * vpr) * V;
     const int z = DIM == 3 ? row / a.n : 0;
     const int y = row - z * a.n;
     const long long o = offs<DIM>(x, y, z, a.P, a.S);
-    const double inv = a.st ? a.st->inv : a.inv_explicit;
     C v[V];
     if constexpr (sizeof(T) == 8) {
         const double2 t = __ldg(reinterpret_cast<const double2*>(a.r64 + o));
         v[0] = t.x * inv;
         v[1] = t.y * inv;
     } else {
-        const ScaleK k = make_scale(inv);
 #pragma unroll
         for (int i = 0; i < V; i += 2) {
             const double2 t = __ldg(reinterpret_cast<const double2*>(a.r64 + o + i));
@@ -1039,12 +1032,26 @@ __device__ __forceinline__ void scale_cast_body(const KArgs& a, int cta) {
     }
     stv(reinterpret_cast<T*>(a.dst) + o, v);
 }
+// g over the padded rows of the finest level, grid-stride over the row
+// vectors (a small launch when it returns at once: scale-ahead steps).
 template <int DIM, class T>
-__global__ void __launch_bounds__(256) k_scale_cast(const KArgs a) { scale_cast_body<DIM, T>(a, blockIdx.x); }
+__device__ __forceinline__ void scale_cast_body(const KArgs& a, int cta, int ncta) {
+    constexpr int V = Tr<T>::V;
+    if (a.gate && a.st->phase != 0) return;
+    if (a.st && a.st->g_ready) return;  // the last update already wrote g (scale-ahead)
+    const int vpr = a.P / V;  // vectors per padded row
+    const int rows = DIM == 3 ? a.n * a.n : a.n;
+    const double inv = a.st ? a.st->inv : a.inv_explicit;
+    const ScaleK k = make_scale(inv);
+    for (int idx = cta * blockDim.x + threadIdx.x; idx < rows * vpr; idx += ncta * blockDim.x)
+        scale_cast_vec<DIM, T>(a, idx, vpr, inv, k);
+}
+template <int DIM, class T>
+__global__ void __launch_bounds__(256) k_scale_cast(const KArgs a) { scale_cast_body<DIM, T>(a, blockIdx.x, gridDim.x); }
 template <int DIM, class T>
 __global__ void __launch_bounds__(256) k_scale_cast_batch(const KItem* __restrict__ items, const int* __restrict__ cta_item) {
     const KItem& it = items[cta_item[blockIdx.x]];
-    scale_cast_body<DIM, T>(it.a, blockIdx.x - it.cta_begin);
+    scale_cast_body<DIM, T>(it.a, blockIdx.x - it.cta_begin, it.ncta);
 }
 
 // ---------------------------------------------------------------- FP64 IR update (Alg. 2 lines 6-7)
@@ -1114,88 +1121,37 @@ __host__ __device__ constexpr int q1_weight(int dx, int dy, int dz) {
 __device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
 
-// Sum of squares as an FP32 double-float (hi + lo) without FP64-pipe
-// instructions (no FP64 arithmetic, no int/float conversion).  Each r is
-// first scaled by 2^-E (E: exponent of the previous ||r||_inf, an exact change
-// of the exponent field; entries below 2^-70 of that scale are dropped, their
-// squares being < 2^-140 of the sum) and split from its bit pattern into hi
-// (top 24 significand bits, exact) and lo (the next 23 bits, truncated; the
-// last 6 bits, < 2^-47 of r, are dropped).  r^2 ~ hi^2 + 2 hi lo, hi^2 exact
-// by FMA TwoProd, summed with TwoSum: relative error ~1e-14.  The result is
-// multiplied by 2^(2E).
-struct SqAcc {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add(double r, int E) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(r);
-        const int e = (int)((b >> 52) & 0x7FF) - E;  // biased exponent of r * 2^-E
-        if (e < 1023 - 70 || e > 1023 + 100) return;  // (the upper bound never binds: r <= ~100 * 2^E)
-        const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-        // r 2^-E truncated to 24 significand bits: FP32 exponent field e - 1023 + 127
-        const float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu));
-        // significand bits 28..6 as an exact FP32 integer (magic 2^23), times
-        // sign * 2^(e - 1069), the weight of bit 6
-        const float m = __fsub_rn(__uint_as_float(0x4B000000u | ((unsigned)(b >> 6) & 0x7FFFFFu)), 8388608.0f);
-        const float l = __fmul_rn(m, __uint_as_float(sign | ((unsigned)(e - 1069 + 127) << 23)));
-        const float p = __fmul_rn(h, h);
-        const float pe = __fmaf_rn(h, h, -p);
-        const float t = __fmaf_rn(2.0f * h, l, pe);
-        float s, err;
-        two_sum(hi, p, s, err);
-        hi = s;
-        lo = __fadd_rn(lo, __fadd_rn(err, t));
-    }
-    __device__ __forceinline__ void add_pair(float h2, float l2) {
-        float s, err;
-        two_sum(hi, h2, s, err);
-        hi = s;
-        lo = __fadd_rn(lo, __fadd_rn(err, l2));
-    }
+
+// The sum of squares in FP64 (one fused multiply-add per point on the FP64
+// pipe, which the update leaves half idle) in place of the integer-built
+// double-float sum: fewer instructions for the issue-bound update.
+struct SqAcc64 {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double r, int) { s = fma(r, r, s); }
 };
 
-// Exponent E (unbiased) used to pre-scale the squares: that of the last ||r||_inf.
-__device__ __forceinline__ int sq_exponent(const DevState* st) {
-    if (!st) return 0;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(st->rnorminf);
-    const int e = (int)((b >> 52) & 0x7FF);
-    return (e == 0 || e == 0x7FF) ? 0 : e - 1023;
-}
 
-// Block reduction in a fixed order: {sum of squares, max |r| key} -> partials.
-// The double-float pairs are combined with TwoSum through warp shuffles; one
-// lane converts the block total to FP64 and rescales it by 2^(2E).
-__device__ __forceinline__ void write_partials(SqAcc sq, unsigned long long nmax, int E, double* partials, int cta) {
-    __shared__ float sh[32], sl[32];
+// Block reduction in a fixed order of FP64 sums of squares and max |r| keys.
+__device__ __forceinline__ void write_partials(SqAcc64 sq, unsigned long long nmax, int, double* partials, int cta) {
+    __shared__ double sh[32];
     __shared__ unsigned long long rm[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(kFull, sq.hi, o), l2 = __shfl_xor_sync(kFull, sq.lo, o);
-        sq.add_pair(h2, l2);
-    }
+    double v = warp_sum(sq.s);
     nmax = warp_max(nmax);
-    if (lane == 0) { sh[w] = sq.hi; sl[w] = sq.lo; rm[w] = nmax; }
+    if (lane == 0) { sh[w] = v; rm[w] = nmax; }
     __syncthreads();
     if (w == 0) {
-        SqAcc t;
-        t.hi = lane < nw ? sh[lane] : 0.f;
-        t.lo = lane < nw ? sl[lane] : 0.f;
+        v = lane < nw ? sh[lane] : 0.0;
         unsigned long long m = lane < nw ? rm[lane] : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float h2 = __shfl_xor_sync(kFull, t.hi, o), l2 = __shfl_xor_sync(kFull, t.lo, o);
-            t.add_pair(h2, l2);
-        }
+        v = warp_sum(v);
         m = warp_max(m);
         if (lane == 0) {
-            const double v = f32_to_f64(t.hi) + f32_to_f64(t.lo);
-            // exact rescaling by 2^(2E) through the exponent field (v is 0 or normal)
-            const long long vb = __double_as_longlong(v);
-            const double vs = (vb & 0x7FF0000000000000ll) ? __longlong_as_double(vb + ((long long)(2 * E) << 52)) : 0.0;
-            partials[2 * (long long)cta] = vs;
+            partials[2 * (long long)cta] = v;
             partials[2 * (long long)cta + 1] = __longlong_as_double((long long)m);
         }
     }
 }
+
 
 // Four consecutive values of a level vector (x multiple of 4), one vector load.
 template <class T>
@@ -1220,11 +1176,6 @@ __device__ __forceinline__ void ld4(const T* p, typename Tr<T>::C (&v)[4]) {
     }
 }
 
-// One thread per 4 consecutive points of a padded row.  u and r (FP64, 32 of
-// the 34 bytes per point) stream through coalesced 16-byte loads and stores;
-// the stencil of c comes through the read-only cache as vector loads.  FP64
-// instructions: the two fused multiply-adds of Alg. 2 lines 6-7 per point
-// (three for FP32/BF16 corrections), nothing else.
 // Four consecutive values rounded to T (16-byte aligned for FP32, 8 for 16-bit types).
 template <class T>
 __device__ __forceinline__ void st4(T* p, const float (&v)[4]) {
@@ -1239,6 +1190,13 @@ __device__ __forceinline__ void st4(T* p, const float (&v)[4]) {
     }
 }
 
+// One thread per 4 consecutive points of a padded row.  u and r (FP64, 32 of
+// the 34-36 bytes per point) stream through coalesced 16-byte loads and
+// stores; the stencil of c comes through the read-only cache as vector loads.
+// FP64 instructions per point: the two fused multiply-adds of Alg. 2 lines 6-7
+// (three for FP32/BF16 corrections) and one for the sum of squares; A c is
+// formed exactly with integer / FP32 instructions.  The last CTA to finish
+// runs the step's finalisation.
 // OP = 1: the Q1 operator (3x3(x3) neighbourhood, integer weights).
 constexpr int kUpdQ = 4;
 template <int DIM, class T, int OP>
@@ -1250,10 +1208,10 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
     const int vpr = a.P / Q;
     const int rows = DIM == 3 ? a.n * a.n : a.n;
     const int total = rows * vpr;
-    const int E = sq_exponent(a.st);
+    const int E = 0;  // (no pre-scaling: the squares are summed in FP64)
     const double alpha = a.st ? a.st->alpha : a.a_step;
     const double beta = alpha * a.h2inv;
-    SqAcc sq;
+    SqAcc64 sq;
     unsigned long long nmax = 0ull;
     // scale-ahead (Alg. 2 line 4 of the next step, fused): g = cast(r inv_pred),
     // inv_pred a power of two; |r| >= thr_pred would overflow T (flagged, and the
@@ -1470,6 +1428,22 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
     if (gout && __any_sync(kFull, gbad) && (threadIdx.x & 31) == 0)
         atomicExch(&const_cast<DevState*>(a.st)->gover, 1);
     write_partials(sq, nmax, E, a.partials, cta);
+    if (a.fin && a.st) {
+        // the last CTA to finish reduces every CTA's partials and runs the
+        // step's finalisation (Alg. 2 line 8 and the next scale): no separate
+        // launch.  Partials are published by a fence before the ticket.
+        DevState* st = const_cast<DevState*>(a.st);
+        __shared__ int last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(&st->fin_count, 1) == ncta - 1;
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            if (threadIdx.x == 0) st->fin_count = 0;  // ready for the next step
+            finalize_body(FIN_STEP, st, a.partials, ncta);
+        }
+    }
 }
 template <int DIM, class T, int OP>
 __global__ void __launch_bounds__(256) k_update(const KArgs a) { update_body<DIM, T, OP>(a, blockIdx.x, gridDim.x); }

@@ -10,6 +10,7 @@
 #include <tuple>
 
 #include "mg_compact.cuh"
+#include "mg_final.cuh"
 #include "mg_march.cuh"
 
 namespace mgi {
@@ -182,6 +183,7 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
         s.ty = 1;
         s.gx = cdiv(rows * (P / per), 256);
         if (kind == K_UPDATE) s.gx = std::min(s.gx, 4 * kSMs);  // grid-stride: one partial per CTA
+        if (kind == K_SCALE) s.gx = std::min(s.gx, 8 * kSMs);   // grid-stride
         s.gy = 1;
         s.smem = 0;
         return s;
@@ -191,7 +193,11 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
     const bool need_g = bmode == M_JACOBI || bmode == M_RESTRICT;
     if (dim == 3 && !q1 && bmode != M_PRE) {  // small levels: the direct kernels (same results)
         TileChoice tc;
-        const bool direct = tile_choice_get(dim, kind, mode, prec, n, &tc) ? tc.rpw == 0 : n <= kDirectMaxN;
+        // default: direct sweeps up to kDirectMaxN, direct restriction (one thread per coarse
+        // point, latency-bound) only below that
+        const bool direct = tile_choice_get(dim, kind, mode, prec, n, &tc)
+                                ? tc.rpw == 0
+                                : n <= (bmode == M_RESTRICT ? kDirectMaxN / 2 : kDirectMaxN);
         if (direct) {
             s.rpw = 0;
             s.tx = 256;
@@ -569,114 +575,6 @@ int launch_init_rb(int dim, const Geom& geo, const double* b, double* r, double*
     return (int)cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- norms and IR control
-// Reduces per-CTA partials in a fixed order (deterministic), then applies the
-// stopping test of Alg. 2 and sets alpha for the next step (line 4):
-// alpha = ||r||_inf / sigma (scaling 1), ||r||_2 / sigma (scaling 2) or 1.
-// kind: FIN_INIT after r = b - A u0, FIN_STEP after an update (partials of
-// stride 2), FIN_GUARD after the true residual, 3 = report only.
-__device__ __forceinline__ void finalize_body(int kind, DevState* st, const double* __restrict__ partials, int nblocks) {
-    // gating (uniform across the block): a step's finalisation only while
-    // iterating, the true-residual check only when it is pending, the report
-    // only when u changed since it was last copied out
-    if (kind == FIN_STEP && st->phase != 0) return;
-    if (kind == FIN_GUARD && st->phase != 1) return;
-    if (kind == FIN_REPORT && !st->dirty) return;
-    const int stride = kind == FIN_STEP ? 2 : 4;
-    double sr = 0.0, sb = 0.0;
-    unsigned long long mr = 0ull;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        sr += partials[(long long)stride * b];
-        unsigned long long m = (unsigned long long)__double_as_longlong(partials[(long long)stride * b + 1]);
-        mr = m > mr ? m : mr;
-        if (stride == 4) sb += partials[(long long)stride * b + 2];
-    }
-    __shared__ double s1[32], s2[32];
-    __shared__ unsigned long long s3[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    sr = warp_sum(sr); sb = warp_sum(sb); mr = warp_max(mr);
-    if (lane == 0) { s1[wid] = sr; s2[wid] = sb; s3[wid] = mr; }
-    __syncthreads();
-    if (wid != 0) return;
-    sr = lane < nw ? s1[lane] : 0.0;
-    sb = lane < nw ? s2[lane] : 0.0;
-    mr = lane < nw ? s3[lane] : 0ull;
-    sr = warp_sum(sr); sb = warp_sum(sb); mr = warp_max(mr);
-    if (lane != 0) return;
-    const double rn = sqrt(sr);
-    const double rinf = __longlong_as_double((long long)mr);
-    // scale-ahead: did this step's update write the next g (with inv_pred, no overflow)?
-    const bool ahead_ok = kind == FIN_STEP && st->scale_ahead && !st->gover && st->inv_pred > 0.0;
-    const double inv_used = st->inv_pred;
-    st->gover = 0;
-    st->g_ready = 0;
-    if (kind == FIN_INIT) {
-        st->bnorm2 = sqrt(sb);
-        st->tol_abs = st->tol_mode == 0 ? st->tol * st->bnorm2 : st->tol;
-        st->iter = 0;
-        st->guard_restarts = 0;
-        st->stag = 0;
-        st->status = MG_OK;
-        st->dirty = 1;
-    }
-    const double bn = st->bnorm2;
-    const double rel = bn > 0.0 ? rn / bn : rn;
-    if (kind == FIN_REPORT) {  // report only: u has been copied out
-        st->rel_true = rel;
-        st->dirty = 0;
-        return;
-    }
-    if (kind == FIN_STEP) {
-        st->iter += 1;
-        st->dirty = 1;
-        st->stag = (rn >= 0.999 * st->rnorm2) ? st->stag + 1 : 0;
-    }
-    if (kind == FIN_GUARD) st->dirty = 0;
-    st->rnorm2 = rn;
-    st->rnorminf = rinf;
-    const int it = st->iter < kMaxHist ? st->iter : kMaxHist;
-    st->hist[it] = rel;
-    if (kind == FIN_GUARD) st->rel_true = rel;
-    if (!isfinite(rn) || !isfinite(rinf)) {
-        st->phase = 3;
-        st->status = MG_ERR_NUMERIC;
-        return;
-    }
-    if (rn <= st->tol_abs) {
-        if (kind == FIN_GUARD || !st->guard) {
-            st->phase = 2;
-            st->status = MG_OK;
-            return;
-        }
-        st->phase = 1;
-        return;
-    }
-    if (kind == FIN_GUARD) st->guard_restarts += 1;
-    if (st->iter >= st->max_iter || st->stag >= 5) {
-        st->phase = 3;
-        st->status = MG_ERR_NOT_CONVERGED;
-        return;
-    }
-    double alpha = 1.0, inv = 1.0;
-    if (st->scaling == 1) { alpha = rinf / st->sigma; inv = st->sigma / rinf; }
-    else if (st->scaling == 2) { alpha = rn / st->sigma; inv = st->sigma / rn; }
-    if (ahead_ok) {  // g = cast(r inv_used) is in place: alpha = 1 / inv_used (powers of two, exact)
-        int e = 0;
-        (void)frexp(inv_used, &e);
-        alpha = ldexp(1.0, 1 - e);
-        inv = inv_used;
-        st->g_ready = 1;
-    }
-    st->alpha = alpha;
-    st->inv = inv;
-    if (st->scale_ahead && rinf > 0.0) {  // the next update's scale: sigma / 2^e, 2^e > ||r||_inf >= 2^(e-1)
-        int e = 0;
-        (void)frexp(rinf, &e);
-        st->inv_pred = ldexp(st->sigma, -e);
-        st->thr_pred = st->glimit / st->inv_pred;  // exact: inv_pred is a power of two
-    }
-    st->phase = 0;
-}
 
 __global__ void k_finalize(int kind, DevState* st, const double* __restrict__ partials, int nblocks) {
     finalize_body(kind, st, partials, nblocks);

@@ -7,9 +7,12 @@
 namespace mgi {
 
 constexpr int kTailThreads = 1024;
-constexpr long long kTailMaxPoints = 8192;   // levels with n^d up to this run in the tail
-constexpr size_t kTailMaxSmem = 200 * 1024;  // shared-memory budget of the tail's level arrays
+constexpr long long kTailMaxPoints = 8192;     // single-CTA tail: levels with n^d up to this
+constexpr long long kTailMaxPointsCl = 1 << 15;  // cluster tail: levels with n^d up to this
+constexpr size_t kTailMaxSmem = 200 * 1024;    // shared-memory budget of the tail's level arrays (per CTA)
 constexpr int kTailMaxOps = 16384;
+constexpr int kTailMaxCluster = 16;            // CTAs of a cluster tail
+constexpr int kTailWholeShift = 30;            // chunk shift of a single-CTA tail (one chunk)
 
 enum TailKind : int {
     TK_SWEEP = 0,     // Jacobi family (mode M_JACOBI / M_ZERO2 / M_ZERO1) on level n
@@ -38,6 +41,8 @@ struct TailOp {
     int rsig;   // TK_RESTRICT with sslot >= 0: target max-norm 2^rsig (power-of-two range)
     int cgmax;  // TK_COARSE mode 1 (CG): step limit
     int op;     // operator: 0 finite differences, 1 Q1 elements
+    int sh;     // chunk shift of level n: point p lives in CTA p >> sh of the cluster
+    int shc;    // chunk shift of the coarser level nc
     int pad_;
     void* gptr;
     double h2inv;
@@ -58,11 +63,15 @@ struct TailItem {
     const DevState* st;
     int nops, m0;
 };
-int launch_tail_batch(int dim, int uniform_prec, const TailItem* items, int nitems, size_t smem, void* stream);
+int launch_tail_batch(int dim, int uniform_prec, const TailItem* items, int nitems, size_t smem, int cs,
+                      void* stream);
 
 // uniform_prec: the storage type of every tail level (selects a kernel
 // specialised for it), or -1 for a mixed-precision tail.
+// cs: CTAs of the thread-block cluster that holds the tail levels (1: one CTA).
 int launch_tail(int dim, int uniform_prec, const TailOp* prog, int nops, const double* minv, int m0,
-                const DevState* st, int gate, size_t smem, void* stream);
+                const DevState* st, int gate, size_t smem, int cs, void* stream);
+// Active clusters of cs tail CTAs with smem bytes each this device can hold (0: none / no device).
+int tail_cluster_ok(int dim, int uniform_prec, int cs, size_t smem);
 
 }  // namespace mgi

@@ -58,7 +58,7 @@ class Result(ctypes.Structure):
 
 class LevelInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("prec", ctypes.c_int32), ("pitch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("bytes", ctypes.c_size_t)]
+                ("tail_ctas", ctypes.c_int32), ("bytes", ctypes.c_size_t)]
 
 
 class KernelTime(ctypes.Structure):
@@ -289,7 +289,7 @@ class Hierarchy:
     def level_info(self, level: int) -> dict:
         li = LevelInfo()
         _check(lib().mg_level_info_get(self.handle, int(level), ctypes.byref(li)), "mg_level_info_get")
-        return dict(n=li.n, prec=li.prec, pitch=li.pitch, bytes=li.bytes)
+        return dict(n=li.n, prec=li.prec, pitch=li.pitch, tail_ctas=li.tail_ctas, bytes=li.bytes)
 
     def level_write(self, level: int, vec: int, src) -> None:
         _check(lib().mg_level_write(self.handle, int(level), int(vec), ctypes.c_void_p(_ptr(src))),

@@ -263,3 +263,40 @@ def test_scale_ahead_on_and_off(oracle, dim, n, lad):
     b = I.random_rhs(dim, n, 800 + n)
     for sa in (0, 1):
         check_solve(oracle, dim, n, lad, b, extra_iters=2, scale_ahead=sa)
+
+
+@pytest.mark.parametrize("dim,n,lad", [(3, 15, "H"), (3, 15, "HSD"), (2, 63, "H"), (3, 15, "D"), (2, 63, "BSD")])
+def test_cluster_tail_equals_single_cta_tail(dim, n, lad):
+    """Levels that fit one CTA's shared memory run the same tail program either in one
+    CTA (no_tail = 0) or distributed over a thread-block cluster (no_tail = 2): the
+    same bits."""
+    b = I.random_rhs(dim, n, 900 + n)
+    u0, r0 = gpu_solve(dim, n, lad, b, no_tail=0)
+    u2, r2 = gpu_solve(dim, n, lad, b, no_tail=2)
+    assert r0["iters"] == r2["iters"] and np.array_equal(u0, u2)
+
+
+@pytest.mark.parametrize("dim,n,lad,gamma", [(3, 63, "H", 1), (3, 127, "H", 1), (3, 127, "HSD", 1), (3, 63, "H", 2),
+                                             (3, 95, "S", 1), (3, 63, "D", 1), (2, 511, "H", 1)])
+def test_cluster_tail_solves(oracle, dim, n, lad, gamma):
+    """The cluster tail (levels up to 31^3 in the distributed shared memory of 16 CTAs)
+    against the oracle, and against the one-CTA tail plus level kernels."""
+    b = I.random_rhs(dim, n, 950 + n)
+    extra = 0 if lad == "D" else 2
+    kw = dict(scaling=0) if lad == "D" else {}
+    check_solve(oracle, dim, n, lad, b, extra_iters=extra, gamma=gamma, no_tail=2, **kw)
+    u0, r0 = gpu_solve(dim, n, lad, b, gamma=gamma, no_tail=2, **kw)
+    u2, r2 = gpu_solve(dim, n, lad, b, gamma=gamma, **kw)
+    assert abs(r0["iters"] - r2["iters"]) <= 1
+    assert np.linalg.norm(u0 - u2) <= 1e-9 * np.linalg.norm(u2)
+
+
+def test_cluster_tail_levels_reported():
+    """At 255^3 (FP16) the cluster tail (no_tail = 2) holds the levels up to 31^3; by
+    default one CTA holds the levels up to 15^3."""
+    with mg.Hierarchy(mg.make_params(3, 255, "H", no_tail=2)) as h:
+        ctas = [h.level_info(l)["tail_ctas"] for l in range(h.nlev)]
+    assert ctas[:4] == [ctas[0]] * 4 and ctas[0] in (8, 16) and ctas[4:] == [0, 0, 0], ctas
+    with mg.Hierarchy(mg.make_params(3, 255, "H")) as h:
+        ctas = [h.level_info(l)["tail_ctas"] for l in range(h.nlev)]
+    assert ctas == [1, 1, 1, 0, 0, 0, 0], ctas
