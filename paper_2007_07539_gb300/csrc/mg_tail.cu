@@ -88,20 +88,24 @@ __device__ void t_sweep(const TailOp& op, const TailSm& x) {
     using C = typename Tr<T>::C;
     const int n = op.n;
     const C c1 = coef<C>(op.cf, 0), c2 = coef<C>(op.cf, 1), c3 = coef<C>(op.cf, 2), k2 = coef<C>(op.cf, 3);
+    // the stage's fields in registers: the stores below go to shared memory,
+    // where the staged stage record lives too
+    const int src = op.src, g = op.g, dst = op.dst, sh = op.sh, mode = op.mode, opk = op.op;
+    const unsigned long long mn = op.mn;
     int lo, hi;
-    owned<CL>(x, npoints<DIM>(n), op.sh, lo, hi);
-    auto get = [&](int t) { return dget<T, CL>(x, op.src, op.sh, t); };
+    owned<CL>(x, npoints<DIM>(n), sh, lo, hi);
+    auto get = [&](int t) { return dget<T, CL>(x, src, sh, t); };
     for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
         int i, j, k;
-        decode<DIM>(p, n, op.mn, i, j, k);
+        decode<DIM>(p, n, mn, i, j, k);
         const int q = p - lo;
-        const C c0 = lget<T>(x, op.src, q);
-        const C nb = cwsum_f<DIM, C>(op.op, get, p, n, i, j, k);
+        const C c0 = lget<T>(x, src, q);
+        const C nb = cwsum_f<DIM, C>(opk, get, p, n, i, j, k);
         C v;
-        if (op.mode == M_JACOBI) v = c1 * c0 + c2 * nb + c3 * lget<T>(x, op.g, q);
-        else if (op.mode == M_ZERO2) v = c3 * (k2 * c0 + c2 * nb);
+        if (mode == M_JACOBI) v = c1 * c0 + c2 * nb + c3 * lget<T>(x, g, q);
+        else if (mode == M_ZERO2) v = c3 * (k2 * c0 + c2 * nb);
         else v = c3 * c0;
-        lput<T>(x, op.dst, q, v);
+        lput<T>(x, dst, q, v);
     }
 }
 
@@ -111,16 +115,18 @@ __device__ void t_resid(const TailOp& op, const TailSm& x) {
     using C = typename Tr<T>::C;
     const int n = op.n;
     const C alpha = coef<C>(op.cf, 4), beta = (C)op_beta_d<DIM>(op.op);
+    const int src = op.src, g = op.g, sh = op.sh, opk = op.op;
+    const unsigned long long mn = op.mn;
     int lo, hi;
-    owned<CL>(x, npoints<DIM>(n), op.sh, lo, hi);
-    auto get = [&](int t) { return dget<T, CL>(x, op.src, op.sh, t); };
+    owned<CL>(x, npoints<DIM>(n), sh, lo, hi);
+    auto get = [&](int t) { return dget<T, CL>(x, src, sh, t); };
     C* r = reinterpret_cast<C*>(tail_dsm + op.dst);
     for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
         int i, j, k;
-        decode<DIM>(p, n, op.mn, i, j, k);
+        decode<DIM>(p, n, mn, i, j, k);
         const int q = p - lo;
-        const C nb = cwsum_f<DIM, C>(op.op, get, p, n, i, j, k);
-        r[q] = lget<T>(x, op.g, q) - alpha * (beta * lget<T>(x, op.src, q) - nb);  // g - alpha (beta c - W)
+        const C nb = cwsum_f<DIM, C>(opk, get, p, n, i, j, k);
+        r[q] = lget<T>(x, g, q) - alpha * (beta * lget<T>(x, src, q) - nb);  // g - alpha (beta c - W)
     }
 }
 
@@ -130,11 +136,13 @@ __device__ void t_restrict(const TailOp& op, const TailSm& x) {
     using C = typename Tr<T>::C;
     const int nf = op.n, nc = op.nc;
     const int Nc = npoints<DIM>(nc);
+    const int src = op.src, sh = op.sh, dst = op.dst, sslot = op.sslot;
+    const unsigned long long mnc = op.mnc;
     int lo, hi;
     owned<CL>(x, Nc, op.shc, lo, hi);
     for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
         int I, J, K;
-        decode<DIM>(p, nc, op.mnc, I, J, K);
+        decode<DIM>(p, nc, mnc, I, J, K);
         const int f0 = DIM == 3 ? ((2 * K) * nf + 2 * J) * nf + 2 * I : (2 * J) * nf + 2 * I;
         C s = 0;
 #pragma unroll
@@ -143,14 +151,14 @@ __device__ void t_restrict(const TailOp& op, const TailSm& x) {
 #pragma unroll
             for (int dj = 0; dj < 3; ++dj) {
                 const int f = f0 + (DIM == 3 ? dk * nf * nf : 0) + dj * nf;
-                const C si = (C)0.25 * dget<C, CL>(x, op.src, op.sh, f) + (C)0.5 * dget<C, CL>(x, op.src, op.sh, f + 1) +
-                             (C)0.25 * dget<C, CL>(x, op.src, op.sh, f + 2);
+                const C si = (C)0.25 * dget<C, CL>(x, src, sh, f) + (C)0.5 * dget<C, CL>(x, src, sh, f + 1) +
+                             (C)0.25 * dget<C, CL>(x, src, sh, f + 2);
                 sj += (dj == 1 ? (C)0.5 : (C)0.25) * si;
             }
             s += (DIM == 3 ? (dk == 1 ? (C)0.5 : (C)0.25) : (C)1) * sj;
         }
-        if (op.sslot >= 0) reinterpret_cast<C*>(tail_dsm + op.scr2)[p] = s;  // single CTA only
-        else lput<TC>(x, op.dst, p - lo, s);
+        if (sslot >= 0) reinterpret_cast<C*>(tail_dsm + op.scr2)[p] = s;  // single CTA only
+        else lput<TC>(x, dst, p - lo, s);
     }
     if (op.sslot >= 0) {
         // restriction into a rescaled FP16 level (DSH_MG, Sec. 6; single-CTA
@@ -174,11 +182,13 @@ __device__ void t_prolong(const TailOp& op, const TailSm& x) {
     const int n = op.n, nc = op.nc;
     // a rescaled coarse level holds its values times 2^k: the weights carry 2^-k
     const C sc = op.sslot >= 0 ? (C)*reinterpret_cast<const double*>(tail_dsm + op.sslot) : (C)1;
+    const int coarse = op.coarse, shc = op.shc, dst = op.dst;
+    const unsigned long long mn = op.mn;
     int lo, hi;
     owned<CL>(x, npoints<DIM>(n), op.sh, lo, hi);
     for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
         int i, j, k;
-        decode<DIM>(p, n, op.mn, i, j, k);
+        decode<DIM>(p, n, mn, i, j, k);
         // fine i = 2I + 1 sits on coarse I; even i lies between coarse i/2 - 1 and i/2
         const int il = (i - 1) >> 1, ih = i >> 1;  // equal for odd i
         const int jl = (j - 1) >> 1, jh = j >> 1;
@@ -200,12 +210,12 @@ __device__ void t_prolong(const TailOp& op, const TailSm& x) {
                 for (int c = 0; c < 2; ++c) {
                     const int I = c ? ih : il;
                     if (I < 0 || I >= nc || (c && ih == il)) continue;
-                    s += (C)dget<TC, CL>(x, op.coarse, op.shc, DIM == 3 ? (K * nc + J) * nc + I : J * nc + I);
+                    s += (C)dget<TC, CL>(x, coarse, shc, DIM == 3 ? (K * nc + J) * nc + I : J * nc + I);
                 }
             }
         }
         const int q = p - lo;
-        lput<T>(x, op.dst, q, lget<T>(x, op.dst, q) + w * s);
+        lput<T>(x, dst, q, lget<T>(x, dst, q) + w * s);
     }
 }
 
