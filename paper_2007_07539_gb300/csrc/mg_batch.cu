@@ -462,7 +462,6 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
         sh.tol_mode = h.p.tol_mode;
         sh.guard = h.p.guard;
         sh.scale_ahead = h.scale_ahead_on() ? 1 : 0;
-        sh.glimit = h.g_limit();
         sh.b = b[i];
         sh.uout = u[i];
     }

@@ -112,7 +112,6 @@ __device__ __forceinline__ void finalize_body(int kind, DevState* st, const doub
         int e = 0;
         (void)frexp(rinf, &e);
         st->inv_pred = ldexp(st->sigma, -e);
-        st->thr_pred = st->glimit / st->inv_pred;  // exact: inv_pred is a power of two
     }
     st->phase = 0;
 }

@@ -1065,7 +1065,6 @@ mg_status mgi_solve_begin(mgi_hier& h, const double* b, double* u) {
     sh.tol_mode = h.p.tol_mode;
     sh.guard = h.p.guard;
     sh.scale_ahead = h.scale_ahead_on() ? 1 : 0;
-    sh.glimit = h.g_limit();
     sh.phase = 0;
     sh.b = c.bd;
     sh.uout = c.ud;

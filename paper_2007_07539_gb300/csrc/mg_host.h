@@ -109,8 +109,7 @@ struct mgi_hier {
     bool scale_ahead_on() const {
         return p.scale_ahead == 1 && p.scaling == 1 && nlev > 0 && lv[nlev - 1].prec != MG_FP64 && !g_alias_r;
     }
-    // overflow threshold of the finest storage type for scaled residual values
-    double g_limit() const { return nlev > 0 && lv[nlev - 1].prec == MG_FP16 ? 65520.0 : 3.0e38; }
+
     void* arena = nullptr;
     size_t arena_bytes = 0;
     size_t footprint = 0;

@@ -78,8 +78,6 @@ struct DevState {
     int gover;        // set by the update when a scaled g value overflowed the storage type
     int fin_count;    // IR update CTAs done in this step (the last one finalises)
     double inv_pred;  // scale-ahead: sigma / 2^e, 2^e the power of two above the last ||r||_inf
-    double thr_pred;  // scale-ahead: |r| >= thr_pred overflows the finest storage type after scaling
-    double glimit;    // the finest storage type's overflow threshold (set at solve start)
     double lscale[MG_MAX_LEVELS];  // power-of-two scale of each rescaled FP16 level's residual
     const double* b;  // caller's right-hand side (device, contiguous)
     double* uout;     // caller's solution (device, contiguous): u0 in, u out

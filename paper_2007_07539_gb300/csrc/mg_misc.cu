@@ -263,7 +263,7 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
         s.ystep = s.ty * s.rpw;
         s.gx = nchunks;
         s.gy = cdiv(n, s.ystep);
-        s.smem = (size_t)sweep3_smem(s.ystep, need_g, 0);
+        s.smem = (size_t)sweep3_smem(s.ystep, need_g, 0, sweep3_stages(bmode, s.rpw));
         const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem, s.rpw);
         int zl = tz_hint > 0 ? tz_hint : pick_march_len(n, (long long)s.gx * s.gy, res, 4, 40, 1);
         zl = clampi(zl, 1, n);

@@ -138,3 +138,27 @@ def test_admission_rejects_oversized_request():
             assert e.value.status == 8
         finally:
             mg.serve_configure(0, 16)
+
+
+def test_batch_with_cluster_tails_equals_alone():
+    """Instances whose coarse tail runs in a thread-block cluster (no_tail = 2) merge
+    into one batched cluster launch and give their alone results bit for bit."""
+    import torch
+    specs = [(3, 63, "H", 31), (3, 95, "HSD", 32), (3, 127, "H", 33)]
+    refs = []
+    for d, n, lad, sd in specs:
+        with mg.Hierarchy(mg.make_params(d, n, lad, zero_guess=1, no_tail=2)) as h:
+            b = torch.from_numpy(I.random_rhs(d, n, sd)).cuda()
+            u = torch.zeros_like(b)
+            r = h.solve(b, u)
+            refs.append((u.cpu().numpy(), r))
+    hs = [mg.Hierarchy(mg.make_params(d, n, lad, zero_guess=1, no_tail=2)) for d, n, lad, sd in specs]
+    assert all(h.level_info(0)["tail_ctas"] > 1 for h in hs)
+    bs = [torch.from_numpy(I.random_rhs(d, n, sd)).cuda() for d, n, lad, sd in specs]
+    us = [torch.zeros_like(b) for b in bs]
+    res = mg.solve_batch(hs, bs, us)
+    for (u_ref, r_ref), u, r in zip(refs, us, res):
+        assert r["merged"] == 1 and r["status"] == 0 and r["iters"] == r_ref["iters"]
+        assert np.array_equal(u.cpu().numpy(), u_ref)
+    for h in hs:
+        h.close()
