@@ -29,7 +29,9 @@
  *   - Pointers may be device pointers (cudaMalloc / torch CUDA tensors) or
  *     host pointers (pinned or pageable); the library detects which with
  *     cudaPointerGetAttributes and copies host data through its own device
- *     staging buffers on the hierarchy's stream.  The caller keeps ownership.
+ *     staging buffers on the hierarchy's stream, except a pinned u, which the
+ *     kernels read and write in place over the host link.  The caller keeps
+ *     ownership.
  *   - Every call returns an mg_status; nothing throws across the ABI.  On an
  *     error mg_last_error() returns a message for the calling thread.
  *   - A hierarchy is bound to the device that was current at creation and to

@@ -868,6 +868,17 @@ bool mgi_is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of a page-locked host allocation that kernels can access in
+// place (pinned memory is mapped into the device's address space), else null.
+static double* mapped_host_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<double*>(a.devicePointer) : nullptr;
+}
+
 static size_t npoints(const mgi_hier& h) {
     size_t n = (size_t)h.lv[h.nlev - 1].geo.n;
     return h.dim == 3 ? n * n * n : n * n;
@@ -1043,6 +1054,14 @@ mg_status mgi_solve_begin(mgi_hier& h, const double* b, double* u) {
     CUCHK(cudaEventRecord(h.e0, s));
     c.bd = b;
     c.ud = u;
+    if (c.u_host) {
+        // a pinned host u is read (initial guess) and written (solution) by the
+        // kernels in place over the host link: no staging copy either way
+        if (double* um = mapped_host_ptr(u)) {
+            c.ud = um;
+            c.u_host = false;
+        }
+    }
     if (c.b_host || c.u_host) {
         if (ensure_staging(h)) FAIL(MG_ERR_OOM, "staging allocation failed");
     }

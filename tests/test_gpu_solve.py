@@ -300,3 +300,19 @@ def test_cluster_tail_levels_reported():
     with mg.Hierarchy(mg.make_params(3, 255, "H")) as h:
         ctas = [h.level_info(l)["tail_ctas"] for l in range(h.nlev)]
     assert ctas == [1, 1, 1, 0, 0, 0, 0], ctas
+
+
+def test_pinned_host_initial_guess_in_place():
+    """A pinned host u is read (initial guess) and written (solution) by the kernels in
+    place: the same result as device arrays."""
+    import torch
+    n = 47
+    b = I.random_rhs(3, n, 305)
+    u0 = I.random_guess(3, n, 306)
+    with mg.Hierarchy(mg.make_params(3, n, "H")) as h:
+        ud = torch.from_numpy(u0.copy()).cuda()
+        r1 = h.solve(torch.from_numpy(b).cuda(), ud)
+        up = torch.from_numpy(u0.copy()).pin_memory()
+        r2 = h.solve(torch.from_numpy(b).pin_memory(), up)
+    assert r1["status"] == 0 and r1["iters"] == r2["iters"]
+    assert np.array_equal(ud.cpu().numpy(), up.numpy())
