@@ -54,7 +54,8 @@ def test_ladders():
                                  dict(max_iter=5000), dict(nu1=-1), dict(levels=9), dict(tol=-1.0), dict(tune=2),
                                  dict(no_tail=5), dict(fuse_pre=3), dict(rescale16=2), dict(base_solver=2),
                                  dict(base_maxit=-1), dict(base_tol=-1.0), dict(base_tol=float("nan")),
-                                 dict(op=2), dict(op=1, fuse_pre=1)])
+                                 dict(op=2), dict(op=1, fuse_pre=1), dict(scale_ahead=2), dict(no_tail=3),
+                                 dict(base_maxit=100001)])
 def test_invalid_params_rejected_without_gpu(bad):
     p = mg.make_params(3, 63)
     for k, v in bad.items():
@@ -79,3 +80,19 @@ def test_footprint_scales_with_precision():
     assert 0 < h < d
     # FP64 u, r plus three level vectors per level: about 2*8 + 3*8*8/7 bytes/DOF for D_MG
     assert 40 * 255**3 < d < 56 * 255**3
+
+
+def test_footprint_of_options():
+    """The operator, the tail layout, scale-ahead and the base solver do not change
+    the device arrays; a rescaled FP16 level adds only its FP32 restriction scratch."""
+    base = mg.footprint_bytes(mg.make_params(3, 127, "H"))
+    assert base > 0
+    for kw in (dict(op=1), dict(no_tail=2), dict(scale_ahead=0), dict(base_solver=1)):
+        assert mg.footprint_bytes(mg.make_params(3, 127, "H", **kw)) == base, kw
+    # no tail: no stage program on the device
+    assert mg.footprint_bytes(mg.make_params(3, 127, "H", no_tail=1)) < base
+    nlev = len(mg.level_count(127))
+    dsh = [mg.FP16] * 2 + [mg.FP32] * (nlev - 2)
+    with_rescale = mg.footprint_bytes(mg.make_params(3, 127, dsh))
+    without = mg.footprint_bytes(mg.make_params(3, 127, dsh, rescale16=0))
+    assert with_rescale > without > 0
