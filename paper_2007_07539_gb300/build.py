@@ -55,7 +55,7 @@ def build(force: bool = False, jobs: int | None = None, extra: list[str] | None 
     os.makedirs(BUILD, exist_ok=True)
     extra = list(extra or [])
     srcs = _sources()
-    jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
+    jobs = jobs or len(srcs)  # all at once: the few long translation units do not wait in a queue
     with concurrent.futures.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, force, extra), srcs))
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):

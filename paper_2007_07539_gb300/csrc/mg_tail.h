@@ -1,6 +1,7 @@
 // Coarse-tail program: the stages of the multigrid cycle on the coarsest
-// levels, executed in order by one CTA with every tail level held in shared
-// memory (mg_tail.cu).
+// levels, executed in order by one CTA (or one thread-block cluster) with every
+// tail level held in shared memory (kernels: mg_tail_body.cuh; launches:
+// mg_tail.cu).
 #pragma once
 #include "mg_internal.h"
 
@@ -65,6 +66,16 @@ struct TailItem {
 };
 int launch_tail_batch(int dim, int uniform_prec, const TailItem* items, int nitems, size_t smem, int cs,
                       void* stream);
+
+// The tail kernels of one dimension, one CTA (CL false) or a cluster (CL
+// true), for a uniform tail storage type or -1 (mixed precisions); each
+// (DIM, CL) is instantiated in its own translation unit.
+using TailFn = void (*)(const TailOp*, int, const double*, int, const DevState*, int, int);
+using TailBatchFn = void (*)(const TailItem*, int);
+template <int DIM, bool CL>
+TailFn tail_kernel(int uniform_prec);
+template <int DIM, bool CL>
+TailBatchFn tail_batch_kernel(int uniform_prec);
 
 // uniform_prec: the storage type of every tail level (selects a kernel
 // specialised for it), or -1 for a mixed-precision tail.

@@ -1,0 +1,8 @@
+// Cluster coarse-tail kernels of 2D hierarchies (one translation unit
+// per dimension and tail shape, so that they compile in parallel).
+#include "mg_tail_body.cuh"
+
+namespace mgi {
+template TailFn tail_kernel<2, true>(int);
+template TailBatchFn tail_batch_kernel<2, true>(int);
+}  // namespace mgi

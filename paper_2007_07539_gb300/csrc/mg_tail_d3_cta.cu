@@ -1,0 +1,8 @@
+// One-cta coarse-tail kernels of 3D hierarchies (one translation unit
+// per dimension and tail shape, so that they compile in parallel).
+#include "mg_tail_body.cuh"
+
+namespace mgi {
+template TailFn tail_kernel<3, false>(int);
+template TailBatchFn tail_batch_kernel<3, false>(int);
+}  // namespace mgi
