@@ -29,6 +29,19 @@
  *                     W-cycle)
  *   or_ir_solve       Alg. 2, mixed-precision IR with residuum scaling; here all
  *                     in FP64
+ *   or_round          round-to-nearest-even into FP32, FP16 or BF16 (Sec. 3,
+ *                     Table 1), written from the formats' definitions
+ *
+ * Optional low-precision emulation (params.emulate = 1, a diagnostic: parity
+ * of the GPU path is stated against the FP64 oracle): every vector a level
+ * stores (the smoother's output, the restricted right-hand side, the base
+ * solution, the corrected c after prolongation) is rounded once to that
+ * level's format, while each operation itself is evaluated in FP64 (Sec. 6:
+ * operations in the precision of the level, results cast on transfer).  The
+ * IR loop then scales the residual to max-norm 2^sigma before the cast and
+ * divides the correction by it again (Sec. 4.3), and a restriction from a
+ * non-FP16 level into an FP16 level is rescaled by a power of two taken from
+ * its max-norm and undone on prolongation (Sec. 6, DSH_MG).
  *
  * Grid vectors are interior-only, contiguous, x fastest:
  *   index(i, j[, k]) = i + n*j [+ n*n*k], point ((i+1)h, (j+1)h[, (k+1)h]).
@@ -62,7 +75,15 @@ typedef struct {
     int true_residual_guard; /* 1: confirm convergence with b - A u */
     int nthreads;         /* OpenMP threads for stencil loops (<= 0: 1) */
     int op;               /* 0: finite differences; 1: Q1 finite elements */
+    /* low-precision emulation (diagnostic) */
+    int emulate;          /* 1: round every stored level vector to prec[l] */
+    int prec[OR_MAX_LEVELS]; /* storage format per level, coarsest first (OR_FP64 ...) */
+    int sigma_log2;       /* scaled residual max-norm 2^sigma; -1: 14 if a level is FP16, else 0 */
+    int rescale16;        /* 1: rescale restrictions from a non-FP16 into an FP16 level */
 } or_params;
+
+/* storage formats of the emulation (Sec. 3, Table 1) */
+enum { OR_FP64 = 0, OR_FP32 = 1, OR_FP16 = 2, OR_BF16 = 3 };
 
 typedef struct {
     int iters;            /* IR iterations performed */
@@ -77,6 +98,47 @@ typedef struct {
 static int g_threads = 1;
 
 static size_t npts(int d, int n) { return d == 2 ? (size_t)n * n : (size_t)n * n * n; }
+
+/*
+ * x rounded to the nearest value of a binary floating-point format with p
+ * significand bits (the leading bit included), least normal exponent emin and
+ * largest finite value maxv, ties to the even significand (Sec. 3; IEEE 754
+ * round-to-nearest-even).  In x's binade [2^e, 2^(e+1)) the format's values
+ * are the multiples of 2^(e-p+1); below 2^emin (the subnormals) they are the
+ * multiples of 2^(emin-p+1).  A rounded magnitude above maxv is an overflow:
+ * infinity with x's sign.  x / q and the product by q are exact in FP64
+ * (powers of two), and rint rounds to the nearest integer, ties to even, in
+ * the default rounding mode.
+ */
+static double round_bin(double x, int p, int emin, double maxv) {
+    if (x == 0.0 || !isfinite(x)) return x;
+    int E;
+    (void)frexp(x, &E); /* |x| = f 2^E with f in [1/2, 1): binade exponent E - 1 */
+    const int e = E - 1 < emin ? emin : E - 1;
+    const double q = ldexp(1.0, e - p + 1);
+    const double y = rint(x / q) * q;
+    return fabs(y) > maxv ? copysign(INFINITY, x) : y;
+}
+
+/*
+ * x stored in format fmt (Table 1): binary32 (24 significand bits, least
+ * normal exponent -126, max (2 - 2^-23) 2^127), binary16 (11, -14, 65504),
+ * bfloat16 (8, -126, (2 - 2^-7) 2^127); OR_FP64 returns x.
+ */
+double or_round(int fmt, double x) {
+    switch (fmt) {
+    case OR_FP32: return round_bin(x, 24, -126, ldexp(2.0 - ldexp(1.0, -23), 127));
+    case OR_FP16: return round_bin(x, 11, -14, 65504.0);
+    case OR_BF16: return round_bin(x, 8, -126, ldexp(2.0 - ldexp(1.0, -7), 127));
+    default: return x;
+    }
+}
+void or_round_array(int fmt, size_t N, const double *x, double *y) {
+    for (size_t p = 0; p < N; ++p) y[p] = or_round(fmt, x[p]);
+}
+static void round_vec(int fmt, size_t N, double *v) {
+    if (fmt != OR_FP64) or_round_array(fmt, N, v, v);
+}
 
 /* Value of v at (i, j, k); zero outside the interior (Dirichlet boundary). */
 static double at(const double *v, int d, int n, int i, int j, int k) {
@@ -349,7 +411,26 @@ typedef struct {
     int d, L;
     int n[OR_MAX_LEVELS];
     double *c[OR_MAX_LEVELS], *g[OR_MAX_LEVELS], *t[OR_MAX_LEVELS];
+    int sigma;              /* emulation: log2 of the residual's target max-norm */
 } or_hier;
+
+/* format of level l's vectors: FP64 unless emulating */
+static int lfmt(const or_params *P, int l) { return P->emulate ? P->prec[l] : OR_FP64; }
+
+/*
+ * Power-of-two rescale of a restricted residual into an FP16 level (Sec. 6):
+ * k with m 2^k in [2^(sigma-1), 2^sigma) for its max-norm m, |k| <= 126;
+ * k = 0 for m = 0.
+ */
+static int rescale_k(size_t N, const double *v, int sigma) {
+    double m = 0.0;
+    for (size_t p = 0; p < N; ++p) { double a = fabs(v[p]); if (a > m) m = a; }
+    if (!(m > 0.0) || !isfinite(m)) return 0;
+    int e;
+    (void)frexp(m, &e); /* m = f 2^e, f in [1/2, 1) */
+    int k = sigma - e;
+    return k > 126 ? 126 : (k < -126 ? -126 : k);
+}
 
 /*
  * Alg. 1 applied recursively on level l, with c the initial guess on entry
@@ -366,14 +447,43 @@ static int cycle(or_hier *H, const or_params *P, int l) {
     size_t N = npts(d, n);
     double *c = H->c[l], *g = H->g[l], *t = H->t[l];
     const int op = P->op;
-    if (l == 0) return or_coarse_solve_op(op, d, n, g, c);
-    for (int s = 0; s < P->nu1; ++s) { or_jacobi_op(op, d, n, P->omega, g, c, t); memcpy(c, t, N * sizeof(double)); }
+    const int f = lfmt(P, l);
+    if (l == 0) {
+        int rc = or_coarse_solve_op(op, d, n, g, c);
+        round_vec(f, N, c);
+        return rc;
+    }
+    for (int s = 0; s < P->nu1; ++s) {
+        or_jacobi_op(op, d, n, P->omega, g, c, t);
+        memcpy(c, t, N * sizeof(double));
+        round_vec(f, N, c);
+    }
     or_residual_op(op, d, n, g, c, t);
+    const int nc = H->n[l - 1], fc = lfmt(P, l - 1);
+    const size_t Nc = npts(d, nc);
     or_restrict(d, n, t, H->g[l - 1]);
-    memset(H->c[l - 1], 0, npts(d, H->n[l - 1]) * sizeof(double));
-    for (int k = 0; k < P->gamma; ++k) { int rc = cycle(H, P, l - 1); if (rc) return rc; }
-    or_prolong_add(d, H->n[l - 1], H->c[l - 1], c);
-    for (int s = 0; s < P->nu2; ++s) { or_jacobi_op(op, d, n, P->omega, g, c, t); memcpy(c, t, N * sizeof(double)); }
+    int k = 0; /* the coarse level's rescale 2^k (emulation, Sec. 6) */
+    if (P->emulate && P->rescale16 && fc == OR_FP16 && f != OR_FP16) {
+        k = rescale_k(Nc, H->g[l - 1], H->sigma);
+        for (size_t p = 0; p < Nc; ++p) H->g[l - 1][p] = ldexp(H->g[l - 1][p], k);
+    }
+    round_vec(fc, Nc, H->g[l - 1]);
+    memset(H->c[l - 1], 0, Nc * sizeof(double));
+    for (int v = 0; v < P->gamma; ++v) { int rc = cycle(H, P, l - 1); if (rc) return rc; }
+    if (k != 0) {
+        /* the correction of the rescaled level, scaled back by 2^-k (exact) */
+        double *cs = H->t[l - 1];
+        for (size_t p = 0; p < Nc; ++p) cs[p] = ldexp(H->c[l - 1][p], -k);
+        or_prolong_add(d, nc, cs, c);
+    } else {
+        or_prolong_add(d, nc, H->c[l - 1], c);
+    }
+    round_vec(f, N, c);
+    for (int s = 0; s < P->nu2; ++s) {
+        or_jacobi_op(op, d, n, P->omega, g, c, t);
+        memcpy(c, t, N * sizeof(double));
+        round_vec(f, N, c);
+    }
     return 0;
 }
 
@@ -382,6 +492,9 @@ static int hier_alloc(or_hier *H, const or_params *P) {
     H->d = P->dim;
     int cnt = or_level_sizes(P->n, P->levels, H->n);
     H->L = cnt - 1;
+    int any16 = 0;
+    for (int l = 0; l < cnt; ++l) any16 |= lfmt(P, l) == OR_FP16;
+    H->sigma = P->sigma_log2 >= 0 ? P->sigma_log2 : (any16 ? 14 : 0);
     for (int l = 0; l < cnt; ++l) {
         size_t N = npts(H->d, H->n[l]);
         H->c[l] = (double *)calloc(N, sizeof(double));
@@ -408,6 +521,8 @@ int or_mg_cycle(const or_params *P, const double *g, double *c) {
     size_t N = npts(P->dim, P->n);
     memcpy(H.g[H.L], g, N * sizeof(double));
     memcpy(H.c[H.L], c, N * sizeof(double));
+    round_vec(lfmt(P, H.L), N, H.g[H.L]); /* the finest level stores g and c in its format */
+    round_vec(lfmt(P, H.L), N, H.c[H.L]);
     int rc = cycle(&H, P, H.L);
     memcpy(c, H.c[H.L], N * sizeof(double));
     int L = H.L;
@@ -483,7 +598,14 @@ int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, 
         if (!(alpha > 0.0)) { status = -1; break; }
         double inv = 1.0 / alpha;
         double *g = H.g[H.L], *c = H.c[H.L];
+        if (P->emulate && P->scaling != 0) {
+            /* g = cast(r 2^sigma / alpha), c = MG(g), and the correction
+               taken with alpha 2^-sigma (both powers of two exact) */
+            inv = ldexp(inv, H.sigma);
+            alpha = ldexp(alpha, -H.sigma);
+        }
         for (size_t p = 0; p < N; ++p) g[p] = inv * r[p];
+        round_vec(lfmt(P, H.L), N, g);
         memset(c, 0, N * sizeof(double));
         if (cycle(&H, P, H.L)) { status = -1; break; }
         for (size_t p = 0; p < N; ++p) u[p] = u[p] + alpha * c[p];

@@ -43,7 +43,9 @@ class Params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("scaling", ctypes.c_int),
                 ("tol_mode", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("true_residual_guard", ctypes.c_int),
-                ("nthreads", ctypes.c_int), ("op", ctypes.c_int)]
+                ("nthreads", ctypes.c_int), ("op", ctypes.c_int),
+                ("emulate", ctypes.c_int), ("prec", ctypes.c_int * 24),
+                ("sigma_log2", ctypes.c_int), ("rescale16", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -74,6 +76,9 @@ def _load():
             lib.or_mg_cycle.restype = i
             lib.or_ir_solve.argtypes = [ctypes.POINTER(Params), _D, _D, ctypes.POINTER(Result), _D]
             lib.or_ir_solve.restype = i
+            lib.or_round.argtypes = [i, d]
+            lib.or_round.restype = d
+            lib.or_round_array.argtypes = [i, ctypes.c_size_t, _D, _D]
             _lib = lib
     return _lib
 
@@ -160,16 +165,43 @@ def level_sizes(n: int, levels: int = 0) -> list[int]:
     return [buf[i] for i in range(cnt)]
 
 
+# storage formats of the emulation (Sec. 3, Table 1)
+FP64, FP32, FP16, BF16 = 0, 1, 2, 3
+
+
+def round_to(fmt: int, x) -> np.ndarray:
+    """x (FP64) rounded to nearest, ties to even, into FP32 / FP16 / BF16 (FP64: x)."""
+    shape = np.shape(x)
+    x = _f64(x).reshape(-1)
+    y = np.empty_like(x)
+    _load().or_round_array(int(fmt), x.size, _p(x), _p(y))
+    return y.reshape(shape)
+
+
 def make_params(dim: int, n: int, *, levels: int = 0, nu1: int = 2, nu2: int = 2,
                 gamma: int = 1, omega: float = 0.8, scaling: int = 1, tol_mode: int = 0,
                 tol: float = 1e-10, max_iter: int = 100, guard: bool = True,
-                nthreads: int = 1, op: int = 0) -> Params:
-    return Params(dim, n, levels, nu1, nu2, gamma, omega, scaling, tol_mode, tol,
-                  max_iter, 1 if guard else 0, nthreads, op)
+                nthreads: int = 1, op: int = 0, prec=None, sigma_log2: int = -1,
+                rescale16: int = 1) -> Params:
+    """prec: per-level storage formats, coarsest first (one entry per level), to
+    run the low-precision emulation; None runs the plain FP64 oracle."""
+    P = Params(dim, n, levels, nu1, nu2, gamma, omega, scaling, tol_mode, tol,
+               max_iter, 1 if guard else 0, nthreads, op)
+    P.sigma_log2 = sigma_log2
+    P.rescale16 = rescale16
+    if prec is not None:
+        nl = len(level_sizes(n, levels))
+        if len(prec) != nl:
+            raise ValueError(f"prec has {len(prec)} entries for {nl} levels")
+        P.emulate = 1
+        for l, f in enumerate(prec):
+            P.prec[l] = int(f)
+    return P
 
 
 def mg_cycle(g, c0=None, **kw) -> np.ndarray:
-    """One multigrid cycle (Alg. 1, recursive) for A c = g from initial guess c0 (default 0)."""
+    """One multigrid cycle (Alg. 1, recursive) for A c = g from initial guess c0 (default 0);
+    with prec=[...] the low-precision emulation (g and c0 rounded to the finest format)."""
     g = _f64(g)
     d, n = _dn(g)
     c = np.zeros_like(g) if c0 is None else _f64(c0).copy()
@@ -180,7 +212,8 @@ def mg_cycle(g, c0=None, **kw) -> np.ndarray:
 
 
 def ir_solve(b, u0=None, **kw):
-    """Alg. 2 in FP64.  Returns (u, info dict, residual history array)."""
+    """Alg. 2 in FP64 (with prec=[...] the low-precision emulation of the levels).
+    Returns (u, info dict, residual history array)."""
     b = _f64(b)
     d, n = _dn(b)
     u = np.zeros_like(b) if u0 is None else _f64(u0).copy()

@@ -1,0 +1,215 @@
+"""Pins of the oracle's low-precision emulation (a diagnostic mode of the oracle).
+
+The rounding into FP32 / FP16 / BF16 is checked against numpy's conversions and
+against a brute-force nearest search over every finite value of the format,
+built from its bit patterns.  The emulated cycle and refinement loop are checked
+against what the arithmetic and the paper fix:
+
+- an all-FP64 emulation with the 2^sigma residual scaling equals the plain
+  oracle bit for bit (powers of two commute with every rounding);
+- the unit roundoff and range of Table 1;
+- FP16 multigrid without residual scaling stalls (Sec. 4.3), while FP32 and
+  BF16, which have FP64-like range, do not;
+- DSH_MG with an unscaled outer residual needs the rescale into its FP16 levels
+  (Sec. 6);
+- low-precision ladders take the FP64 iteration count (Sec. 8, Table 3).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2007_07539_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------- rounding
+def _samples(seed, count, lo_log2, hi_log2):
+    """Signed values log-uniform in [2^lo, 2^hi), with random FP64 significands."""
+    rng = np.random.default_rng(seed)
+    mag = np.exp2(rng.uniform(lo_log2, hi_log2, count))
+    return np.where(rng.random(count) < 0.5, -mag, mag)
+
+
+def _finite_table(fmt):
+    """Every finite non-negative value of the format in increasing order (index =
+    bit pattern), plus the first value past the largest finite one, which stands
+    for the overflow to infinity (its pattern is the infinity's)."""
+    if fmt == "fp16":
+        pats = np.arange(0, 0x7C00, dtype=np.uint16)
+        vals = pats.view(np.float16).astype(np.float64)
+        return np.append(vals, 65536.0)
+    pats = np.arange(0, 0x7F80, dtype=np.uint32) << np.uint32(16)  # bfloat16: the top half of a binary32
+    vals = pats.view(np.float32).astype(np.float64)
+    return np.append(vals, 2.0**128)
+
+
+def _nearest_brute(table, x):
+    """Nearest table value to |x|, ties to the even bit pattern; the top entry is infinity."""
+    a = np.abs(x)
+    hi = np.searchsorted(table, a, side="left").clip(1, len(table) - 1)
+    lo = hi - 1
+    dlo, dhi = a - table[lo], table[hi] - a  # exact: neighbours within a factor two of a
+    pick = np.where(dlo < dhi, lo, np.where(dhi < dlo, hi, np.where(lo % 2 == 0, lo, hi)))
+    out = table[pick].copy()
+    out[pick == len(table) - 1] = np.inf
+    out[a >= table[-1]] = np.inf
+    return np.copysign(out, x)
+
+
+def _ties(table, count, seed):
+    """Exact midpoints of neighbouring values of the format (representable in FP64), and
+    their FP64 neighbours."""
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, len(table) - 1, count)
+    mid = (table[i] + table[i + 1]) / 2
+    return np.concatenate([mid, np.nextafter(mid, 0), np.nextafter(mid, np.inf), -mid])
+
+
+@pytest.mark.parametrize("fmt", ["fp16", "bf16"])
+def test_round_matches_brute_force_nearest(oracle, fmt):
+    """Round-to-nearest-even against a search over every finite value of the format:
+    normals, subnormals, exact ties, overflow."""
+    table = _finite_table(fmt)
+    code = oracle.FP16 if fmt == "fp16" else oracle.BF16
+    top = 17 if fmt == "fp16" else 129
+    low = -27 if fmt == "fp16" else -136
+    x = np.concatenate([_samples(1, 20000, low, top), _ties(table, 5000, 2), [0.0, -0.0]])
+    got = oracle.round_to(code, x)
+    want = _nearest_brute(table, x)
+    bad = np.flatnonzero(~((got == want) | (np.isnan(got) & np.isnan(want))))
+    assert bad.size == 0, (x[bad[:5]], got[bad[:5]], want[bad[:5]])
+    assert np.array_equal(np.signbit(got[-2:]), [False, True])
+
+
+def test_round_matches_numpy_conversions(oracle):
+    """FP16 and FP32 against numpy's float64 -> float16 / float32 conversions."""
+    x16 = np.concatenate([_samples(3, 20000, -27, 17), _ties(_finite_table("fp16"), 3000, 4)])
+    with np.errstate(over="ignore"):
+        assert np.array_equal(oracle.round_to(oracle.FP16, x16), x16.astype(np.float16).astype(np.float64))
+        x32 = _samples(5, 20000, -152, 129)
+        assert np.array_equal(oracle.round_to(oracle.FP32, x32), x32.astype(np.float32).astype(np.float64))
+    x = _samples(6, 100, -40, 40)
+    assert np.array_equal(oracle.round_to(oracle.FP64, x), x)
+
+
+def test_round_table1_limits(oracle):
+    """Table 1: largest value, least normal value and unit roundoff of FP16 and FP32,
+    and the rounding at their edges."""
+    rows = {}
+    with open(os.path.join(GOLDEN, "fp_formats.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                name, rmin, rmax, ulog = line.split()
+                rows[name] = (float(rmin), float(rmax), int(ulog))
+    for name, code, p, emin in (("FP16", oracle.FP16, 11, -14), ("FP32", oracle.FP32, 24, -126)):
+        def r(v):
+            return float(oracle.round_to(code, v))
+        rmin, rmax, ulog = rows[name]
+        u = 2.0**ulog
+        assert ulog == -p
+        top = (2 - 2 * u) * 2.0 ** (1 - emin)  # the largest value: the printed maximum to 3 digits
+        assert abs(top / rmax - 1) < 5e-3 and r(top) == top and r(rmax) <= top
+        tiny = 2.0**emin
+        assert abs(tiny / rmin - 1) < 5e-3 and r(tiny) == tiny
+        assert r(1 + u) == 1.0  # a tie at the unit roundoff goes to the even 1
+        assert r(1 + u + u * u) == 1 + 2 * u
+        assert r(1 + 3 * u) == 1 + 4 * u  # a tie goes to the even neighbour above
+        mid = (2 - u) * 2.0 ** (1 - emin)  # halfway from the maximum to the next power of two
+        assert r(np.nextafter(mid, 0)) == top and np.isinf(r(mid)) and r(-mid) == -np.inf
+        sub = 2.0 ** (emin - p + 1)  # least subnormal
+        assert r(sub / 2) == 0.0 and r(sub * 0.75) == sub and r(1.5 * sub) == 2 * sub
+
+
+# ----------------------------------------------------------------------------- cycles and solves
+def _lad(oracle, name, nlev):
+    """The per-level formats of the Table 2 variants, coarsest first: H all FP16,
+    HSD FP16 on the two finest levels, FP64 base, FP32 between; DSH the reverse;
+    S all FP32, B all BF16, D all FP64."""
+    H, S, D, B = oracle.FP16, oracle.FP32, oracle.FP64, oracle.BF16
+    if name in ("H", "S", "D", "B"):
+        return [{"H": H, "S": S, "D": D, "B": B}[name]] * nlev
+    fine, coarse = (H, D) if name == "HSD" else (D, H)
+    return [coarse] + [S] * (nlev - 3) + [fine, fine]
+
+
+@pytest.mark.parametrize("dim,n,gamma", [(2, 31, 1), (3, 15, 1), (3, 15, 2)])
+def test_all_fp64_emulation_is_the_plain_oracle(oracle, dim, n, gamma):
+    """With every level FP64 and the residual scaled to 2^14 (sigma forced), the
+    emulated refinement equals the plain FP64 oracle bit for bit: the scaling by a
+    power of two and its compensation in the update are exact."""
+    b = I.random_rhs(dim, n, 5)
+    nl = len(oracle.level_sizes(n))
+    u0, i0, h0 = oracle.ir_solve(b, gamma=gamma)
+    u1, i1, h1 = oracle.ir_solve(b, gamma=gamma, prec=[oracle.FP64] * nl, sigma_log2=14)
+    assert i0["iters"] == i1["iters"]
+    assert np.array_equal(u0, u1) and np.array_equal(h0, h1)
+    c0 = oracle.mg_cycle(b, gamma=gamma)
+    c1 = oracle.mg_cycle(b, gamma=gamma, prec=[oracle.FP64] * nl)
+    assert np.array_equal(c0, c1)
+
+
+def test_emulated_cycle_stores_level_formats(oracle):
+    """One emulated cycle's result is a vector of the finest level's format and lies
+    within a few units of that format's roundoff of the FP64 cycle."""
+    dim, n = 3, 31
+    g = I.random_rhs(dim, n, 6)
+    nl = len(oracle.level_sizes(n))
+    c64 = oracle.mg_cycle(g)
+    for code, u in ((oracle.FP16, 2.0**-11), (oracle.BF16, 2.0**-8), (oracle.FP32, 2.0**-24)):
+        c = oracle.mg_cycle(g * 2.0**10, prec=[code] * nl) / 2.0**10
+        assert np.array_equal(oracle.round_to(code, c * 2.0**10), c * 2.0**10)
+        err = np.linalg.norm(c - c64) / np.linalg.norm(c64)
+        assert u / 8 < err < 50 * u, (code, err)
+
+
+@pytest.mark.parametrize("dim,n", [(3, 31), (2, 127)])
+def test_fp16_without_residual_scaling_stalls(oracle, dim, n):
+    """Sec. 4.3: without the residual scaling the FP16 correction underflows once the
+    residual is small, and the refinement stalls far above 1e-10; FP32 and BF16
+    (FP32's exponent range) converge unscaled, so the range is the cause.  With the
+    scaling FP16 converges."""
+    b = I.random_rhs(dim, n, 2)
+    nl = len(oracle.level_sizes(n))
+    _, i64, _ = oracle.ir_solve(b)
+    _, ih, _ = oracle.ir_solve(b, prec=_lad(oracle, "H", nl), scaling=0, max_iter=30)
+    assert not ih["converged"] and ih["rel_res"] > 1e-6
+    for name in ("S", "B"):
+        _, inf, _ = oracle.ir_solve(b, prec=_lad(oracle, name, nl), scaling=0)
+        assert inf["converged"] and inf["iters"] <= i64["iters"] + 1
+    _, ihs, _ = oracle.ir_solve(b, prec=_lad(oracle, "H", nl))
+    assert ihs["converged"]
+
+
+@pytest.mark.parametrize("dim,n", [(3, 31), (2, 127)])
+def test_dsh_unscaled_needs_the_fp16_rescale(oracle, dim, n):
+    """Sec. 6 (DSH_MG): with an unscaled outer residual the restricted residual on the
+    FP16 levels shrinks into FP16's subnormals; rescaling it by a power of two on
+    restriction restores the FP64 iteration count."""
+    b = I.random_rhs(dim, n, 2)
+    nl = len(oracle.level_sizes(n))
+    lad = [oracle.FP16] * (nl - 2) + [oracle.FP32, oracle.FP64]
+    _, i64, _ = oracle.ir_solve(b)
+    _, i0, _ = oracle.ir_solve(b, prec=lad, scaling=0, rescale16=0, max_iter=30)
+    _, i1, _ = oracle.ir_solve(b, prec=lad, scaling=0, rescale16=1)
+    assert not i0["converged"]
+    assert i1["converged"] and i1["iters"] == i64["iters"]
+
+
+@pytest.mark.parametrize("dim,n,rhs", [(3, 31, "random"), (2, 127, "random"), (3, 31, "manufactured")])
+def test_low_precision_ladders_keep_the_fp64_iteration_count(oracle, dim, n, rhs):
+    """Sec. 8 / Table 3: the multigrid preconditioner in FP16 (all levels, or with FP32 /
+    FP64 coarse levels) needs as many refinement steps as in FP64; so does BF16."""
+    b = I.random_rhs(dim, n, 2) if rhs == "random" else I.manufactured_rhs(dim, n)
+    nl = len(oracle.level_sizes(n))
+    _, i64, _ = oracle.ir_solve(b)
+    for name in ("H", "HSD", "DSH", "B"):
+        _, inf, _ = oracle.ir_solve(b, prec=_lad(oracle, name, nl))
+        assert inf["converged"] and inf["rel_res_true"] <= 1e-10
+        assert abs(inf["iters"] - i64["iters"]) <= 1, (name, inf["iters"], i64["iters"])
+
+
+def test_emulation_parameters_checked(oracle):
+    with pytest.raises(ValueError):
+        oracle.make_params(3, 15, prec=[oracle.FP16] * 2)
