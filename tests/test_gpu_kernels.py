@@ -3,6 +3,9 @@
 evaluated on the same storage-rounded inputs.  Bound per point:
 |gpu - oracle| <= tol * M with tol = 1e-12 (FP64), 1e-5 (FP32), 5e-3
 (FP16/BF16) and M the componentwise scaled magnitude of the operation.
+FP16 and BF16 outputs are also held to one rounding of the exact result:
+|gpu - round(oracle)| <= one spacing of the format + the FP32 arithmetic's
+error bound (check_rounded).
 Sizes span several CTA tiles, multi-chunk rows and ragged (padded) rows."""
 import math
 
@@ -11,7 +14,7 @@ import pytest
 
 from paper_2007_07539_gb300 import inputs as I
 from paper_2007_07539_gb300 import mg
-from _helpers import TOL, as_f64, check_close, empty_storage, to_storage
+from _helpers import TOL, as_f64, check_close, check_rounded, empty_storage, to_storage
 
 pytestmark = pytest.mark.gpu
 
@@ -88,6 +91,7 @@ def test_jacobi_sweep(oracle, case):
     ref = oracle.jacobi(g, c, OMEGA)
     mag = np.abs(c) + OMEGA * dinv(dim, n) * (np.abs(g) + oracle.apply_A(c, absmode=True))
     check_close(out, ref, mag, prec, "jacobi")
+    check_rounded(oracle, out, ref, mag, prec, "jacobi")
 
 
 @pytest.mark.parametrize("case", CASES, ids=ids)
@@ -103,6 +107,7 @@ def test_two_sweeps_from_zero(oracle, case):
     c1 = OMEGA * dinv(dim, n) * np.abs(g)
     mag = c1 + OMEGA * dinv(dim, n) * (np.abs(g) + oracle.apply_A(c1, absmode=True))
     check_close(out, ref, mag, prec, "zero2")
+    check_rounded(oracle, out, ref, mag, prec, "zero2")
 
 
 RCASES = [(3, n, pf, pc) for n in (7, 15, 47, 95) for pf in ALLP for pc in (pf, mg.FP32)] + \
@@ -136,6 +141,7 @@ def test_residual_restriction(oracle, case):
     mag = oracle.restrict(np.abs(g) + oracle.apply_A(c, absmode=True))
     worst = pf if TOL[pf] > TOL[pc] else pc
     check_close(out, ref, mag, worst, "restrict")
+    check_rounded(oracle, out, ref, mag, pc, "restrict", k=64)
 
 
 @pytest.mark.parametrize("case", [c for c in RCASES if c[0] == 3], ids=rids)
@@ -185,6 +191,7 @@ def test_prolongation_and_correction(oracle, case):
     mag = np.abs(cf) + oracle.prolong_add(np.abs(cc), np.zeros_like(cf))
     worst = pf if TOL[pf] > TOL[pc] else pc
     check_close(out, ref, mag, worst, "prolong")
+    check_rounded(oracle, out, ref, mag, pf, "prolong")
 
 
 @pytest.mark.parametrize("case", RCASES, ids=rids)
@@ -219,6 +226,7 @@ def test_base_level_solve(oracle, dim, n, prec):
     ref = oracle.coarse_solve(g)
     mag = oracle.coarse_solve(np.abs(g))
     check_close(out, ref, mag, prec, "coarse")
+    check_rounded(oracle, out, ref, mag, prec, "coarse")
 
 
 @pytest.mark.parametrize("dim,n,prec", [(3, 47, mg.FP16), (3, 95, mg.BF16), (3, 63, mg.FP32), (3, 31, mg.FP64),
@@ -236,11 +244,13 @@ def test_scale_cast_and_first_sweeps(oracle, dim, n, prec):
         g = read(h, L, mg.VEC_G, n, dim, prec)
         out = read(h, L, mg.VEC_C, n, dim, prec)
     check_close(g, r * s, np.abs(r * s), prec, "scale-cast")
+    check_rounded(oracle, g, r * s, np.abs(r * s), prec, "scale-cast")
     assert g[tuple([0] * dim)] == 0.0
     ref = oracle.jacobi(g, oracle.jacobi(g, np.zeros_like(g), OMEGA), OMEGA)
     c1 = OMEGA * dinv(dim, n) * np.abs(g)
     mag = c1 + OMEGA * dinv(dim, n) * (np.abs(g) + oracle.apply_A(c1, absmode=True))
     check_close(out, ref, mag, prec, "scale-cast+zero2")
+    check_rounded(oracle, out, ref, mag, prec, "scale-cast+zero2")
 
 
 @pytest.mark.parametrize("dim,n,prec", [(3, n, p) for n in (15, 95) for p in ALLP] +

@@ -213,3 +213,32 @@ def test_low_precision_ladders_keep_the_fp64_iteration_count(oracle, dim, n, rhs
 def test_emulation_parameters_checked(oracle):
     with pytest.raises(ValueError):
         oracle.make_params(3, 15, prec=[oracle.FP16] * 2)
+
+
+# ----------------------------------------------------------------------------- the kernels' one-rounding check
+@pytest.mark.parametrize("prec_name", ["fp16", "bf16"])
+def test_one_rounding_check_separates_fp32_arithmetic_from_an_extra_rounding(oracle, prec_name):
+    """The GPU kernel tests hold FP16/BF16 outputs to one rounding of the exact result
+    (check_rounded).  A Jacobi sweep computed in FP32 (numpy) and rounded once passes;
+    the same sweep with one intermediate value rounded to the storage format fails."""
+    from _helpers import check_rounded, to_storage
+    from paper_2007_07539_gb300 import mg
+    prec = mg.FP16 if prec_name == "fp16" else mg.BF16
+    dim, n, om = 3, 15, 0.8
+    h = 1.0 / (n + 1)
+    dinv = h * h / 6
+    cs, gs = (2.0**14 * dinv, 2.0**13) if prec == mg.FP16 else (1.0, 1.0 / dinv)
+    _, c = to_storage(I.uniform(1, (n,) * dim) * cs, prec)
+    _, g = to_storage(I.uniform(2, (n,) * dim) * gs, prec)
+    ref = oracle.jacobi(g, c, om)
+    mag = np.abs(c) + om * dinv * (np.abs(g) + oracle.apply_A(c, absmode=True))
+    c32, g32 = c.astype(np.float32), g.astype(np.float32)
+    p = np.pad(c32, 1)
+    nb = (p[1:-1, 1:-1, :-2] + p[1:-1, 1:-1, 2:] + p[1:-1, :-2, 1:-1] + p[1:-1, 2:, 1:-1]
+          + p[:-2, 1:-1, 1:-1] + p[2:, 1:-1, 1:-1])
+    part = np.float32(om * dinv) * g32 + np.float32(om / 6) * nb
+    once = to_storage((np.float32(1 - om) * c32 + part).astype(np.float64), prec)[1]
+    check_rounded(oracle, once, ref, mag, prec, "fp32 sweep")
+    twice = to_storage((1 - om) * c + to_storage(part.astype(np.float64), prec)[1], prec)[1]
+    with pytest.raises(AssertionError):
+        check_rounded(oracle, twice, ref, mag, prec, "extra rounding")
