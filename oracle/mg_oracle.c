@@ -31,6 +31,9 @@
  *                     in FP64
  *   or_round          round-to-nearest-even into FP32, FP16 or BF16 (Sec. 3,
  *                     Table 1), written from the formats' definitions
+ *   or_cg_solve_fmt   conjugate gradients on the base level (Sec. 6: the CG
+ *                     base solver), optionally with its vectors stored in a
+ *                     low-precision format
  *
  * Optional low-precision emulation (params.emulate = 1, a diagnostic: parity
  * of the GPU path is stated against the FP64 oracle): every vector a level
@@ -80,6 +83,10 @@ typedef struct {
     int prec[OR_MAX_LEVELS]; /* storage format per level, coarsest first (OR_FP64 ...) */
     int sigma_log2;       /* scaled residual max-norm 2^sigma; -1: 14 if a level is FP16, else 0 */
     int rescale16;        /* 1: rescale restrictions from a non-FP16 into an FP16 level */
+    /* base solver (Sec. 6) */
+    int base_solver;      /* 0: exact (Cholesky); 1: conjugate gradients */
+    double base_tol;      /* CG: stop at ||r||_2 <= base_tol ||g||_2 */
+    int base_maxit;       /* CG: step limit (<= 0: the number of unknowns) */
 } or_params;
 
 /* storage formats of the emulation (Sec. 3, Table 1) */
@@ -394,6 +401,55 @@ int or_coarse_solve_op(int op, int d, int n, const double *g, double *c) {
 }
 int or_coarse_solve(int d, int n, const double *g, double *c) { return or_coarse_solve_op(0, d, n, g, c); }
 
+/*
+ * Conjugate gradients for A c = g on an n^d grid (Sec. 6: the base solver),
+ * from c = 0, in the textbook order of Hestenes and Stiefel:
+ *   r = g, p = r
+ *   repeat:  q = A p;  a = r.r / p.q;  c += a p;  r -= a q;
+ *            b = r_new.r_new / r.r;  p = r + b p
+ * Stops when ||r||_2 <= tol ||g||_2 for the recursively updated r, after
+ * maxit steps, or when p.q is not positive (breakdown; g = 0 included).
+ * With fmt != OR_FP64 the stored vectors c, r, p are rounded to fmt after
+ * each update (the CG of a low-precision base level); A p and the dot
+ * products stay in FP64.  Returns the steps taken, or -1 on allocation
+ * failure.
+ */
+int or_cg_solve_fmt(int op, int d, int n, int fmt, const double *g, double *c, double tol, int maxit) {
+    size_t N = npts(d, n);
+    double *r = (double *)malloc(N * sizeof(double));
+    double *p = (double *)malloc(N * sizeof(double));
+    double *q = (double *)malloc(N * sizeof(double));
+    if (!r || !p || !q) { free(r); free(p); free(q); return -1; }
+    double rr = 0.0;
+    for (size_t i = 0; i < N; ++i) {
+        c[i] = 0.0;
+        r[i] = or_round(fmt, g[i]);
+        p[i] = r[i];
+        rr += r[i] * r[i];
+    }
+    const double thr = tol * tol * rr;
+    int it = 0;
+    while (it < maxit && rr > thr) {
+        or_apply_A_op(op, d, n, p, q, 0);
+        double pq = 0.0;
+        for (size_t i = 0; i < N; ++i) pq += p[i] * q[i];
+        if (!(pq > 0.0)) break;
+        const double a = rr / pq;
+        double rn = 0.0;
+        for (size_t i = 0; i < N; ++i) {
+            c[i] = or_round(fmt, c[i] + a * p[i]);
+            r[i] = or_round(fmt, r[i] - a * q[i]);
+            rn += r[i] * r[i];
+        }
+        const double b = rn / rr;
+        for (size_t i = 0; i < N; ++i) p[i] = or_round(fmt, r[i] + b * p[i]);
+        rr = rn;
+        ++it;
+    }
+    free(r); free(p); free(q);
+    return it;
+}
+
 /* Coarsening rule: n_{l-1} = (n_l - 1)/2 while n_l is odd and > 3.
  * Fills sizes[0..L] with sizes[L] = n (finest) and returns the level count. */
 int or_level_sizes(int n, int levels_req, int *sizes) {
@@ -449,6 +505,10 @@ static int cycle(or_hier *H, const or_params *P, int l) {
     const int op = P->op;
     const int f = lfmt(P, l);
     if (l == 0) {
+        if (P->base_solver == 1) {
+            const int maxit = P->base_maxit > 0 ? P->base_maxit : (int)N;
+            return or_cg_solve_fmt(op, d, n, f, g, c, P->base_tol, maxit) < 0 ? -1 : 0;
+        }
         int rc = or_coarse_solve_op(op, d, n, g, c);
         round_vec(f, N, c);
         return rc;

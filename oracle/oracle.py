@@ -45,7 +45,9 @@ class Params(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("true_residual_guard", ctypes.c_int),
                 ("nthreads", ctypes.c_int), ("op", ctypes.c_int),
                 ("emulate", ctypes.c_int), ("prec", ctypes.c_int * 24),
-                ("sigma_log2", ctypes.c_int), ("rescale16", ctypes.c_int)]
+                ("sigma_log2", ctypes.c_int), ("rescale16", ctypes.c_int),
+                ("base_solver", ctypes.c_int), ("base_tol", ctypes.c_double),
+                ("base_maxit", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -76,6 +78,8 @@ def _load():
             lib.or_mg_cycle.restype = i
             lib.or_ir_solve.argtypes = [ctypes.POINTER(Params), _D, _D, ctypes.POINTER(Result), _D]
             lib.or_ir_solve.restype = i
+            lib.or_cg_solve_fmt.argtypes = [i, i, i, i, _D, _D, d, i]
+            lib.or_cg_solve_fmt.restype = i
             lib.or_round.argtypes = [i, d]
             lib.or_round.restype = d
             lib.or_round_array.argtypes = [i, ctypes.c_size_t, _D, _D]
@@ -158,6 +162,20 @@ def coarse_solve(g, op: int = 0) -> np.ndarray:
     return c
 
 
+def cg_solve(g, tol: float = 1e-4, maxit: int = 0, op: int = 0, fmt: int = 0):
+    """Conjugate gradients for A c = g from c = 0 (Sec. 6 base solver): stops at
+    ||r||_2 <= tol ||g||_2, after maxit steps (<= 0: the number of unknowns) or on
+    breakdown; fmt rounds the stored vectors (emulation).  Returns (c, steps)."""
+    g = _f64(g)
+    d, n = _dn(g)
+    c = np.zeros_like(g)
+    it = _load().or_cg_solve_fmt(int(op), d, n, int(fmt), _p(g), _p(c), float(tol),
+                                 int(maxit) if maxit > 0 else g.size)
+    if it < 0:
+        raise RuntimeError("oracle CG failed")
+    return c, it
+
+
 def level_sizes(n: int, levels: int = 0) -> list[int]:
     """Level sizes, coarsest first: n_{l-1} = (n_l - 1)/2 while n_l is odd and > 3."""
     buf = (ctypes.c_int * 24)()
@@ -182,13 +200,18 @@ def make_params(dim: int, n: int, *, levels: int = 0, nu1: int = 2, nu2: int = 2
                 gamma: int = 1, omega: float = 0.8, scaling: int = 1, tol_mode: int = 0,
                 tol: float = 1e-10, max_iter: int = 100, guard: bool = True,
                 nthreads: int = 1, op: int = 0, prec=None, sigma_log2: int = -1,
-                rescale16: int = 1) -> Params:
+                rescale16: int = 1, base_solver: int = 0, base_tol: float = 1e-4,
+                base_maxit: int = 0) -> Params:
     """prec: per-level storage formats, coarsest first (one entry per level), to
-    run the low-precision emulation; None runs the plain FP64 oracle."""
+    run the low-precision emulation; None runs the plain FP64 oracle.
+    base_solver 1: CG on the base level (Sec. 6) to base_tol, relative."""
     P = Params(dim, n, levels, nu1, nu2, gamma, omega, scaling, tol_mode, tol,
                max_iter, 1 if guard else 0, nthreads, op)
     P.sigma_log2 = sigma_log2
     P.rescale16 = rescale16
+    P.base_solver = base_solver
+    P.base_tol = base_tol
+    P.base_maxit = base_maxit
     if prec is not None:
         nl = len(level_sizes(n, levels))
         if len(prec) != nl:

@@ -30,8 +30,9 @@ enum TailKind : int {
 // dynamic shared memory, where level arrays are compact (x fastest, n^d
 // values, no pads); gptr is the padded global array of TK_LOAD / TK_STORE.
 // mn / mnc are ceil(2^40 / n) and ceil(2^40 / nc): q = (p * mn) >> 40 is p / n
-// for every p < 2^13 (division by an invariant integer through a fixed-point
-// reciprocal, exact here because p * (mn - 2^40 / n) < 2^40 / n).
+// for every point p of a tail level, p < 2^15 (division by an invariant integer
+// through a fixed-point reciprocal, exact because p * (mn - 2^40 / n) < p <
+// 2^40 / n for n < 2^10).
 struct TailOp {
     int kind, mode, prec, prec_c;
     int n, nc, P, S;
@@ -57,7 +58,8 @@ constexpr int kTailChunk = 32;  // stages staged in shared memory at a time
 
 inline unsigned long long tail_magic(int n) { return ((1ull << 40) + (unsigned long long)n - 1) / (unsigned long long)n; }
 
-// One instance of a batched tail launch (one CTA each; gated on its state).
+// One instance of a batched tail launch (one CTA, or one cluster, each; gated
+// on its state).
 struct TailItem {
     const TailOp* prog;
     const double* minv;

@@ -210,6 +210,35 @@ def test_low_precision_ladders_keep_the_fp64_iteration_count(oracle, dim, n, rhs
         assert abs(inf["iters"] - i64["iters"]) <= 1, (name, inf["iters"], i64["iters"])
 
 
+@pytest.mark.parametrize("dim,n,case", [(3, 31, "random"), (2, 127, "random"), (3, 31, "k1"), (2, 63, "k20")])
+def test_paper_ladders_with_fp16_cg_base(oracle, dim, n, case):
+    """Sec. 8, Table 3 settings: DSH_MG with the CG base solver in FP16 (level 0), FP16
+    level 1, FP32 level 2, FP64 above, and H_MG / HSD_MG with the CG base, need as many
+    refinement steps as D_MG; the manufactured cases start from u0 uniform in [0, 1)."""
+    if case == "random":
+        b, u0 = I.random_rhs(dim, n, 2), None
+    else:
+        b, u0 = I.manufactured_rhs(dim, n, int(case[1:])), I.random_guess(dim, n, 5)
+    nl = len(oracle.level_sizes(n))
+    H, S, D = oracle.FP16, oracle.FP32, oracle.FP64
+    _, i64, _ = oracle.ir_solve(b, u0)
+    for lad in ([H, H, S] + [D] * (nl - 3), [H] * nl, [D, D, S] + [H] * (nl - 3)):
+        _, inf, _ = oracle.ir_solve(b, u0, prec=lad, base_solver=1)
+        assert inf["converged"] and inf["rel_res_true"] <= 1e-10
+        assert inf["iters"] <= i64["iters"] + 1, (lad, inf["iters"], i64["iters"])
+
+
+def test_emulated_fp16_cg_is_a_low_precision_cg(oracle):
+    """The base solver's CG with its vectors stored in FP16: every stored value is an
+    FP16 value, and the solution meets the relative 1e-4 test up to FP16's resolution."""
+    g = oracle.round_to(oracle.FP16, I.uniform(24, (3, 3, 3)) * 2.0**13)
+    c, steps = oracle.cg_solve(g, tol=1e-4, fmt=oracle.FP16)
+    assert np.array_equal(oracle.round_to(oracle.FP16, c), c)
+    ref = oracle.coarse_solve(g)
+    assert 1 <= steps <= 27
+    assert np.linalg.norm(c - ref) <= 4e-3 * np.linalg.norm(ref)
+
+
 def test_emulation_parameters_checked(oracle):
     with pytest.raises(ValueError):
         oracle.make_params(3, 15, prec=[oracle.FP16] * 2)

@@ -191,6 +191,51 @@ def test_coarse_solve_matches_numpy(oracle, dim, n):
     assert np.abs(oracle.coarse_solve(g) - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("dim,n", [(3, 3), (2, 7), (3, 5), (2, 3)])
+def test_cg_terminates_after_the_distinct_eigenvalues(oracle, dim, n):
+    """CG (Sec. 6 base solver) reaches the exact solution in as many steps as A has
+    distinct eigenvalues (g has a component on each).  The eigenvalues are the sums of
+    the 1-D ones, (4/h^2) sum_a sin^2(m_a pi h / 2); on the 3^3 grid they are
+    (4/h^2)(3/2 + k sqrt(2)/4), k = -3..3: seven values."""
+    g = I.uniform(21, (n,) * dim)
+    h = 1.0 / (n + 1)
+    s1 = np.sin(np.arange(1, n + 1) * math.pi * h / 2) ** 2
+    grids = np.meshgrid(*([s1] * dim), indexing="ij")
+    lam = 4.0 / h**2 * sum(grids)
+    distinct = len(np.unique(np.round(lam.ravel() / lam.max(), 10)))
+    if (dim, n) == (3, 3):
+        assert distinct == 7
+    c, steps = oracle.cg_solve(g, tol=1e-12)
+    ref = np.linalg.solve(lap(dim, n).toarray(), g.ravel()).reshape(g.shape)
+    assert steps <= distinct
+    assert np.abs(c - ref).max() <= 1e-12 * np.abs(ref).max()
+    _, early = oracle.cg_solve(g, tol=1e-12, maxit=distinct - 1)
+    assert early == distinct - 1 and steps == distinct  # no earlier step reaches 1e-12
+
+
+def test_cg_first_step_is_steepest_descent(oracle):
+    """One CG step from c = 0 is the exact line search along g: c = (g.g / g.Ag) g."""
+    g = I.uniform(22, (7, 7, 7))
+    c, steps = oracle.cg_solve(g, tol=0.0, maxit=1)
+    Ag = lap(3, 7) @ g.ravel()
+    assert steps == 1
+    assert np.abs(c - (g.ravel() @ g.ravel()) / (g.ravel() @ Ag) * g).max() <= 1e-14 * np.abs(c).max()
+
+
+def test_cg_stopping_rule(oracle):
+    """CG stops at the first step whose residual is at most tol ||g||_2 (Sec. 6: the
+    base solver's residual test, relative here)."""
+    g = I.uniform(23, (15, 15, 15))
+    A = lap(3, 15)
+    c, steps = oracle.cg_solve(g, tol=1e-4)
+    rel = np.linalg.norm(g.ravel() - A @ c.ravel()) / np.linalg.norm(g)
+    assert 1 < steps < g.size and rel <= 1.0001e-4
+    cp, _ = oracle.cg_solve(g, tol=1e-4, maxit=steps - 1)
+    assert np.linalg.norm(g.ravel() - A @ cp.ravel()) / np.linalg.norm(g) > 1e-4
+    _, none = oracle.cg_solve(np.zeros_like(g))
+    assert none == 0
+
+
 def test_level_sizes(oracle):
     assert oracle.level_sizes(127) == [3, 7, 15, 31, 63, 127]        # 6 levels, coarsest 3x3
     assert oracle.level_sizes(511) == [3, 7, 15, 31, 63, 127, 255, 511]
