@@ -228,6 +228,27 @@ def test_paper_ladders_with_fp16_cg_base(oracle, dim, n, case):
         assert inf["iters"] <= i64["iters"] + 1, (lad, inf["iters"], i64["iters"])
 
 
+def test_fp16_finest_level_caps_a_fast_cycle(oracle):
+    """When the FP64 cycle contracts much faster than an FP16 correction is accurate
+    (Q1 operator, W(2,2)-cycle: 5 steps to 1e-10), the ladders with FP16 finest levels
+    need more steps, while DSH_MG (FP64 finest levels, FP16 only on the coarsest)
+    keeps the FP64 count: the finest levels' precision bounds the per-step gain."""
+    dim, n = 3, 31
+    b = I.manufactured_load(dim, n, 1)
+    nl = len(oracle.level_sizes(n))
+    H, S, D = oracle.FP16, oracle.FP32, oracle.FP64
+    kw = dict(op=1, gamma=2)
+    _, i64, _ = oracle.ir_solve(b, **kw)
+    its = {}
+    for name, lad in (("H", [H] * nl), ("HSD", [D, D, S] + [H] * (nl - 3)), ("DSH", [H, H, S] + [D] * (nl - 3))):
+        _, inf, _ = oracle.ir_solve(b, prec=lad, **kw)
+        assert inf["converged"]
+        its[name] = inf["iters"]
+    assert i64["iters"] <= 6
+    assert its["DSH"] == i64["iters"]
+    assert its["H"] >= i64["iters"] + 2 and its["HSD"] >= i64["iters"] + 2, (its, i64["iters"])
+
+
 def test_emulated_fp16_cg_is_a_low_precision_cg(oracle):
     """The base solver's CG with its vectors stored in FP16: every stored value is an
     FP16 value, and the solution meets the relative 1e-4 test up to FP16's resolution."""
