@@ -44,7 +44,11 @@
  * IR loop then scales the residual to max-norm 2^sigma before the cast and
  * divides the correction by it again (Sec. 4.3), and a restriction from a
  * non-FP16 level into an FP16 level is rescaled by a power of two taken from
- * its max-norm and undone on prolongation (Sec. 6, DSH_MG).
+ * its max-norm and undone on prolongation (Sec. 6, DSH_MG).  With scale_ahead
+ * the scale of Alg. 2 line 4 is instead the power of two 2^sigma / 2^e with
+ * 2^(e-1) <= ||r||_inf < 2^e of the previous step's residual (any scale is
+ * exact in exact arithmetic), and the scaled residual is truncated to FP32
+ * before the cast, as when the update itself forms the next right-hand side.
  *
  * Grid vectors are interior-only, contiguous, x fastest:
  *   index(i, j[, k]) = i + n*j [+ n*n*k], point ((i+1)h, (j+1)h[, (k+1)h]).
@@ -87,6 +91,8 @@ typedef struct {
     int base_solver;      /* 0: exact (Cholesky); 1: conjugate gradients */
     double base_tol;      /* CG: stop at ||r||_2 <= base_tol ||g||_2 */
     int base_maxit;       /* CG: step limit (<= 0: the number of unknowns) */
+    int scale_ahead;      /* emulation, max-norm scaling: the next g scaled by the power of two from the
+                             previous residual's max-norm, through an FP32 truncation */
 } or_params;
 
 /* storage formats of the emulation (Sec. 3, Table 1) */
@@ -618,6 +624,19 @@ double or_norminf(size_t N, const double *v) {
  * step and after the last.  Returns 0 on convergence, 1 if max_iter was hit,
  * -1 on failure (allocation, base solve, non-finite residual).
  */
+/* x truncated toward zero to binary32 precision (0 below its normal range,
+   infinity at and above 2^128): the low 29 of FP64's 52 fraction bits cleared */
+static double trunc_f32(double x) {
+    if (!isfinite(x)) return x;
+    const double a = fabs(x);
+    if (a < ldexp(1.0, -126)) return copysign(0.0, x);
+    if (a >= ldexp(1.0, 128)) return copysign(INFINITY, x);
+    int E;
+    const double f = frexp(a, &E);                 /* a = f 2^E, f in [1/2, 1) */
+    const double m = floor(ldexp(f, 24));          /* the 24 leading significand bits */
+    return copysign(ldexp(m, E - 24), x);
+}
+
 int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, double *history) {
     or_hier H;
     g_threads = P->nthreads > 0 ? P->nthreads : 1;
@@ -635,6 +654,10 @@ int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, 
     res->bnorm = bnorm;
     double scale = P->tol_mode == 0 ? bnorm : 1.0;
     int it = 0;
+    const int fL = lfmt(P, H.L);
+    const int ahead_on = P->emulate && P->scale_ahead && P->scaling == 1 && fL != OR_FP64;
+    double inv_pred = 0.0; /* scale-ahead: 2^sigma / 2^e from the previous residual's max-norm */
+    int ahead = 0;         /* the current r is the result of a refinement step */
     for (;;) {
         double rn = or_norm2(N, r);
         if (!isfinite(rn)) { status = -1; break; }
@@ -646,6 +669,7 @@ int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, 
             double tn = or_norm2(N, ac);
             if (tn <= P->tol * scale) { status = 0; break; }
             memcpy(r, ac, N * sizeof(double));
+            ahead = 0;
             res->guard_restarts++;
             rn = tn;
             res->rel_res = bnorm > 0 ? rn / bnorm : rn;
@@ -664,8 +688,29 @@ int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, 
             inv = ldexp(inv, H.sigma);
             alpha = ldexp(alpha, -H.sigma);
         }
-        for (size_t p = 0; p < N; ++p) g[p] = inv * r[p];
-        round_vec(lfmt(P, H.L), N, g);
+        int done = 0;
+        if (ahead_on && ahead && inv_pred > 0.0) {
+            /* scale-ahead: g = cast(trunc_f32(r inv_pred)) unless a value is
+               beyond the format's range, then the scale above */
+            const double lim = fL == OR_FP16 ? 65520.0 : 3.0e38;
+            int over = 0;
+            for (size_t p = 0; p < N; ++p) {
+                const double t = trunc_f32(r[p] * inv_pred);
+                over |= !(fabs(t) < lim);
+                g[p] = or_round(fL, t);
+            }
+            if (!over) { inv = inv_pred; alpha = 1.0 / inv_pred; done = 1; }
+        }
+        if (ahead_on) {
+            int e;
+            (void)frexp(or_norminf(N, r), &e); /* 2^(e-1) <= ||r||_inf < 2^e */
+            inv_pred = ldexp(1.0, H.sigma - e);
+            ahead = 1;
+        }
+        if (!done) {
+            for (size_t p = 0; p < N; ++p) g[p] = inv * r[p];
+            round_vec(fL, N, g);
+        }
         memset(c, 0, N * sizeof(double));
         if (cycle(&H, P, H.L)) { status = -1; break; }
         for (size_t p = 0; p < N; ++p) u[p] = u[p] + alpha * c[p];

@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
                 ("emulate", ctypes.c_int), ("prec", ctypes.c_int * 24),
                 ("sigma_log2", ctypes.c_int), ("rescale16", ctypes.c_int),
                 ("base_solver", ctypes.c_int), ("base_tol", ctypes.c_double),
-                ("base_maxit", ctypes.c_int)]
+                ("base_maxit", ctypes.c_int), ("scale_ahead", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -201,10 +201,11 @@ def make_params(dim: int, n: int, *, levels: int = 0, nu1: int = 2, nu2: int = 2
                 tol: float = 1e-10, max_iter: int = 100, guard: bool = True,
                 nthreads: int = 1, op: int = 0, prec=None, sigma_log2: int = -1,
                 rescale16: int = 1, base_solver: int = 0, base_tol: float = 1e-4,
-                base_maxit: int = 0) -> Params:
+                base_maxit: int = 0, scale_ahead: int = 0) -> Params:
     """prec: per-level storage formats, coarsest first (one entry per level), to
     run the low-precision emulation; None runs the plain FP64 oracle.
-    base_solver 1: CG on the base level (Sec. 6) to base_tol, relative."""
+    base_solver 1: CG on the base level (Sec. 6) to base_tol, relative.
+    scale_ahead 1 (emulation): the power-of-two scale from the previous residual."""
     P = Params(dim, n, levels, nu1, nu2, gamma, omega, scaling, tol_mode, tol,
                max_iter, 1 if guard else 0, nthreads, op)
     P.sigma_log2 = sigma_log2
@@ -212,6 +213,7 @@ def make_params(dim: int, n: int, *, levels: int = 0, nu1: int = 2, nu2: int = 2
     P.base_solver = base_solver
     P.base_tol = base_tol
     P.base_maxit = base_maxit
+    P.scale_ahead = scale_ahead
     if prec is not None:
         nl = len(level_sizes(n, levels))
         if len(prec) != nl:

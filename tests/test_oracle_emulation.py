@@ -260,6 +260,31 @@ def test_emulated_fp16_cg_is_a_low_precision_cg(oracle):
     assert np.linalg.norm(c - ref) <= 4e-3 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("dim,n,case", [(3, 31, "random"), (2, 127, "random"), (2, 255, "fd_k1"), (3, 31, "q1_k1")])
+def test_scale_ahead_keeps_the_iteration_count(oracle, dim, n, case):
+    """The scale of Alg. 2 line 4 taken as the power of two from the previous step's
+    max-norm, with the scaled residual truncated to FP32 before the cast: a different
+    scale (the histories differ) but the same number of refinement steps, for FP16,
+    HSD and BF16 ladders."""
+    kw = dict(op=1) if case.startswith("q1") else {}
+    if case == "random":
+        b = I.random_rhs(dim, n, 2)
+    elif case == "fd_k1":
+        b = I.manufactured_rhs(dim, n, 1)
+    else:
+        b = I.manufactured_load(dim, n, 1)
+    nl = len(oracle.level_sizes(n))
+    changed = False
+    for name in ("H", "HSD", "B"):
+        lad = _lad(oracle, name, nl)
+        _, i0, h0 = oracle.ir_solve(b, prec=lad, **kw)
+        _, i1, h1 = oracle.ir_solve(b, prec=lad, scale_ahead=1, **kw)
+        assert i0["converged"] and i1["converged"]
+        assert i1["iters"] == i0["iters"], (name, i0["iters"], i1["iters"])
+        changed |= not np.array_equal(h0, h1)
+    assert changed
+
+
 def test_emulation_parameters_checked(oracle):
     with pytest.raises(ValueError):
         oracle.make_params(3, 15, prec=[oracle.FP16] * 2)
