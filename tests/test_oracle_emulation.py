@@ -134,19 +134,19 @@ def _lad(oracle, name, nlev):
     return [coarse] + [S] * (nlev - 3) + [fine, fine]
 
 
-@pytest.mark.parametrize("dim,n,gamma", [(2, 31, 1), (3, 15, 1), (3, 15, 2)])
-def test_all_fp64_emulation_is_the_plain_oracle(oracle, dim, n, gamma):
+@pytest.mark.parametrize("dim,n,gamma,op", [(2, 31, 1, 0), (3, 15, 1, 0), (3, 15, 2, 0), (3, 15, 1, 1), (2, 31, 2, 1)])
+def test_all_fp64_emulation_is_the_plain_oracle(oracle, dim, n, gamma, op):
     """With every level FP64 and the residual scaled to 2^14 (sigma forced), the
     emulated refinement equals the plain FP64 oracle bit for bit: the scaling by a
-    power of two and its compensation in the update are exact."""
+    power of two and its compensation in the update are exact (both operators)."""
     b = I.random_rhs(dim, n, 5)
     nl = len(oracle.level_sizes(n))
-    u0, i0, h0 = oracle.ir_solve(b, gamma=gamma)
-    u1, i1, h1 = oracle.ir_solve(b, gamma=gamma, prec=[oracle.FP64] * nl, sigma_log2=14)
+    u0, i0, h0 = oracle.ir_solve(b, gamma=gamma, op=op)
+    u1, i1, h1 = oracle.ir_solve(b, gamma=gamma, op=op, prec=[oracle.FP64] * nl, sigma_log2=14)
     assert i0["iters"] == i1["iters"]
     assert np.array_equal(u0, u1) and np.array_equal(h0, h1)
-    c0 = oracle.mg_cycle(b, gamma=gamma)
-    c1 = oracle.mg_cycle(b, gamma=gamma, prec=[oracle.FP64] * nl)
+    c0 = oracle.mg_cycle(b, gamma=gamma, op=op)
+    c1 = oracle.mg_cycle(b, gamma=gamma, op=op, prec=[oracle.FP64] * nl)
     assert np.array_equal(c0, c1)
 
 
