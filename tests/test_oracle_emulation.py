@@ -285,6 +285,20 @@ def test_scale_ahead_keeps_the_iteration_count(oracle, dim, n, case):
     assert changed
 
 
+def test_fp16_iteration_count_is_grid_independent(oracle):
+    """Sec. 8: the refinement needs a bounded number of steps as the grid is refined;
+    with every level in FP16 the counts stay within one step from 15^3 to 63^3 and
+    from 31^2 to 511^2."""
+    for dim, ns in ((3, (15, 31, 63)), (2, (31, 63, 127, 255, 511))):
+        its = []
+        for n in ns:
+            nl = len(oracle.level_sizes(n))
+            _, inf, _ = oracle.ir_solve(I.random_rhs(dim, n, 11), prec=[oracle.FP16] * nl, nthreads=4)
+            assert inf["converged"]
+            its.append(inf["iters"])
+        assert max(its) - min(its) <= 1 and max(its) <= 20, (dim, its)
+
+
 def test_emulation_parameters_checked(oracle):
     with pytest.raises(ValueError):
         oracle.make_params(3, 15, prec=[oracle.FP16] * 2)
