@@ -47,6 +47,14 @@ int main(int argc, char** argv) {
         std::printf("\n");
         return 0;
     }
+    if (argc == 4 && !std::strcmp(argv[1], "geom")) {  // dim nmax: every level size up to nmax
+        const int dim = std::atoi(argv[2]), nmax = std::atoi(argv[3]);
+        for (int n = 1; n <= nmax; ++n) {
+            const mgi::Geom g = mgi::make_geom(dim, n);
+            std::printf("%d %d %lld %lld %lld\n", n, g.P, g.S, g.base, g.total);
+        }
+        return 0;
+    }
     return 2;
 }
 '''
@@ -100,3 +108,21 @@ def test_sweep_coefficients_reproduce_the_oracle_sweeps(oracle, hostprog, dim, o
     assert np.abs(got2 - ref2).max() <= 1e-13 * np.abs(ref2).max()
     res = g + alpha * W(c) + a5 * c
     assert np.abs(res - oracle.residual(g, c, op=op)).max() <= 1e-12 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_padded_layout(hostprog, dim):
+    """The padded level layout: row pitch a multiple of 16 elements with room for the
+    zero pad column, the interior start (0, 0[, 0]) 16-byte aligned for every storage
+    type, and everything a stencil or a vector access of a row can touch inside the
+    allocation: from row -1 of plane -1, x = -1 and a 16-byte vector before it, up to
+    the last pitch element of row n of plane n and a 16-byte vector after it."""
+    rows = [list(map(int, ln.split())) for ln in
+            subprocess.check_output([hostprog, "geom", str(dim), "1100"], text=True).splitlines()]
+    assert len(rows) == 1100
+    for n, P, S, base, total in rows:
+        assert P % 16 == 0 and P >= n + 1 and S == P * (n + 1)
+        assert base % 16 == 0 and total % 128 == 0  # 16 elements: >= 32 bytes for every type
+        lo = base - P - (S if dim == 3 else 0) - 1 - 8
+        hi = base + n * P + (n * S if dim == 3 else 0) + (P - 1) + 8
+        assert lo >= 0 and hi < total, (n, P, base, total)
