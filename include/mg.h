@@ -186,6 +186,32 @@ const char* mg_last_error(void);
 /* Device bytes a hierarchy with these parameters will hold (0 if invalid). */
 size_t mg_footprint_bytes(const mg_params* p);
 
+/* The operations of one IR step's multigrid cycle as the library schedules
+ * them, computed on the host without a device: the Alg. 1 recursion (nu1
+ * pre-smoothing sweeps, residual-restriction, gamma visits of the coarser
+ * level, prolongation, nu2 post-smoothing sweeps; base solve on level 0),
+ * preceded by the scale-and-cast of Alg. 2 line 4, with the coarse tail and
+ * the FP16 rescale of Sec. 6 where the hierarchy has them.
+ * rec receives records of 6 int32 values (caller-owned, 6 * cap entries):
+ *   kind    0 stencil kernel, 1 base solve, 3 zero fill, 7 coarse-tail
+ *           launch, 8 rescale into an FP16 level; 100 + stage for a stage of
+ *           the preceding coarse-tail launch (0 sweep, 1 residual,
+ *           2 restriction, 3 prolongation, 4 base solve, 5 zero, 6 load,
+ *           7 store)
+ *   level   level index (0 = coarsest)
+ *   kernel  for kind 0: 0 sweep, 1 IR update, 2 scale-and-cast,
+ *           3 prolongation; else -1
+ *   mode    sweep mode (0 Jacobi, 1 two sweeps from zero, 2 one sweep from
+ *           zero, 3 residual-restriction, 4 one-pass pre-smoothing and
+ *           restriction; + 16 for the Q1 operator); base-solve stages: 0
+ *           exact, 1 CG
+ *   prec, prec_c  storage types of the level and of the next coarser level
+ * Records beyond cap are counted but not written.  The cluster tail's size
+ * needs a device; the description shows the plan without that probe.
+ * Returns MG_OK with the record count in *count, or MG_ERR_INVALID (invalid
+ * parameters, count NULL, rec NULL with cap > 0). */
+mg_status mg_describe_cycle(const mg_params* p, int32_t* rec, int32_t cap, int32_t* count);
+
 /* ---------------------------------------------------------------- the five calls */
 
 /* Creates a hierarchy: level geometry, per-level precision ladder, padded

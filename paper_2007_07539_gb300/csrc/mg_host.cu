@@ -257,7 +257,7 @@ struct Gen {
         op.sh = kernel_shape(h->dim, kkind, mode, op.prec, f.n, f.P, 0);
         a.xstep = op.sh.xstep; a.ystep = op.sh.ystep; a.zstep = op.sh.zstep; a.zlen = op.sh.zlen;
         a.err = &h->st->kerr;
-        if (h->dim == 3 && kkind == K_SWEEP && op.sh.rpw > 0) {  // TMA boxes: TY+2 rows of the swept vector, TY rows of g
+        if (h->dim == 3 && kkind == K_SWEEP && op.sh.rpw > 0 && !h->describe_only) {  // TMA boxes: TY+2 rows of the swept vector, TY rows of g
             op.has_maps = true;
             const int rows = op.sh.ty * op.sh.rpw;
             // the one-pass pre-smoothing + restriction reads g boxes of TY+4 rows
@@ -381,7 +381,7 @@ struct Gen {
         const int L = h->nlev - 1;
         if (l == L && top_from_r && !h->g_alias_r)  // Alg. 2 line 4: g_L = cast(r / alpha)
             out->push_back(kernel(L, K_SCALE, 0, nullptr, h->lv[L].g, nullptr));
-        if (l == h->tail_level && h->tail_prog) {
+        if (l == h->tail_level && (h->tail_prog || h->describe_only)) {
             Op op{};
             op.kind = OP_TAIL;
             op.level = l;
@@ -775,6 +775,41 @@ extern "C" size_t mg_footprint_bytes(const mg_params* p) {
     mgi_hier h;
     if (plan_hier(p, h, false) != MG_OK) return 0;
     return h.footprint;
+}
+
+extern "C" mg_status mg_describe_cycle(const mg_params* p, int* rec, int cap, int* count) {
+    if (!count || cap < 0 || (cap > 0 && !rec)) FAIL(MG_ERR_INVALID, "count is NULL or rec / cap inconsistent");
+    *count = 0;
+    mgi_hier h;
+    const mg_status st = plan_hier(p, h, false);
+    if (st != MG_OK) return st;
+    h.describe_only = true;
+    DevState dummy{};  // stands in for the device state (its address is recorded, never read)
+    h.st = &dummy;
+    std::vector<Op> ops;
+    mgi_build_cycle(h, ops, true, 0, nullptr);
+    int n = 0;
+    auto put = [&](int kind, int level, int kkind, int mode, int prec, int prec_c) {
+        if (n < cap) {
+            int* r = rec + 6 * (size_t)n;
+            r[0] = kind; r[1] = level; r[2] = kkind; r[3] = mode; r[4] = prec; r[5] = prec_c;
+        }
+        ++n;
+    };
+    for (const Op& op : ops) {
+        put(op.kind, op.level, op.kind == OP_KERNEL ? op.kkind : -1, op.kind == OP_COARSE ? h.p.base_solver : op.mode,
+            op.prec, op.prec_c);
+        if (op.kind != OP_TAIL) continue;
+        for (int k = op.prog_off; k < op.prog_off + op.prog_len; ++k) {
+            const TailOp& t = h.tail_host[k];
+            int level = -1;
+            for (int l = 0; l < h.nlev; ++l)
+                if (h.lv[l].geo.n == t.n) level = l;
+            put(100 + t.kind, level, -1, t.mode, t.prec, t.prec_c);
+        }
+    }
+    *count = n;
+    return MG_OK;
 }
 
 extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, mg_hierarchy** out) {

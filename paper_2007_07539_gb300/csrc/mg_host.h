@@ -88,6 +88,7 @@ struct mgi_hier {
     std::vector<TailOp> tail_host;         // tail programs (all visits), mirrored on the device
     size_t step_tail_ops = 0;              // tail stages of the IR step (stage calls append after)
     TailOp* tail_prog = nullptr;           // device copy (capacity kTailMaxOps)
+    bool describe_only = false;            // host-only schedule (mg_describe_cycle): no device objects
     int tail_soff[MG_MAX_LEVELS][3] = {};  // shared-memory byte offsets of c, t, g of tail levels
     int tail_rscr = 0;                     // shared-memory byte offset of the tail's residual scratch
     size_t tail_smem = 0;                  // dynamic shared memory of the tail kernel

@@ -31,7 +31,7 @@ VEC_C, VEC_G, VEC_T, VEC_U, VEC_R = range(5)
 EXPORTS = ["mg_params_init", "mg_level_count", "mg_last_error", "mg_footprint_bytes",
            "mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
            "mg_serve_configure", "mg_solve_batch", "mg_profile_solve", "mg_level_write", "mg_level_read",
-           "mg_level_info_get", "mg_run_stage", "mg_residual_norms_noalloc", "mg_axpy"]
+           "mg_level_info_get", "mg_run_stage", "mg_residual_norms_noalloc", "mg_axpy", "mg_describe_cycle"]
 
 
 class Params(ctypes.Structure):
@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
             L.mg_last_error.restype = ctypes.c_char_p
             L.mg_footprint_bytes.argtypes = [P]
             L.mg_footprint_bytes.restype = ctypes.c_size_t
+            L.mg_describe_cycle.argtypes = [P, ctypes.POINTER(i32), i32, ctypes.POINTER(i32)]
             L.mg_create_hierarchy.argtypes = [P, vp, ctypes.POINTER(H)]
             L.mg_solve.argtypes = [H, vp, vp, R]
             L.mg_submit.argtypes = [H, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -207,6 +208,19 @@ def make_params(dim: int, n: int, ladder_name: str | list[int] = "D", **kw) -> P
 
 def footprint_bytes(p: Params) -> int:
     return int(lib().mg_footprint_bytes(ctypes.byref(p)))
+
+
+CYCLE_FIELDS = ("kind", "level", "kernel", "mode", "prec", "prec_c")
+
+
+def describe_cycle(p: Params) -> list[dict]:
+    """The operations of one IR step's cycle as the library schedules them
+    (mg_describe_cycle; no device needed): one dict per record."""
+    cnt = ctypes.c_int32(0)
+    _check(lib().mg_describe_cycle(ctypes.byref(p), None, 0, ctypes.byref(cnt)), "mg_describe_cycle")
+    buf = (ctypes.c_int32 * (6 * max(cnt.value, 1)))()
+    _check(lib().mg_describe_cycle(ctypes.byref(p), buf, cnt.value, ctypes.byref(cnt)), "mg_describe_cycle")
+    return [dict(zip(CYCLE_FIELDS, buf[6 * k: 6 * k + 6])) for k in range(cnt.value)]
 
 
 def _ptr(x) -> int:
