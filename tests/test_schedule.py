@@ -83,6 +83,28 @@ def test_cycle_follows_alg1(dim, n, lad, gamma, nu, no_tail):
     assert not any(r["kind"] == KERNEL and r["kernel"] == K_UPDATE for r in recs)
 
 
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_one_pass_presmoothing_replaces_first_visits(gamma):
+    """fuse_pre = 1 (3D, nu1 = 2): each first visit runs the two sweeps from zero and the
+    residual-restriction as one pass (mode 4); later visits keep Jacobi sweeps and a
+    separate residual-restriction.  Everything else is unchanged."""
+    dim, n, nu = 3, 63, 2
+    nlev = len(mg.level_count(n))
+    L = nlev - 1
+    recs = describe(dim, n, "H", gamma=gamma, fuse_pre=1, no_tail=1)
+    c = Counter()
+    for r in recs:
+        if r["kind"] == KERNEL and r["kernel"] == K_SWEEP:
+            c[(r["mode"], r["level"])] += 1
+    for l in range(1, L + 1):
+        visits = gamma ** (L - l)
+        first = 1 if l == L else gamma ** (L - l - 1)
+        assert c[(4, l)] == first
+        assert c[(M_ZERO2, l)] == 0
+        assert c[(M_RESTRICT, l)] == visits - first
+        assert c[(M_JACOBI, l)] == (visits - first) * nu + visits * nu
+
+
 def test_fp64_finest_without_scaling_reads_the_residual():
     """D_MG with no scaling: the finest g is the FP64 residual itself, no scale-and-cast."""
     recs = describe(3, 31, "D", scaling=0)
