@@ -626,7 +626,7 @@ double or_norminf(size_t N, const double *v) {
  */
 /* x truncated toward zero to binary32 precision (0 below its normal range,
    infinity at and above 2^128): the low 29 of FP64's 52 fraction bits cleared */
-static double trunc_f32(double x) {
+double or_trunc_f32(double x) {
     if (!isfinite(x)) return x;
     const double a = fabs(x);
     if (a < ldexp(1.0, -126)) return copysign(0.0, x);
@@ -635,6 +635,22 @@ static double trunc_f32(double x) {
     const double f = frexp(a, &E);                 /* a = f 2^E, f in [1/2, 1) */
     const double m = floor(ldexp(f, 24));          /* the 24 leading significand bits */
     return copysign(ldexp(m, E - 24), x);
+}
+
+/* Scale-ahead cast of the emulation (reading R21 of Alg. 2 line 4): g =
+   cast_fmt(trunc_f32(r inv)).  Returns 1 when some truncated value lies at or
+   beyond the format's overflow threshold (it would round to infinity: 65520
+   for FP16, the midpoint above FP16's largest finite value; 3.0e38 as a bound
+   below BF16's / FP32's, above any value reached), else 0.  g is written either way. */
+int or_scale_ahead_cast(int fmt, size_t N, const double *r, double inv, double *g) {
+    const double lim = fmt == OR_FP16 ? 65520.0 : 3.0e38;
+    int over = 0;
+    for (size_t p = 0; p < N; ++p) {
+        const double t = or_trunc_f32(r[p] * inv);
+        over |= !(fabs(t) < lim);
+        g[p] = or_round(fmt, t);
+    }
+    return over;
 }
 
 int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, double *history) {
@@ -692,14 +708,7 @@ int or_ir_solve(const or_params *P, const double *b, double *u, or_result *res, 
         if (ahead_on && ahead && inv_pred > 0.0) {
             /* scale-ahead: g = cast(trunc_f32(r inv_pred)) unless a value is
                beyond the format's range, then the scale above */
-            const double lim = fL == OR_FP16 ? 65520.0 : 3.0e38;
-            int over = 0;
-            for (size_t p = 0; p < N; ++p) {
-                const double t = trunc_f32(r[p] * inv_pred);
-                over |= !(fabs(t) < lim);
-                g[p] = or_round(fL, t);
-            }
-            if (!over) { inv = inv_pred; alpha = 1.0 / inv_pred; done = 1; }
+            if (!or_scale_ahead_cast(fL, N, r, inv_pred, g)) { inv = inv_pred; alpha = 1.0 / inv_pred; done = 1; }
         }
         if (ahead_on) {
             int e;

@@ -83,6 +83,10 @@ def _load():
             lib.or_round.argtypes = [i, d]
             lib.or_round.restype = d
             lib.or_round_array.argtypes = [i, ctypes.c_size_t, _D, _D]
+            lib.or_trunc_f32.argtypes = [d]
+            lib.or_trunc_f32.restype = d
+            lib.or_scale_ahead_cast.argtypes = [i, ctypes.c_size_t, _D, d, _D]
+            lib.or_scale_ahead_cast.restype = i
             _lib = lib
     return _lib
 
@@ -194,6 +198,28 @@ def round_to(fmt: int, x) -> np.ndarray:
     y = np.empty_like(x)
     _load().or_round_array(int(fmt), x.size, _p(x), _p(y))
     return y.reshape(shape)
+
+
+def trunc_f32(x) -> np.ndarray:
+    """x truncated toward zero to FP32 precision (0 below 2^-126, infinity at and
+    above 2^128): the truncation of the emulated scale-ahead cast (reading R21)."""
+    shape = np.shape(x)
+    x = _f64(x).reshape(-1)
+    f = _load().or_trunc_f32
+    return np.array([f(float(v)) for v in x]).reshape(shape)
+
+
+def scale_ahead_cast(fmt: int, r, inv: float):
+    """The emulated scale-ahead cast g = round_fmt(trunc_f32(r inv)) (reading R21
+    of Alg. 2 line 4).  Returns (g, over): over is True when a truncated value
+    reaches the format's overflow threshold (the step then falls back to the
+    plain scale-and-cast)."""
+    r = _f64(r)
+    shape = r.shape
+    r = r.reshape(-1)
+    g = np.empty_like(r)
+    over = _load().or_scale_ahead_cast(int(fmt), r.size, _p(r), float(inv), _p(g))
+    return g.reshape(shape), bool(over)
 
 
 def make_params(dim: int, n: int, *, levels: int = 0, nu1: int = 2, nu2: int = 2,

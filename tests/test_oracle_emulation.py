@@ -331,3 +331,74 @@ def test_one_rounding_check_separates_fp32_arithmetic_from_an_extra_rounding(ora
     twice = to_storage((1 - om) * c + to_storage(part.astype(np.float64), prec)[1], prec)[1]
     with pytest.raises(AssertionError):
         check_rounded(oracle, twice, ref, mag, prec, "extra rounding")
+
+
+# ----------------------------------------------------------------------------- scale-ahead truncation
+def _trunc_f32_numpy(x):
+    """Truncation toward zero to binary32 built from numpy's round-to-nearest
+    conversion: a result larger in magnitude than x steps one float32 spacing back
+    toward zero; results below the least normal 2^-126 flush to zero (FTZ, as
+    the truncation from the bit pattern does), |x| >= 2^128 gives infinity."""
+    x = np.asarray(x, dtype=np.float64)
+    with np.errstate(over="ignore"):
+        f = x.astype(np.float32)
+    up = np.abs(f.astype(np.float64)) > np.abs(x)
+    f = np.where(up, np.nextafter(f, np.float32(0)), f).astype(np.float64)
+    f = np.where(np.abs(f) < 2.0**-126, np.copysign(0.0, x), f)
+    f = np.where(np.abs(x) >= 2.0**128, np.copysign(np.inf, x), f)
+    return np.where(np.isnan(x), x, f)
+
+
+def test_trunc_f32_matches_numpy_round_toward_zero(oracle):
+    """The FP32 truncation of the emulated scale-ahead cast (reading R21) against
+    numpy: random values over binary32's whole range and beyond, exact binary32
+    values (unchanged), exact midpoints between neighbouring binary32 values (the
+    lower magnitude wins, unlike round-to-nearest) and their FP64 neighbours,
+    the underflow edge 2^-126 and the overflow edge 2^128."""
+    rng = np.random.default_rng(11)
+    f32 = _samples(12, 4000, -125, 127).astype(np.float32)
+    nxt = np.nextafter(f32, np.float32(np.inf) * np.sign(f32))
+    mid = (f32.astype(np.float64) + nxt.astype(np.float64)) / 2  # exact in FP64
+    edges = [2.0**-126, np.nextafter(2.0**-126, 0), 2.0**-126 * (1 + 2.0**-30), 2.0**-149, 2.0**-127,
+             2.0**128, np.nextafter(2.0**128, 0), 2.0**128 - 2.0**103, np.nextafter(2.0**128 - 2.0**103, 0),
+             float(np.finfo(np.float32).max), 65520.0, np.nextafter(65520.0, 0), 1.0, 1 + 2.0**-24, 0.0]
+    x = np.concatenate([_samples(13, 20000, -140, 130), f32.astype(np.float64), mid,
+                        np.nextafter(mid, 0), np.nextafter(mid, np.inf), edges, -np.asarray(edges),
+                        rng.uniform(-1, 1, 1000)])
+    got = oracle.trunc_f32(x)
+    want = _trunc_f32_numpy(x)
+    bad = np.flatnonzero(~((got == want) & (np.signbit(got) == np.signbit(want))))
+    assert bad.size == 0, (x[bad[:5]], got[bad[:5]], want[bad[:5]])
+    # every midpoint goes to the neighbour of smaller magnitude
+    assert np.array_equal(oracle.trunc_f32(mid), np.where(np.abs(f32) < np.abs(nxt), f32, nxt).astype(np.float64))
+    assert oracle.trunc_f32(np.array([np.inf, -np.inf])).tolist() == [np.inf, -np.inf]
+    assert np.isnan(oracle.trunc_f32(np.array([np.nan])))[0]
+
+
+def test_scale_ahead_cast_overflow_flag(oracle):
+    """The fallback flag of the emulated scale-ahead cast: for FP16 it is set exactly
+    when a truncated value rounds to infinity in FP16 (numpy's conversion), i.e. at
+    65520 and above; BF16 and FP32 flag values from 3.0e38, below their overflow
+    thresholds.  The cast values are round(trunc(r inv)) in every case."""
+    rng = np.random.default_rng(21)
+    inv = 2.0**14
+    base = rng.uniform(-1, 1, 4096)
+    for t in (65504.0, np.nextafter(65520.0, 0), 65519.99, 65520.0, 65535.0, 70000.0):
+        for sign in (1.0, -1.0):
+            r = base.copy()
+            r[17] = sign * t / inv
+            g, over = oracle.scale_ahead_cast(oracle.FP16, r, inv)
+            tr = _trunc_f32_numpy(r * inv)
+            with np.errstate(over="ignore"):
+                g16 = tr.astype(np.float16).astype(np.float64)
+            assert over == bool(np.isinf(g16).any()), (t, over)
+            assert np.array_equal(g, g16)
+    g, over = oracle.scale_ahead_cast(oracle.FP16, base, inv)
+    assert not over and np.max(np.abs(g)) <= 2.0**14
+    for fmt in (oracle.BF16, oracle.FP32):
+        for t, want in ((2.9e38, False), (np.nextafter(3.0e38, 0), False), (3.0e38 * (1 + 2.0**-20), True), (3.5e38, True)):
+            r = base.copy()
+            r[5] = t / 2.0**100
+            g, over = oracle.scale_ahead_cast(fmt, r, 2.0**100)
+            assert over == want, (fmt, t)
+            assert np.array_equal(g, oracle.round_to(fmt, _trunc_f32_numpy(r * 2.0**100)))
