@@ -17,7 +17,10 @@
 // on the GPU (e.g. issued on different streams) race on the array and give
 // wrong norms: serialise them.  The first call on a device looks up the
 // array's device address (cudaGetSymbolAddress) with that device current; make
-// that first call before any stream capture is active.
+// that first call before any stream capture is active.  The address is kept
+// per device together with the identity of the CUDA context it belongs to:
+// after cudaDeviceReset (a new primary context) the next call on that device
+// looks the address up again, so it too should come before any capture.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,6 +28,7 @@
 
 #include "mg_device.cuh"
 #include "mg_host.h"
+#include "mg_noalloc.h"
 
 namespace {
 
@@ -37,6 +41,7 @@ static __device__ __align__(256) double g_norm_scratch[kMaxBlocks * 4];
 
 std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context identity the address belongs to (0: none)
 
 // Per-CTA partials of a fixed block of kPointsPerBlock points (contiguous
 // layout, explicit boundary checks): {sum r^2, max |r| key, sum b^2, 0}.
@@ -130,13 +135,41 @@ __global__ void __launch_bounds__(1024) k_resnorm_final(const double* __restrict
     }
 }
 
-bool on_device(const void* p) {
+// mgi::noalloc_ptr_class of a pointer on the current device `dev`
+int ptr_class(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 1;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return mgi::noalloc_ptr_class((int)a.type, a.device, dev);
+}
+
+// Unique identity of the calling thread's current CUDA context (cuCtxGetId,
+// fetched through the runtime's driver entry point; never reused within the
+// process), 0 if unavailable.
+unsigned long long current_ctx_id() {
+    using GetCur = int (*)(void**);
+    using GetId = int (*)(void*, unsigned long long*);
+    static GetCur get_cur = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<GetCur>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
 }
 
 }  // namespace
@@ -153,20 +186,31 @@ extern "C" mg_status mg_residual_norms_noalloc(int32_t dim, int32_t n, const dou
                       std::to_string((long long)kMaxBlocks * kPointsPerBlock) + " points");
         return MG_ERR_INVALID;
     }
-    if (!on_device(b) || !on_device(u) || !on_device(norms)) {
-        mgi_set_error("b, u and norms must be device pointers");
-        return MG_ERR_INVALID;
-    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess) {
         mgi_set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
         return MG_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        mgi_set_error("device ordinal " + std::to_string(dev) + " is beyond the " + std::to_string(kMaxDevices) +
+                      " devices this entry point keeps scratch addresses for");
+        return MG_ERR_INVALID;
+    }
+    const void* ptrs[3] = {b, u, norms};
+    for (const void* q : ptrs) {
+        const int c = ptr_class(q, dev);
+        if (c == 1) { mgi_set_error("b, u and norms must be device (or managed) pointers"); return MG_ERR_INVALID; }
+        if (c == 2) {
+            mgi_set_error("b, u and norms must be memory of the current device " + std::to_string(dev));
+            return MG_ERR_INVALID;
+        }
     }
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_addr[dev]) {  // once per device, with that device current
+        const unsigned long long ctx = current_ctx_id();
+        if (!g_scratch_addr[dev] || ctx != g_scratch_ctx[dev]) {  // once per device (and context), that device current
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_norm_scratch);
             if (e != cudaSuccess) {
@@ -174,6 +218,7 @@ extern "C" mg_status mg_residual_norms_noalloc(int32_t dim, int32_t n, const dou
                 return MG_ERR_CUDA;
             }
             g_scratch_addr[dev] = static_cast<double*>(p);
+            g_scratch_ctx[dev] = ctx;
         }
         scratch = g_scratch_addr[dev];
     }

@@ -22,6 +22,7 @@ CUDA_INC = "/usr/local/cuda/include"
 
 PROGRAM = r'''
 #include "mg_tail.h"
+#include "mg_noalloc.h"
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -53,6 +54,13 @@ int main(int argc, char** argv) {
             const mgi::Geom g = mgi::make_geom(dim, n);
             std::printf("%d %d %lld %lld %lld\n", n, g.P, g.S, g.base, g.total);
         }
+        return 0;
+    }
+    if (argc == 2 && !std::strcmp(argv[1], "ptrclass")) {  // type device current -> class, every combination
+        for (int type = 0; type < 4; ++type)
+            for (int dev = 0; dev < 3; ++dev)
+                for (int cur = 0; cur < 3; ++cur)
+                    std::printf("%d %d %d %d\n", type, dev, cur, mgi::noalloc_ptr_class(type, dev, cur));
         return 0;
     }
     return 2;
@@ -126,3 +134,17 @@ def test_padded_layout(hostprog, dim):
         lo = base - P - (S if dim == 3 else 0) - 1 - 8
         hi = base + n * P + (n * S if dim == 3 else 0) + (P - 1) + 8
         assert lo >= 0 and hi < total, (n, P, base, total)
+
+
+def test_noalloc_pointer_checks(hostprog):
+    """mg_residual_norms_noalloc's pointer check, on the fields of
+    cudaPointerAttributes without a device: memory of the current device and
+    managed memory pass; host or unregistered memory is rejected (class 1);
+    another device's memory is rejected (class 2) -- the kernels could not
+    read it without peer access, which a one-GPU test cannot set up."""
+    rows = [list(map(int, ln.split())) for ln in
+            subprocess.check_output([hostprog, "ptrclass"], text=True).splitlines()]
+    assert len(rows) == 36
+    for typ, dev, cur, cls in rows:
+        want = 0 if typ == 3 else (1 if typ in (0, 1) else (0 if dev == cur else 2))
+        assert cls == want, (typ, dev, cur, cls)
