@@ -112,29 +112,44 @@ def oracle_iters(name: str) -> int:
         return int(json.load(f)[name]["iters"])
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_oracle_sample(b, steps: int = 1, op: int = 0):
-    """The FP64 oracle on the same 255^3 workload, bounded: solves with max_iter = 0
-    (initial and final residual) and max_iter = 1 are timed; the per-step cost is their
-    difference and DOF/s to 1e-10 is extrapolated with the oracle's own iteration count
-    for this workload (tests/golden/oracle_solves.json, written by the oracle)."""
+    """The FP64 oracle, as it stands, on the same 255^3 workload: one complete solve to
+    relative residual 1e-10 (about 5 s on 16 host cores), timed; DOF/s = n^3 / time."""
     from oracle import oracle as O
     O.build()
     cores = os.cpu_count() or 1
-    iters = oracle_iters(GOLDEN_KEY[op])
-    t0s, t1s = [], []
+    ts, iters = [], None
     for _ in range(steps):
         t = time.perf_counter()
-        O.ir_solve(b, max_iter=0, nthreads=cores, op=op)
-        t0s.append(time.perf_counter() - t)
-        t = time.perf_counter()
-        O.ir_solve(b, max_iter=1, nthreads=cores, op=op)
-        t1s.append(time.perf_counter() - t)
-    t0, t1 = min(t0s), min(t1s)
-    t_solve = t0 + iters * max(t1 - t0, 0.0)
+        _, info, _ = O.ir_solve(b, nthreads=cores, op=op)
+        ts.append(time.perf_counter() - t)
+        iters = info["iters"]
+        if not info["converged"]:
+            raise RuntimeError(f"oracle solve did not converge: {info}")
+    t_solve = min(ts)
     dofs = b.size / t_solve
-    sample = (f"oracle FP64 IR on the 255^3 workload, {cores} threads: solves with 0 and 1 IR steps timed "
-              f"({t0:.2f} s, {t1:.2f} s), extrapolated to the oracle's {iters} steps ({t_solve:.1f} s per solve)")
-    return dofs, cores, sample, t0 + t1
+    sample = (f"one complete FP64 oracle solve of the 255^3 workload ({iters} IR steps to 1e-10) on "
+              f"{cores} threads of {cpu_model()}: {t_solve:.2f} s")
+    return dofs, cores, sample, t_solve
 
 
 def reference_arm(args):
@@ -158,7 +173,8 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(walls), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD.replace("H_MG", "reference: FP64 CPU oracle of the same method; H_MG")},
-            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -329,54 +345,87 @@ def extra_workloads(mg, I, torch, flush, quick=False):
                          "launches_per_solve": rb[0]["launches"],
                          "max_iters": max(r["iters"] for r in rb)}
 
-    # ---- serving stream
-    reqs = I.serving_workload(count=24 if quick else 64)
-    pool = {}
-
-    def hier(d, nn, lad):
-        key = (d, nn, lad)
-        if key not in pool:
-            pool[key] = mg.Hierarchy(mg.make_params(d, nn, lad, zero_guess=1))
-        return pool[key]
-
-    bufs = [(torch.from_numpy(I.random_rhs(q["dim"], q["n"], q["seed"])).cuda(),) for q in reqs]
-    t_fp16 = t_fp64 = 0.0
-    for q, (bb,) in zip(reqs, bufs):  # serial FP16 and FP64 references of the same stream
+    # ---- serving stream: Poisson arrivals of 2D / 3D requests.  The server keeps up to
+    # four pooled hierarchies per request shape (plans and graphs resident; working arenas
+    # from the device-memory pool per request, cached while memory allows); a request goes
+    # to its shape's hierarchies in turn and queues behind a busy one.  The pool's budget
+    # bounds the working memory of everything admitted.
+    reqs = I.serving_workload(count=48 if quick else 512)
+    shapes = sorted({(q["dim"], q["n"]) for q in reqs})
+    t16, t64 = {}, {}
+    for d, nn in shapes:  # serial references per request shape (median of the shape's solves)
+        bb = torch.from_numpy(I.random_rhs(d, nn, 5000)).cuda()
         uu = torch.zeros_like(bb)
-        t_fp16 += solve_ms(hier(q["dim"], q["n"], "HS"), bb, uu, 1)[0]
-        t_fp64 += solve_ms(hier(q["dim"], q["n"], "D"), bb, uu, 1)[0]
+        with mg.Hierarchy(mg.make_params(d, nn, "HS", zero_guess=1)) as h:
+            solve_ms(h, bb, uu, 1)
+            t16[(d, nn)] = solve_ms(h, bb, uu, 3)[0]
+        with mg.Hierarchy(mg.make_params(d, nn, "D", zero_guess=1, scaling=0)) as h:
+            solve_ms(h, bb, uu, 1)
+            t64[(d, nn)] = solve_ms(h, bb, uu, 1)[0]
+        del bb, uu
+    t_fp16 = sum(t16[(q["dim"], q["n"])] for q in reqs)
+    t_fp64 = sum(t64[(q["dim"], q["n"])] for q in reqs)
     rate = 0.8 * len(reqs) / (t_fp16 * 1e-3)
-    # arrivals: the workload's exponential gaps rescaled to this rate
-    mean_gap = reqs[-1]["arrival_s"] / len(reqs)
+    mean_gap = reqs[-1]["arrival_s"] / len(reqs)  # the workload's exponential gaps rescaled to this rate
     arr = [q["arrival_s"] / (mean_gap * rate) for q in reqs]
-    # one resident hierarchy per request (a request for a busy hierarchy queues behind it)
-    served = [mg.Hierarchy(mg.make_params(q["dim"], q["n"], "HS", zero_guess=1)) for q in reqs]
-    us = [torch.zeros_like(bb) for (bb,) in bufs]
-    mg.serve_configure(0, 16)
+    budget = 4 << 30
+    mg.serve_configure(budget, 16)
+    per_shape = 4
+    pool_h = {sh: [mg.Hierarchy(mg.make_params(sh[0], sh[1], "HS", zero_guess=1, pooled=1))
+                   for _ in range(per_shape)] for sh in shapes}
+    turn = {sh: 0 for sh in shapes}
+    served = []
+    for q in reqs:
+        sh = (q["dim"], q["n"])
+        served.append(pool_h[sh][turn[sh] % per_shape])
+        turn[sh] += 1
+    bufs = [torch.from_numpy(I.random_rhs(q["dim"], q["n"], q["seed"])).cuda() for q in reqs]
+    us = [torch.zeros_like(bb) for bb in bufs]
+    for sh, hl in pool_h.items():  # warm-up: one solve per hierarchy builds its graph
+        bb = torch.from_numpy(I.random_rhs(sh[0], sh[1], 1)).cuda()
+        for h in hl:
+            h.solve(bb, torch.zeros_like(bb))
+        del bb
     torch.cuda.synchronize()
+    st0 = mg.serve_stats()
     t0 = time.perf_counter()
-    pending, lat = {}, []
+    pending, lat, statuses = {}, [], []
     i = 0
     while i < len(reqs) or pending:
         now = time.perf_counter() - t0
         while i < len(reqs) and arr[i] <= now:
-            pending[i] = served[i].submit(bufs[i][0], us[i])
+            pending[i] = served[i].submit(bufs[i], us[i])
             i += 1
         for j in list(pending):
             r = served[j].poll(pending[j])
             if r is not None:
                 lat.append(time.perf_counter() - t0 - arr[j])
+                statuses.append(r["status"])
                 del pending[j]
         time.sleep(0.0002)
     t_s = time.perf_counter() - t0
+    st1 = mg.serve_stats()
     dof_s = sum(q["n"] ** q["dim"] for q in reqs)
     lat_ms = sorted(1e3 * x for x in lat)
     out["serving"] = {"requests": len(reqs), "ladder": "FP16 fine / FP32 coarse (HS)", "rate_per_s": rate,
                       "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-                      "served_dofs": dof_s / t_s, "serial_fp16_device_ms": t_fp16,
-                      "serial_fp64_device_ms": t_fp64, "serial_fp64_dofs": dof_s / (t_fp64 * 1e-3)}
-    for h in served + list(pool.values()):
-        h.close()
+                      "served_dofs": dof_s / t_s, "wall_s": t_s, "all_ok": all(x == 0 for x in statuses),
+                      "serial_fp16_device_ms": t_fp16, "serial_fp64_device_ms": t_fp64,
+                      "serial_fp64_dofs": dof_s / (t_fp64 * 1e-3),
+                      "serial_times": "per request shape, median of 3 FP16 / 1 FP64 device-timed solves, summed over the stream",
+                      "pool_budget_bytes": budget, "pool_peak_reserved_bytes": st1["peak_reserved_bytes"],
+                      "pool_peak_in_use_bytes": st1["peak_in_use_bytes"],
+                      "requests_that_waited_for_memory": st1["memory_waits"] - st0["memory_waits"],
+                      "arena_reuses": st1["arena_reuses"] - st0["arena_reuses"],
+                      "arena_evictions": st1["arena_evictions"] - st0["arena_evictions"],
+                      "peak_inflight": st1["peak_inflight"], "hierarchies": per_shape * len(shapes),
+                      "shapes": len(shapes)}
+    for hl in pool_h.values():
+        for h in hl:
+            h.close()
+    del served, pool_h, bufs, us
+    mg.serve_configure(0, 16)
+    torch.cuda.empty_cache()
 
     # ---- vector bandwidth versus size (Sec. 8.2, Fig. 6): y <- a x + y, 3 bytes-moved
     # vectors per value (read x, read y, write y), event-timed on torch's stream
@@ -524,6 +573,14 @@ def main():
     sweep_ms = sum(k["total_ms"] for k in sweeps)
     byshare = sorted(ktimes, key=lambda k: -k["total_ms"])[:8]
 
+    def finest_frac(kind, mode=None):
+        """Algorithmic GB/s of a finest-level kernel over the measured peak (CUDA events)."""
+        ks = [k for k in ktimes if k["level"] == finest and k["kind"] == kind and (mode is None or k["mode"] == mode)]
+        ms = sum(k["total_ms"] for k in ks)
+        if not ks or ms <= 0:
+            return None
+        return round(sum(k["bytes"] * k["launches"] for k in ks) / (ms * 1e-3) / 1e9 / peak, 3)
+
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
@@ -538,6 +595,9 @@ def main():
                    "b and u (133 MB each) exceed the 129 MB L2", "wall_s_timed_region": wall,
                    "parallelism": f"{world} independent instance(s), one per GPU, no collective on the data path",
                    "tile_shapes": "autotuned at creation" if tune else "wave model",
+                   "hbm_frac_finest_jacobi": finest_frac(0, 0), "hbm_frac_finest_zero_start": finest_frac(0, 1),
+                   "hbm_frac_finest_residual_restrict": finest_frac(0, 3), "hbm_frac_finest_prolong": finest_frac(2),
+                   "hbm_frac_ir_update": finest_frac(5),
                    "finest_sweeps_gbs": sweep_bytes / (sweep_ms * 1e-3) / 1e9 if sweep_ms else None,
                    "kernel_shares": [{"kernel": f"{k['name']}@L{k['level']}", "ms": round(k["total_ms"], 4),
                                       "share": round(k["total_ms"] / tot_ms, 4),
@@ -554,10 +614,20 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras and args.op == 0:
         hH.close()
         hD.close()
-        line["config"]["extras"] = extra_workloads(mg, I, torch, flush)
+        ex = extra_workloads(mg, I, torch, flush)
+        # the headline secondary figures as short top-level keys (the full records follow in extras)
+        c, e5 = line["config"], ex["n511_manufactured"]
+        c.update({"n511_hsd_ms": e5["hsd_ms"], "n511_fp64_ms": e5["fp64_mg_ms"],
+                  "n511_speedup": e5["speedup_vs_fp64_mg"], "n511_iters": e5["hsd_iters"],
+                  "n511_fp64_iters": e5["fp64_mg_iters"], "n511_oracle_iters": oracle_iters("3d_n511_manufactured"),
+                  "batched_dofs": ex["batched_64"]["batch_dofs"],
+                  "serving_p50_ms": ex["serving"]["p50_ms"], "serving_p99_ms": ex["serving"]["p99_ms"],
+                  "serving_dofs": ex["serving"]["served_dofs"]})
+        c["extras"] = ex
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, _ = cpu_oracle_sample(b, 1, args.op)
-        line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": sample,
+                                "cpu_model": cpu_model()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     hH.close()

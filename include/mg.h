@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define MG_ABI_VERSION 1
+#define MG_ABI_VERSION 2
 #define MG_MAX_LEVELS 16
 
 /* Storage precision of one multigrid level (Table 2, Fig. 1).  Arithmetic
@@ -141,7 +141,23 @@ typedef struct mg_params {
                            values would overflow the storage type, that step falls back to
                            the scale-and-cast with alpha = ||r||_inf.  0: always
                            alpha = ||r||_inf and the separate pass */
-    int32_t reserved[1];/* must be 0 */
+    int32_t wait_polls; /* bound on each wait of the 3D stencil kernels for their TMA tile copies,
+                           in polls of the copy barrier (each poll may suspend the thread for a
+                           short hardware-chosen time): -1 (default) about a second in all;
+                           >= 0 that many polls (a diagnostic for the timeout path: 0 gives up at
+                           once, while the copies still land).  A wait that gives up stops the
+                           solve with MG_ERR_TIMEOUT; the kernel first waits, with the default
+                           bound, for every copy it issued, so none is in flight at its exit,
+                           and later solves are unaffected */
+    int32_t pooled;     /* 0 (default): the hierarchy allocates its working arena (the level
+                           vectors and the FP64 u and r, nearly all of mg_footprint_bytes) at
+                           creation and holds it until mg_destroy.  1: the hierarchy holds
+                           only its plan and small control state; the arena is taken from the
+                           library's device-memory pool when a solve is admitted (mg_submit)
+                           or started (mg_solve, mg_solve_batch) and handed back to the pool
+                           when it completes, so idle hierarchies hold no working memory and
+                           the serving budget bounds the memory in use (mg_serve_configure) */
+    int32_t reserved[4];/* must be 0 */
 } mg_params;
 
 /* Outcome of one solve. */
@@ -225,21 +241,33 @@ mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, mg_hierarch
 /* Solves A u = b (Alg. 2).  b: n^d FP64 values, read only.  u: n^d FP64
  * values, in: initial guess (ignored when zero_guess = 1), out: solution.
  * Blocks until the solve has finished.  Returns the solve status (also in
- * res->status): MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_NUMERIC, or a CUDA error.
+ * res->status): MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_NUMERIC, MG_ERR_TIMEOUT
+ * (a stencil kernel's bounded wait for its tile copies gave up; see
+ * mg_params.wait_polls), MG_ERR_OOM (staging or, for a pooled hierarchy, its
+ * arena could not be allocated) or a CUDA error.
  * On a failed solve u holds the last iterate.  res may be NULL. */
 mg_status mg_solve(mg_hierarchy* h, const double* b, double* u, mg_result* res);
 
-/* Queues a solve of A u = b on hierarchy h and returns at once with a ticket.
- * Requests are admitted to the device by a memory budget (see
- * mg_serve_configure); admitted requests run concurrently with other
- * requests of other hierarchies and with new arrivals.  b and u must stay
- * valid until mg_poll reports completion.  Errors: MG_ERR_INVALID,
- * MG_ERR_ADMISSION (the request's footprint exceeds the whole budget). */
+/* Queues a solve of A u = b on hierarchy h and returns at once with a ticket
+ * (the serving workload: requests of different sizes arriving over time).  A
+ * background worker admits queued requests in arrival order when a slot is
+ * free (mg_serve_configure), the hierarchy has no other request running and,
+ * for a pooled hierarchy (mg_params.pooled = 1), its working arena fits the
+ * device-memory pool's budget now: the arena is then taken from the pool, and
+ * returned to it when the request completes.  Requests that do not fit wait;
+ * a later request may pass a waiting one at most 8 times.  Admitted requests
+ * run concurrently, each as one CUDA graph on its hierarchy's stream, with
+ * the requests already running and with new arrivals.  A resident hierarchy
+ * (pooled = 0) holds its arena outside the pool and is admitted by slots
+ * alone.  b and u must stay valid until mg_poll reports completion.  Errors:
+ * MG_ERR_INVALID, MG_ERR_ADMISSION (a pooled hierarchy's working arena
+ * exceeds the whole budget, so it can never be admitted). */
 mg_status mg_submit(mg_hierarchy* h, const double* b, double* u, uint64_t* ticket);
 
 /* Completion test for a ticket of mg_submit: MG_BUSY while queued or running;
- * otherwise the solve's status, with the result in *res (may be NULL).  A
- * completed ticket may be polled again until mg_destroy. */
+ * otherwise the solve's status, with the result in *res (may be NULL).  The
+ * poll that reports completion retires the ticket: polling it again returns
+ * MG_ERR_INVALID (unknown ticket), and the engine keeps no finished requests. */
 mg_status mg_poll(mg_hierarchy* h, uint64_t ticket, mg_result* res);
 
 /* Waits for outstanding requests of h, then frees all its device and host
@@ -248,11 +276,30 @@ mg_status mg_destroy(mg_hierarchy* h);
 
 /* ---------------------------------------------------------------- serving and batching */
 
-/* Sets the serving engine's device-memory budget for request working sets
- * (bytes; 0 = 80% of the free device memory at the first submit) and the
- * maximum number of requests in flight (0 = 16).  Call before the first
- * mg_submit of the process. */
+/* Sets, for the current device, the budget of the device-memory pool that
+ * holds the working arenas of pooled hierarchies (bytes; 0 = 80% of the free
+ * device memory at the pool's next use), and the maximum number of serving
+ * requests in flight (0 = 16).  The pool never holds more than the budget:
+ * lowering it returns empty chunks to the device and evicts cached arenas of
+ * idle hierarchies at once, the rest as running solves complete.  The peak
+ * counters of mg_serve_stats_get restart from the current values. */
 mg_status mg_serve_configure(size_t budget_bytes, int32_t max_inflight);
+
+/* Counters of the current device's memory pool and of the serving engine. */
+typedef struct mg_serve_stats {
+    uint64_t budget_bytes;        /* the pool's budget */
+    uint64_t reserved_bytes;      /* device memory the pool holds now (<= budget) */
+    uint64_t in_use_bytes;        /* working arenas of solves running now */
+    uint64_t peak_in_use_bytes;   /* maxima since the process started */
+    uint64_t peak_reserved_bytes;
+    uint64_t arena_acquires;      /* arenas taken from the pool */
+    uint64_t arena_reuses;        /* ... that found their hierarchy's cached arena intact */
+    uint64_t arena_evictions;     /* cached arenas given up to make room */
+    uint64_t submitted, completed;/* serving requests */
+    uint64_t memory_waits;        /* requests that waited at least once for the pool */
+    int32_t inflight, peak_inflight, queued, reserved_;
+} mg_serve_stats;
+mg_status mg_serve_stats_get(mg_serve_stats* out);
 
 /* Solves `count` independent problems together, one per hierarchy (each
  * hierarchy at most once; none with serving requests in flight).  b[i], u[i],
@@ -292,8 +339,10 @@ mg_status mg_axpy(int32_t prec, int64_t n, double a, const void* x, void* y, voi
  * Computes, for the finite-difference operator A (op = 0: 5/7-point, h = 1/(n+1)):
  *   norms[0] = ||b - A u||_2,  norms[1] = ||b - A u||_inf,  norms[2] = ||b||_2
  * b, u: n^d FP64 values, contiguous, x fastest, device memory, read only.
- * norms: 3 doubles of device memory, written.  All three must be device
- * pointers (else MG_ERR_INVALID).  Asynchronous: enqueued on cuda_stream
+ * norms: 3 doubles of device memory, written.  All three must be memory of
+ * the current device (or managed memory), else MG_ERR_INVALID: host memory,
+ * and another device's memory, which the kernels could not read without peer
+ * access, are rejected before any launch.  Asynchronous: enqueued on cuda_stream
  * (NULL = legacy default stream); the norms are valid once the stream has
  * reached them.
  * Scratch: per-CTA partial sums in one static device array of 2 MiB that
@@ -302,9 +351,31 @@ mg_status mg_axpy(int32_t prec, int64_t n, double a, const void* x, void* y, voi
  * All calls share that array: calls whose work overlaps on the GPU (e.g. on
  * different streams) race and must be serialised by the caller.  The first
  * call on a device looks up the array's device address with that device
- * current; make it before any stream capture begins. */
+ * current; make it before any stream capture begins.  The address is kept
+ * per device and CUDA context: after cudaDeviceReset the next call on that
+ * device looks it up again (also outside any capture). */
 mg_status mg_residual_norms_noalloc(int32_t dim, int32_t n, const double* b, const double* u,
                                     double* norms, void* cuda_stream);
+
+/* ---------------------------------------------------------------- host-side fault injection */
+
+/* Allocation sites that mg_fault_inject can make fail. */
+typedef enum {
+    MG_FAULT_ARENA = 0,   /* the working arena: at mg_create_hierarchy, or for a pooled
+                             hierarchy the pool's growth when a solve is admitted */
+    MG_FAULT_STAGING = 1, /* the device staging buffers of host b / u at the first solve
+                             with host pointers */
+    MG_FAULT_SITES = 2
+} mg_fault_site;
+
+/* Failure detection without a device fault (the paper has no counterpart; it
+ * tests the library's error paths): the next `count` allocations at `site`
+ * fail as if the device were out of memory, without calling the allocator,
+ * and take the library's own failure path (MG_ERR_OOM; nothing is leaked, the
+ * caller's u is left unchanged, later calls are unaffected).  count = 0
+ * cancels pending failures.  Process-wide; thread-safe.  Errors:
+ * MG_ERR_INVALID for an unknown site or count < 0. */
+mg_status mg_fault_inject(int32_t site, int32_t count);
 
 /* ---------------------------------------------------------------- profiling */
 

@@ -23,6 +23,15 @@ using namespace mgi;
         if (e_ != cudaSuccess) SFAIL(MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// Stage calls work on the hierarchy's level arrays: a pooled hierarchy holds
+// them only while one of its solves runs.
+#define NEED_ARENA(h)                                                                                   \
+    do {                                                                                                \
+        if (!(h)->bound)                                                                                \
+            SFAIL(MG_ERR_INVALID, "a pooled hierarchy holds no working arena outside a solve; stage calls " \
+                                  "need a resident hierarchy (pooled = 0)");                            \
+    } while (0)
+
 static void* vec_ptr(mgi_hier& h, int level, int vec, int& prec, Geom& geo, void** alloc, size_t* bytes) {
     if (level < 0 || level >= h.nlev) return nullptr;
     Level& L = h.lv[level];
@@ -55,6 +64,7 @@ static mg_status order_after_user(mgi_hier& h) {
 extern "C" mg_status mg_level_write(mg_hierarchy* hh, int32_t level, int32_t vec, const void* src) {
     mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
     if (!h || !src) SFAIL(MG_ERR_INVALID, "NULL argument");
+    NEED_ARENA(h);
     int prec = 0;
     Geom geo;
     void* dst = vec_ptr(*h, level, vec, prec, geo, nullptr, nullptr);
@@ -81,6 +91,7 @@ extern "C" mg_status mg_level_write(mg_hierarchy* hh, int32_t level, int32_t vec
 extern "C" mg_status mg_level_read(mg_hierarchy* hh, int32_t level, int32_t vec, void* dst) {
     mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
     if (!h || !dst) SFAIL(MG_ERR_INVALID, "NULL argument");
+    NEED_ARENA(h);
     int prec = 0;
     Geom geo;
     void* src = vec_ptr(*h, level, vec, prec, geo, nullptr, nullptr);
@@ -149,6 +160,7 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
     mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
     if (!h) SFAIL(MG_ERR_INVALID, "NULL hierarchy");
     if (level < 0 || level >= h->nlev) SFAIL(MG_ERR_INVALID, "no such level");
+    NEED_ARENA(h);
     SCK(cudaSetDevice(h->device));
     mg_status st0 = order_after_user(*h);
     if (st0) return st0;

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -434,6 +435,25 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
                       mg_status* status) {
     for (size_t i = 0; i < hs.size(); ++i)
         if (!mgi_is_device_ptr(b[i]) || !mgi_is_device_ptr(u[i])) return false;
+    // pooled instances take their working arenas first (the plan holds their addresses);
+    // the whole batch must fit the pool's budget at once
+    std::vector<mgi_hier*> took;
+    auto unbind_all = [&]() {
+        for (mgi_hier* h : took) mgi_unbind(*h);
+    };
+    for (mgi_hier* h : hs) {
+        if (h->bound) continue;
+        cudaSetDevice(h->device);
+        const mg_status bs = mgi_bind(*h);
+        if (bs != MG_OK) {
+            for (mgi_hier* t : took) cudaStreamSynchronize(t->stream);
+            unbind_all();
+            if (bs == MG_BUSY) mgi_set_error("the batch's working arenas do not fit the memory pool's budget at once");
+            *status = bs == MG_BUSY ? MG_ERR_OOM : bs;
+            return true;
+        }
+        took.push_back(h);
+    }
     Plan* p = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -442,7 +462,11 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
         if (!p) {
             std::string why;
             p = build_plan(hs, why);
-            if (!p) return false;
+            if (!p) {
+                for (mgi_hier* t : took) cudaStreamSynchronize(t->stream);
+                unbind_all();
+                return false;
+            }
             g_plans.push_back(p);
         }
     }
@@ -462,13 +486,16 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
         sh.tol_mode = h.p.tol_mode;
         sh.guard = h.p.guard;
         sh.scale_ahead = h.scale_ahead_on() ? 1 : 0;
+
         sh.b = b[i];
         sh.uout = u[i];
     }
-    // the caller's pending work on each instance's stream comes first
+    // the caller's pending work on each instance's stream comes first, and the
+    // clearing of freshly bound pooled arenas
     for (mgi_hier* h : hs) {
         cudaEventRecord(h->ev_in, h->user_stream);
         cudaStreamWaitEvent(p->stream, h->ev_in, 0);
+        cudaStreamWaitEvent(p->stream, h->ev_bind, 0);
     }
     cudaStream_t s = p->stream;
     cudaError_t e = cudaMemcpyAsync(p->d_stage, p->h_stage, (size_t)n * sizeof(DevState), cudaMemcpyHostToDevice, s);
@@ -479,9 +506,12 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         mgi_set_error(std::string("batch: ") + cudaGetErrorString(e));
+        cudaStreamSynchronize(s);
+        unbind_all();
         *status = MG_ERR_CUDA;
         return true;
     }
+    unbind_all();
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p->e0, p->e1);
     mg_status first_bad = MG_OK;
@@ -499,7 +529,7 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
         r.launches = p->launches_init + st.loops * p->launches_body + p->launches_report + 2;
         r.merged = 1;
         if (st.kerr) {
-            r.status = MG_ERR_CUDA;
+            r.status = MG_ERR_TIMEOUT;
             mgi_set_error("a stencil kernel timed out waiting for its TMA tile copies");
         }
         if (res) res[i] = r;

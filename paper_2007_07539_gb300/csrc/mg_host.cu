@@ -11,15 +11,21 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mg_host.h"
 
 using namespace mgi;
+
+// mg_solve on a pooled hierarchy: polls of 100 us while the pool is held by other solves
+constexpr int kBindWaitPolls = 600000;
 
 namespace mgi {
 int residual64_blocks(int dim, int n);
@@ -40,6 +46,24 @@ void mgi_set_error(const std::string& s) { g_err = s; }
     } while (0)
 
 extern "C" const char* mg_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------- host-side fault injection
+// Pending injected allocation failures per site (mg_fault_inject).  The
+// allocation sites consult mgi_fault_take before calling the allocator and
+// take the allocator's own failure path when it returns true.
+static std::atomic<int> g_fault[MG_FAULT_SITES];
+bool mgi_fault_take(int site) {
+    if (site < 0 || site >= MG_FAULT_SITES) return false;
+    int v = g_fault[site].load();
+    while (v > 0)
+        if (g_fault[site].compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+extern "C" mg_status mg_fault_inject(int32_t site, int32_t count) {
+    if (site < 0 || site >= MG_FAULT_SITES || count < 0) FAIL(MG_ERR_INVALID, "mg_fault_inject: bad site or count");
+    g_fault[site].store(count);
+    return MG_OK;
+}
 
 // ---------------------------------------------------------------- parameters
 extern "C" void mg_params_init(mg_params* p, int32_t dim, int32_t n) {
@@ -65,6 +89,8 @@ extern "C" void mg_params_init(mg_params* p, int32_t dim, int32_t n) {
     p->base_maxit = 0;
     p->base_tol = 1e-4;
     p->scale_ahead = 1;
+    p->wait_polls = -1;
+    p->pooled = 0;
 }
 
 extern "C" int32_t mg_level_count(int32_t n, int32_t levels_req, int32_t* sizes) {
@@ -118,22 +144,23 @@ int mgi_validate(const mg_params* p, std::string& why) {
     if (p->op != 0 && p->op != 1) { why = "op must be 0 (finite differences) or 1 (Q1 finite elements)"; return 0; }
     if (p->op == 1 && p->fuse_pre == 1) { why = "fuse_pre is for the finite-difference operator (op = 0)"; return 0; }
     if (p->scale_ahead != 0 && p->scale_ahead != 1) { why = "scale_ahead must be 0 or 1"; return 0; }
-    if (p->reserved[0] != 0) { why = "reserved fields must be 0"; return 0; }
+    if (p->wait_polls < -1) { why = "wait_polls must be -1 (default) or >= 0"; return 0; }
+    if (p->pooled != 0 && p->pooled != 1) { why = "pooled must be 0 or 1"; return 0; }
+    for (int i = 0; i < 4; ++i)
+        if (p->reserved[i] != 0) { why = "reserved fields must be 0"; return 0; }
     return L;
 }
 
 // ---------------------------------------------------------------- footprint
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-struct Layout {
-    size_t level_off[MG_MAX_LEVELS][3];
-    size_t u_off, r_off, part_off, st_off, minv_off, tprog_off, rsc_off, rpart_off, total;
-    size_t part_cap;
-};
-
 static size_t update_blocks_max(const mgi_hier& h);
 
-static void compute_layout(mgi_hier& h, Layout& lay) {
+// Working arena: the level vectors, u, r and the FP32 scratch of rescaled
+// restrictions; persistent part: partials, control state, base inverse, tail
+// program, rescale partials (HierLayout).  A resident hierarchy holds both in
+// one allocation, the working arena at total - work_total.
+static void compute_layout(mgi_hier& h, HierLayout& lay) {
     size_t off = 0;
     for (int l = 0; l < h.nlev; ++l) {
         size_t b = align_up((size_t)h.lv[l].geo.total * h.lv[l].esz, 256);
@@ -143,6 +170,16 @@ static void compute_layout(mgi_hier& h, Layout& lay) {
     size_t b64 = align_up((size_t)gf.total * 8, 256);
     lay.u_off = off; off += b64;
     lay.r_off = off; off += b64;
+    // FP32 restriction into a rescaled FP16 level run as plain kernels (any
+    // rescaled level: a W-cycle beyond the tail's program capacity drops the tail)
+    size_t rsc = 0;
+    for (int l = 0; l < h.nlev; ++l)
+        if (h.rescaled(l)) rsc = std::max(rsc, (size_t)h.lv[l].geo.total * 4);
+    lay.has_rsc = rsc > 0;
+    lay.rsc_off = 0;
+    if (rsc) { lay.rsc_off = off; off += align_up(rsc, 256); }
+    lay.work_total = align_up(off, 4096);
+    off = 0;
     size_t nb = std::max<size_t>((size_t)residual64_blocks(h.dim, gf.n) * 4, update_blocks_max(h) * 2);
     lay.part_cap = nb;
     lay.part_off = off; off += align_up(nb * 8, 256);
@@ -150,17 +187,31 @@ static void compute_layout(mgi_hier& h, Layout& lay) {
     lay.minv_off = off; off += align_up((size_t)h.m0 * h.m0 * 8, 256);
     lay.tprog_off = off;
     if (h.tail_level >= 0) off += align_up(sizeof(TailOp) * kTailMaxOps, 256);
-    // FP32 restriction into a rescaled FP16 level run as plain kernels (any
-    // rescaled level: a W-cycle beyond the tail's program capacity drops the tail)
-    size_t rsc = 0;
-    for (int l = 0; l < h.nlev; ++l)
-        if (h.rescaled(l)) rsc = std::max(rsc, (size_t)h.lv[l].geo.total * 4);
-    lay.rsc_off = lay.rpart_off = 0;
-    if (rsc) {
-        lay.rsc_off = off; off += align_up(rsc, 256);
-        lay.rpart_off = off; off += align_up(kRescaleCtas * sizeof(float), 256);
+    lay.rpart_off = off;
+    if (rsc) off += align_up(kRescaleCtas * sizeof(float), 256);
+    lay.pers_total = align_up(off, 4096);
+    lay.total = lay.pers_total + lay.work_total;
+}
+
+// Points the levels, u, r and the rescale scratch at a working arena.
+static void bind_work(mgi_hier& h, char* work) {
+    const HierLayout& lay = h.lay;
+    h.work = work;
+    for (int l = 0; l < h.nlev; ++l) {
+        const size_t bo = (size_t)h.lv[l].geo.base * h.lv[l].esz;
+        h.lv[l].c = work + lay.level_off[l][0] + bo;
+        h.lv[l].g = work + lay.level_off[l][1] + bo;
+        h.lv[l].t = work + lay.level_off[l][2] + bo;
+        h.lv[l].alloc[0] = work + lay.level_off[l][0];
+        h.lv[l].alloc[1] = work + lay.level_off[l][1];
+        h.lv[l].alloc[2] = work + lay.level_off[l][2];
     }
-    lay.total = off;
+    const Geom& gf = h.lv[h.nlev - 1].geo;
+    h.u_alloc = (double*)(work + lay.u_off);
+    h.r_alloc = (double*)(work + lay.r_off);
+    h.u = h.u_alloc + gf.base;
+    h.r = h.r_alloc + gf.base;
+    h.rsc_alloc = lay.has_rsc ? (float*)(work + lay.rsc_off) : nullptr;
 }
 
 // ---------------------------------------------------------------- base-level operator inverse
@@ -256,7 +307,8 @@ struct Gen {
         a.cf = make_sweep_coef(h->dim, h->p.op, a.omega, a.h2inv);
         op.sh = kernel_shape(h->dim, kkind, mode, op.prec, f.n, f.P, 0);
         a.xstep = op.sh.xstep; a.ystep = op.sh.ystep; a.zstep = op.sh.zstep; a.zlen = op.sh.zlen;
-        a.err = &h->st->kerr;
+        a.err = h->st ? &h->st->kerr : nullptr;
+        a.wait_polls = h->p.wait_polls >= 0 ? h->p.wait_polls + 1 : 0;
         if (h->dim == 3 && kkind == K_SWEEP && op.sh.rpw > 0 && !h->describe_only) {  // TMA boxes: TY+2 rows of the swept vector, TY rows of g
             op.has_maps = true;
             const int rows = op.sh.ty * op.sh.rpw;
@@ -555,6 +607,7 @@ static void free_hier(mgi_hier* h) {
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->solve_exec) cudaGraphExecDestroy(h->solve_exec);
     if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->p.pooled == 1) pool_drop(h->device, h);
     if (h->arena) cudaFree(h->arena);
     if (h->bstage) cudaFree(h->bstage);
     if (h->ustage) cudaFree(h->ustage);
@@ -563,6 +616,7 @@ static void free_hier(mgi_hier* h) {
     if (h->e1) cudaEventDestroy(h->e1);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_state) cudaEventDestroy(h->ev_state);
+    if (h->ev_bind) cudaEventDestroy(h->ev_bind);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     if (h->stream) cudaStreamDestroy(h->stream);
     cudaSetDevice(dev);
@@ -764,10 +818,9 @@ static mg_status plan_hier(const mg_params* p, mgi_hier& h, bool probe) {
     plan_tail(h, p->no_tail == 1, probe && p->no_tail == 2);
     h.m0 = 1;
     for (int a = 0; a < p->dim; ++a) h.m0 *= sizes[0];
-    Layout lay;
-    compute_layout(h, lay);
-    h.footprint = lay.total;
-    h.part_cap = lay.part_cap;
+    compute_layout(h, h.lay);
+    h.footprint = h.lay.total;
+    h.part_cap = h.lay.part_cap;
     return MG_OK;
 }
 
@@ -821,39 +874,26 @@ extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, 
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { delete h; FAIL(MG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)); }
     h->user_stream = (cudaStream_t)cuda_stream;
-    Layout lay;
-    compute_layout(*h, lay);
-    e = cudaMalloc(&h->arena, lay.total);
+    const HierLayout& lay = h->lay;
+    const bool pooled = h->p.pooled == 1;
+    // a resident hierarchy holds both parts in one allocation; a pooled one only
+    // the persistent part (its working arena comes from the pool per solve)
+    const size_t bytes = pooled ? lay.pers_total : lay.total;
+    e = (!pooled && mgi_fault_take(MG_FAULT_ARENA)) ? cudaErrorMemoryAllocation : cudaMalloc(&h->arena, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         h->arena = nullptr;
         free_hier(h);
-        FAIL(MG_ERR_OOM, "device allocation of " + std::to_string(lay.total) + " bytes failed");
+        FAIL(MG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
     }
-    h->arena_bytes = lay.total;
+    h->arena_bytes = bytes;
     char* base = (char*)h->arena;
-    for (int l = 0; l < h->nlev; ++l) {
-        const size_t bo = (size_t)h->lv[l].geo.base * h->lv[l].esz;
-        h->lv[l].c = base + lay.level_off[l][0] + bo;
-        h->lv[l].g = base + lay.level_off[l][1] + bo;
-        h->lv[l].t = base + lay.level_off[l][2] + bo;
-        h->lv[l].alloc[0] = base + lay.level_off[l][0];
-        h->lv[l].alloc[1] = base + lay.level_off[l][1];
-        h->lv[l].alloc[2] = base + lay.level_off[l][2];
-    }
-    const Geom& gf = h->lv[h->nlev - 1].geo;
-    h->u_alloc = (double*)(base + lay.u_off);
-    h->r_alloc = (double*)(base + lay.r_off);
-    h->u = h->u_alloc + gf.base;
-    h->r = h->r_alloc + gf.base;
     h->partials = (double*)(base + lay.part_off);
     if (h->tail_level >= 0) h->tail_prog = (TailOp*)(base + lay.tprog_off);
     h->st = (DevState*)(base + lay.st_off);
     h->minv = (double*)(base + lay.minv_off);
-    if (lay.rsc_off) {
-        h->rsc_alloc = (float*)(base + lay.rsc_off);
-        h->rsc_part = (float*)(base + lay.rpart_off);
-    }
+    if (lay.has_rsc) h->rsc_part = (float*)(base + lay.rpart_off);
+    if (!pooled) bind_work(*h, base + lay.pers_total);
     std::vector<double> inv;
     if (!coarse_inverse(h->dim, h->p.op, h->lv[0].geo.n, inv)) { free_hier(h); FAIL(MG_ERR_INVALID, "singular base-level operator"); }
 #define CK_CREATE(call)                                                                       \
@@ -870,16 +910,72 @@ extern "C" mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, 
     CK_CREATE(cudaEventCreate(&h->e1));
     CK_CREATE(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
     CK_CREATE(cudaEventCreateWithFlags(&h->ev_state, cudaEventDisableTiming));
+    CK_CREATE(cudaEventCreateWithFlags(&h->ev_bind, cudaEventDisableTiming));
     CK_CREATE(cudaMallocHost((void**)&h->st_host, sizeof(DevState)));
     std::memset(h->st_host, 0, sizeof(DevState));
-    CK_CREATE(cudaMemsetAsync(h->arena, 0, lay.total, h->stream));
+    CK_CREATE(cudaMemsetAsync(h->arena, 0, bytes, h->stream));
     CK_CREATE(cudaMemcpyAsync(h->minv, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, h->stream));
     CK_CREATE(cudaStreamSynchronize(h->stream));
 #undef CK_CREATE
-    if (p->tune == 1) autotune(*h);
-    build_step(*h);
+    if (!pooled) {
+        if (p->tune == 1) autotune(*h);
+        build_step(*h);
+        h->built_for = h->work;
+        h->bound = true;
+    } else if (p->tune == 1) {
+        // tile shapes are timed on the hierarchy's own arrays: take an arena from
+        // the pool for it if one fits now (it stays cached for the first solve);
+        // otherwise the shapes come from the wave model
+        if (mgi_bind(*h) == MG_OK) {
+            autotune(*h);
+            h->built_for = nullptr;  // rebuild the step with the tuned shapes at the next bind
+            cudaStreamSynchronize(h->stream);
+            mgi_unbind(*h);
+        }
+        cudaGetLastError();
+    }
     *out = reinterpret_cast<mg_hierarchy*>(h);
     return MG_OK;
+}
+
+// ---------------------------------------------------------------- pooled working arenas
+mg_status mgi_bind(mgi_hier& h) {
+    if (h.p.pooled != 1 || h.bound) return MG_OK;
+    char* base = nullptr;
+    bool kept = false;
+    const int rc = pool_acquire(h.device, &h, h.lay.work_total, &base, &kept);
+    if (rc == 1) FAIL(MG_BUSY, "the memory pool's budget is held by other solves");
+    if (rc == 2)
+        FAIL(MG_ERR_ADMISSION, "working arena of " + std::to_string(h.lay.work_total) +
+                                   " B exceeds the memory pool's budget of " + std::to_string(pool_budget(h.device)) + " B");
+    if (rc == 3) FAIL(MG_ERR_OOM, "device allocation for the memory pool failed");
+    h.bound = true;
+    if (!kept || base != h.work) {
+        // a block that held another hierarchy's arrays (or nothing): the padded
+        // layout needs its pads and guards zero, so the whole arena is cleared
+        bind_work(h, base);
+        cudaError_t e = cudaMemsetAsync(base, 0, h.lay.work_total, h.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h.ev_bind, h.stream);
+        if (e != cudaSuccess) {
+            pool_release(h.device, &h);
+            h.bound = false;
+            FAIL(MG_ERR_CUDA, std::string("arena clear: ") + cudaGetErrorString(e));
+        }
+    }
+    if (h.built_for != h.work) {  // launches and graphs hold the arena's addresses
+        if (h.graph_exec) { cudaGraphExecDestroy(h.graph_exec); h.graph_exec = nullptr; }
+        if (h.solve_exec) { cudaGraphExecDestroy(h.solve_exec); h.solve_exec = nullptr; }
+        mgi_batch_forget(&h);
+        build_step(h);
+        h.built_for = h.work;
+    }
+    return MG_OK;
+}
+
+void mgi_unbind(mgi_hier& h) {
+    if (h.p.pooled != 1 || !h.bound) return;
+    pool_release(h.device, &h);
+    h.bound = false;
 }
 
 extern "C" mg_status mg_destroy(mg_hierarchy* hh) {
@@ -922,6 +1018,7 @@ static size_t npoints(const mgi_hier& h) {
 static int ensure_staging(mgi_hier& h) {
     if (h.bstage) return 0;
     size_t bytes = npoints(h) * 8;
+    if (mgi_fault_take(MG_FAULT_STAGING)) return 1;
     if (cudaMalloc(&h.bstage, bytes) != cudaSuccess) { cudaGetLastError(); h.bstage = nullptr; return 1; }
     if (cudaMalloc(&h.ustage, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -1075,7 +1172,32 @@ static int push_state(mgi_hier& h) {
 // Starts a solve: resolves host/device pointers, writes the control state,
 // then launches either the whole-solve graph or the initial residual (the
 // host-driven loop, used when graphs are off or for per-kernel profiling).
+static mg_status solve_begin_bound(mgi_hier& h, const double* b, double* u);
 mg_status mgi_solve_begin(mgi_hier& h, const double* b, double* u) {
+    const bool was_bound = h.bound;
+    mg_status st = mgi_bind(h);
+    if (st != MG_OK) return st;
+    if (h.prof) {  // per-kernel events of the step as built for this arena
+        const size_t nops = h.step.size();
+        if (h.prof_ev.size() != 2 * nops) {
+            for (cudaEvent_t e : h.prof_ev) cudaEventDestroy(e);
+            h.prof_ev.assign(2 * nops, nullptr);
+            for (auto& e : h.prof_ev)
+                if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); e = nullptr; }
+        }
+        h.prof_ms.assign(nops, 0.0);
+        h.prof_cnt.assign(nops, 0);
+    }
+    st = solve_begin_bound(h, b, u);
+    if (st != MG_OK && !was_bound) {
+        cudaStreamSynchronize(h.stream);
+        cudaGetLastError();
+        mgi_unbind(h);
+    }
+    return st;
+}
+
+static mg_status solve_begin_bound(mgi_hier& h, const double* b, double* u) {
     SolveCtx& c = h.ctx;
     c = SolveCtx{};
     c.b_user = b;
@@ -1159,6 +1281,9 @@ int mgi_solve_advance(mgi_hier& h) {
     auto fail = [&](int code) {
         mgi_set_error(std::string("launch: ") + cudaGetErrorString((cudaError_t)code));
         c.active = false;
+        cudaStreamSynchronize(h.stream);  // nothing of this solve may still run on a released arena
+        cudaGetLastError();
+        mgi_unbind(h);
         return -MG_ERR_CUDA;
     };
     if (c.graph && !c.finishing) {
@@ -1213,10 +1338,13 @@ int mgi_solve_advance(mgi_hier& h) {
     r.seconds = ms * 1e-3;
     r.launches = c.launches;
     if (s.kerr) {  // a stencil kernel's bounded wait for its tile copies ran out: results are not valid
-        r.status = MG_ERR_CUDA;
-        mgi_set_error("a stencil kernel timed out waiting for its TMA tile copies");
+        r.status = MG_ERR_TIMEOUT;
+        mgi_set_error(s.kerr == 2 ? "a stencil kernel timed out waiting for its TMA tile copies, and a copy "
+                                    "had still not completed when it drained them"
+                                  : "a stencil kernel timed out waiting for its TMA tile copies");
     }
     c.active = false;
+    mgi_unbind(h);  // the last action's event has completed: no work on the arena is in flight
     return 1;
 }
 
@@ -1226,6 +1354,12 @@ extern "C" mg_status mg_solve(mg_hierarchy* hh, const double* b, double* u, mg_r
     if (mgi_serve_busy(h)) FAIL(MG_ERR_INVALID, "hierarchy has serving requests in flight");
     CUCHK(cudaSetDevice(h->device));
     mg_status st = mgi_solve_begin(*h, b, u);
+    // a pooled hierarchy waits while other solves hold the pool's budget
+    for (int k = 0; st == MG_BUSY && k < kBindWaitPolls; ++k) {
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+        st = mgi_solve_begin(*h, b, u);
+    }
+    if (st == MG_BUSY) FAIL(MG_ERR_OOM, "the memory pool's budget stayed held by other solves for 60 s");
     if (st != MG_OK) return st;
     for (;;) {
         cudaError_t e = cudaEventSynchronize(h->ev_state);
@@ -1303,19 +1437,12 @@ extern "C" mg_status mg_profile_solve(mg_hierarchy* hh, const double* b, double*
     mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
     if (!h) FAIL(MG_ERR_INVALID, "NULL hierarchy");
     CUCHK(cudaSetDevice(h->device));
-    const size_t nops = h->step.size();
-    if (h->prof_ev.size() != 2 * nops) {
-        for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
-        h->prof_ev.assign(2 * nops, nullptr);
-        for (auto& e : h->prof_ev) CUCHK(cudaEventCreate(&e));
-    }
-    h->prof_ms.assign(nops, 0.0);
-    h->prof_cnt.assign(nops, 0);
-    h->prof = true;
+    h->prof = true;  // the solve sizes the per-kernel events for the step it runs
     mg_result r{};
     mg_status st = mg_solve(hh, b, u, &r);
     h->prof = false;
     h->prof_pending = false;
+    const size_t nops = std::min(h->step.size(), h->prof_ms.size());
     if (res) *res = r;
     if (count) *count = (int32_t)nops;
     for (size_t i = 0; i < nops && (int32_t)i < max_out && out; ++i) {

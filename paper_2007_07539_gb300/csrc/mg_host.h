@@ -42,6 +42,22 @@ struct Op {
     SweepMaps maps{};
 };
 
+// Device memory of a hierarchy, in two parts.  The working arena (the level
+// vectors c, g, t of every level, the finest level's FP64 u and r, the FP32
+// scratch of rescaled restrictions: nearly all the bytes) and the persistent
+// part (norm partials, control state, base-level inverse, tail program,
+// rescale partials).  Offsets are relative to each part's base.
+struct HierLayout {
+    size_t level_off[MG_MAX_LEVELS][3] = {};
+    size_t u_off = 0, r_off = 0, rsc_off = 0;
+    bool has_rsc = false;
+    size_t work_total = 0;
+    size_t part_off = 0, st_off = 0, minv_off = 0, tprog_off = 0, rpart_off = 0;
+    size_t pers_total = 0;
+    size_t total = 0;  // both parts of a resident hierarchy (one allocation)
+    size_t part_cap = 0;
+};
+
 struct SolveCtx {
     const double* b_user = nullptr;
     double* u_user = nullptr;
@@ -111,9 +127,14 @@ struct mgi_hier {
         return p.scale_ahead == 1 && p.scaling == 1 && nlev > 0 && lv[nlev - 1].prec != MG_FP64 && !g_alias_r;
     }
 
-    void* arena = nullptr;
+    void* arena = nullptr;        // persistent part (and, resident hierarchies, the working arena behind it)
     size_t arena_bytes = 0;
-    size_t footprint = 0;
+    size_t footprint = 0;         // both parts
+    HierLayout lay;
+    char* work = nullptr;         // working arena the level pointers point into (null: none yet)
+    char* built_for = nullptr;    // working arena the step's launches and graphs were built for
+    bool bound = false;           // pooled (mg_params.pooled): a working arena from the pool is held
+    cudaEvent_t ev_bind = nullptr;  // pooled: recorded on the stream after a fresh arena was zeroed
     SolveCtx ctx;
     // launch accounting and per-kernel profiling of the IR step
     int step_kernels = 0;            // kernels per IR step (memsets excluded)
@@ -127,6 +148,8 @@ struct mgi_hier {
 }  // namespace mgi
 
 void mgi_set_error(const std::string& s);
+// true (once per pending count) when mg_fault_inject asked the next allocation at this site to fail
+bool mgi_fault_take(int site);
 int mgi_validate(const mg_params* p, std::string& why);
 int mgi_run_op(mgi::mgi_hier& h, const mgi::Op& op, cudaStream_t s);
 void* mgi_build_cycle(mgi::mgi_hier& h, std::vector<mgi::Op>& ops, bool top_from_r, int gate,
@@ -145,3 +168,29 @@ void mgi_batch_forget(mgi::mgi_hier* h);
 // serving engine hooks
 void mgi_serve_forget(mgi::mgi_hier* h);
 bool mgi_serve_busy(mgi::mgi_hier* h);
+// Working arena of a pooled hierarchy (mg_pool.cu / mg_host.cu).
+//   mgi_bind: takes the arena from the pool (if not held) and points the levels
+//   at it, rebuilding the step's launches when its address changed.  Returns
+//   MG_OK, MG_BUSY (does not fit the budget now: memory in use by other
+//   solves), MG_ERR_ADMISSION (larger than the whole budget), MG_ERR_OOM or
+//   MG_ERR_CUDA.  A resident hierarchy is always bound (MG_OK).
+//   mgi_unbind: hands the arena back (kept as a cache for this hierarchy until
+//   another needs the room); call only once no work on it is in flight.
+mg_status mgi_bind(mgi::mgi_hier& h);
+void mgi_unbind(mgi::mgi_hier& h);
+namespace mgi {
+// The device-memory pool of pooled working arenas (one per device).
+//   pool_acquire: 0 ok (*base set; *kept: the block this hierarchy held last,
+//   contents intact), 1 no room now, 2 never fits the budget, 3 allocation
+//   error.
+int pool_acquire(int device, mgi_hier* h, size_t bytes, char** base, bool* kept);
+void pool_release(int device, mgi_hier* h);
+void pool_drop(int device, mgi_hier* h);      // h is destroyed: its block (if any) becomes free
+size_t pool_budget(int device);
+void pool_set_budget(int device, size_t bytes); // 0: 80% of the device's free memory at the next use
+struct PoolStats {
+    size_t budget, reserved, in_use, peak_in_use, peak_reserved;
+    unsigned long long acquires, reuses, evictions, chunks;
+};
+PoolStats pool_stats(int device);
+}  // namespace mgi

@@ -158,7 +158,8 @@ struct KArgs {
     int xstep, ystep, zstep, zlen;  // tile strides / march length
     int gate;            // 1: return at once unless st->phase == 0
     int fin;             // K_UPDATE: the last CTA runs the step's finalisation (FIN_STEP)
-    int* err;            // set to 1 when a bounded copy wait runs out (3D sweeps)
+    int* err;            // set to 1 when a bounded copy wait runs out (3D sweeps), 2 if the drain also did
+    int wait_polls;      // 3D sweeps: k + 1 for k polls per wait for a plane's copies; 0: the default bound
     SweepCoef cf;        // sweep coefficients of this level (host-computed)
 };
 

@@ -266,8 +266,34 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* m, 
         "l"(reinterpret_cast<unsigned long long>(m)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
-constexpr unsigned kWaitTries = 1u << 20;  // first wait of a thread
-constexpr unsigned kDrainTries = 1u << 10; // every wait after one ran out
+// Polls of one wait for a plane's tile copies (each poll may suspend the thread
+// for a short hardware-chosen time: about a second in all).  KArgs::wait_polls
+// = k + 1 > 0 replaces it by k polls for the waits of the march (a diagnostic
+// setting: k = 0 gives up at once), never for the drain after a failed wait;
+// 0 (the zero-initialised value) keeps the default.
+constexpr unsigned kWaitTries = 1u << 20;
+__device__ __forceinline__ unsigned march_wait_polls(const KArgs& a) {
+    return a.wait_polls > 0 ? (unsigned)(a.wait_polls - 1) : kWaitTries;
+}
+// After a wait of the march gave up: the CTA stops issuing copies, and its
+// leader waits, with the full bound, for the last S planes it issued (march
+// indices q_last-S+1 .. q_last, stage q % S, phase parity (q / S) & 1: each
+// stage's latest phase; earlier phases of a stage completed before it was
+// reissued), so that no bulk copy is still writing into the CTA's shared
+// memory when it exits.  A phase that completed already passes at once.
+// Returns false if a copy did not complete even then.
+__device__ __forceinline__ bool drain_copies(unsigned bar0, int S, int q_last) {
+    bool ok = true;
+    for (int q = q_last - S + 1 > 0 ? q_last - S + 1 : 0; q <= q_last; ++q)
+        ok = mbar_wait(bar0 + 8 * (q % S), (unsigned)(q / S) & 1u, kWaitTries) && ok;
+    return ok;
+}
+// Marks the solve as stopped by a wait that gave up (DevState::kerr, reported
+// as MG_ERR_TIMEOUT; phase 3 makes every later gated kernel return at once).
+__device__ __forceinline__ void march_wait_failed(const KArgs& a) {
+    if (a.err) atomicExch(a.err, 1);
+    if (a.st) *reinterpret_cast<volatile int*>(&const_cast<DevState*>(a.st)->phase) = 3;
+}
 
 // ---------------------------------------------------------------- 3D sweep
 // One CTA = TY warps; warp w owns fine row y0 + w of a 32*V-point x-chunk and
@@ -338,17 +364,15 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
         tma_load_3d(st, &maps.src, xc, y0 - 1, p + 1, bar);
         if (with_g) tma_load_3d(st + CB, &maps.g, xg, y0, p + 1, bar);
     };
-    // the next plane to wait for: its stage and phase advance one plane at a time
+    // the next plane to wait for: its stage and phase advance one plane at a time.
+    // A wait that gives up marks this thread failed; the CTA learns of it at the
+    // next barrier (__syncthreads_or), stops issuing and drains (drain_copies).
     int wst = 0;
     unsigned wpar = 0;
-    bool failed = false;
+    bool failed = false, abort = false;
     auto wait_next = [&]() {
-        if (!mbar_wait(bar0 + 8 * wst, wpar, failed ? kDrainTries : kWaitTries)) {
-            if (!failed) {
-                if (a.err) atomicExch(a.err, 1);
-                // stop the solve: every later gated kernel returns at once
-                if (a.st) *reinterpret_cast<volatile int*>(&const_cast<DevState*>(a.st)->phase) = 3;
-            }
+        if (!failed && !mbar_wait(bar0 + 8 * wst, wpar, march_wait_polls(a))) {
+            march_wait_failed(a);
             failed = true;
         }
         if (++wst == S) { wst = 0; wpar ^= 1u; }
@@ -419,13 +443,41 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     }
     int so = SB;  // stage of plane z
 
+    // Restriction: the coarse rows of coarse plane K from the z-sums that every
+    // warp flushed to shared memory after fine plane 2K+2 (t = z - zb even,
+    // t >= 2), taken one plane later, after the next plane's barrier: warp w < TJ
+    // forms coarse row J0 + w from tile rows 2w, 2w+1, 2w+2 (y weights 1/4, 1/2,
+    // 1/4).  The flush area is written again only two planes later, after
+    // another barrier, so one barrier per plane serves both.
+    auto coarse_rows = [&](int K) {
+        const int TJ = (R - 1) / 2;
+        if (w < TJ) {
+            const int J = (y0 >> 1) + w;
+            const C* f0 = reinterpret_cast<const C*>(flush) + ((2 * w) * 32 + lane) * VH;
+            const C* f1 = f0 + 32 * VH;
+            const C* f2 = f1 + 32 * VH;
+            const int I0 = (x0 + lane * V) >> 1;
+            if (lane_in && J < a.nc && K < a.nc && (lane < 31 || x0 + CW >= a.P)) {
+                TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
+#pragma unroll
+                for (int k = 0; k < VH; ++k)
+                    if (I0 + k < a.nc) st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
+            }
+        }
+    };
+
     // One plane: cm / c0 hold planes z-1 / z, cp receives plane z+1 (and the
     // X / D sums of the same planes for Q1).
     auto step = [&](int z, const P2 (&cm)[RPW][NP], const P2 (&c0)[RPW][NP], P2 (&cp)[RPW][NP],
                     const P2 (&Xm)[RPW][NP], const P2 (&X0)[RPW][NP], P2 (&Xp)[RPW][NP],
                     const P2 (&dm)[RPW][NP], const P2 (&d0)[RPW][NP], P2 (&dp)[RPW][NP]) {
-        __syncthreads();  // every warp is done with plane z-2's stage
+        // every warp is done with plane z-2's stage, and every wait so far succeeded
+        if (__syncthreads_or(failed ? 1 : 0)) { abort = true; return; }
         if (leader) issue(z + S - 2);
+        if constexpr (MODE == M_RESTRICT && !Q1) {  // the flush of plane z-1 (t - 1 even, >= 2)
+            const int tp = z - 1 - zb;
+            if (tp >= 2 && !(tp & 1)) coarse_rows((zb >> 1) + (tp >> 1) - 1);
+        }
         wait_next();      // plane z+1
         int s1 = so + SB;
         if (s1 >= S * SB) s1 -= S * SB;
@@ -485,28 +537,17 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
 #pragma unroll
                     for (int k = 0; k < VH; ++k) acc[r][k] += (C)0.5 * q[r][k];
             } else {
-                if (t >= 2) {
+                if (t >= 2) {  // consumed by coarse_rows after the next barrier (Q1: at once,
+                               // which keeps its register pressure down)
 #pragma unroll
                     for (int r = 0; r < RPW; ++r) {
                         C* fl = reinterpret_cast<C*>(flush) + ((w + r * TY) * 32 + lane) * VH;
 #pragma unroll
                         for (int k = 0; k < VH; ++k) fl[k] = acc[r][k] + (C)0.25 * q[r][k];
                     }
-                    __syncthreads();
-                    const int TJ = (R - 1) / 2;
-                    if (w < TJ) {
-                        const int J = (y0 >> 1) + w, K = (zb >> 1) + (t >> 1) - 1;
-                        const C* f0 = reinterpret_cast<const C*>(flush) + ((2 * w) * 32 + lane) * VH;
-                        const C* f1 = f0 + 32 * VH;
-                        const C* f2 = f1 + 32 * VH;
-                        const int I0 = (x0 + lane * V) >> 1;
-                        if (lane_in && J < a.nc && K < a.nc && (lane < 31 || x0 + CW >= a.P)) {
-                            TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
-#pragma unroll
-                            for (int k = 0; k < VH; ++k)
-                                if (I0 + k < a.nc)
-                                    st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
-                        }
+                    if constexpr (Q1) {
+                        __syncthreads();
+                        coarse_rows((zb >> 1) + (t >> 1) - 1);
                     }
                 }
 #pragma unroll
@@ -517,13 +558,30 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
         }
         so = s1;
     };
-    for (int z = zb; z < ze;) {
+    int z = zb;
+    for (; z < ze;) {
         step(z, pa, pb, pc, qa, qb, qc, da, db, dc);
-        if (++z >= ze) break;
+        if (abort || ++z >= ze) break;
         step(z, pb, pc, pa, qb, qc, qa, db, dc, da);
-        if (++z >= ze) break;
+        if (abort || ++z >= ze) break;
         step(z, pc, pa, pb, qc, qa, qb, dc, da, db);
+        if (abort) break;
         ++z;
+    }
+    // abort is uniform across the CTA (set from a barrier's result).  The last
+    // plane issued: min(z + S - 3, ze) when step z stopped before its issue,
+    // ze after the whole march.
+    if (!abort) {
+        abort = __syncthreads_or(failed ? 1 : 0) != 0;
+        z = ze;
+        if constexpr (MODE == M_RESTRICT && !Q1) {  // the flush of the march's last plane
+            const int tp = ze - 1 - zb;
+            if (!abort && tp >= 2 && !(tp & 1)) coarse_rows((zb >> 1) + (tp >> 1) - 1);
+        }
+    }
+    if (abort && leader) {
+        const int p_last = min(z + S - 3, ze);
+        if (!drain_copies(bar0, S, p_last - zb + 1) && a.err) atomicExch(a.err, 2);
     }
 }
 
@@ -708,15 +766,14 @@ __device__ __forceinline__ void pre3_body(const KArgs& a, const SweepMaps& maps,
         mbar_expect_tx(bar, gbox);
         tma_load_3d(smem_u32(gring + s * GBs), &maps.src, xc, y0 - 2, p + 1, bar);
     };
+    // bounded waits as in sweep3_body: a wait that gives up stops the issuing at
+    // the next barrier, and the leader drains the copies it issued
     int wst = 0;
     unsigned wpar = 0;
-    bool failed = false;
+    bool failed = false, abort = false;
     auto wait_next = [&]() {
-        if (!mbar_wait(bar0 + 8 * wst, wpar, failed ? kDrainTries : kWaitTries)) {
-            if (!failed) {
-                if (a.err) atomicExch(a.err, 1);
-                if (a.st) *reinterpret_cast<volatile int*>(&const_cast<DevState*>(a.st)->phase) = 3;
-            }
+        if (!failed && !mbar_wait(bar0 + 8 * wst, wpar, march_wait_polls(a))) {
+            march_wait_failed(a);
             failed = true;
         }
         if (++wst == SG) { wst = 0; wpar ^= 1u; }
@@ -797,8 +854,10 @@ __device__ __forceinline__ void pre3_body(const KArgs& a, const SweepMaps& maps,
         }
     };
 
-    for (int p = zb - 2; p <= ze + 1; ++p) {
-        __syncthreads();  // the g slot of p+3 and the c slot of p-1 are free
+    int p = zb - 2;
+    for (; p <= ze + 1; ++p) {
+        // the g slot of p+3 and the c slot of p-1 are free, and every wait so far succeeded
+        if (__syncthreads_or(failed ? 1 : 0)) { abort = true; break; }
         if (leader) issue(p + 3);
         wait_next();      // g plane p
         // ---- stage A: c on plane p-1, rows y0-1 .. y0+R
@@ -862,6 +921,17 @@ __device__ __forceinline__ void pre3_body(const KArgs& a, const SweepMaps& maps,
 #pragma unroll
             for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * qv[k];
         }
+    }
+    // abort is uniform across the CTA (set from a barrier's result).  The last
+    // plane issued: min(p + 2, ze + 1) when iteration p stopped before its
+    // issue, ze + 1 after the whole march; march index = plane - zb + 2.
+    if (!abort) {
+        abort = __syncthreads_or(failed ? 1 : 0) != 0;
+        p = ze + 1;
+    }
+    if (abort && leader) {
+        const int p_last = min(p + 2, ze + 1);
+        if (!drain_copies(bar0, SG, p_last - zb + 2) && a.err) atomicExch(a.err, 2);
     }
 }
 template <class T, class TC>
@@ -1123,8 +1193,10 @@ __device__ __forceinline__ double to_f64(double v) { return v; }
 
 
 // The sum of squares in FP64 (one fused multiply-add per point on the FP64
-// pipe, which the update leaves half idle) in place of the integer-built
-// double-float sum: fewer instructions for the issue-bound update.
+// pipe) in place of the integer-built double-float sum: fewer instructions for
+// the issue-bound update.  (An FP32 sum of the squares of the scaled FP32
+// values the scale-ahead path already forms was measured slower at 255^3:
+// 120.6 against 112.3 us.)
 struct SqAcc64 {
     double s = 0.0;
     __device__ __forceinline__ void add(double r, int) { s = fma(r, r, s); }

@@ -7,12 +7,14 @@
 // the kernels of different solves overlap on the device, and in the serving
 // engine new requests start while others are running ("continuous
 // batching"): a queued request is admitted as soon as its hierarchy is idle,
-// a slot is free (max_inflight) and its working-set bytes fit the memory
-// budget next to the requests already in flight.
+// a slot is free (max_inflight) and, for a pooled hierarchy, its working arena
+// fits the device-memory pool next to the requests already in flight.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <string>
@@ -34,6 +36,10 @@ mg_status mgi_batch_run(std::vector<mgi_hier*>& hs, const double* const* b, doub
     for (int i = 0; i < n; ++i) {
         cudaSetDevice(hs[i]->device);
         mg_status st = mgi_solve_begin(*hs[i], b[i], u[i]);
+        if (st == MG_BUSY) {
+            mgi_set_error("the batch's working arenas do not fit the memory pool's budget at once");
+            st = MG_ERR_OOM;
+        }
         if (st != MG_OK) {
             state[i] = 2;
             if (res) { res[i] = mg_result{}; res[i].status = st; }
@@ -70,7 +76,20 @@ mg_status mgi_batch_run(std::vector<mgi_hier*>& hs, const double* const* b, doub
 }
 
 // ---------------------------------------------------------------- serving engine
+// Admission.  A queued request is admitted when a slot is free
+// (max_inflight), its hierarchy has no other request running, and -- for a
+// pooled hierarchy (mg_params.pooled = 1) -- its working arena can be taken
+// from the device-memory pool now (mgi_bind: the pool evicts cached arenas of
+// idle hierarchies to make room, but never exceeds its budget and never takes
+// memory of running solves).  Requests that do not fit wait in the queue in
+// arrival order; later, smaller requests may pass a waiting one, but at most
+// kMaxBypass times, after which admission stops behind it until it fits.  A
+// resident hierarchy (pooled = 0) holds its arena since creation, outside the
+// pool, and is admitted by slots alone.  On completion the arena goes back to
+// the pool (kept as that hierarchy's cache until another request needs it).
 namespace {
+
+constexpr int kMaxBypass = 8;
 
 struct Req {
     uint64_t ticket = 0;
@@ -78,7 +97,8 @@ struct Req {
     const double* b = nullptr;
     double* u = nullptr;
     int state = 0;  // 0 queued, 1 running, 2 done
-    size_t bytes = 0;
+    int bypassed = 0;
+    bool waited_memory = false;
     mg_result res{};
 };
 
@@ -87,16 +107,15 @@ struct Engine {
     std::condition_variable cv;      // wakes the worker (new work)
     std::condition_variable done_cv; // wakes waiters (request finished)
     bool started = false;
-    bool configured = false;
-    size_t budget = 0;
     int max_inflight = 16;
-    size_t used = 0;
     uint64_t next_ticket = 1;
     std::deque<Req*> queue;
     std::vector<Req*> running;
     std::unordered_map<uint64_t, Req*> all;
     std::unordered_map<mgi_hier*, int> pending;
     std::unordered_set<mgi_hier*> busy;
+    uint64_t submitted = 0, completed = 0, memory_waits = 0;
+    int peak_inflight = 0;
 };
 
 Engine& engine() {
@@ -107,12 +126,48 @@ Engine& engine() {
 void finish(Engine& E, Req* r, const mg_result& res) {
     r->res = res;
     r->state = 2;
-    E.used -= r->bytes;
     E.busy.erase(r->h);
     E.pending[r->h] -= 1;
+    ++E.completed;
     for (size_t i = 0; i < E.running.size(); ++i)
         if (E.running[i] == r) { E.running.erase(E.running.begin() + i); break; }
     E.done_cv.notify_all();
+}
+
+// One admission pass over the queue (engine lock held).  Returns the
+// requests admitted, their arenas bound.
+std::vector<Req*> admit(Engine& E) {
+    std::vector<Req*> out;
+    std::vector<Req*> waiting;  // queued requests passed over in this pass
+    for (auto it = E.queue.begin(); it != E.queue.end();) {
+        Req* r = *it;
+        if ((int)E.running.size() >= E.max_inflight) break;
+        if (E.busy.count(r->h)) { ++it; continue; }
+        cudaSetDevice(r->h->device);
+        const mg_status st = mgi_bind(*r->h);
+        if (st == MG_BUSY) {  // does not fit the pool's budget now
+            if (!r->waited_memory) { r->waited_memory = true; ++E.memory_waits; }
+            if (r->bypassed >= kMaxBypass) break;  // nothing passes it any more
+            waiting.push_back(r);
+            ++it;
+            continue;
+        }
+        it = E.queue.erase(it);
+        if (st != MG_OK) {  // cannot be admitted at all: complete with the error
+            mg_result res{};
+            res.status = st;
+            E.running.push_back(r);
+            finish(E, r, res);
+            continue;
+        }
+        for (Req* w : waiting) ++w->bypassed;
+        E.busy.insert(r->h);
+        r->state = 1;
+        E.running.push_back(r);
+        E.peak_inflight = std::max(E.peak_inflight, (int)E.running.size());
+        out.push_back(r);
+    }
+    return out;
 }
 
 void worker() {
@@ -123,22 +178,13 @@ void worker() {
             std::unique_lock<std::mutex> lk(E.mu);
             if (E.queue.empty() && E.running.empty())
                 E.cv.wait(lk, [&] { return !E.queue.empty() || !E.running.empty(); });
-            for (auto it = E.queue.begin(); it != E.queue.end();) {
-                Req* r = *it;
-                if ((int)E.running.size() >= E.max_inflight) break;
-                if (E.busy.count(r->h) || E.used + r->bytes > E.budget) { ++it; continue; }
-                E.used += r->bytes;
-                E.busy.insert(r->h);
-                r->state = 1;
-                E.running.push_back(r);
-                to_begin.push_back(r);
-                it = E.queue.erase(it);
-            }
+            to_begin = admit(E);
         }
         for (Req* r : to_begin) {
             cudaSetDevice(r->h->device);
             mg_status st = mgi_solve_begin(*r->h, r->b, r->u);
             if (st != MG_OK) {
+                mgi_unbind(*r->h);
                 std::lock_guard<std::mutex> lk(E.mu);
                 mg_result res{};
                 res.status = st;
@@ -158,6 +204,11 @@ void worker() {
             int rc = q == cudaSuccess ? mgi_solve_advance(*r->h) : -MG_ERR_CUDA;
             progressed = true;
             if (rc == 0) continue;
+            if (rc < 0) {  // the arena goes back only once nothing of the solve runs
+                cudaStreamSynchronize(r->h->stream);
+                cudaGetLastError();
+                mgi_unbind(*r->h);
+            }
             mg_result res = r->h->ctx.res;
             if (rc < 0) res.status = -rc;
             std::lock_guard<std::mutex> lk(E.mu);
@@ -167,18 +218,8 @@ void worker() {
     }
 }
 
-size_t default_budget() {
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-        cudaGetLastError();
-        fr = (size_t)8 << 30;
-    }
-    return fr / 10 * 8;
-}
-
 void ensure_started(Engine& E) {
     if (E.started) return;
-    if (E.budget == 0) E.budget = default_budget();
     std::thread(worker).detach();
     E.started = true;
 }
@@ -189,15 +230,46 @@ extern "C" mg_status mg_serve_configure(size_t budget_bytes, int32_t max_infligh
     Engine& E = engine();
     std::lock_guard<std::mutex> lk(E.mu);
     if (max_inflight < 0) { mgi_set_error("max_inflight < 0"); return MG_ERR_INVALID; }
-    E.budget = budget_bytes ? budget_bytes : (E.started ? default_budget() : 0);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); mgi_set_error("no CUDA device"); return MG_ERR_CUDA; }
+    pool_set_budget(dev, budget_bytes);
     E.max_inflight = max_inflight > 0 ? max_inflight : 16;
-    E.configured = true;
+    return MG_OK;
+}
+
+extern "C" mg_status mg_serve_stats_get(mg_serve_stats* out) {
+    if (!out) { mgi_set_error("NULL argument"); return MG_ERR_INVALID; }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); mgi_set_error("no CUDA device"); return MG_ERR_CUDA; }
+    const PoolStats ps = pool_stats(dev);
+    Engine& E = engine();
+    std::lock_guard<std::mutex> lk(E.mu);
+    std::memset(out, 0, sizeof(*out));
+    out->budget_bytes = ps.budget;
+    out->reserved_bytes = ps.reserved;
+    out->in_use_bytes = ps.in_use;
+    out->peak_in_use_bytes = ps.peak_in_use;
+    out->peak_reserved_bytes = ps.peak_reserved;
+    out->arena_acquires = ps.acquires;
+    out->arena_reuses = ps.reuses;
+    out->arena_evictions = ps.evictions;
+    out->submitted = E.submitted;
+    out->completed = E.completed;
+    out->memory_waits = E.memory_waits;
+    out->inflight = (int32_t)E.running.size();
+    out->peak_inflight = E.peak_inflight;
+    out->queued = (int32_t)E.queue.size();
     return MG_OK;
 }
 
 extern "C" mg_status mg_submit(mg_hierarchy* hh, const double* b, double* u, uint64_t* ticket) {
     mgi_hier* h = reinterpret_cast<mgi_hier*>(hh);
     if (!h || !b || !u || !ticket) { mgi_set_error("NULL argument"); return MG_ERR_INVALID; }
+    if (h->p.pooled == 1 && h->lay.work_total > pool_budget(h->device)) {
+        mgi_set_error("request working arena " + std::to_string(h->lay.work_total) + " B exceeds the serving budget " +
+                      std::to_string(pool_budget(h->device)) + " B");
+        return MG_ERR_ADMISSION;
+    }
     Engine& E = engine();
     std::lock_guard<std::mutex> lk(E.mu);
     ensure_started(E);
@@ -205,17 +277,11 @@ extern "C" mg_status mg_submit(mg_hierarchy* hh, const double* b, double* u, uin
     r->h = h;
     r->b = b;
     r->u = u;
-    r->bytes = h->footprint;
-    if (r->bytes > E.budget) {
-        delete r;
-        mgi_set_error("request working set " + std::to_string(h->footprint) + " B exceeds the serving budget " +
-                      std::to_string(E.budget) + " B");
-        return MG_ERR_ADMISSION;
-    }
     r->ticket = E.next_ticket++;
     E.all[r->ticket] = r;
     E.pending[h] += 1;
     E.queue.push_back(r);
+    ++E.submitted;
     *ticket = r->ticket;
     E.cv.notify_all();
     return MG_OK;
@@ -230,7 +296,11 @@ extern "C" mg_status mg_poll(mg_hierarchy* hh, uint64_t ticket, mg_result* res) 
     Req* r = it->second;
     if (r->state != 2) return MG_BUSY;
     if (res) *res = r->res;
-    return (mg_status)r->res.status;
+    const mg_status st = (mg_status)r->res.status;
+    // the final poll retires the ticket (the engine keeps no finished requests)
+    E.all.erase(it);
+    delete r;
+    return st;
 }
 
 bool mgi_serve_busy(mgi_hier* h) {

@@ -31,7 +31,9 @@ VEC_C, VEC_G, VEC_T, VEC_U, VEC_R = range(5)
 EXPORTS = ["mg_params_init", "mg_level_count", "mg_last_error", "mg_footprint_bytes",
            "mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
            "mg_serve_configure", "mg_solve_batch", "mg_profile_solve", "mg_level_write", "mg_level_read",
-           "mg_level_info_get", "mg_run_stage", "mg_residual_norms_noalloc", "mg_axpy", "mg_describe_cycle"]
+           "mg_level_info_get", "mg_run_stage", "mg_residual_norms_noalloc", "mg_axpy", "mg_describe_cycle",
+           "mg_fault_inject", "mg_serve_stats_get"]
+FAULT_ARENA, FAULT_STAGING = 0, 1
 
 
 class Params(ctypes.Structure):
@@ -43,7 +45,8 @@ class Params(ctypes.Structure):
                 ("graph", ctypes.c_int32), ("no_tail", ctypes.c_int32), ("tune", ctypes.c_int32),
                 ("fuse_pre", ctypes.c_int32), ("rescale16", ctypes.c_int32), ("base_solver", ctypes.c_int32),
                 ("base_maxit", ctypes.c_int32), ("base_tol", ctypes.c_double), ("op", ctypes.c_int32),
-                ("scale_ahead", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("scale_ahead", ctypes.c_int32), ("wait_polls", ctypes.c_int32), ("pooled", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Result(ctypes.Structure):
@@ -54,6 +57,19 @@ class Result(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("reserved_bytes", ctypes.c_uint64),
+                ("in_use_bytes", ctypes.c_uint64), ("peak_in_use_bytes", ctypes.c_uint64),
+                ("peak_reserved_bytes", ctypes.c_uint64), ("arena_acquires", ctypes.c_uint64),
+                ("arena_reuses", ctypes.c_uint64), ("arena_evictions", ctypes.c_uint64),
+                ("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("memory_waits", ctypes.c_uint64),
+                ("inflight", ctypes.c_int32), ("peak_inflight", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved_"}
 
 
 class LevelInfo(ctypes.Structure):
@@ -133,6 +149,10 @@ def lib() -> ctypes.CDLL:
             L.mg_residual_norms_noalloc.restype = ctypes.c_int
             L.mg_axpy.argtypes = [i32, ctypes.c_int64, ctypes.c_double, vp, vp, vp]
             L.mg_axpy.restype = ctypes.c_int
+            L.mg_serve_stats_get.argtypes = [ctypes.POINTER(ServeStats)]
+            L.mg_serve_stats_get.restype = ctypes.c_int
+            L.mg_fault_inject.argtypes = [i32, i32]
+            L.mg_fault_inject.restype = ctypes.c_int
             for f in ("mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
                       "mg_serve_configure", "mg_solve_batch", "mg_level_write", "mg_level_read",
                       "mg_level_info_get", "mg_run_stage", "mg_profile_solve"):
@@ -355,6 +375,13 @@ def serve_configure(budget_bytes: int = 0, max_inflight: int = 0) -> None:
     _check(lib().mg_serve_configure(int(budget_bytes), int(max_inflight)), "mg_serve_configure")
 
 
+def serve_stats() -> dict:
+    """mg_serve_stats_get: the current device's memory pool and serving counters."""
+    st = ServeStats()
+    _check(lib().mg_serve_stats_get(ctypes.byref(st)), "mg_serve_stats_get")
+    return st.as_dict()
+
+
 def residual_norms_noalloc(dim: int, n: int, b, u, norms, stream=None) -> None:
     """mg_residual_norms_noalloc: writes ||b - A u||_2, ||b - A u||_inf and ||b||_2 into the
     3-element device array `norms`, enqueued on `stream` (default: torch's current stream).
@@ -370,3 +397,9 @@ def axpy(prec: int, a: float, x, y, stream=None) -> None:
     n = x.numel()
     _check(lib().mg_axpy(int(prec), ctypes.c_int64(n), ctypes.c_double(a), ctypes.c_void_p(_ptr(x)),
                          ctypes.c_void_p(_ptr(y)), ctypes.c_void_p(_stream_handle(stream))), "mg_axpy")
+
+
+def fault_inject(site: int, count: int) -> None:
+    """mg_fault_inject: the next `count` allocations at `site` (FAULT_ARENA,
+    FAULT_STAGING) fail as if the device were out of memory (host-side; 0 cancels)."""
+    _check(lib().mg_fault_inject(int(site), int(count)), "mg_fault_inject")

@@ -55,7 +55,7 @@ def test_ladders():
                                  dict(no_tail=5), dict(fuse_pre=3), dict(rescale16=2), dict(base_solver=2),
                                  dict(base_maxit=-1), dict(base_tol=-1.0), dict(base_tol=float("nan")),
                                  dict(op=2), dict(op=1, fuse_pre=1), dict(scale_ahead=2), dict(no_tail=3),
-                                 dict(base_maxit=100001)])
+                                 dict(base_maxit=100001), dict(wait_polls=-2), dict(pooled=2)])
 def test_invalid_params_rejected_without_gpu(bad):
     p = mg.make_params(3, 63)
     for k, v in bad.items():
@@ -96,3 +96,29 @@ def test_footprint_of_options():
     with_rescale = mg.footprint_bytes(mg.make_params(3, 127, dsh))
     without = mg.footprint_bytes(mg.make_params(3, 127, dsh, rescale16=0))
     assert with_rescale > without > 0
+
+
+def test_fault_inject_validates_its_arguments_without_gpu():
+    """mg_fault_inject is host-side: bad sites and counts are rejected, valid
+    requests are accepted and cancelled with count 0 (no device needed)."""
+    L = mg.lib()
+    assert L.mg_fault_inject(-1, 1) == 2 and L.mg_fault_inject(2, 1) == 2 and L.mg_fault_inject(0, -1) == 2
+    assert L.mg_fault_inject(mg.FAULT_ARENA, 3) == 0 and L.mg_fault_inject(mg.FAULT_ARENA, 0) == 0
+    assert L.mg_fault_inject(mg.FAULT_STAGING, 0) == 0
+
+
+def test_params_struct_matches_the_header():
+    """The binding's mg_params mirrors include/mg.h: the C size (compiled with gcc)
+    equals ctypes' size, and the defaults of the new fields."""
+    import subprocess
+    import tempfile
+    src = '#include <stdio.h>\n#include "mg.h"\nint main(void){printf("%zu %zu", sizeof(mg_params), sizeof(mg_result));return 0;}\n'
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "s.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "s")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, c])
+        out = subprocess.check_output([exe]).decode().split()
+    assert int(out[0]) == ctypes.sizeof(mg.Params) and int(out[1]) == ctypes.sizeof(mg.Result)
+    p = mg.make_params(3, 31)
+    assert p.wait_polls == -1 and p.pooled == 0 and list(p.reserved) == [0, 0, 0, 0]
