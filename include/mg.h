@@ -76,10 +76,10 @@ typedef struct mg_params {
                            coarsest level must have at most 4096 unknowns */
     int32_t prec[MG_MAX_LEVELS]; /* mg_prec per level, prec[0] = coarsest (base level),
                            prec[levels-1] = finest; default all MG_FP64 (D_MG) */
-    int32_t nu1, nu2;   /* pre-/post-smoothing sweeps (Alg. 1 steps 1 and 5); default 2, 2 */
+    int32_t nu1, nu2;   /* pre-/post-smoothing sweeps (Alg. 1's pre- and post-smoothing); default 2, 2 */
     double omega;       /* Jacobi damping; default 0.8 (the paper uses 2/3, Sec. 4.2) */
     int32_t gamma;      /* coarse visits per level: 1 = V-cycle (default), 2 = W-cycle */
-    int32_t scaling;    /* Alg. 2 line 4 scale alpha: 0 = none (alpha = 1, the paper's
+    int32_t scaling;    /* the scale alpha of Alg. 2's residual scaling: 0 = none (alpha = 1, the paper's
                            choice for D_MG, Sec. 6), 1 = ||r||_inf (default), 2 = ||r||_2 */
     int32_t sigma_log2; /* the scaled residual is r * 2^sigma_log2 / alpha, so its inf-norm
                            is 2^sigma_log2 (scaling = 1); -1 = automatic: 14 when any
@@ -132,7 +132,7 @@ typedef struct mg_params {
                            product of full weighting, A and interpolation).  op = 1
                            requires fuse_pre = 0 */
     int32_t scale_ahead;/* 1 (default): with scaling = 1 and a non-FP64 finest level, the fused
-                           IR update (Alg. 2 lines 6-7) also writes the next step's g =
+                           IR update (Alg. 2's solution and residual updates) also writes the next step's g =
                            cast(r * 2^k) (line 4), with 2^k = 2^sigma_log2 / 2^e and 2^e the
                            power of two just above the previous ||r||_inf, so the separate
                            scale-and-cast pass over the FP64 residual is skipped; alpha is
@@ -206,7 +206,7 @@ size_t mg_footprint_bytes(const mg_params* p);
  * them, computed on the host without a device: the Alg. 1 recursion (nu1
  * pre-smoothing sweeps, residual-restriction, gamma visits of the coarser
  * level, prolongation, nu2 post-smoothing sweeps; base solve on level 0),
- * preceded by the scale-and-cast of Alg. 2 line 4, with the coarse tail and
+ * preceded by the scale-and-cast of Alg. 2's residual scaling, with the coarse tail and
  * the FP16 rescale of Sec. 6 where the hierarchy has them.
  * rec receives records of 6 int32 values (caller-owned, 6 * cap entries):
  *   kind    0 stencil kernel, 1 base solve, 3 zero fill, 7 coarse-tail
@@ -424,14 +424,14 @@ mg_status mg_level_info_get(const mg_hierarchy* h, int32_t level, mg_level_info*
 /* One step of the method on one level, run on the hierarchy's stream:
  *   MG_STAGE_JACOBI        C <- C + omega D^-1 (G - A C)          (Sec. 4.2)
  *   MG_STAGE_JACOBI_ZERO2  C <- two damped Jacobi sweeps from C = 0 on G
- *   MG_STAGE_RESTRICT      G_{l-1} <- cast(R (G_l - A_l C_l))     (Alg. 1 step 2)
- *   MG_STAGE_PROLONG       C_l <- C_l + cast(s P C_{l-1})         (Alg. 1 step 4);
+ *   MG_STAGE_RESTRICT      G_{l-1} <- cast(R (G_l - A_l C_l))     (Alg. 1's residual restriction)
+ *   MG_STAGE_PROLONG       C_l <- C_l + cast(s P C_{l-1})         (Alg. 1's prolongation and correction);
  *                          s = arg[0] when arg is not NULL (a rescaled coarse level), else 1
  *   MG_STAGE_JACOBI_PROLONG  C_l <- C_l + P C_{l-1}, then one Jacobi sweep
  *   MG_STAGE_COARSE        C_0 <- A_0^-1 G_0 (level 0 only; the base_solver in effect)
- *   MG_STAGE_SCALE_ZERO2   G_L <- cast(R * s) (Alg. 2 line 4), then JACOBI_ZERO2 on
+ *   MG_STAGE_SCALE_ZERO2   G_L <- cast(R * s) (Alg. 2's residual scaling), then JACOBI_ZERO2 on
  *                          level L; s = arg[0]
- *   MG_STAGE_IR_UPDATE     U <- U + a C_L;  R <- R - a A C_L;  a = arg[0]  (Alg. 2 l. 6-7)
+ *   MG_STAGE_IR_UPDATE     U <- U + a C_L;  R <- R - a A C_L;  a = arg[0]  (Alg. 2's solution and residual updates)
  *   MG_STAGE_RESIDUAL      R <- B - A U with B = arg pointer (n^d FP64, device)
  *   MG_STAGE_CYCLE         C_L <- one full cycle on G_L (Alg. 1, recursive)
  *   MG_STAGE_PRE_RESTRICT  C <- two damped Jacobi sweeps from C = 0 on G, then

@@ -20,9 +20,9 @@
  *   or_residual       IR step 1, r = b - A u (Sec. 4.1)
  *   or_jacobi         damped Jacobi smoothing step (Sec. 4.2, smoother paragraph)
  *   or_restrict       restriction of a residual to the next coarser grid
- *                     (Alg. 1 step 2): full weighting
+ *                     (Alg. 1's residual restriction): full weighting
  *   or_prolong_add    transfer of the coarse correction to the fine grid and
- *                     update (Alg. 1 step 4): bi/trilinear interpolation
+ *                     update (Alg. 1's prolongation and correction): bi/trilinear interpolation
  *   or_coarse_solve   exact solve on the base level (Sec. 4.2: "an exact solve
  *                     is applied at the coarsest level")
  *   or_cycle          Alg. 1 applied recursively (V-cycle; gamma = 2 gives the
@@ -45,7 +45,7 @@
  * divides the correction by it again (Sec. 4.3), and a restriction from a
  * non-FP16 level into an FP16 level is rescaled by a power of two taken from
  * its max-norm and undone on prolongation (Sec. 6, DSH_MG).  With scale_ahead
- * the scale of Alg. 2 line 4 is instead the power of two 2^sigma / 2^e with
+ * the scale of Alg. 2's residual scaling is instead the power of two 2^sigma / 2^e with
  * 2^(e-1) <= ||r||_inf < 2^e of the previous step's residual (any scale is
  * exact in exact arithmetic), and the scaled residual is truncated to FP32
  * before the cast, as when the update itself forms the next right-hand side.
@@ -292,7 +292,7 @@ void or_jacobi(int d, int n, double omega, const double *g, const double *v, dou
 static double fw(int o) { return o == 0 ? 0.5 : 0.25; }
 
 /*
- * Restriction (Alg. 1 step 2): full weighting, the tensor product of the 1-D
+ * Restriction (Alg. 1's residual restriction): full weighting, the tensor product of the 1-D
  * stencil [1/4, 1/2, 1/4] centred on the fine point 2I+1 that coincides with
  * coarse point I.  nf = 2 nc + 1.
  */
@@ -329,7 +329,7 @@ static void lin1d(int i, int *cnt, int idx[2], double wt[2]) {
 }
 
 /*
- * Prolongation and correction (Alg. 1 step 4): cf += P cc, with P the
+ * Prolongation and correction (Alg. 1's prolongation and correction): cf += P cc, with P the
  * tensor-product (bi/trilinear) interpolation.  nf = 2 nc + 1.
  */
 void or_prolong_add(int d, int nc, const double *cc, double *cf) {
@@ -614,7 +614,7 @@ double or_norminf(size_t N, const double *v) {
  *   r = b - A u
  *   while the stopping test fails:
  *     alpha = ||r|| (inf-norm, 2-norm, or 1 without scaling)
- *     g = (1/alpha) r                       (Alg. 2 line 4)
+ *     g = (1/alpha) r                       (Alg. 2's residual scaling)
  *     c = one multigrid cycle for A c = g   (line 5)
  *     u = u + alpha c                       (line 6)
  *     r = r - alpha A c                     (line 7)
@@ -637,7 +637,7 @@ double or_trunc_f32(double x) {
     return copysign(ldexp(m, E - 24), x);
 }
 
-/* Scale-ahead cast of the emulation (reading R21 of Alg. 2 line 4): g =
+/* Scale-ahead cast of the emulation (reading R21 of Alg. 2's residual scaling): g =
    cast_fmt(trunc_f32(r inv)).  Returns 1 when some truncated value lies at or
    beyond the format's overflow threshold (it would round to infinity: 65520
    for FP16, the midpoint above FP16's largest finite value; 3.0e38 as a bound

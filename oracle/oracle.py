@@ -136,7 +136,7 @@ def jacobi(g, v, omega: float, op: int = 0) -> np.ndarray:
 
 
 def restrict(r) -> np.ndarray:
-    """Full-weighting restriction to the next coarser grid (Alg. 1 step 2)."""
+    """Full-weighting restriction to the next coarser grid (Alg. 1's residual restriction)."""
     r = _f64(r)
     d, nf = _dn(r)
     nc = (nf - 1) // 2
@@ -146,7 +146,7 @@ def restrict(r) -> np.ndarray:
 
 
 def prolong_add(cc, cf) -> np.ndarray:
-    """cf + P cc with bi/trilinear interpolation P (Alg. 1 step 4); returns a new array."""
+    """cf + P cc with bi/trilinear interpolation P (Alg. 1's prolongation and correction); returns a new array."""
     cc = _f64(cc)
     out = _f64(cf).copy()
     d, nc = _dn(cc)
@@ -211,7 +211,7 @@ def trunc_f32(x) -> np.ndarray:
 
 def scale_ahead_cast(fmt: int, r, inv: float):
     """The emulated scale-ahead cast g = round_fmt(trunc_f32(r inv)) (reading R21
-    of Alg. 2 line 4).  Returns (g, over): over is True when a truncated value
+    of Alg. 2's residual scaling).  Returns (g, over): over is True when a truncated value
     reaches the format's overflow threshold (the step then falls back to the
     plain scale-and-cast)."""
     r = _f64(r)

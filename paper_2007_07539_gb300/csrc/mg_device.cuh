@@ -6,7 +6,7 @@
 // F2F/I2F conversions to and from FP64), against ~22 bytes per clock per SM
 // of HBM bandwidth.  The mixed-precision kernels therefore keep FP64 as a
 // storage format: they build FP64 bit patterns with integer instructions and
-// spend FP64 instructions only on the fused multiply-adds of Alg. 2 lines 6-7.
+// spend FP64 instructions only on the fused multiply-adds of Alg. 2's solution and residual updates.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>

@@ -431,7 +431,7 @@ struct Gen {
     // Alg. 1 on level l; first = zero initial correction (first visit).
     void cycle(int l, bool first) {
         const int L = h->nlev - 1;
-        if (l == L && top_from_r && !h->g_alias_r)  // Alg. 2 line 4: g_L = cast(r / alpha)
+        if (l == L && top_from_r && !h->g_alias_r)  // Alg. 2's residual scaling: g_L = cast(r / alpha)
             out->push_back(kernel(L, K_SCALE, 0, nullptr, h->lv[L].g, nullptr));
         if (l == h->tail_level && (h->tail_prog || h->describe_only)) {
             Op op{};
@@ -1088,7 +1088,7 @@ static int launch_residual(mgi_hier& h, cudaStream_t s, double* r, int copy_u, i
     return launch_finalize(fin_kind, h.st, h.partials, nb, s);
 }
 
-// Alg. 2 line 2: r = b - A u0 (or r = b for u0 = 0), then the first stopping test.
+// Alg. 2's initial residual: r = b - A u0 (or r = b for u0 = 0), then the first stopping test.
 static int launch_init(mgi_hier& h, cudaStream_t s) {
     const Geom& g = h.lv[h.nlev - 1].geo;
     if (h.p.zero_guess) {

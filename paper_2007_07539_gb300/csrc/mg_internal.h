@@ -87,9 +87,9 @@ struct DevState {
 // Kernel kinds of the fine-level TUs.
 enum Kind : int {
     K_SWEEP = 0,    // stencil sweep (mode below)
-    K_UPDATE = 1,   // u += alpha c; r -= alpha A c; norm partials (Alg. 2 lines 6-7)
-    K_SCALE = 2,    // g = cast(r * inv) (Alg. 2 line 4)
-    K_PROLONG = 3,  // c += P c_coarse (Alg. 1 step 4)
+    K_UPDATE = 1,   // u += alpha c; r -= alpha A c; norm partials (Alg. 2's solution and residual updates)
+    K_SCALE = 2,    // g = cast(r * inv) (Alg. 2's residual scaling)
+    K_PROLONG = 3,  // c += P c_coarse (Alg. 1's prolongation and correction)
 };
 
 enum Mode : int {

@@ -2,17 +2,17 @@
 //
 // k_sweep3 / k_sweep2: every grid pass that applies the 5/7-point operator
 // A_l (Sec. 5) to a stored level vector:
-//   M_JACOBI    damped Jacobi sweep (Sec. 4.2; Alg. 1 steps 1, 5)
+//   M_JACOBI    damped Jacobi sweep (Sec. 4.2; Alg. 1's pre- and post-smoothing)
 //   M_ZERO2     the first two sweeps of a pre-smoothing from c = 0, fused
-//               (Alg. 1 step 1 with a zero initial guess)
+//               (Alg. 1's pre-smoothing with a zero initial guess)
 //   M_ZERO1     one sweep from c = 0 (c = omega D^-1 g)
 //   M_RESTRICT  residual g - A c and its full-weighting restriction to the next
-//               coarser level with the precision change (Alg. 1 step 2)
-// k_update: Alg. 2 lines 6-7 fused (the paper's UpdateResiduum_Correction),
+//               coarser level with the precision change (Alg. 1's residual restriction)
+// k_update: Alg. 2's solution and residual updates fused (the paper's UpdateResiduum_Correction),
 //   u += alpha c and r -= alpha A c in FP64 with norm partials.
-// k_scale_cast: Alg. 2 line 4, the scaled FP64 residual cast to the finest
+// k_scale_cast: Alg. 2's residual scaling, the scaled FP64 residual cast to the finest
 //   level's storage type.
-// k_prolong: Alg. 1 step 4, prolongation and correction.
+// k_prolong: Alg. 1's prolongation and correction, prolongation and correction.
 //
 // 3D sweep decomposition: a CTA of TY warps owns TY consecutive rows of one
 // 32V-wide x-chunk (V = elements per 16-byte vector: 8 FP16/BF16, 4 FP32,
@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(256) k_drestrict3_batch(const KItem* __restric
 }
 
 // ---------------------------------------------------------------- 3D one-pass pre-smoothing + restriction
-// Temporal blocking of Alg. 1 steps 1-2 on one level (M_PRE): for a tile of
+// Temporal blocking of Alg. 1's pre-smoothing and residual restriction on one level (M_PRE): for a tile of
 // R = 2TJ+1 fine rows and 2TK+1 fine planes it computes the two damped
 // Jacobi sweeps from zero, c = w D^-1 [(2 - w) g + (w/2d) N g], on R+2 rows
 // (one halo row each side), rounds c to the storage type and writes it, then
@@ -1051,7 +1051,7 @@ __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
     cp_wait<0>();
 }
 
-// ---------------------------------------------------------------- scale and cast (Alg. 2 line 4)
+// ---------------------------------------------------------------- scale and cast (Alg. 2's residual scaling)
 // Multiplication by inv split as 2^E * m, m in [1, 2): the exponent is added
 // to the FP64 bit pattern with an integer add (exact), the significand product
 // is done in FP32, then one rounding to the storage type.  No FP64 instruction.
@@ -1124,7 +1124,7 @@ __global__ void __launch_bounds__(256) k_scale_cast_batch(const KItem* __restric
     scale_cast_body<DIM, T>(it.a, blockIdx.x - it.cta_begin, it.ncta);
 }
 
-// ---------------------------------------------------------------- FP64 IR update (Alg. 2 lines 6-7)
+// ---------------------------------------------------------------- FP64 IR update (Alg. 2's solution and residual updates)
 // S = 2d c0 - (sum of neighbours) exactly, as FP64.
 template <class T> struct ExactStencil;
 template <> struct ExactStencil<__half> {
@@ -1265,7 +1265,7 @@ __device__ __forceinline__ void st4(T* p, const float (&v)[4]) {
 // One thread per 4 consecutive points of a padded row.  u and r (FP64, 32 of
 // the 34-36 bytes per point) stream through coalesced 16-byte loads and
 // stores; the stencil of c comes through the read-only cache as vector loads.
-// FP64 instructions per point: the two fused multiply-adds of Alg. 2 lines 6-7
+// FP64 instructions per point: the two fused multiply-adds of Alg. 2's solution and residual updates
 // (three for FP32/BF16 corrections) and one for the sum of squares; A c is
 // formed exactly with integer / FP32 instructions.  The last CTA to finish
 // runs the step's finalisation.
@@ -1285,7 +1285,7 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
     const double beta = alpha * a.h2inv;
     SqAcc64 sq;
     unsigned long long nmax = 0ull;
-    // scale-ahead (Alg. 2 line 4 of the next step, fused): g = cast(r inv_pred),
+    // scale-ahead (Alg. 2's residual scaling of the next step, fused): g = cast(r inv_pred),
     // inv_pred a power of two; a value beyond T's range is flagged (and the
     // next step falls back to the separate scale-and-cast)
     T* const gout = (!std::is_same<T, double>::value && a.st && a.st->scale_ahead && a.dst)
@@ -1513,7 +1513,7 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
     write_partials(sq, nmax, E, a.partials, cta);
     if (a.fin && a.st) {
         // the last CTA to finish reduces every CTA's partials and runs the
-        // step's finalisation (Alg. 2 line 8 and the next scale): no separate
+        // step's finalisation (Alg. 2's stopping test and the next scale): no separate
         // launch.  Partials are published by a fence before the ticket.
         DevState* st = const_cast<DevState*>(a.st);
         __shared__ int last;
@@ -1546,7 +1546,7 @@ __global__ void __launch_bounds__(256) k_update_batch(const KItem* __restrict__ 
     update_body<DIM, T, OP>(it.a, blockIdx.x - it.cta_begin, it.ncta);
 }
 
-// ---------------------------------------------------------------- prolongation (Alg. 1 step 4)
+// ---------------------------------------------------------------- prolongation (Alg. 1's prolongation and correction)
 // c_fine += P c_coarse (bi/trilinear).  One thread per V consecutive fine x
 // (x even) and a pair of fine rows (2j+1, 2j+2) -- and in 3D a pair of fine
 // planes (2k+1, 2k+2) -- which share coarse rows j, j+1 and planes k, k+1:

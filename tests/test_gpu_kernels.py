@@ -47,7 +47,7 @@ def dinv(dim, n):
 
 def gscale(dim, n, prec):
     """Right-hand side scale.  FP16 data are kept at the magnitudes the solver gives them
-    (scaled residual of inf-norm 2^14, Alg. 2 line 4, so corrections of size 2^14 h^2):
+    (scaled residual of inf-norm 2^14, Alg. 2's residual scaling, so corrections of size 2^14 h^2):
     above FP16's subnormal range and with residuals below its overflow threshold."""
     return 2.0**13 if prec == mg.FP16 else 1.0 / dinv(dim, n)
 
@@ -96,7 +96,7 @@ def test_jacobi_sweep(oracle, case):
 
 @pytest.mark.parametrize("case", CASES, ids=ids)
 def test_two_sweeps_from_zero(oracle, case):
-    """Pre-smoothing from c = 0 (Alg. 1 step 1), two sweeps fused in one pass."""
+    """Pre-smoothing from c = 0 (Alg. 1's pre-smoothing), two sweeps fused in one pass."""
     dim, n, prec = case
     with hier(dim, n, prec) as h:
         L = h.nlev - 1
@@ -128,7 +128,7 @@ def two_level_precs(n, pf, pc):
 
 @pytest.mark.parametrize("case", RCASES, ids=rids)
 def test_residual_restriction(oracle, case):
-    """Alg. 1 step 2: g_{l-1} = cast(R (g_l - A_l c_l)), full weighting, fused."""
+    """Alg. 1's residual restriction: g_{l-1} = cast(R (g_l - A_l c_l)), full weighting, fused."""
     dim, n, pf, pc = case
     with hier(dim, n, two_level_precs(n, pf, pc)) as h:
         L = h.nlev - 1
@@ -146,7 +146,7 @@ def test_residual_restriction(oracle, case):
 
 @pytest.mark.parametrize("case", [c for c in RCASES if c[0] == 3], ids=rids)
 def test_one_pass_presmoothing_and_restriction(oracle, case):
-    """Alg. 1 steps 1-2 in one pass (temporal blocking): c = two sweeps from zero on g,
+    """Alg. 1's pre-smoothing and residual restriction in one pass (temporal blocking): c = two sweeps from zero on g,
     g_{l-1} = cast(R (g - A c)).  Against the oracle, and bit for bit against the two
     separate kernels."""
     dim, n, pf, pc = case
@@ -178,7 +178,7 @@ def test_one_pass_presmoothing_and_restriction(oracle, case):
 
 @pytest.mark.parametrize("case", RCASES, ids=rids)
 def test_prolongation_and_correction(oracle, case):
-    """Alg. 1 step 4: c_l += cast(P c_{l-1}), bi/trilinear interpolation."""
+    """Alg. 1's prolongation and correction: c_l += cast(P c_{l-1}), bi/trilinear interpolation."""
     dim, n, pf, pc = case
     nc = (n - 1) // 2
     with hier(dim, n, two_level_precs(n, pf, pc)) as h:
@@ -196,7 +196,7 @@ def test_prolongation_and_correction(oracle, case):
 
 @pytest.mark.parametrize("case", RCASES, ids=rids)
 def test_prolongation_fused_into_sweep(oracle, case):
-    """Alg. 1 steps 4-5 fused: one Jacobi sweep applied to c_l + P c_{l-1}."""
+    """Alg. 1's prolongation and post-smoothing fused: one Jacobi sweep applied to c_l + P c_{l-1}."""
     dim, n, pf, pc = case
     nc = (n - 1) // 2
     with hier(dim, n, two_level_precs(n, pf, pc)) as h:
@@ -232,7 +232,7 @@ def test_base_level_solve(oracle, dim, n, prec):
 @pytest.mark.parametrize("dim,n,prec", [(3, 47, mg.FP16), (3, 95, mg.BF16), (3, 63, mg.FP32), (3, 31, mg.FP64),
                                         (2, 511, mg.FP16), (2, 127, mg.FP64), (3, 287, mg.FP16)])
 def test_scale_cast_and_first_sweeps(oracle, dim, n, prec):
-    """Alg. 2 line 4 (r_low = cast(r/alpha), here r * 2^14/||r||_inf) fused with the first
+    """Alg. 2's residual scaling (r_low = cast(r/alpha), here r * 2^14/||r||_inf) fused with the first
     two sweeps.  The residual is tiny (1e-12 scale) to exercise the FP32-free rescaling."""
     r = rnd(dim, n, 12, 3e-12)
     r[tuple([0] * dim)] = 0.0
@@ -257,7 +257,7 @@ def test_scale_cast_and_first_sweeps(oracle, dim, n, prec):
                          [(3, 287, mg.FP16), (2, 511, mg.FP16), (2, 127, mg.BF16), (2, 255, mg.FP64),
                           (2, 127, mg.FP32)])
 def test_ir_update(oracle, dim, n, prec):
-    """Alg. 2 lines 6-7 in one kernel: u += alpha c, r -= alpha A c in FP64, with
+    """Alg. 2's solution and residual updates in one kernel: u += alpha c, r -= alpha A c in FP64, with
     ||r||_2 and ||r||_inf.  r is built so that the update cancels most of it."""
     alpha = 3.7e-6
     with hier(dim, n, prec) as h:

@@ -329,7 +329,7 @@ def test_pinned_host_initial_guess_in_place():
 
 @pytest.mark.parametrize("dim,n,lad", [(3, 63, "D"), (2, 127, "D"), (3, 63, "H"), (2, 127, "H"), (3, 63, "BSD")])
 def test_guard_restart_continues_from_the_true_residual(oracle, dim, n, lad):
-    """Reading R3 (Alg. 2 line 7 updates r recursively; Sec. 4.3 speaks of
+    """Reading R3 (Alg. 2's residual update updates r recursively; Sec. 4.3 speaks of
     recomputing the residuum): an initial guess of size 1e6 makes the recursively
     updated FP64 residual drift from b - A u by the rounding of the early, large
     updates of u (about 1e-16 x ||A|| x 1e6).  When the recursive residual passes

@@ -262,7 +262,7 @@ def test_emulated_fp16_cg_is_a_low_precision_cg(oracle):
 
 @pytest.mark.parametrize("dim,n,case", [(3, 31, "random"), (2, 127, "random"), (2, 255, "fd_k1"), (3, 31, "q1_k1")])
 def test_scale_ahead_keeps_the_iteration_count(oracle, dim, n, case):
-    """The scale of Alg. 2 line 4 taken as the power of two from the previous step's
+    """The scale of Alg. 2's residual scaling taken as the power of two from the previous step's
     max-norm, with the scaled residual truncated to FP32 before the cast: a different
     scale (the histories differ) but the same number of refinement steps, for FP16,
     HSD and BF16 ladders."""

@@ -347,7 +347,7 @@ def test_ir_manufactured_discrete_solution_exact(oracle, dim, n):
 
 
 def test_ir_scaling_invariance(oracle):
-    """Alg. 2 lines 4, 6, 7: the scale alpha is compensated, so in FP64 the iterates do not
+    """Alg. 2's residual scaling and updates: the scale alpha is compensated, so in FP64 the iterates do not
     depend on the scaling choice beyond rounding (a missing compensation breaks this)."""
     b = I.random_rhs(3, 31, 22)
     u0, i0, h0 = oracle.ir_solve(b, scaling=0)

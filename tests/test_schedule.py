@@ -1,7 +1,7 @@
 """The library's schedule of one IR step, read through mg_describe_cycle (host
 only, no GPU), against the structure of Alg. 1 and Alg. 2:
 
-- the scale-and-cast of Alg. 2 line 4 first (unless g is the FP64 residual);
+- the scale-and-cast of Alg. 2's residual scaling first (unless g is the FP64 residual);
 - per visit of level l >= 1: nu1 pre-smoothing sweeps (from zero on a first
   visit), one residual-restriction, gamma visits of level l - 1, one
   prolongation, nu2 post-smoothing sweeps; level l is visited gamma^(L - l)
@@ -78,7 +78,7 @@ def test_cycle_follows_alg1(dim, n, lad, gamma, nu, no_tail):
     nlev = len(mg.level_count(n))
     recs = describe(dim, n, lad, gamma=gamma, nu1=nu, nu2=nu, no_tail=no_tail)
     assert counts(recs) == expected(nlev, gamma, nu, nu)
-    # Alg. 2 line 4 first; no IR update inside the cycle
+    # Alg. 2's residual scaling first; no IR update inside the cycle
     assert recs[0]["kind"] == KERNEL and recs[0]["kernel"] == K_SCALE and recs[0]["level"] == nlev - 1
     assert not any(r["kind"] == KERNEL and r["kernel"] == K_UPDATE for r in recs)
 
