@@ -387,39 +387,53 @@ def extra_workloads(mg, I, torch, flush, quick=False):
             h.solve(bb, torch.zeros_like(bb))
         del bb
     torch.cuda.synchronize()
-    st0 = mg.serve_stats()
-    t0 = time.perf_counter()
-    pending, lat, statuses = {}, [], []
-    i = 0
-    while i < len(reqs) or pending:
-        now = time.perf_counter() - t0
-        while i < len(reqs) and arr[i] <= now:
-            pending[i] = served[i].submit(bufs[i], us[i])
-            i += 1
-        for j in list(pending):
-            r = served[j].poll(pending[j])
-            if r is not None:
-                lat.append(time.perf_counter() - t0 - arr[j])
-                statuses.append(r["status"])
-                del pending[j]
-        time.sleep(0.0002)
-    t_s = time.perf_counter() - t0
-    st1 = mg.serve_stats()
     dof_s = sum(q["n"] ** q["dim"] for q in reqs)
-    lat_ms = sorted(1e3 * x for x in lat)
-    out["serving"] = {"requests": len(reqs), "ladder": "FP16 fine / FP32 coarse (HS)", "rate_per_s": rate,
-                      "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-                      "served_dofs": dof_s / t_s, "wall_s": t_s, "all_ok": all(x == 0 for x in statuses),
-                      "serial_fp16_device_ms": t_fp16, "serial_fp64_device_ms": t_fp64,
-                      "serial_fp64_dofs": dof_s / (t_fp64 * 1e-3),
-                      "serial_times": "per request shape, median of 3 FP16 / 1 FP64 device-timed solves, summed over the stream",
-                      "pool_budget_bytes": budget, "pool_peak_reserved_bytes": st1["peak_reserved_bytes"],
-                      "pool_peak_in_use_bytes": st1["peak_in_use_bytes"],
-                      "requests_that_waited_for_memory": st1["memory_waits"] - st0["memory_waits"],
-                      "arena_reuses": st1["arena_reuses"] - st0["arena_reuses"],
-                      "arena_evictions": st1["arena_evictions"] - st0["arena_evictions"],
-                      "peak_inflight": st1["peak_inflight"], "hierarchies": per_shape * len(shapes),
-                      "shapes": len(shapes)}
+
+    def stream(merge):
+        """One pass of the request stream; returns its latency / throughput / pool record."""
+        mg.serve_options(merge)
+        torch.cuda.synchronize()
+        st0 = mg.serve_stats()
+        t0 = time.perf_counter()
+        pending, lat, slow, statuses = {}, [], [], []
+        i = 0
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and arr[i] <= now:
+                pending[i] = served[i].submit(bufs[i], us[i])
+                i += 1
+            for j in list(pending):
+                r = served[j].poll(pending[j])
+                if r is not None:
+                    lat.append(time.perf_counter() - t0 - arr[j])
+                    slow.append(lat[-1] / (1e-3 * t16[(reqs[j]["dim"], reqs[j]["n"])]))
+                    statuses.append(r["status"])
+                    del pending[j]
+            time.sleep(0.0002)
+        t_s = time.perf_counter() - t0
+        st1 = mg.serve_stats()
+        mg.serve_options(False)
+        lat_ms = sorted(1e3 * x for x in lat)
+        return {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "slowdown_p50": float(np.percentile(slow, 50)), "slowdown_p99": float(np.percentile(slow, 99)),
+                "slowdown": "latency over the request shape's serial device time",
+                "served_dofs": dof_s / t_s, "wall_s": t_s, "all_ok": all(x == 0 for x in statuses),
+                "pool_peak_reserved_bytes": st1["peak_reserved_bytes"], "pool_peak_in_use_bytes": st1["peak_in_use_bytes"],
+                "requests_that_waited_for_memory": st1["memory_waits"] - st0["memory_waits"],
+                "arena_reuses": st1["arena_reuses"] - st0["arena_reuses"],
+                "arena_evictions": st1["arena_evictions"] - st0["arena_evictions"],
+                "merged_requests": st1["merged_requests"] - st0["merged_requests"],
+                "merged_groups": st1["merged_groups"] - st0["merged_groups"], "peak_inflight": st1["peak_inflight"]}
+
+    plain = stream(False)
+    merged = stream(True)  # requests admitted together run as level-synchronous groups
+    out["serving"] = dict(plain, requests=len(reqs), ladder="FP16 fine / FP32 coarse (HS)", rate_per_s=rate,
+                          serial_fp16_device_ms=t_fp16, serial_fp64_device_ms=t_fp64,
+                          serial_fp64_dofs=dof_s / (t_fp64 * 1e-3),
+                          serial_times="per request shape, median of 3 FP16 / 1 FP64 device-timed solves, summed "
+                                       "over the stream",
+                          pool_budget_bytes=budget, hierarchies=per_shape * len(shapes), shapes=len(shapes),
+                          with_merged_groups=merged)
     for hl in pool_h.values():
         for h in hl:
             h.close()
@@ -464,7 +478,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="tile shapes from the wave model instead of the autotuner")
     ap.add_argument("--kernel-dump", default=None, help="write every kernel's profiled time to this JSON file")
     ap.add_argument("--ncu-case", action="store_true",
-                    help="only two FP16 solves of the workload (a small launch list for ncu captures)")
+                    help="only two solves of the workload, kernel by kernel (a small launch list for ncu captures)")
+    ap.add_argument("--ncu-ladder", default="H", choices=["H", "D"],
+                    help="with --ncu-case: H (FP16 levels, the default) or D (all-FP64 MG, no scaling)")
     ap.add_argument("--op", type=int, default=0, choices=[0, 1],
                     help="operator: 0 the 7-point finite-difference stencil (the headline workload), "
                          "1 the trilinear Q1 finite elements of Sec. 5")
@@ -503,7 +519,10 @@ def main():
     graph = 0 if args.ncu_case else args.graph
     # tile shapes of the stencil kernels autotuned at creation (results do not depend on them)
     tune = 0 if args.no_tune else 1
-    hH = mg.Hierarchy(mg.make_params(DIM, N, "H", zero_guess=1, graph=graph, tune=tune, op=args.op))
+    # fuse_pre = 2: the autotuner also picks, per level, one fused pre-smoothing + restriction
+    # pass or two launches (sweeps per launch)
+    hH = mg.Hierarchy(mg.make_params(DIM, N, "H", zero_guess=1, graph=graph, tune=tune, op=args.op,
+                                     fuse_pre=2 if tune and args.op == 0 else 0))
     hD = mg.Hierarchy(mg.make_params(DIM, N, "D", zero_guess=1, scaling=0, graph=graph, tune=tune, op=args.op))
 
     def run(h, bb, uu, k):
@@ -518,9 +537,9 @@ def main():
         return secs, res
 
     if args.ncu_case:
-        run(hH, bd, ud, 2)
+        run(hD if args.ncu_ladder == "D" else hH, bd, ud, 2)
         torch.cuda.synchronize()
-        print(json.dumps({"ncu_case": "2 FP16 solves done"}), flush=True)
+        print(json.dumps({"ncu_case": f"2 {'FP64' if args.ncu_ladder == 'D' else 'FP16'} solves done"}), flush=True)
         return 0
     run(hH, bd, ud, args.warmup)
     run(hD, bd, ud, max(1, min(args.warmup, 2)))
@@ -595,6 +614,8 @@ def main():
                    "b and u (133 MB each) exceed the 129 MB L2", "wall_s_timed_region": wall,
                    "parallelism": f"{world} independent instance(s), one per GPU, no collective on the data path",
                    "tile_shapes": "autotuned at creation" if tune else "wave model",
+                   "pre_smoothing_launches_per_level": {hH.level_info(l)["n"]: hH.level_info(l)["pre_launches"]
+                                                        for l in range(hH.nlev) if hH.level_info(l)["tail_ctas"] == 0},
                    "hbm_frac_finest_jacobi": finest_frac(0, 0), "hbm_frac_finest_zero_start": finest_frac(0, 1),
                    "hbm_frac_finest_residual_restrict": finest_frac(0, 3), "hbm_frac_finest_prolong": finest_frac(2),
                    "hbm_frac_ir_update": finest_frac(5),
@@ -622,7 +643,12 @@ def main():
                   "n511_fp64_iters": e5["fp64_mg_iters"], "n511_oracle_iters": oracle_iters("3d_n511_manufactured"),
                   "batched_dofs": ex["batched_64"]["batch_dofs"],
                   "serving_p50_ms": ex["serving"]["p50_ms"], "serving_p99_ms": ex["serving"]["p99_ms"],
-                  "serving_dofs": ex["serving"]["served_dofs"]})
+                  "serving_dofs": ex["serving"]["served_dofs"],
+                  "serving_merged_p50_ms": ex["serving"]["with_merged_groups"]["p50_ms"],
+                  "serving_merged_p99_ms": ex["serving"]["with_merged_groups"]["p99_ms"],
+                  "serving_merged_dofs": ex["serving"]["with_merged_groups"]["served_dofs"],
+                  "serving_pool_peak_bytes": ex["serving"]["pool_peak_reserved_bytes"],
+                  "serving_pool_budget_bytes": ex["serving"]["pool_budget_bytes"]})
         c["extras"] = ex
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, _ = cpu_oracle_sample(b, 1, args.op)

@@ -105,11 +105,13 @@ typedef struct mg_params {
                            length -- and the fastest is kept for this process (shared by later
                            hierarchies with the same level sizes and types).  Results do not
                            depend on the tile shape.  Default 0: shapes from the wave model */
-    int32_t fuse_pre;   /* 1: pre-smoothing (two sweeps from zero) and residual-restriction in one
-                           pass over each level (3D; temporal blocking: half the bytes and one
-                           launch, bit-identical results).  Default 0: two kernels, which are
-                           faster on GB300 at every level size measured (both forms are bound
-                           by latency, not DRAM) */
+    int32_t fuse_pre;   /* sweeps per launch of the pre-smoothing: 1: the two sweeps from zero and
+                           the residual-restriction in one pass over each level (3D finite
+                           differences; temporal blocking: half the bytes and one launch,
+                           bit-identical results); 2: per level, whichever of the one pass and
+                           the two launches the autotuner (tune = 1) times faster (without tune:
+                           two launches); default 0: two launches, which are faster on GB300 at
+                           every level size measured (both forms are bound by latency, not DRAM) */
     int32_t rescale16;  /* 1 (default): when a restriction goes from a non-FP16 level into an
                            FP16 level (DSH_MG, Sec. 6), the restricted residual is divided by a
                            power of two s so that its inf-norm lies in [2^(k-1), 2^k), k the
@@ -184,6 +186,9 @@ typedef struct mg_level_info {
     int32_t tail_ctas;/* 0: the level runs as level kernels; else it is in the coarse tail,
                          held by this many CTAs (1, or a thread-block cluster of 8 / 16) */
     size_t bytes;     /* device bytes held for this level */
+    int32_t pre_launches; /* launches of the level's pre-smoothing and residual-restriction in
+                         the IR step (1: one fused pass, 2: two; 0: none, e.g. coarse tail) */
+    int32_t reserved_;
 } mg_level_info;
 
 /* ---------------------------------------------------------------- basics */
@@ -297,9 +302,22 @@ typedef struct mg_serve_stats {
     uint64_t arena_evictions;     /* cached arenas given up to make room */
     uint64_t submitted, completed;/* serving requests */
     uint64_t memory_waits;        /* requests that waited at least once for the pool */
+    uint64_t merged_groups;       /* merged groups run (mg_serve_options) */
+    uint64_t merged_requests;     /* requests that ran inside one */
     int32_t inflight, peak_inflight, queued, reserved_;
 } mg_serve_stats;
 mg_status mg_serve_stats_get(mg_serve_stats* out);
+
+/* merge_groups = 1: requests admitted in the same pass of the serving worker
+ * whose hierarchies the level-synchronous launches cover (3D, V-cycle, coarse
+ * tail, zero initial guess, device pointers) run together as one merged group,
+ * as in mg_solve_batch: one CUDA graph whose every step operation is a single
+ * launch over the (instance, tile) items of all members, each member keeping
+ * its own scale, norms and stopping test (its result equals its solve alone
+ * bit for bit).  A group completes when its last member converges.  The other
+ * requests run as before, each as its own graph.  0 (default): no merging.
+ * MG_ERR_INVALID for other values. */
+mg_status mg_serve_options(int32_t merge_groups);
 
 /* Solves `count` independent problems together, one per hierarchy (each
  * hierarchy at most once; none with serving requests in flight).  b[i], u[i],
@@ -431,7 +449,10 @@ mg_status mg_level_info_get(const mg_hierarchy* h, int32_t level, mg_level_info*
  *   MG_STAGE_COARSE        C_0 <- A_0^-1 G_0 (level 0 only; the base_solver in effect)
  *   MG_STAGE_SCALE_ZERO2   G_L <- cast(R * s) (Alg. 2's residual scaling), then JACOBI_ZERO2 on
  *                          level L; s = arg[0]
- *   MG_STAGE_IR_UPDATE     U <- U + a C_L;  R <- R - a A C_L;  a = arg[0]  (Alg. 2's solution and residual updates)
+ *   MG_STAGE_IR_UPDATE     U <- U + a C_L;  R <- R - a A C_L;  a = arg[0]  (Alg. 2's solution and residual updates);
+ *                          when the finest level is not FP64 and arg[1] > 0 (a power of two s), also
+ *                          G_L <- cast(trunc_FP32(R s)) of the updated R (the next step's residual scaling,
+ *                          as the solve's update forms it); arg holds 2 doubles
  *   MG_STAGE_RESIDUAL      R <- B - A U with B = arg pointer (n^d FP64, device)
  *   MG_STAGE_CYCLE         C_L <- one full cycle on G_L (Alg. 1, recursive)
  *   MG_STAGE_PRE_RESTRICT  C <- two damped Jacobi sweeps from C = 0 on G, then

@@ -126,6 +126,17 @@ extern "C" mg_status mg_level_info_get(const mg_hierarchy* hh, int32_t level, mg
     out->pitch = L.geo.P;
     out->tail_ctas = h->tail_level >= 0 && level <= h->tail_level ? h->tail_cs : 0;
     out->bytes = 3 * (size_t)L.geo.total * L.esz;
+    // the step's first visit of the level: one fused pre-smoothing + restriction pass, or two launches
+    bool pre = false, zero = false, restr = false;
+    for (const Op& op : h->step) {
+        if (op.kind != OP_KERNEL || op.kkind != K_SWEEP || op.level != level) continue;
+        const int m = op.mode & M_BASE;
+        pre |= m == M_PRE;
+        zero |= m == M_ZERO2 || m == M_ZERO1;
+        restr |= m == M_RESTRICT;
+    }
+    out->pre_launches = pre ? 1 : (zero && restr ? 2 : 0);
+    out->reserved_ = 0;
     return MG_OK;
 }
 
@@ -261,6 +272,10 @@ extern "C" mg_status mg_run_stage(mg_hierarchy* hh, int32_t stage, int32_t level
             if (!arg) SFAIL(MG_ERR_INVALID, "arg[0] (alpha) required");
             Op op = mgi_update_op(*h, lv.c, 0, nullptr);
             op.a.a_step = arg[0];
+            // arg[1] > 0 (a power of two): also write G_L = cast(trunc_FP32(R_new arg[1]))
+            op.a.dst = lv.prec != MG_FP64 && arg[1] > 0.0 ? lv.g : nullptr;
+            op.a.inv_explicit = op.a.dst ? arg[1] : 0.0;
+            op.mode = (op.mode & ~M_SA) | (op.a.dst ? M_SA : 0);
             rc = mgi_run_op(*h, op, s);
             if (!rc) {
                 SCK(cudaStreamSynchronize(s));

@@ -64,11 +64,18 @@ struct Plan {
     DevState* d_stage = nullptr;  // initial / final states, staged in one copy
     DevState* h_stage = nullptr;  // pinned host mirror
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t edone = nullptr;   // the final states are back on the host
     int launches_init = 0, launches_body = 0, launches_report = 0;
+    bool busy = false;             // a run of this plan is in flight
+    unsigned long long stamp = 0;  // last use (the plan cache keeps the most recent kMaxPlans)
 };
 
 std::mutex g_mu;
 std::vector<Plan*> g_plans;
+unsigned long long g_tick = 0;
+// Plans are cached per list of hierarchies; a serving loop meets many lists,
+// so the least recently used idle plans beyond this many are freed.
+constexpr size_t kMaxPlans = 64;
 
 void free_plan(Plan* p) {
     if (!p) return;
@@ -78,6 +85,7 @@ void free_plan(Plan* p) {
     if (p->h_stage) cudaFreeHost(p->h_stage);
     if (p->e0) cudaEventDestroy(p->e0);
     if (p->e1) cudaEventDestroy(p->e1);
+    if (p->edone) cudaEventDestroy(p->edone);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
@@ -289,19 +297,25 @@ __global__ void k_states_gather(DevState* __restrict__ dst, DevState* const* src
 constexpr int kStateWords = (int)(offsetof(DevState, hist) / 8);
 static_assert(offsetof(DevState, hist) % 8 == 0, "state control block is copied as 8-byte words");
 
+}  // namespace
+
+bool mgi_batch_mergeable(const mgi_hier& h) {
+    if (h.dim != 3 || h.tail_level < 0 || !h.p.zero_guess) return false;
+    int tails = 0;
+    for (const Op& op : h.step) tails += op.kind == OP_TAIL;
+    return tails == 1;  // a V-cycle (a W-cycle visits the tail more than once)
+}
+
+namespace {
+
 // Builds the merged plan and its graph; nullptr (with the reason) when the
 // batch is not covered.
 Plan* build_plan(const std::vector<mgi_hier*>& hs, std::string& why) {
     const int n = (int)hs.size();
     if (n == 0) { why = "empty"; return nullptr; }
     for (mgi_hier* h : hs) {
-        if (h->dim != 3) { why = "2D instance"; return nullptr; }
         if (h->device != hs[0]->device) { why = "instances on different devices"; return nullptr; }
-        if (h->tail_level < 0) { why = "instance without a coarse tail"; return nullptr; }
-        if (!h->p.zero_guess) { why = "non-zero initial guess"; return nullptr; }
-        int tails = 0;
-        for (const Op& op : h->step) tails += op.kind == OP_TAIL;
-        if (tails != 1) { why = "W-cycle schedule"; return nullptr; }
+        if (!mgi_batch_mergeable(*h)) { why = "2D instance, no coarse tail, initial guess or W-cycle"; return nullptr; }
     }
     Plan* p = new Plan();
     p->hs = hs;
@@ -367,6 +381,7 @@ Plan* build_plan(const std::vector<mgi_hier*>& hs, std::string& why) {
     if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess) return bad("stream", e);
     if ((e = cudaEventCreate(&p->e0)) != cudaSuccess) return bad("event", e);
     if ((e = cudaEventCreate(&p->e1)) != cudaSuccess) return bad("event", e);
+    if ((e = cudaEventCreateWithFlags(&p->edone, cudaEventDisableTiming)) != cudaSuccess) return bad("event", e);
     p->launches_init = count_kernels(p->init) + 1;
     p->launches_body = count_kernels(p->step) + count_kernels(p->guard) + 1;
     p->launches_report = count_kernels(p->report);
@@ -429,30 +444,41 @@ Plan* build_plan(const std::vector<mgi_hier*>& hs, std::string& why) {
 
 }  // namespace
 
-// Level-synchronous batch solve; returns false (and the caller takes the
-// concurrent path) when the batch is not covered.
-bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double* const* u, mg_result* res,
-                      mg_status* status) {
+namespace mgi {
+struct MergedRun {
+    Plan* p = nullptr;
+    std::vector<mgi_hier*> took;  // pooled instances this run bound (unbound at the finish)
+    bool failed = false;
+};
+}  // namespace mgi
+
+// Starts a level-synchronous batch solve on the plan's own stream.  Returns
+// nullptr with *status = MG_OK when the batch is not covered (the caller takes
+// the concurrent path), nullptr with an error status when it failed to start.
+MergedRun* mgi_batch_merged_start(std::vector<mgi_hier*>& hs, const double* const* b, double* const* u,
+                                  mg_status* status) {
+    *status = MG_OK;
     for (size_t i = 0; i < hs.size(); ++i)
-        if (!mgi_is_device_ptr(b[i]) || !mgi_is_device_ptr(u[i])) return false;
+        if (!mgi_is_device_ptr(b[i]) || !mgi_is_device_ptr(u[i])) return nullptr;
     // pooled instances take their working arenas first (the plan holds their addresses);
     // the whole batch must fit the pool's budget at once
-    std::vector<mgi_hier*> took;
+    MergedRun* run = new MergedRun();
     auto unbind_all = [&]() {
-        for (mgi_hier* h : took) mgi_unbind(*h);
+        for (mgi_hier* t : run->took) cudaStreamSynchronize(t->stream);
+        for (mgi_hier* h : run->took) mgi_unbind(*h);
     };
     for (mgi_hier* h : hs) {
         if (h->bound) continue;
         cudaSetDevice(h->device);
         const mg_status bs = mgi_bind(*h);
         if (bs != MG_OK) {
-            for (mgi_hier* t : took) cudaStreamSynchronize(t->stream);
             unbind_all();
+            delete run;
             if (bs == MG_BUSY) mgi_set_error("the batch's working arenas do not fit the memory pool's budget at once");
             *status = bs == MG_BUSY ? MG_ERR_OOM : bs;
-            return true;
+            return nullptr;
         }
-        took.push_back(h);
+        run->took.push_back(h);
     }
     Plan* p = nullptr;
     {
@@ -463,13 +489,26 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
             std::string why;
             p = build_plan(hs, why);
             if (!p) {
-                for (mgi_hier* t : took) cudaStreamSynchronize(t->stream);
                 unbind_all();
-                return false;
+                delete run;
+                return nullptr;
             }
             g_plans.push_back(p);
+            while (g_plans.size() > kMaxPlans) {  // free the least recently used idle plan
+                size_t victim = g_plans.size();
+                for (size_t i = 0; i < g_plans.size(); ++i)
+                    if (!g_plans[i]->busy && g_plans[i] != p &&
+                        (victim == g_plans.size() || g_plans[i]->stamp < g_plans[victim]->stamp))
+                        victim = i;
+                if (victim == g_plans.size()) break;
+                free_plan(g_plans[victim]);
+                g_plans.erase(g_plans.begin() + (long)victim);
+            }
         }
+        p->busy = true;
+        p->stamp = ++g_tick;
     }
+    run->p = p;
     cudaSetDevice(p->device);
     const int n = (int)hs.size();
     // initial control states (as a single solve's start writes them)
@@ -486,7 +525,6 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
         sh.tol_mode = h.p.tol_mode;
         sh.guard = h.p.guard;
         sh.scale_ahead = h.scale_ahead_on() ? 1 : 0;
-
         sh.b = b[i];
         sh.uout = u[i];
     }
@@ -503,15 +541,37 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
     if (e == cudaSuccess) e = cudaGraphLaunch(p->exec, s);
     if (e == cudaSuccess) e = cudaEventRecord(p->e1, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->h_stage, p->d_stage, (size_t)n * sizeof(DevState), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaEventRecord(p->edone, s);
     if (e != cudaSuccess) {
         mgi_set_error(std::string("batch: ") + cudaGetErrorString(e));
-        cudaStreamSynchronize(s);
-        unbind_all();
-        *status = MG_ERR_CUDA;
-        return true;
+        run->failed = true;
     }
-    unbind_all();
+    return run;
+}
+
+bool mgi_batch_merged_ready(MergedRun* run) {
+    if (run->failed) return true;
+    return cudaEventQuery(run->p->edone) != cudaErrorNotReady;
+}
+
+mg_status mgi_batch_merged_finish(MergedRun* run, mg_result* res) {
+    Plan* p = run->p;
+    cudaSetDevice(p->device);
+    cudaError_t e = run->failed ? cudaErrorLaunchFailure : cudaEventSynchronize(p->edone);
+    cudaStreamSynchronize(p->stream);
+    for (mgi_hier* h : run->took) mgi_unbind(*h);
+    const bool failed = run->failed || e != cudaSuccess;
+    if (e != cudaSuccess && !run->failed) mgi_set_error(std::string("batch: ") + cudaGetErrorString(e));
+    delete run;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        p->busy = false;
+    }
+    const int n = (int)p->hs.size();
+    if (failed) {
+        for (int i = 0; i < n && res; ++i) { res[i] = mg_result{}; res[i].status = MG_ERR_CUDA; res[i].merged = 1; }
+        return MG_ERR_CUDA;
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p->e0, p->e1);
     mg_status first_bad = MG_OK;
@@ -520,7 +580,7 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
         mg_result r{};
         r.iters = st.iter;
         r.status = st.status;
-        r.levels = hs[i]->nlev;
+        r.levels = p->hs[i]->nlev;
         r.guard_restarts = st.guard_restarts;
         r.bnorm = st.bnorm2;
         r.rel_res = st.bnorm2 > 0 ? st.rnorm2 / st.bnorm2 : st.rnorm2;
@@ -535,7 +595,16 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
         if (res) res[i] = r;
         if (r.status != MG_OK && first_bad == MG_OK) first_bad = (mg_status)r.status;
     }
-    *status = first_bad;
+    return first_bad;
+}
+
+// Level-synchronous batch solve; returns false (and the caller takes the
+// concurrent path) when the batch is not covered.
+bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double* const* u, mg_result* res,
+                      mg_status* status) {
+    MergedRun* run = mgi_batch_merged_start(hs, b, u, status);
+    if (!run) return *status != MG_OK;
+    *status = mgi_batch_merged_finish(run, res);
     return true;
 }
 
@@ -543,7 +612,7 @@ bool mgi_batch_merged(std::vector<mgi_hier*>& hs, const double* const* b, double
 void mgi_batch_forget(mgi_hier* h) {
     std::lock_guard<std::mutex> lk(g_mu);
     for (size_t i = 0; i < g_plans.size();) {
-        if (std::find(g_plans[i]->hs.begin(), g_plans[i]->hs.end(), h) != g_plans[i]->hs.end()) {
+        if (!g_plans[i]->busy && std::find(g_plans[i]->hs.begin(), g_plans[i]->hs.end(), h) != g_plans[i]->hs.end()) {
             free_plan(g_plans[i]);
             g_plans.erase(g_plans.begin() + i);
         } else {

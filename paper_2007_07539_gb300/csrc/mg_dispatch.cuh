@@ -76,7 +76,11 @@ KFn pick(int kind, int mode, int prec_c) {
             default: break;
         }
     }
-    if (kind == K_UPDATE) return q1 ? &k_update<DIM, T, 1> : &k_update<DIM, T, 0>;
+    if (kind == K_UPDATE) {
+        if (!std::is_same<T, double>::value && (mode & M_SA))
+            return q1 ? &k_update<DIM, T, 1, 1> : &k_update<DIM, T, 0, 1>;
+        return q1 ? &k_update<DIM, T, 1> : &k_update<DIM, T, 0>;
+    }
     if (kind == K_SCALE) return &k_scale_cast<DIM, T>;
     switch (prec_c) {
         case MG_FP64: return pick_tc<DIM, T, double>(kind, mode);
@@ -213,7 +217,12 @@ int launch_batch_t(int kind, int mode, int prec_c, int rpw, const void* items, c
     }
     using FK = void (*)(const KItem*, const int*);
     FK f = nullptr;
-    if (kind == K_UPDATE) f = (mode & M_FEM) ? &k_update_batch<3, T, 1> : &k_update_batch<3, T, 0>;
+    if (kind == K_UPDATE) {
+        if (!std::is_same<T, double>::value && (mode & M_SA))
+            f = (mode & M_FEM) ? &k_update_batch<3, T, 1, 1> : &k_update_batch<3, T, 0, 1>;
+        else
+            f = (mode & M_FEM) ? &k_update_batch<3, T, 1> : &k_update_batch<3, T, 0>;
+    }
     else if (kind == K_SCALE) f = &k_scale_cast_batch<3, T>;
     else if (kind == K_PROLONG) {
         switch (prec_c) {

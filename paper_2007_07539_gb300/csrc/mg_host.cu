@@ -131,8 +131,8 @@ int mgi_validate(const mg_params* p, std::string& why) {
     if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) { why = "tol must be finite and >= 0"; return 0; }
     if (p->max_iter < 0 || p->max_iter > kMaxIter) { why = "max_iter out of range"; return 0; }
     if (p->no_tail < 0 || p->no_tail > 2) { why = "no_tail must be 0, 1 or 2"; return 0; }
-    if ((p->tune != 0 && p->tune != 1) || (p->fuse_pre != 0 && p->fuse_pre != 1)) {
-        why = "tune and fuse_pre must be 0 or 1";
+    if ((p->tune != 0 && p->tune != 1) || p->fuse_pre < 0 || p->fuse_pre > 2) {
+        why = "tune must be 0 or 1 and fuse_pre 0, 1 or 2";
         return 0;
     }
     if ((p->rescale16 != 0 && p->rescale16 != 1) || (p->base_solver != 0 && p->base_solver != 1)) {
@@ -463,7 +463,9 @@ struct Gen {
         }
         // one pass for the two sweeps from zero and the residual-restriction
         const bool resc = h->rescaled(l - 1);
-        const bool fused = first && h->p.nu1 == 2 && h->dim == 3 && h->p.fuse_pre == 1 && !resc;
+        const bool fused = first && h->p.nu1 == 2 && h->dim == 3 && !resc && h->p.op == 0 &&
+                           (h->p.fuse_pre == 1 ||
+                            (h->p.fuse_pre == 2 && fuse_choice_get(h->lv[l].prec, h->lv[l - 1].prec, h->lv[l].geo.n) == 1));
         if (fused) {
             Op op = kernel(l, K_SWEEP, M_PRE, gbuf(l), h->lv[l - 1].g, gbuf(l));
             op.a.dst2 = cbuf(l);
@@ -543,8 +545,10 @@ Op mgi_update_op(mgi_hier& h, const void* cL, int gate, const DevState* st) {
     gen.gate = gate;
     gen.st = st;
     gen.top_from_r = true;
-    // scale-ahead: the update also writes the next step's g (used only when st is set)
-    return gen.kernel(L, K_UPDATE, 0, cL, h.scale_ahead_on() ? h.lv[L].g : nullptr, nullptr);
+    // scale-ahead: the update also writes the next step's g (the M_SA instantiation)
+    Op op = gen.kernel(L, K_UPDATE, 0, cL, h.scale_ahead_on() ? h.lv[L].g : nullptr, nullptr);
+    if (op.a.dst && h.lv[L].prec != MG_FP64) op.mode |= M_SA;
+    return op;
 }
 
 static size_t update_blocks_max(const mgi_hier& h) {
@@ -746,7 +750,7 @@ static void autotune(mgi_hier& h) {
         const int n = lv.geo.n;
         cold = 3.0 * (double)lv.geo.total * (double)lv.esz > 32.0 * 1048576.0;
         for (int mode : {M_PRE, M_ZERO2, M_RESTRICT, M_JACOBI}) {
-            if (mode == M_PRE && h.p.fuse_pre != 1) continue;
+            if (mode == M_PRE && (h.p.fuse_pre == 0 || h.p.op != 0)) continue;
             const int kmode = mode | (h.p.op == 1 ? M_FEM : 0);  // the key of the kernel's shapes
             TileChoice have;
             if (tile_choice_get(3, K_SWEEP, kmode, lv.prec, n, &have)) continue;
@@ -786,6 +790,19 @@ static void autotune(mgi_hier& h) {
                 }
             }
             tile_choice_set(3, K_SWEEP, kmode, lv.prec, n, &best);
+        }
+        // sweeps per launch of the pre-smoothing (fuse_pre = 2): the one-pass form
+        // (two sweeps from zero and the residual-restriction, M_PRE) against the two
+        // launches, each in its tuned shape; kept only when clearly faster
+        if (h.p.fuse_pre == 2 && h.p.op == 0 && h.p.nu1 == 2 && !h.rescaled(l - 1) &&
+            fuse_choice_get(lv.prec, h.lv[l - 1].prec, n) < 0) {
+            Op zero2 = mgi_kernel_op(h, l, K_SWEEP, M_ZERO2, lv.g, lv.c, nullptr, 0, nullptr);
+            Op restr = mgi_kernel_op(h, l, K_SWEEP, M_RESTRICT, lv.c, h.lv[l - 1].g, lv.g, 0, nullptr);
+            Op pre = mgi_kernel_op(h, l, K_SWEEP, M_PRE, lv.g, h.lv[l - 1].g, lv.g, 0, nullptr);
+            pre.a.dst2 = lv.c;
+            const float t2 = time_op(zero2) + time_op(restr);
+            const float t1 = time_op(pre);
+            fuse_choice_set(lv.prec, h.lv[l - 1].prec, n, t1 < 0.97f * t2 ? 1 : 0);
         }
     }
     cudaStreamSynchronize(s);

@@ -165,6 +165,17 @@ mg_status mgi_batch_run(std::vector<mgi::mgi_hier*>& hs, const double* const* b,
 bool mgi_batch_merged(std::vector<mgi::mgi_hier*>& hs, const double* const* b, double* const* u, mg_result* res,
                       mg_status* status);
 void mgi_batch_forget(mgi::mgi_hier* h);
+// Asynchronous form of the level-synchronous batch (mg_batch.cu): start returns
+// nullptr with *status = MG_OK when the batch is not covered; ready polls;
+// finish fills res (one per instance), hands back the arenas start bound and
+// frees the run.
+namespace mgi { struct MergedRun; }
+mgi::MergedRun* mgi_batch_merged_start(std::vector<mgi::mgi_hier*>& hs, const double* const* b, double* const* u,
+                                       mg_status* status);
+bool mgi_batch_merged_ready(mgi::MergedRun* run);
+mg_status mgi_batch_merged_finish(mgi::MergedRun* run, mg_result* res);
+// The batch is one the level-synchronous launches cover (3D, V-cycle, coarse tail, zero initial guess).
+bool mgi_batch_mergeable(const mgi::mgi_hier& h);
 // serving engine hooks
 void mgi_serve_forget(mgi::mgi_hier* h);
 bool mgi_serve_busy(mgi::mgi_hier* h);

@@ -103,6 +103,10 @@ enum Mode : int {
 // hierarchy with the Q1 finite-element operator (op = 1); M_BASE masks it off.
 constexpr int M_FEM = 16;
 constexpr int M_BASE = 15;
+// Flag or'ed into the mode of the IR update when it also writes the next
+// step's scaled g (scale-ahead, non-FP64 finest levels): that instantiation
+// sums the squares of r in FP32, from the scaled FP32 values it forms for g.
+constexpr int M_SA = 32;
 
 // The operator of a level, A = alpha (beta I - W), W the sum of neighbour
 // values with positive integer weights (Sec. 5):
@@ -213,6 +217,10 @@ struct TileChoice {
 constexpr int kDirectMaxN = 63;
 void tile_choice_set(int dim, int kind, int mode, int prec, int n, const TileChoice* c);  // nullptr: erase
 bool tile_choice_get(int dim, int kind, int mode, int prec, int n, TileChoice* c);
+// Sweeps per launch of a 3D level's pre-smoothing (two sweeps from zero and the
+// residual-restriction): 1 = one fused pass (M_PRE), 0 = two launches; -1: not tuned.
+void fuse_choice_set(int prec, int prec_c, int n, int fused);
+int fuse_choice_get(int prec, int prec_c, int n);
 
 // TMA descriptors of the 3D sweeps: the swept vector (boxes of TY+2 rows with
 // a 16-byte x-halo on each side) and the right-hand side (TY rows, no halo).

@@ -12,7 +12,7 @@
 //   u += alpha c and r -= alpha A c in FP64 with norm partials.
 // k_scale_cast: Alg. 2's residual scaling, the scaled FP64 residual cast to the finest
 //   level's storage type.
-// k_prolong: Alg. 1's prolongation and correction, prolongation and correction.
+// k_prolong: Alg. 1's prolongation and correction.
 //
 // 3D sweep decomposition: a CTA of TY warps owns TY consecutive rows of one
 // 32V-wide x-chunk (V = elements per 16-byte vector: 8 FP16/BF16, 4 FP32,
@@ -449,18 +449,23 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     // forms coarse row J0 + w from tile rows 2w, 2w+1, 2w+2 (y weights 1/4, 1/2,
     // 1/4).  The flush area is written again only two planes later, after
     // another barrier, so one barrier per plane serves both.
+    // The values of a coarse row are split over two warps (halves of each lane's
+    // VH values) where VH allows, so that 2 TJ of the TY warps share the work.
     auto coarse_rows = [&](int K) {
+        constexpr int SPLIT = VH >= 2 ? 2 : 1;
+        constexpr int VS = VH / SPLIT;
         const int TJ = (R - 1) / 2;
-        if (w < TJ) {
-            const int J = (y0 >> 1) + w;
-            const C* f0 = reinterpret_cast<const C*>(flush) + ((2 * w) * 32 + lane) * VH;
+        if (w < TJ * SPLIT) {
+            const int jr = w / SPLIT, k0 = (w % SPLIT) * VS;
+            const int J = (y0 >> 1) + jr;
+            const C* f0 = reinterpret_cast<const C*>(flush) + ((2 * jr) * 32 + lane) * VH + k0;
             const C* f1 = f0 + 32 * VH;
             const C* f2 = f1 + 32 * VH;
-            const int I0 = (x0 + lane * V) >> 1;
+            const int I0 = ((x0 + lane * V) >> 1) + k0;
             if (lane_in && J < a.nc && K < a.nc && (lane < 31 || x0 + CW >= a.P)) {
                 TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
 #pragma unroll
-                for (int k = 0; k < VH; ++k)
+                for (int k = 0; k < VS; ++k)
                     if (I0 + k < a.nc) st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
             }
         }
@@ -1271,7 +1276,13 @@ __device__ __forceinline__ void st4(T* p, const float (&v)[4]) {
 // runs the step's finalisation.
 // OP = 1: the Q1 operator (3x3(x3) neighbourhood, integer weights).
 constexpr int kUpdQ = 4;
-template <int DIM, class T, int OP>
+// SA = 1 (non-FP64 T; launched only with a.dst set): the scale-ahead form.  It
+// writes the next step's g = cast(trunc_FP32(r 2^k)) (reading R21) and sums the
+// squares of those FP32 values in FP32 per thread (scaled back by 2^-2k in
+// FP64), which leaves the FP64 pipe -- the update's second roof -- with the two
+// fused multiply-adds of Alg. 2's solution and residual updates.  The norm's
+// relative error stays below 1e-5 (reading R11).  SA = 0: no g, FP64 squares.
+template <int DIM, class T, int OP, int SA = 0>
 __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
     using C = typename Tr<T>::C;
     constexpr int Q = kUpdQ;
@@ -1288,12 +1299,15 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
     // scale-ahead (Alg. 2's residual scaling of the next step, fused): g = cast(r inv_pred),
     // inv_pred a power of two; a value beyond T's range is flagged (and the
     // next step falls back to the separate scale-and-cast)
-    T* const gout = (!std::is_same<T, double>::value && a.st && a.st->scale_ahead && a.dst)
-                        ? reinterpret_cast<T*>(a.dst) : nullptr;
+    // (a stage call without a control state passes the power of two in inv_explicit)
+    constexpr bool kSA = SA == 1 && !std::is_same<T, double>::value;
+    T* const gout = kSA ? reinterpret_cast<T*>(a.dst) : nullptr;
+    const double inv_pred = kSA ? (a.st ? a.st->inv_pred : a.inv_explicit) : 0.0;
     int gke = 0;            // inv_pred = 2^k: FP32 biased exponent of r * 2^k = FP64 biased exponent + k - 896
     unsigned glim = ~0u;    // |FP32 bits| at which T overflows
-    if (gout) {
-        const long long ib = __double_as_longlong(a.st->inv_pred);
+    float sqf = 0.0f;       // kSA: FP32 sum of squares of r 2^k
+    if (kSA) {
+        const long long ib = __double_as_longlong(inv_pred);
         gke = (int)((ib >> 52) & 0x7FF) - 1023 - 896;
         glim = std::is_same<T, __half>::value ? 0x477FF000u : 0x7F61B1E6u;  // 65520, 3.0e38
     }
@@ -1413,7 +1427,7 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
                     if (ExactStencil<T>::kTwoTerm && !std::is_same<T, __half>::value) r = fma(-beta, s2, r);
                     rr[i] = r;
                     uu[i] = fma(alpha, to_f64(cc), uu[i]);
-                    sq.add(r, E);
+                    if constexpr (!kSA) sq.add(r, E);
                     nmax = key_max(nmax, abs_key(r));
                 }
             }
@@ -1454,7 +1468,7 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
                     const double r = fma(-beta, sx, rr[i]);
                     rr[i] = r;
                     uu[i] = fma(alpha, half_to_f64(c0[i]), uu[i]);
-                    sq.add(r, E);
+                    if constexpr (!kSA) sq.add(r, E);
                     nmax = key_max(nmax, abs_key(r));
                 }
             }
@@ -1475,7 +1489,7 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
                 if (ExactStencil<T>::kTwoTerm) r = fma(-beta, s2, r);
                 rr[i] = r;
                 uu[i] = fma(alpha, to_f64(c0[i]), uu[i]);
-                sq.add(r, E);
+                if constexpr (!kSA) sq.add(r, E);
                 const unsigned long long k = abs_key(r);
                 nmax = key_max(nmax, k);
             }
@@ -1486,8 +1500,8 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
         *reinterpret_cast<double2*>(up + 2) = make_double2(uu[2], uu[3]);
         *reinterpret_cast<double2*>(rp) = make_double2(rr[0], rr[1]);
         *reinterpret_cast<double2*>(rp + 2) = make_double2(rr[2], rr[3]);
-        if constexpr (!std::is_same<T, double>::value) {
-            if (gout) {  // pads of r are 0, so pads of g stay 0
+        if constexpr (kSA) {
+            {  // pads of r are 0, so pads of g stay 0
                 // r * 2^k truncated to FP32 from the bit pattern (integer
                 // instructions; 0 below the FP32 normal range), then one rounding
                 // to T; an exponent or value beyond T's range is flagged
@@ -1503,13 +1517,18 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
                     const unsigned fb = (ein != 0 && e > 0) ? (e < 255 ? mag : 0x7F800000u) : 0u;
                     gbad |= ein == 0x7FF || fb >= glim;
                     gv[i] = __uint_as_float((ein != 0 ? sign : 0u) | fb);
+                    sqf = __fmaf_rn(gv[i], gv[i], sqf);  // pads of r are 0: they add nothing
                 }
                 st4(gout + o, gv);
             }
         }
     }
-    if (gout && __any_sync(kFull, gbad) && (threadIdx.x & 31) == 0)
+    if (kSA && a.st && __any_sync(kFull, gbad) && (threadIdx.x & 31) == 0)
         atomicExch(&const_cast<DevState*>(a.st)->gover, 1);
+    if constexpr (kSA) {  // (r 2^k)^2 2^-2k: powers of two, exact
+        const double ip = 1.0 / inv_pred;
+        sq.s = (double)sqf * ip * ip;
+    }
     write_partials(sq, nmax, E, a.partials, cta);
     if (a.fin && a.st) {
         // the last CTA to finish reduces every CTA's partials and runs the
@@ -1536,14 +1555,14 @@ template <class T, int OP>
 struct UpdLB {
     static constexpr int kMinBlocks = (std::is_same<T, __half>::value && OP == 0) ? 4 : 1;
 };
-template <int DIM, class T, int OP>
+template <int DIM, class T, int OP, int SA = 0>
 __global__ void __launch_bounds__(256, UpdLB<T, OP>::kMinBlocks) k_update(const KArgs a) {
-    update_body<DIM, T, OP>(a, blockIdx.x, gridDim.x);
+    update_body<DIM, T, OP, SA>(a, blockIdx.x, gridDim.x);
 }
-template <int DIM, class T, int OP>
+template <int DIM, class T, int OP, int SA = 0>
 __global__ void __launch_bounds__(256) k_update_batch(const KItem* __restrict__ items, const int* __restrict__ cta_item) {
     const KItem& it = items[cta_item[blockIdx.x]];
-    update_body<DIM, T, OP>(it.a, blockIdx.x - it.cta_begin, it.ncta);
+    update_body<DIM, T, OP, SA>(it.a, blockIdx.x - it.cta_begin, it.ncta);
 }
 
 // ---------------------------------------------------------------- prolongation (Alg. 1's prolongation and correction)

@@ -76,6 +76,16 @@ bool tile_choice_get(int dim, int kind, int mode, int prec, int n, TileChoice* c
     *c = it->second;
     return true;
 }
+// Sweeps per launch of a 3D level's pre-smoothing, chosen by the autotuner:
+// kept with the tile shapes under the pseudo kernel kind -1 (mode = the coarse type).
+void fuse_choice_set(int prec, int prec_c, int n, int fused) {
+    const TileChoice c{fused, 0};
+    tile_choice_set(3, -1, prec_c, prec, n, &c);
+}
+int fuse_choice_get(int prec, int prec_c, int n) {
+    TileChoice c;
+    return tile_choice_get(3, -1, prec_c, prec, n, &c) ? c.rpw : -1;
+}
 
 // Resident CTAs per SM of a kernel, from the runtime's occupancy calculator
 // (cached: the answer depends only on the arguments), else from shared memory.

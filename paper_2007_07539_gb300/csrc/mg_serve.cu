@@ -99,7 +99,16 @@ struct Req {
     int state = 0;  // 0 queued, 1 running, 2 done
     int bypassed = 0;
     bool waited_memory = false;
+    bool in_group = false;  // runs inside a merged (level-synchronous) group
     mg_result res{};
+};
+
+// Requests admitted together that the level-synchronous launches cover run
+// as one merged group (mg_serve_options): one CUDA graph whose launches each
+// cover the (instance, tile) items of all members.
+struct Group {
+    MergedRun* run = nullptr;
+    std::vector<Req*> reqs;
 };
 
 struct Engine {
@@ -114,8 +123,9 @@ struct Engine {
     std::unordered_map<uint64_t, Req*> all;
     std::unordered_map<mgi_hier*, int> pending;
     std::unordered_set<mgi_hier*> busy;
-    uint64_t submitted = 0, completed = 0, memory_waits = 0;
+    uint64_t submitted = 0, completed = 0, memory_waits = 0, merged_groups = 0, merged_requests = 0;
     int peak_inflight = 0;
+    bool merge = false;
 };
 
 Engine& engine() {
@@ -172,13 +182,51 @@ std::vector<Req*> admit(Engine& E) {
 
 void worker() {
     Engine& E = engine();
+    std::vector<Group> groups;
     for (;;) {
         std::vector<Req*> to_begin, snapshot;
+        bool merge = false;
         {
             std::unique_lock<std::mutex> lk(E.mu);
             if (E.queue.empty() && E.running.empty())
                 E.cv.wait(lk, [&] { return !E.queue.empty() || !E.running.empty(); });
             to_begin = admit(E);
+            merge = E.merge;
+        }
+        // requests admitted together that the merged launches cover run as one group
+        if (merge && to_begin.size() >= 2) {
+            std::vector<Req*> cand, rest;
+            for (Req* r : to_begin) {
+                const bool ok = mgi_batch_mergeable(*r->h) && r->h->device == to_begin[0]->h->device &&
+                                mgi_is_device_ptr(r->b) && mgi_is_device_ptr(r->u);
+                (ok ? cand : rest).push_back(r);
+            }
+            if (cand.size() >= 2) {
+                std::vector<mgi_hier*> hs;
+                std::vector<const double*> bs;
+                std::vector<double*> us;
+                for (Req* r : cand) { hs.push_back(r->h); bs.push_back(r->b); us.push_back(r->u); }
+                cudaSetDevice(cand[0]->h->device);
+                mg_status st = MG_OK;
+                MergedRun* run = mgi_batch_merged_start(hs, bs.data(), us.data(), &st);
+                if (run) {
+                    for (Req* r : cand) r->in_group = true;
+                    groups.push_back(Group{run, cand});
+                    std::lock_guard<std::mutex> lk(E.mu);
+                    ++E.merged_groups;
+                    E.merged_requests += cand.size();
+                    to_begin = rest;
+                } else if (st != MG_OK) {
+                    for (Req* r : cand) {
+                        mgi_unbind(*r->h);
+                        std::lock_guard<std::mutex> lk(E.mu);
+                        mg_result res{};
+                        res.status = st;
+                        finish(E, r, res);
+                    }
+                    to_begin = rest;
+                }
+            }
         }
         for (Req* r : to_begin) {
             cudaSetDevice(r->h->device);
@@ -196,8 +244,21 @@ void worker() {
             snapshot = E.running;
         }
         bool progressed = false;
+        for (size_t gi = 0; gi < groups.size();) {
+            Group& g = groups[gi];
+            if (!mgi_batch_merged_ready(g.run)) { ++gi; continue; }
+            std::vector<mg_result> res(g.reqs.size());
+            mgi_batch_merged_finish(g.run, res.data());  // the group's stream has completed
+            for (size_t i = 0; i < g.reqs.size(); ++i) {
+                mgi_unbind(*g.reqs[i]->h);
+                std::lock_guard<std::mutex> lk(E.mu);
+                finish(E, g.reqs[i], res[i]);
+            }
+            groups.erase(groups.begin() + (long)gi);
+            progressed = true;
+        }
         for (Req* r : snapshot) {
-            if (r->state != 1) continue;
+            if (r->state != 1 || r->in_group) continue;
             cudaSetDevice(r->h->device);
             cudaError_t q = cudaEventQuery(r->h->ev_state);
             if (q == cudaErrorNotReady) continue;
@@ -237,6 +298,14 @@ extern "C" mg_status mg_serve_configure(size_t budget_bytes, int32_t max_infligh
     return MG_OK;
 }
 
+extern "C" mg_status mg_serve_options(int32_t merge_groups) {
+    if (merge_groups != 0 && merge_groups != 1) { mgi_set_error("merge_groups must be 0 or 1"); return MG_ERR_INVALID; }
+    Engine& E = engine();
+    std::lock_guard<std::mutex> lk(E.mu);
+    E.merge = merge_groups == 1;
+    return MG_OK;
+}
+
 extern "C" mg_status mg_serve_stats_get(mg_serve_stats* out) {
     if (!out) { mgi_set_error("NULL argument"); return MG_ERR_INVALID; }
     int dev = 0;
@@ -256,6 +325,8 @@ extern "C" mg_status mg_serve_stats_get(mg_serve_stats* out) {
     out->submitted = E.submitted;
     out->completed = E.completed;
     out->memory_waits = E.memory_waits;
+    out->merged_groups = E.merged_groups;
+    out->merged_requests = E.merged_requests;
     out->inflight = (int32_t)E.running.size();
     out->peak_inflight = E.peak_inflight;
     out->queued = (int32_t)E.queue.size();

@@ -32,7 +32,7 @@ EXPORTS = ["mg_params_init", "mg_level_count", "mg_last_error", "mg_footprint_by
            "mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
            "mg_serve_configure", "mg_solve_batch", "mg_profile_solve", "mg_level_write", "mg_level_read",
            "mg_level_info_get", "mg_run_stage", "mg_residual_norms_noalloc", "mg_axpy", "mg_describe_cycle",
-           "mg_fault_inject", "mg_serve_stats_get"]
+           "mg_fault_inject", "mg_serve_stats_get", "mg_serve_options"]
 FAULT_ARENA, FAULT_STAGING = 0, 1
 
 
@@ -65,6 +65,7 @@ class ServeStats(ctypes.Structure):
                 ("peak_reserved_bytes", ctypes.c_uint64), ("arena_acquires", ctypes.c_uint64),
                 ("arena_reuses", ctypes.c_uint64), ("arena_evictions", ctypes.c_uint64),
                 ("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("memory_waits", ctypes.c_uint64),
+                ("merged_groups", ctypes.c_uint64), ("merged_requests", ctypes.c_uint64),
                 ("inflight", ctypes.c_int32), ("peak_inflight", ctypes.c_int32), ("queued", ctypes.c_int32),
                 ("reserved_", ctypes.c_int32)]
 
@@ -74,7 +75,8 @@ class ServeStats(ctypes.Structure):
 
 class LevelInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("prec", ctypes.c_int32), ("pitch", ctypes.c_int32),
-                ("tail_ctas", ctypes.c_int32), ("bytes", ctypes.c_size_t)]
+                ("tail_ctas", ctypes.c_int32), ("bytes", ctypes.c_size_t), ("pre_launches", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -151,6 +153,8 @@ def lib() -> ctypes.CDLL:
             L.mg_axpy.restype = ctypes.c_int
             L.mg_serve_stats_get.argtypes = [ctypes.POINTER(ServeStats)]
             L.mg_serve_stats_get.restype = ctypes.c_int
+            L.mg_serve_options.argtypes = [i32]
+            L.mg_serve_options.restype = ctypes.c_int
             L.mg_fault_inject.argtypes = [i32, i32]
             L.mg_fault_inject.restype = ctypes.c_int
             for f in ("mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
@@ -323,7 +327,8 @@ class Hierarchy:
     def level_info(self, level: int) -> dict:
         li = LevelInfo()
         _check(lib().mg_level_info_get(self.handle, int(level), ctypes.byref(li)), "mg_level_info_get")
-        return dict(n=li.n, prec=li.prec, pitch=li.pitch, tail_ctas=li.tail_ctas, bytes=li.bytes)
+        return dict(n=li.n, prec=li.prec, pitch=li.pitch, tail_ctas=li.tail_ctas, bytes=li.bytes,
+                    pre_launches=li.pre_launches)
 
     def level_write(self, level: int, vec: int, src) -> None:
         _check(lib().mg_level_write(self.handle, int(level), int(vec), ctypes.c_void_p(_ptr(src))),
@@ -333,8 +338,8 @@ class Hierarchy:
         _check(lib().mg_level_read(self.handle, int(level), int(vec), ctypes.c_void_p(_ptr(dst))),
                "mg_level_read")
 
-    def run_stage(self, stage: int, level: int, arg: float | None = None, ptr=None):
-        a = (ctypes.c_double * 2)(arg if arg is not None else 0.0, 0.0)
+    def run_stage(self, stage: int, level: int, arg: float | None = None, ptr=None, arg2: float = 0.0):
+        a = (ctypes.c_double * 2)(arg if arg is not None else 0.0, arg2)
         out = (ctypes.c_double * 2)()
         _check(lib().mg_run_stage(self.handle, int(stage), int(level), a if arg is not None else None,
                                   ctypes.c_void_p(_ptr(ptr)) if ptr is not None else None, out),
@@ -373,6 +378,11 @@ def solve_batch(hs: list[Hierarchy], bs: list, us: list) -> list[dict]:
 
 def serve_configure(budget_bytes: int = 0, max_inflight: int = 0) -> None:
     _check(lib().mg_serve_configure(int(budget_bytes), int(max_inflight)), "mg_serve_configure")
+
+
+def serve_options(merge_groups: bool) -> None:
+    """mg_serve_options: run requests admitted together as merged level-synchronous groups."""
+    _check(lib().mg_serve_options(1 if merge_groups else 0), "mg_serve_options")
 
 
 def serve_stats() -> dict:

@@ -280,6 +280,38 @@ def test_ir_update(oracle, dim, n, prec):
     assert ninf == np.abs(ro).max()
 
 
+@pytest.mark.parametrize("dim,n,prec", [(3, 95, mg.FP16), (3, 255, mg.FP16), (3, 95, mg.BF16), (3, 47, mg.FP32),
+                                        (2, 511, mg.FP16), (2, 127, mg.BF16)])
+def test_ir_update_writes_the_next_scaled_residual(oracle, dim, n, prec):
+    """The update's scale-ahead output (reading R21 of Alg. 2's residual scaling): with a power of
+    two s it also writes the next step's g = cast(trunc_FP32(r_new s)).  Checked bit for bit
+    against the oracle's emulated cast applied to the kernel's own updated r (pinned against
+    numpy's FP32 / FP16 conversions on CPU), with s putting max |r_new s| near 2^14, as in a
+    solve.  u and r are checked as in test_ir_update."""
+    alpha = 3.7e-6
+    fmt = {mg.FP16: oracle.FP16, mg.BF16: oracle.BF16, mg.FP32: oracle.FP32}[prec]
+    with hier(dim, n, prec) as h:
+        L = h.nlev - 1
+        c = write(h, L, mg.VEC_C, rnd(dim, n, 23, 1000.0), prec)
+        u = rnd(dim, n, 24)
+        r = alpha * oracle.apply_A(c) * (1.0 + 1e-3 * rnd(dim, n, 25))
+        rref = r - alpha * oracle.apply_A(c)
+        _, e = np.frexp(np.abs(rref).max())
+        s = 2.0 ** (14 - int(e))  # the power of two of the scale-ahead rule
+        h.level_write(L, mg.VEC_U, u)
+        h.level_write(L, mg.VEC_R, r)
+        h.run_stage(mg.STAGE_IR_UPDATE, L, arg=alpha, arg2=s)
+        ro = read(h, L, mg.VEC_R, n, dim, mg.FP64)
+        go = read(h, L, mg.VEC_G, n, dim, prec)
+        uo = read(h, L, mg.VEC_U, n, dim, mg.FP64)
+    check_close(uo, u + alpha * c, np.abs(u) + alpha * np.abs(c), mg.FP64, "update u")
+    assert np.abs(ro - rref).max() <= 1e-9 * np.abs(rref).max()
+    want, over = oracle.scale_ahead_cast(fmt, ro, s)
+    assert not over
+    assert np.array_equal(go, want), (np.abs(go - want).max(), np.count_nonzero(go != want))
+    assert 2.0**13 <= np.abs(go).max() <= 2.0**14
+
+
 @pytest.mark.parametrize("dim,n", [(3, 15), (3, 95), (2, 127), (2, 1023)])
 def test_fp64_residual(oracle, dim, n):
     """IR step 1 (Sec. 4.1): r = b - A u in FP64, with norms."""

@@ -181,3 +181,46 @@ def test_injected_pool_growth_failure():
         u = torch.zeros_like(b)
         assert h.solve(b, u)["status"] == 0
     mg.serve_configure(0, 16)
+
+
+def test_serving_merges_requests_admitted_together(oracle):
+    """With mg_serve_options(1), requests admitted in the same pass whose hierarchies the
+    level-synchronous launches cover run as one merged group.  One slot is held by a long
+    request while six others queue; opening the slots admits the six together.  Every
+    result equals its alone solve bitwise (the merged launches keep each instance's own
+    scale, norms and stopping test) and the oracle within 1e-6."""
+    import torch
+    specs = [(3, 63, "H", 81), (3, 95, "H", 82), (3, 127, "HSD", 83), (3, 63, "H", 84), (3, 47, "H", 85),
+             (3, 95, "H", 86)]
+    refs = [alone(d, n, lad, I.random_rhs(d, n, sd)) for d, n, lad, sd in specs]
+    mg.serve_configure(0, 1)
+    mg.serve_options(True)
+    try:
+        big = mg.Hierarchy(mg.make_params(3, 255, "H", zero_guess=1, pooled=1))
+        hs = [mg.Hierarchy(mg.make_params(d, n, lad, zero_guess=1, pooled=1)) for d, n, lad, sd in specs]
+        bb = torch.from_numpy(I.random_rhs(3, 255, 80)).cuda()
+        ub = torch.zeros_like(bb)
+        bs = [torch.from_numpy(I.random_rhs(d, n, sd)).cuda() for d, n, lad, sd in specs]
+        us = [torch.zeros_like(x) for x in bs]
+        torch.cuda.synchronize()
+        s0 = mg.serve_stats()
+        tb = big.submit(bb, ub)  # holds the only slot for a few milliseconds
+        time.sleep(2e-3)
+        tickets = [h.submit(x, u) for h, x, u in zip(hs, bs, us)]
+        mg.serve_configure(0, 16)  # the six queued requests are admitted in one pass
+        done = wait_all(hs + [big], tickets + [tb])
+        s1 = mg.serve_stats()
+        assert s1["merged_requests"] - s0["merged_requests"] >= 2, s1
+        assert s1["merged_groups"] - s0["merged_groups"] >= 1
+        for (u_ref, r_ref), u, r, (d, n, lad, sd) in zip(refs, us, done[:-1], specs):
+            assert r["status"] == 0 and r["iters"] == r_ref["iters"]
+            assert np.array_equal(u.cpu().numpy(), u_ref), (n, lad)
+            uo, info, _ = oracle.ir_solve(I.random_rhs(d, n, sd))
+            assert np.linalg.norm(u.cpu().numpy() - uo) <= 1e-6 * np.linalg.norm(uo)
+        assert done[-1]["status"] == 0
+        assert sum(r["merged"] for r in done[:-1]) >= 2
+        for h in hs + [big]:
+            h.close()
+    finally:
+        mg.serve_options(False)
+        mg.serve_configure(0, 16)

@@ -358,3 +358,48 @@ def test_guard_restart_continues_from_the_true_residual(oracle, dim, n, lad):
     u2, res2 = gpu_solve(dim, n, lad, b, u0, guard=0, **kw)
     assert res2["guard_restarts"] == 0 and res2["rel_res"] <= 1e-10
     assert res2["rel_res_true"] > 1e-8, res2
+
+
+def test_autotuned_sweeps_per_launch():
+    """fuse_pre = 2: for every 3D level above the coarse tail the autotuner times the
+    pre-smoothing and residual-restriction as one fused pass (two sweeps from zero and the
+    restriction, one launch) against the two launches and keeps the faster; the choice is
+    visible per level (pre_launches 1 or 2) and the solution is the same bit for bit."""
+    import torch
+    n = 127
+    b = torch.from_numpy(I.random_rhs(3, n, 402)).cuda()
+    out, launches = [], []
+    for fp in (0, 2):
+        with mg.Hierarchy(mg.make_params(3, n, "H", zero_guess=1, tune=1, fuse_pre=fp)) as h:
+            u = torch.zeros_like(b)
+            res = h.solve(b, u)
+            assert res["status"] == 0
+            out.append(u.cpu().numpy())
+            launches.append([h.level_info(l)["pre_launches"] for l in range(h.nlev)
+                             if h.level_info(l)["tail_ctas"] == 0])
+    assert np.array_equal(out[0], out[1])
+    assert launches[0] and all(k == 2 for k in launches[0])
+    assert len(launches[1]) == len(launches[0]) and all(k in (1, 2) for k in launches[1])
+
+
+@pytest.mark.parametrize("dim,n,lad", [(3, 127, "H"), (2, 255, "H"), (3, 95, "BSD"), (3, 63, "S")])
+def test_update_fp32_norm_within_1e5(oracle, dim, n, lad):
+    """With a low-precision finest level the fused update sums the squares of r in
+    FP32 (of the scaled FP32 truncation it writes as the next g).  Without the
+    guard the solve's reported ||r||_2 is that sum's: it must match the FP64 norm
+    of the recursive residual left in the hierarchy (MG_VEC_R) within 1e-5, the
+    bound the stopping decision is allowed (reading R11)."""
+    import torch
+    b = I.random_rhs(dim, n, 17)
+    p = mg.make_params(dim, n, lad, zero_guess=1, guard=0)
+    with mg.Hierarchy(p) as h:
+        bd = torch.from_numpy(b).cuda()
+        ud = torch.zeros_like(bd)
+        res = h.solve(bd, ud)
+        r = np.zeros_like(b)
+        h.level_read(h.nlev - 1, mg.VEC_R, r)
+    assert res["status"] == 0
+    rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert abs(res["rel_res"] - rel) <= 1e-5 * rel, (res["rel_res"], rel)
+    # the recursive residual is the oracle's b - A u up to the FP64 drift
+    assert np.linalg.norm(oracle.residual(b, ud.cpu().numpy())) <= 2e-10 * np.linalg.norm(b)
