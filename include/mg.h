@@ -249,7 +249,10 @@ mg_status mg_create_hierarchy(const mg_params* p, void* cuda_stream, mg_hierarch
  * res->status): MG_OK, MG_ERR_NOT_CONVERGED, MG_ERR_NUMERIC, MG_ERR_TIMEOUT
  * (a stencil kernel's bounded wait for its tile copies gave up; see
  * mg_params.wait_polls), MG_ERR_OOM (staging or, for a pooled hierarchy, its
- * arena could not be allocated) or a CUDA error.
+ * arena could not be allocated) or a CUDA error.  A pooled hierarchy takes its
+ * working arena from the pool for the solve, waiting up to 60 s while other
+ * solves hold the budget (then MG_ERR_OOM), and hands it back at the end;
+ * MG_ERR_ADMISSION if the arena exceeds the whole budget.
  * On a failed solve u holds the last iterate.  res may be NULL. */
 mg_status mg_solve(mg_hierarchy* h, const double* b, double* u, mg_result* res);
 
@@ -331,8 +334,11 @@ mg_status mg_serve_options(int32_t merge_groups);
  * different sizes included; res[i].merged = 1.  Otherwise the instances run
  * as concurrent solves on their own streams (res[i].merged = 0).  Each
  * instance keeps its own residual scale, norms and stopping test and stops
- * independently; its result equals its solve alone bit for bit.  Returns
- * MG_OK if every instance converged, else the first failing status. */
+ * independently; its result equals its solve alone bit for bit.  Pooled
+ * hierarchies (mg_params.pooled = 1) take their working arenas from the pool
+ * for the batch and hand them back after it (MG_ERR_OOM when they do not fit
+ * the budget at once).  Returns MG_OK if every instance converged, else the
+ * first failing status. */
 mg_status mg_solve_batch(int32_t count, mg_hierarchy* const* hs, const double* const* b,
                          double* const* u, mg_result* res);
 
@@ -434,7 +440,9 @@ typedef enum { MG_VEC_C = 0, MG_VEC_G = 1, MG_VEC_T = 2, MG_VEC_U = 3, MG_VEC_R 
 
 /* Copies n_l^d interior values (contiguous, x fastest, element type = the
  * vector's storage type: double/float/half/bfloat16) into or out of a level
- * vector.  src/dst may be host or device pointers. */
+ * vector.  src/dst may be host or device pointers.  These and mg_run_stage
+ * need a resident hierarchy (pooled = 0): a pooled one holds no level arrays
+ * outside a solve (MG_ERR_INVALID). */
 mg_status mg_level_write(mg_hierarchy* h, int32_t level, int32_t vec, const void* src);
 mg_status mg_level_read(mg_hierarchy* h, int32_t level, int32_t vec, void* dst);
 mg_status mg_level_info_get(const mg_hierarchy* h, int32_t level, mg_level_info* out);

@@ -275,8 +275,8 @@ constexpr unsigned kWaitTries = 1u << 20;
 __device__ __forceinline__ unsigned march_wait_polls(const KArgs& a) {
     return a.wait_polls > 0 ? (unsigned)(a.wait_polls - 1) : kWaitTries;
 }
-// After a wait of the march gave up: the CTA stops issuing copies, and its
-// leader waits, with the full bound, for the last S planes it issued (march
+// After the leader's own wait gave up: it issues no more copies and waits,
+// with the full bound, for the last S planes it issued (march
 // indices q_last-S+1 .. q_last, stage q % S, phase parity (q / S) & 1: each
 // stage's latest phase; earlier phases of a stage completed before it was
 // reissued), so that no bulk copy is still writing into the CTA's shared
@@ -354,9 +354,11 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     const unsigned cbox = (unsigned)((R + 2) * RB), gbox = (unsigned)(R * 512);
     const int xc = (x0 * (int)sizeof(T) - 16) / UB, xg = x0 * (int)sizeof(T) / UB;  // 16-byte aligned starts
     // plane p (zb-1 <= p <= ze) is the q-th of the march, q = p - zb + 1: stage q % S, phase (q / S) & 1
+    int q_issued = -1;  // leader: the march index of the last plane issued
     auto issue = [&](int p) {
         if (p > ze) return;
         const int q = p - zb + 1, s = q % S;
+        q_issued = q;
         const unsigned bar = bar0 + 8 * s;
         const unsigned st = smem_u32(base + s * SB);
         const bool with_g = NEED_G && p >= zb && p < ze;
@@ -365,11 +367,16 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
         if (with_g) tma_load_3d(st + CB, &maps.g, xg, y0, p + 1, bar);
     };
     // the next plane to wait for: its stage and phase advance one plane at a time.
-    // A wait that gives up marks this thread failed; the CTA learns of it at the
-    // next barrier (__syncthreads_or), stops issuing and drains (drain_copies).
+    // A wait that gives up marks this thread failed (and the solve timed out);
+    // a failed thread waits no more.  The leader reissues a stage only after its
+    // own wait saw that stage's previous copy land, so once its own wait gives
+    // up it issues nothing more and, at the end, drains what it issued
+    // (drain_copies); the other threads march on over whatever the ring holds.
+    // Every thread thus waits at most one full bound in vain, and no copy is
+    // in flight into a stage being reissued or when the CTA exits.
     int wst = 0;
     unsigned wpar = 0;
-    bool failed = false, abort = false;
+    bool failed = false;
     auto wait_next = [&]() {
         if (!failed && !mbar_wait(bar0 + 8 * wst, wpar, march_wait_polls(a))) {
             march_wait_failed(a);
@@ -476,9 +483,8 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     auto step = [&](int z, const P2 (&cm)[RPW][NP], const P2 (&c0)[RPW][NP], P2 (&cp)[RPW][NP],
                     const P2 (&Xm)[RPW][NP], const P2 (&X0)[RPW][NP], P2 (&Xp)[RPW][NP],
                     const P2 (&dm)[RPW][NP], const P2 (&d0)[RPW][NP], P2 (&dp)[RPW][NP]) {
-        // every warp is done with plane z-2's stage, and every wait so far succeeded
-        if (__syncthreads_or(failed ? 1 : 0)) { abort = true; return; }
-        if (leader) issue(z + S - 2);
+        __syncthreads();  // every warp is done with plane z-2's stage
+        if (leader && !failed) issue(z + S - 2);
         if constexpr (MODE == M_RESTRICT && !Q1) {  // the flush of plane z-1 (t - 1 even, >= 2)
             const int tp = z - 1 - zb;
             if (tp >= 2 && !(tp & 1)) coarse_rows((zb >> 1) + (tp >> 1) - 1);
@@ -563,31 +569,20 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
         }
         so = s1;
     };
-    int z = zb;
-    for (; z < ze;) {
+    for (int z = zb; z < ze;) {
         step(z, pa, pb, pc, qa, qb, qc, da, db, dc);
-        if (abort || ++z >= ze) break;
+        if (++z >= ze) break;
         step(z, pb, pc, pa, qb, qc, qa, db, dc, da);
-        if (abort || ++z >= ze) break;
+        if (++z >= ze) break;
         step(z, pc, pa, pb, qc, qa, qb, dc, da, db);
-        if (abort) break;
         ++z;
     }
-    // abort is uniform across the CTA (set from a barrier's result).  The last
-    // plane issued: min(z + S - 3, ze) when step z stopped before its issue,
-    // ze after the whole march.
-    if (!abort) {
-        abort = __syncthreads_or(failed ? 1 : 0) != 0;
-        z = ze;
-        if constexpr (MODE == M_RESTRICT && !Q1) {  // the flush of the march's last plane
-            const int tp = ze - 1 - zb;
-            if (!abort && tp >= 2 && !(tp & 1)) coarse_rows((zb >> 1) + (tp >> 1) - 1);
-        }
+    if constexpr (MODE == M_RESTRICT && !Q1) {  // the flush of the march's last plane
+        __syncthreads();
+        const int tp = ze - 1 - zb;
+        if (tp >= 2 && !(tp & 1)) coarse_rows((zb >> 1) + (tp >> 1) - 1);
     }
-    if (abort && leader) {
-        const int p_last = min(z + S - 3, ze);
-        if (!drain_copies(bar0, S, p_last - zb + 1) && a.err) atomicExch(a.err, 2);
-    }
+    if (leader && failed && !drain_copies(bar0, S, q_issued) && a.err) atomicExch(a.err, 2);
 }
 
 template <int MODE, class T, class TC, int RPW, int OP = 0>
@@ -764,18 +759,20 @@ __device__ __forceinline__ void pre3_body(const KArgs& a, const SweepMaps& maps,
     const int xc = (x0 * (int)sizeof(T) - 16) / UB;
     auto gslot = [&](int p) { return gring + ((p - zb + 2) % SG) * GBs; };   // p >= zb - 2
     auto cslot = [&](int p) { return cring + ((p - zb + 1) % SC) * CBs; };   // p >= zb - 1
+    int q_issued = -1;  // leader: the march index of the last g plane issued
     auto issue = [&](int p) {
         if (p > ze + 1) return;
         const int q = p - zb + 2, s = q % SG;
+        q_issued = q;
         const unsigned bar = bar0 + 8 * s;
         mbar_expect_tx(bar, gbox);
         tma_load_3d(smem_u32(gring + s * GBs), &maps.src, xc, y0 - 2, p + 1, bar);
     };
-    // bounded waits as in sweep3_body: a wait that gives up stops the issuing at
-    // the next barrier, and the leader drains the copies it issued
+    // bounded waits as in sweep3_body: a thread whose wait gave up waits no
+    // more; the leader stops issuing after its own failed wait and drains
     int wst = 0;
     unsigned wpar = 0;
-    bool failed = false, abort = false;
+    bool failed = false;
     auto wait_next = [&]() {
         if (!failed && !mbar_wait(bar0 + 8 * wst, wpar, march_wait_polls(a))) {
             march_wait_failed(a);
@@ -859,11 +856,9 @@ __device__ __forceinline__ void pre3_body(const KArgs& a, const SweepMaps& maps,
         }
     };
 
-    int p = zb - 2;
-    for (; p <= ze + 1; ++p) {
-        // the g slot of p+3 and the c slot of p-1 are free, and every wait so far succeeded
-        if (__syncthreads_or(failed ? 1 : 0)) { abort = true; break; }
-        if (leader) issue(p + 3);
+    for (int p = zb - 2; p <= ze + 1; ++p) {
+        __syncthreads();  // the g slot of p+3 and the c slot of p-1 are free
+        if (leader && !failed) issue(p + 3);
         wait_next();      // g plane p
         // ---- stage A: c on plane p-1, rows y0-1 .. y0+R
         if (p >= zb) {
@@ -927,17 +922,7 @@ __device__ __forceinline__ void pre3_body(const KArgs& a, const SweepMaps& maps,
             for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * qv[k];
         }
     }
-    // abort is uniform across the CTA (set from a barrier's result).  The last
-    // plane issued: min(p + 2, ze + 1) when iteration p stopped before its
-    // issue, ze + 1 after the whole march; march index = plane - zb + 2.
-    if (!abort) {
-        abort = __syncthreads_or(failed ? 1 : 0) != 0;
-        p = ze + 1;
-    }
-    if (abort && leader) {
-        const int p_last = min(p + 2, ze + 1);
-        if (!drain_copies(bar0, SG, p_last - zb + 2) && a.err) atomicExch(a.err, 2);
-    }
+    if (leader && failed && !drain_copies(bar0, SG, q_issued) && a.err) atomicExch(a.err, 2);
 }
 template <class T, class TC>
 __global__ void __launch_bounds__(288, 3) k_pre3(const KArgs a, const __grid_constant__ SweepMaps maps) {
