@@ -135,16 +135,6 @@ template <> struct Pair<float> {
     static __device__ __forceinline__ t mul(t a, t b) { return __fmul2_rn(a, b); }
     static __device__ __forceinline__ t fma(t a, t b, t c) { return __ffma2_rn(a, b, c); }
 };
-// The same operations as two scalar instructions (used where the pair
-// operands would need register moves: the residual-restriction kernel).
-template <class C> struct ScalarPair {
-    using t = typename Pair<C>::t;
-    static __device__ __forceinline__ t mk(C a, C b) { return Pair<C>::mk(a, b); }
-    static __device__ __forceinline__ t splat(C a) { return Pair<C>::mk(a, a); }
-    static __device__ __forceinline__ t add(t a, t b) { return Pair<C>::mk(a.x + b.x, a.y + b.y); }
-    static __device__ __forceinline__ t mul(t a, t b) { return Pair<C>::mk(a.x * b.x, a.y * b.y); }
-    static __device__ __forceinline__ t fma(t a, t b, t c) { return Pair<C>::mk(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
-};
 template <> struct Pair<double> {
     using t = double2;
     static __device__ __forceinline__ t mk(double a, double b) { return make_double2(a, b); }
@@ -154,6 +144,19 @@ template <> struct Pair<double> {
     static __device__ __forceinline__ t fma(t a, t b, t c) {
         return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
     }
+};
+
+// Scalar operations with their rounding spelled out (no contraction).
+template <class C> struct SA;
+template <> struct SA<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <> struct SA<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 };
 
 // The lane's V values of a shared-memory row as V/2 pairs of the arithmetic type.
@@ -222,18 +225,28 @@ __device__ __forceinline__ uint4 pad_mask(int x, int n) {
     return make_uint4(m[0], m[1], m[2], m[3]);
 }
 
-// Full weighting along x of one fine row: q[k] = (r[2k] + 2 r[2k+1] + r[2k+2]) / 4,
-// r[V] taken from the next lane.
+// Full weighting (Sec. 2, the transpose of trilinear interpolation) in integer
+// weights: along each axis 1 2 1, summed as (r[2k] + 2 r[2k+1]) + r[2k+2], and
+// the coarse value scaled by 2^-d once at the end.  Every partial sum is then the
+// one weighted 1/4 1/2 1/4 times a power of two, so the result has the same bits
+// (no partial sum is near the FP32 / FP64 range limits), at two operations per
+// axis instead of three.
+// Along x of one fine row: q[k] = (r[2k] + 2 r[2k+1]) + r[2k+2], r[V] taken from
+// the next lane.
 template <class C, int V, int VH>
 __device__ __forceinline__ void fw_x(const C (&out)[V], int lane, C (&q)[VH]) {
+    using A = SA<C>;
     C rn = __shfl_down_sync(kFull, out[0], 1);
     if (lane == 31) rn = 0;
 #pragma unroll
     for (int k = 0; k < VH; ++k) {
         C r2 = (2 * k + 2 < V) ? out[(2 * k + 2) % V] : rn;
-        q[k] = (C)0.25 * out[2 * k] + (C)0.5 * out[2 * k + 1] + (C)0.25 * r2;
+        q[k] = A::add(A::fma((C)2, out[2 * k + 1], out[2 * k]), r2);
     }
 }
+// One more axis of the weighting: (a + 2 b) + c.
+template <class C>
+__device__ __forceinline__ C fw_121(C a, C b, C c) { return SA<C>::add(SA<C>::fma((C)2, b, a), c); }
 
 // ---------------------------------------------------------------- TMA / mbarrier
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -325,7 +338,7 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     using C = typename Tr<T>::C;
     constexpr bool Q1 = OP == 1;
     static_assert(!Q1 || RPW == 1, "the Q1 sweep keeps one row per warp");
-    using PR = typename std::conditional<MODE == M_RESTRICT, ScalarPair<C>, Pair<C>>::type;
+    using PR = Pair<C>;
     using P2 = typename PR::t;
     constexpr int V = Tr<T>::V;
     constexpr int NP = V / 2;
@@ -453,29 +466,29 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     // Restriction: the coarse rows of coarse plane K from the z-sums that every
     // warp flushed to shared memory after fine plane 2K+2 (t = z - zb even,
     // t >= 2), taken one plane later, after the next plane's barrier: warp w < TJ
-    // forms coarse row J0 + w from tile rows 2w, 2w+1, 2w+2 (y weights 1/4, 1/2,
-    // 1/4).  The flush area is written again only two planes later, after
-    // another barrier, so one barrier per plane serves both.
+    // forms coarse row J0 + w from tile rows 2w, 2w+1, 2w+2 (y weights 1 2 1,
+    // then the scale 1/64 of the integer weights, fw_x).  The flush area is
+    // written again only two planes later, after another barrier, so one barrier
+    // per plane serves both.  Coarse planes are taken in order K = zb/2, zb/2+1, ...
     // The values of a coarse row are split over two warps (halves of each lane's
     // VH values) where VH allows, so that 2 TJ of the TY warps share the work.
-    auto coarse_rows = [&](int K) {
-        constexpr int SPLIT = VH >= 2 ? 2 : 1;
-        constexpr int VS = VH / SPLIT;
-        const int TJ = (R - 1) / 2;
-        if (w < TJ * SPLIT) {
-            const int jr = w / SPLIT, k0 = (w % SPLIT) * VS;
-            const int J = (y0 >> 1) + jr;
-            const C* f0 = reinterpret_cast<const C*>(flush) + ((2 * jr) * 32 + lane) * VH + k0;
-            const C* f1 = f0 + 32 * VH;
-            const C* f2 = f1 + 32 * VH;
-            const int I0 = ((x0 + lane * V) >> 1) + k0;
-            if (lane_in && J < a.nc && K < a.nc && (lane < 31 || x0 + CW >= a.P)) {
-                TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
+    constexpr int SPLIT = VH >= 2 ? 2 : 1;
+    constexpr int VS = VH / SPLIT;
+    const int Jc = (y0 >> 1) + w / SPLIT;
+    const int I0 = ((x0 + lane * V) >> 1) + (w % SPLIT) * VS;
+    const bool cw = MODE == M_RESTRICT && w < ((R - 1) / 2) * SPLIT && lane_in && Jc < a.nc &&
+                    (lane < 31 || x0 + CW >= a.P);
+    const C* f0 = reinterpret_cast<const C*>(flush) + ((2 * (w / SPLIT)) * 32 + lane) * VH + (w % SPLIT) * VS;
+    int Kc = zb >> 1;  // the next coarse plane
+    TC* cd = reinterpret_cast<TC*>(a.dst) + (cw ? (long long)Kc * a.Sc + (long long)Jc * a.Pc + I0 : 0ll);
+    auto coarse_rows = [&]() {
+        if (cw && Kc < a.nc) {
 #pragma unroll
-                for (int k = 0; k < VS; ++k)
-                    if (I0 + k < a.nc) st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
-            }
+            for (int k = 0; k < VS; ++k)
+                if (I0 + k < a.nc) st1(cd + k, SA<C>::mul(fw_121(f0[k], f0[32 * VH + k], f0[64 * VH + k]), (C)(1.0 / 64)));
         }
+        ++Kc;
+        cd += a.Sc;
     };
 
     // One plane: cm / c0 hold planes z-1 / z, cp receives plane z+1 (and the
@@ -487,7 +500,7 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
         if (leader && !failed) issue(z + S - 2);
         if constexpr (MODE == M_RESTRICT && !Q1) {  // the flush of plane z-1 (t - 1 even, >= 2)
             const int tp = z - 1 - zb;
-            if (tp >= 2 && !(tp & 1)) coarse_rows((zb >> 1) + (tp >> 1) - 1);
+            if (tp >= 2 && !(tp & 1)) coarse_rows();
         }
         wait_next();      // plane z+1
         int s1 = so + SB;
@@ -538,15 +551,15 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
         }
         if constexpr (MODE == M_RESTRICT) {
             // z: fine planes 2K, 2K+1, 2K+2 (t = 0, 1, 2 from the range start)
-            // weigh 1/4, 1/2, 1/4; after an even plane t >= 2 the rows' z-sums go
+            // weigh 1 2 1; after an even plane t >= 2 the rows' z-sums go
             // through shared memory and warp w forms coarse row J0 + w from
-            // tile rows 2w, 2w+1, 2w+2 (y weights 1/4, 1/2, 1/4)
+            // tile rows 2w, 2w+1, 2w+2 (coarse_rows)
             const int t = z - zb;
             if (t & 1) {
 #pragma unroll
                 for (int r = 0; r < RPW; ++r)
 #pragma unroll
-                    for (int k = 0; k < VH; ++k) acc[r][k] += (C)0.5 * q[r][k];
+                    for (int k = 0; k < VH; ++k) acc[r][k] = SA<C>::fma((C)2, q[r][k], acc[r][k]);
             } else {
                 if (t >= 2) {  // consumed by coarse_rows after the next barrier (Q1: at once,
                                // which keeps its register pressure down)
@@ -554,17 +567,17 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
                     for (int r = 0; r < RPW; ++r) {
                         C* fl = reinterpret_cast<C*>(flush) + ((w + r * TY) * 32 + lane) * VH;
 #pragma unroll
-                        for (int k = 0; k < VH; ++k) fl[k] = acc[r][k] + (C)0.25 * q[r][k];
+                        for (int k = 0; k < VH; ++k) fl[k] = SA<C>::add(acc[r][k], q[r][k]);
                     }
                     if constexpr (Q1) {
                         __syncthreads();
-                        coarse_rows((zb >> 1) + (t >> 1) - 1);
+                        coarse_rows();
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < RPW; ++r)
 #pragma unroll
-                    for (int k = 0; k < VH; ++k) acc[r][k] = (C)0.25 * q[r][k];
+                    for (int k = 0; k < VH; ++k) acc[r][k] = q[r][k];
             }
         }
         so = s1;
@@ -580,7 +593,7 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     if constexpr (MODE == M_RESTRICT && !Q1) {  // the flush of the march's last plane
         __syncthreads();
         const int tp = ze - 1 - zb;
-        if (tp >= 2 && !(tp & 1)) coarse_rows((zb >> 1) + (tp >> 1) - 1);
+        if (tp >= 2 && !(tp & 1)) coarse_rows();
     }
     if (leader && failed && !drain_copies(bar0, S, q_issued) && a.err) atomicExch(a.err, 2);
 }
@@ -608,17 +621,6 @@ __global__ void __launch_bounds__(SweepLB<MODE, RPW, OP>::kThreads, SweepLB<MODE
 // operands through the read-only path.  They perform the same IEEE operations
 // in the same order as k_sweep3 (finite differences), so a level gives the same
 // bits whichever of the two runs it.
-template <class C> struct SA;
-template <> struct SA<float> {
-    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-};
-template <> struct SA<double> {
-    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-};
 
 template <int MODE, class T>
 __device__ __forceinline__ void dsweep3_body(const KArgs& a, int cta) {
@@ -697,12 +699,11 @@ __device__ __forceinline__ void drestrict3_body(const KArgs& a, int cta) {
 #pragma unroll
         for (int dz = 0; dz < 3; ++dz) {
             const int fy = 2 * J + dy, fz = 2 * K + dz, fx = 2 * I;
-            q[dz] = A::add(A::add(A::mul((C)0.25, resid(fx, fy, fz)), A::mul((C)0.5, resid(fx + 1, fy, fz))),
-                           A::mul((C)0.25, resid(fx + 2, fy, fz)));
+            q[dz] = fw_121(resid(fx, fy, fz), resid(fx + 1, fy, fz), resid(fx + 2, fy, fz));
         }
-        zr[dy] = A::add(A::add(A::mul((C)0.25, q[0]), A::mul((C)0.5, q[1])), A::mul((C)0.25, q[2]));
+        zr[dy] = fw_121(q[0], q[1], q[2]);
     }
-    const C v = A::add(A::add(A::mul((C)0.25, zr[0]), A::mul((C)0.5, zr[1])), A::mul((C)0.25, zr[2]));
+    const C v = A::mul(fw_121(zr[0], zr[1], zr[2]), (C)(1.0 / 64));  // integer weights (fw_x)
     st1(reinterpret_cast<TC*>(a.dst) + offs<3>(I, J, K, a.Pc, a.Sc), v);
 }
 template <class T, class TC>
@@ -729,7 +730,7 @@ __global__ void __launch_bounds__(256) k_drestrict3_batch(const KItem* __restric
 template <class T, class TC>
 __device__ __forceinline__ void pre3_body(const KArgs& a, const SweepMaps& maps, int bx, int by, int bz) {
     using C = typename Tr<T>::C;
-    using PR = ScalarPair<C>;
+    using PR = Pair<C>;
     using P2 = typename PR::t;
     constexpr int V = Tr<T>::V;
     constexpr int NP = V / 2;
@@ -896,12 +897,12 @@ __device__ __forceinline__ void pre3_body(const KArgs& a, const SweepMaps& maps,
         const int t = q - zb;
         if (t & 1) {
 #pragma unroll
-            for (int k = 0; k < VH; ++k) acc[k] += (C)0.5 * qv[k];
+            for (int k = 0; k < VH; ++k) acc[k] = SA<C>::fma((C)2, qv[k], acc[k]);
         } else {
             if (t >= 2) {  // fine planes 2K, 2K+1, 2K+2 done: coarse plane K
                 C* fl = reinterpret_cast<C*>(flush) + (w * 32 + lane) * VH;
 #pragma unroll
-                for (int k = 0; k < VH; ++k) fl[k] = acc[k] + (C)0.25 * qv[k];
+                for (int k = 0; k < VH; ++k) fl[k] = SA<C>::add(acc[k], qv[k]);
                 __syncthreads();
                 const int TJ = (R - 1) / 2;
                 if (w < TJ) {
@@ -914,12 +915,12 @@ __device__ __forceinline__ void pre3_body(const KArgs& a, const SweepMaps& maps,
                         TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)K * a.Sc + (long long)J * a.Pc;
 #pragma unroll
                         for (int k = 0; k < VH; ++k)
-                            if (I0 + k < a.nc) st1(cd + I0 + k, (C)0.25 * f0[k] + (C)0.5 * f1[k] + (C)0.25 * f2[k]);
+                            if (I0 + k < a.nc) st1(cd + I0 + k, SA<C>::mul(fw_121(f0[k], f1[k], f2[k]), (C)(1.0 / 64)));
                     }
                 }
             }
 #pragma unroll
-            for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * qv[k];
+            for (int k = 0; k < VH; ++k) acc[k] = qv[k];
         }
     }
     if (leader && failed && !drain_copies(bar0, SG, q_issued) && a.err) atomicExch(a.err, 2);
@@ -1021,7 +1022,7 @@ __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
             const int t = y - yb;
             if (t & 1) {
 #pragma unroll
-                for (int k = 0; k < VH; ++k) acc[k] += (C)0.5 * q[k];
+                for (int k = 0; k < VH; ++k) acc[k] = SA<C>::fma((C)2, q[k], acc[k]);
             } else {
                 if (t >= 2) {
                     const int J = (yb >> 1) + (t >> 1) - 1;
@@ -1030,11 +1031,11 @@ __global__ void __launch_bounds__(256) k_sweep2(const KArgs a) {
                         TC* cd = reinterpret_cast<TC*>(a.dst) + (long long)J * a.Pc;
 #pragma unroll
                         for (int k = 0; k < VH; ++k)
-                            if (I0 + k < a.nc) st1(cd + I0 + k, acc[k] + (C)0.25 * q[k]);
+                            if (I0 + k < a.nc) st1(cd + I0 + k, SA<C>::mul(SA<C>::add(acc[k], q[k]), (C)(1.0 / 16)));
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < VH; ++k) acc[k] = (C)0.25 * q[k];
+                for (int k = 0; k < VH; ++k) acc[k] = q[k];
             }
         }
     }
