@@ -427,7 +427,11 @@ typedef struct mg_kernel_time {
 /* Runs mg_solve with one launch per kernel (no CUDA graph) and CUDA events
  * around every kernel of every IR step; fills out[0..min(count, max_out)-1]
  * with one record per kernel of the step schedule (in launch order) and sets
- * *count to the schedule length.  Same arguments and result as mg_solve. */
+ * *count to the schedule length.  Before each step the stream is held for a
+ * few tens of microseconds (a bounded sleep, not timed) so that the host has
+ * enqueued the whole step when the device starts it: every event pair then
+ * times its kernel, not the host's launch gaps.  Same arguments and result as
+ * mg_solve. */
 mg_status mg_profile_solve(mg_hierarchy* h, const double* b, double* u, mg_result* res,
                            mg_kernel_time* out, int32_t max_out, int32_t* count);
 

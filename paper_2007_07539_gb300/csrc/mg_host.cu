@@ -1058,6 +1058,10 @@ static int launch_step(mgi_hier& h) {
     cudaStream_t s = h.stream;
     h.ctx.launches += h.step_kernels;
     if (h.prof) {
+        // the device waits while the host enqueues the step (a few us per
+        // kernel and event pair): each event pair then brackets its kernel alone
+        int rc0 = launch_hold(20000 + 8000 * (long long)h.step.size(), s);
+        if (rc0) return rc0;
         for (size_t i = 0; i < h.step.size(); ++i) {
             cudaError_t e = cudaEventRecord(h.prof_ev[2 * i], s);
             if (e != cudaSuccess) return (int)e;

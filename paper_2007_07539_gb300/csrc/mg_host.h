@@ -11,6 +11,10 @@
 
 namespace mgi {
 
+// Holds the stream for about ns nanoseconds (bounded; mg_misc.cu), so that work
+// enqueued behind it is queued before the device reaches it (per-kernel profiling).
+int launch_hold(long long ns, void* stream);
+
 struct Level {
     Geom geo;
     int prec = MG_FP64;

@@ -604,6 +604,25 @@ int launch_finalize(int kind, DevState* st, const double* partials, int nblocks,
     return (int)cudaGetLastError();
 }
 
+// Holds the stream for about ns nanoseconds (one thread sleeping on the
+// global timer; at most 2^16 sleeps of at most 1 us each, so it always ends).
+// The per-kernel profile launches it ahead of each step so that the host has
+// enqueued the step's kernels and events before the device reaches them: the
+// event pairs then time the kernels, not the host's enqueue gaps.
+__global__ void k_hold(long long ns) {
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (int i = 0; i < (1 << 16); ++i) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if ((long long)(t - t0) >= ns) return;
+        __nanosleep(1000);
+    }
+}
+int launch_hold(long long ns, void* stream) {
+    k_hold<<<1, 1, 0, (cudaStream_t)stream>>>(ns);
+    return (int)cudaGetLastError();
+}
+
 // Sets the condition of the device-side IR loop (a WHILE node of the solve
 // graph).  The body-count limit ends the loop even if the state never leaves
 // phases 0/1, so the graph always terminates.
