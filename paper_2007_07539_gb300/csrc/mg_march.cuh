@@ -317,13 +317,13 @@ __device__ __forceinline__ void march_wait_failed(const KArgs& a) {
 // thread into a 6-stage ring and completed on the stage's mbarrier.  The
 // lane's own row of planes z-1, z, z+1 stays in registers (three arrays that
 // swap roles each plane: the loop body is unrolled three times).
-// Launch bounds: 8 warps (9 for the residual-restriction tiles).  One row per
-// warp: 4 CTAs per SM (3 for restriction); two rows per warp: 2 CTAs per SM.
+// Launch bounds: 8 warps (9 for the residual-restriction tiles), 2 CTAs per SM:
+// one row per warp keeps a four-plane window (two planes per step), two rows
+// per warp two three-plane windows, Q1 three in-plane sums per plane.
 template <int MODE, int RPW, int OP = 0>
 struct SweepLB {
     static constexpr int kThreads = MODE == M_RESTRICT ? 288 : 256;
-    // Q1 keeps three in-plane sums per plane in registers: 2 CTAs per SM
-    static constexpr int kMinBlocks = (RPW == 2 || OP == 1) ? 2 : (MODE == M_RESTRICT ? 3 : 4);
+    static constexpr int kMinBlocks = 2;
 };
 // The body takes the CTA's tile coordinates (bx, by, bz) explicitly: the
 // single-grid kernel passes blockIdx, the batched kernel the coordinates of
@@ -346,6 +346,8 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     constexpr int VH = V / 2 > 0 ? V / 2 : 1;
     constexpr int S = sweep3_stages(MODE, RPW);  // planes z-1, z, z+1 in use, z+2 .. z+S-2 in flight
     constexpr bool NEED_G = MODE == M_JACOBI || MODE == M_RESTRICT;
+    // finite differences, one row per warp: two planes per step (see step2)
+    constexpr bool TWO = !Q1 && RPW == 1;
     constexpr int UB = sizeof(T) == 2 ? 4 : 8;  // bytes of one tensor-map unit
     constexpr int RB = kSweepRowBytes;
     if (a.gate && a.st->phase != 0) return;
@@ -356,7 +358,8 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     const int CB = sweep3_cbytes(R);
     const int SB = sweep3_stage_bytes(R, NEED_G);
     unsigned char* flush = base + S * SB;
-    const int flush_bytes = MODE == M_RESTRICT ? R * 32 * VH * (int)sizeof(C) : 0;
+    // restriction: the rows' z-sums (two buffers, alternating, for TWO)
+    const int flush_bytes = MODE == M_RESTRICT ? (TWO ? 2 : 1) * R * 32 * VH * (int)sizeof(C) : 0;
     const unsigned bar0 = smem_u32(flush + (flush_bytes + 15) / 16 * 16);
     const int x0 = bx * a.xstep, x = x0 + lane * V;
     const int y0 = by * a.ystep;
@@ -481,11 +484,12 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     const C* f0 = reinterpret_cast<const C*>(flush) + ((2 * (w / SPLIT)) * 32 + lane) * VH + (w % SPLIT) * VS;
     int Kc = zb >> 1;  // the next coarse plane
     TC* cd = reinterpret_cast<TC*>(a.dst) + (cw ? (long long)Kc * a.Sc + (long long)Jc * a.Pc + I0 : 0ll);
-    auto coarse_rows = [&]() {
+    auto coarse_rows = [&](int buf = 0) {
         if (cw && Kc < a.nc) {
+            const C* f = f0 + buf * (R * 32 * VH);
 #pragma unroll
             for (int k = 0; k < VS; ++k)
-                if (I0 + k < a.nc) st1(cd + k, SA<C>::mul(fw_121(f0[k], f0[32 * VH + k], f0[64 * VH + k]), (C)(1.0 / 64)));
+                if (I0 + k < a.nc) st1(cd + k, SA<C>::mul(fw_121(f[k], f[32 * VH + k], f[64 * VH + k]), (C)(1.0 / 64)));
         }
         ++Kc;
         cd += a.Sc;
@@ -582,18 +586,118 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
         }
         so = s1;
     };
-    for (int z = zb; z < ze;) {
-        step(z, pa, pb, pc, qa, qb, qc, da, db, dc);
-        if (++z >= ze) break;
-        step(z, pb, pc, pa, qb, qc, qa, db, dc, da);
-        if (++z >= ze) break;
-        step(z, pc, pa, pb, qc, qa, qb, dc, da, db);
-        ++z;
-    }
-    if constexpr (MODE == M_RESTRICT && !Q1) {  // the flush of the march's last plane
-        __syncthreads();
-        const int tp = ze - 1 - zb;
-        if (tp >= 2 && !(tp & 1)) coarse_rows();
+    if constexpr (TWO) {
+        // Finite differences, one row per warp, two planes per step: planes z
+        // (t = z - zb even) and z+1 (t odd) from the four-plane window A = z-1,
+        // B = z, C = z+1, D = z+2 of the warp's row, each with the operations of
+        // step -- two independent chains per warp and one barrier per two planes.
+        // The leader issues planes z+4 and z+5 into the stages of z-2 and z-1,
+        // which no warp uses after the barrier.  Restriction: the z-sum of plane
+        // t (even, t >= 2) goes to flush buffer (t / 2) & 1, and its coarse rows
+        // are formed after the next step's barrier; the next write into that
+        // buffer follows one more barrier.
+        // The values of plane z (stage st) of the warp's row.
+        auto row_out = [&](const unsigned char* st, const P2 (&cm)[NP], const P2 (&c0)[NP], const P2 (&cp)[NP],
+                           P2 (&out)[NP]) {
+            P2 ym[NP], yp[NP], g[NP];
+            lds_pairs<T>(st + own[0] - RB, lane, ym);
+            lds_pairs<T>(st + own[0] + RB, lane, yp);
+            const C left = lds_one<T>(st + own[0], lane * V - 1);
+            const C right = lds_one<T>(st + own[0], lane * V + V);
+            if (NEED_G) lds_pairs<T>(st + gown[0], lane, g);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const P2 xs = xsum(c0, left, right, k);
+                const P2 nb = PR::add(PR::add(xs, PR::add(ym[k], yp[k])), PR::add(cm[k], cp[k]));
+                P2 v;
+                if (MODE == M_JACOBI) v = PR::fma(c2, nb, PR::fma(c1, c0[k], PR::mul(c3, g[k])));
+                else if (MODE == M_ZERO2) v = PR::mul(c3, PR::fma(c2, nb, PR::mul(k2, c0[k])));
+                else if (MODE == M_ZERO1) v = PR::mul(c3, c0[k]);
+                else v = PR::fma(h2v, nb, PR::fma(mh6, c0[k], g[k]));
+                out[k] = v;
+            }
+        };
+        // the plane's result: stored (sweeps) or x-restricted (restriction)
+        auto plane_done = [&](int z, const P2 (&out)[NP], C (&q)[VH]) {
+            if constexpr (MODE == M_RESTRICT) {
+                C o1[V];
+#pragma unroll
+                for (int k = 0; k < NP; ++k) { o1[2 * k] = out[k].x; o1[2 * k + 1] = out[k].y; }
+                fw_x<C, V, VH>(o1, lane, q);
+            } else {
+                (void)q;
+                if (do_store[0]) st_pairs<T>(dst_row[0] + (long long)z * a.S, out, wm);
+            }
+        };
+        auto step2 = [&](int z, const P2 (&A)[NP], const P2 (&B)[NP], P2 (&Cn)[NP], P2 (&D)[NP]) {
+            __syncthreads();  // every warp is done with the stages of planes z-2 and z-1
+            if (leader && !failed) {
+                issue(z + S - 2);
+                issue(z + S - 1);
+            }
+            const int t = z - zb;  // even
+            if constexpr (MODE == M_RESTRICT)
+                if (t >= 4) coarse_rows(((t - 2) >> 1) & 1);  // the z-sums of plane z-2
+            const bool two = z + 1 < ze;
+            wait_next();            // plane z+1
+            if (two) wait_next();   // plane z+2 (<= ze)
+            int s1 = so + SB;
+            if (s1 >= S * SB) s1 -= S * SB;
+            int s2 = s1 + SB;
+            if (s2 >= S * SB) s2 -= S * SB;
+            C q0[VH], q1[VH];
+            P2 o0[NP], o1[NP];
+            lds_pairs<T>(base + s1 + own[0], lane, Cn);
+            row_out(base + so, A, B, Cn, o0);
+            plane_done(z, o0, q0);
+            if (two) {
+                lds_pairs<T>(base + s2 + own[0], lane, D);
+                row_out(base + s1, B, Cn, D, o1);
+                plane_done(z + 1, o1, q1);
+            }
+            if constexpr (MODE != M_RESTRICT) {
+                so = s2;
+                return;
+            }
+            // z weights 1 2 1: plane t closes the coarse plane of planes t-2, t-1, t
+            if (t >= 2) {
+                C* fl = reinterpret_cast<C*>(flush) + ((((t >> 1) & 1) * R + w) * 32 + lane) * VH;
+#pragma unroll
+                for (int k = 0; k < VH; ++k) fl[k] = SA<C>::add(acc[0][k], q0[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < VH; ++k) acc[0][k] = q0[k];
+            if (two) {
+#pragma unroll
+                for (int k = 0; k < VH; ++k) acc[0][k] = SA<C>::fma((C)2, q1[k], acc[0][k]);
+            }
+            so = s2;
+        };
+        for (int z = zb; z < ze;) {
+            step2(z, pa[0], pb[0], pc[0], qa[0]);
+            if ((z += 2) >= ze) break;
+            step2(z, pc[0], qa[0], pa[0], pb[0]);
+            z += 2;
+        }
+        if constexpr (MODE == M_RESTRICT) {
+            const int tl = (ze - 1 - zb) & ~1;  // the last step's even plane
+            __syncthreads();
+            if (tl >= 2) coarse_rows((tl >> 1) & 1);
+        }
+    } else {
+        for (int z = zb; z < ze;) {
+            step(z, pa, pb, pc, qa, qb, qc, da, db, dc);
+            if (++z >= ze) break;
+            step(z, pb, pc, pa, qb, qc, qa, db, dc, da);
+            if (++z >= ze) break;
+            step(z, pc, pa, pb, qc, qa, qb, dc, da, db);
+            ++z;
+        }
+        if constexpr (MODE == M_RESTRICT && !Q1) {  // the flush of the march's last plane
+            __syncthreads();
+            const int tp = ze - 1 - zb;
+            if (tp >= 2 && !(tp & 1)) coarse_rows();
+        }
     }
     if (leader && failed && !drain_copies(bar0, S, q_issued) && a.err) atomicExch(a.err, 2);
 }

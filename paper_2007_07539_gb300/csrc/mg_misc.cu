@@ -234,7 +234,8 @@ MarchShape kernel_shape(int dim, int kind, int mode, int prec, int n, int P, int
             s.gx = nchunks;
             s.gy = cdiv(nc, TJ);
             s.smem = bmode == M_PRE ? (size_t)pre3_smem(rows, rows * 32 * VH * (int)cs)
-                                   : (size_t)sweep3_smem(rows, true, rows * 32 * VH * (int)cs, sweep3_stages(M_RESTRICT, s.rpw));
+                                   : (size_t)sweep3_smem(rows, true, (q1 ? 1 : 2) * rows * 32 * VH * (int)cs,
+                                                         sweep3_stages(M_RESTRICT, s.rpw));
             const int res = resident_ctas(dim, kind, mode, prec, prec, s.tx * s.ty, s.smem, s.rpw);
             TileChoice tc;
             if (tz_hint <= 0 && tile_choice_get(dim, kind, mode, prec, n, &tc)) tz_hint = tc.zlen;
