@@ -1414,10 +1414,13 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
         const T* c = reinterpret_cast<const T*>(a.src) + o;
         double* up = a.u64 + o;
         double* rp = a.rw64 + o;
-        const double2 u01 = *reinterpret_cast<const double2*>(up);
-        const double2 u23 = *reinterpret_cast<const double2*>(up + 2);
-        const double2 r01 = *reinterpret_cast<const double2*>(rp);
-        const double2 r23 = *reinterpret_cast<const double2*>(rp + 2);
+        // u and r are read and written once per step (streaming, evict-first in
+        // L2), so that the next step's g, written here, and the levels' vectors
+        // stay in L2 for the kernels that follow
+        const double2 u01 = __ldcs(reinterpret_cast<const double2*>(up));
+        const double2 u23 = __ldcs(reinterpret_cast<const double2*>(up + 2));
+        const double2 r01 = __ldcs(reinterpret_cast<const double2*>(rp));
+        const double2 r23 = __ldcs(reinterpret_cast<const double2*>(rp + 2));
         C c0[Q], ym[Q], yp[Q], zm[Q], zp[Q];
         double uu[Q] = {u01.x, u01.y, u23.x, u23.y};
         double rr[Q] = {r01.x, r01.y, r23.x, r23.y};
@@ -1586,10 +1589,10 @@ __device__ __forceinline__ void update_body(const KArgs& a, int cta, int ncta) {
         }
         }
         }
-        *reinterpret_cast<double2*>(up) = make_double2(uu[0], uu[1]);
-        *reinterpret_cast<double2*>(up + 2) = make_double2(uu[2], uu[3]);
-        *reinterpret_cast<double2*>(rp) = make_double2(rr[0], rr[1]);
-        *reinterpret_cast<double2*>(rp + 2) = make_double2(rr[2], rr[3]);
+        __stcs(reinterpret_cast<double2*>(up), make_double2(uu[0], uu[1]));
+        __stcs(reinterpret_cast<double2*>(up + 2), make_double2(uu[2], uu[3]));
+        __stcs(reinterpret_cast<double2*>(rp), make_double2(rr[0], rr[1]));
+        __stcs(reinterpret_cast<double2*>(rp + 2), make_double2(rr[2], rr[3]));
         if constexpr (kSA) {
             {  // pads of r are 0, so pads of g stay 0
                 // r * 2^k truncated to FP32 from the bit pattern (integer
