@@ -401,6 +401,28 @@ typedef enum {
  * MG_ERR_INVALID for an unknown site or count < 0. */
 mg_status mg_fault_inject(int32_t site, int32_t count);
 
+/* ---------------------------------------------------------------- tile shapes (diagnostics) */
+
+/* Fixes the launch shape of one 3D finite-difference stencil kernel for levels
+ * of n points per dimension (FD operator, op = 0), process-wide, as the
+ * autotuner (mg_params.tune) records its choices; later solves and stage calls
+ * on such levels use it.  The results do not depend on the shape (the kernels
+ * apply the same operations in the same order); this call lets tests and
+ * measurements pin a shape.
+ *   kernel         0 Jacobi sweep, 1 two sweeps from zero, 2 residual-restriction
+ *   prec           mg_prec of the level
+ *   rows_per_warp  -1: forget the shape (the wave model, or the autotuner at the
+ *                  next tuned creation, decides again); 0: the direct kernel (one
+ *                  thread per vector or coarse point); 1: the marching kernel with
+ *                  one row per warp (two planes per step); 2: two rows per warp
+ *                  (sweeps only, n >= 16)
+ *   march_len      planes per CTA along z (sweeps) or coarse planes per CTA
+ *                  (restriction), >= 1; ignored for rows_per_warp 0 and -1
+ * Errors: MG_ERR_INVALID for an unknown kernel or precision, n outside
+ * 3..1290 (the 3D grid limit of mg_params), or a shape outside those above.
+ * Needs no device. */
+mg_status mg_tile_set(int32_t kernel, int32_t prec, int32_t n, int32_t rows_per_warp, int32_t march_len);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Device time of one kernel of the IR step, summed over the steps of a solve. */

@@ -116,6 +116,28 @@ extern "C" mg_status mg_level_read(mg_hierarchy* hh, int32_t level, int32_t vec,
     return MG_OK;
 }
 
+// A tile shape fixed from outside, recorded where the autotuner records its
+// choices (kernel_shape reads them for solves and stage calls alike).
+extern "C" mg_status mg_tile_set(int32_t kernel, int32_t prec, int32_t n, int32_t rows_per_warp, int32_t march_len) {
+    static const int kModes[3] = {M_JACOBI, M_ZERO2, M_RESTRICT};
+    if (kernel < 0 || kernel > 2) SFAIL(MG_ERR_INVALID, "mg_tile_set: kernel must be 0 (Jacobi), 1 (two sweeps from zero) or 2 (restriction)");
+    if (prec < MG_FP64 || prec > MG_BF16) SFAIL(MG_ERR_INVALID, "mg_tile_set: unknown precision");
+    if (n < 3 || n > 1290) SFAIL(MG_ERR_INVALID, "mg_tile_set: n out of range (3..1290)");
+    const bool restr = kernel == 2;
+    if (rows_per_warp < -1 || rows_per_warp > (restr ? 1 : 2) || (rows_per_warp == 2 && n < 16))
+        SFAIL(MG_ERR_INVALID, "mg_tile_set: rows_per_warp out of range");
+    if (rows_per_warp > 0 && (march_len < 1 || march_len > (restr ? (n - 1) / 2 : n)))
+        SFAIL(MG_ERR_INVALID, "mg_tile_set: march_len out of range");
+    if (restr && n < 5) SFAIL(MG_ERR_INVALID, "mg_tile_set: the restriction needs n >= 5");
+    if (rows_per_warp < 0) {
+        tile_choice_set(3, K_SWEEP, kModes[kernel], prec, n, nullptr);
+    } else {
+        const TileChoice c{rows_per_warp, rows_per_warp > 0 ? march_len : 0};
+        tile_choice_set(3, K_SWEEP, kModes[kernel], prec, n, &c);
+    }
+    return MG_OK;
+}
+
 extern "C" mg_status mg_level_info_get(const mg_hierarchy* hh, int32_t level, mg_level_info* out) {
     const mgi_hier* h = reinterpret_cast<const mgi_hier*>(hh);
     if (!h || !out) SFAIL(MG_ERR_INVALID, "NULL argument");

@@ -32,7 +32,7 @@ EXPORTS = ["mg_params_init", "mg_level_count", "mg_last_error", "mg_footprint_by
            "mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
            "mg_serve_configure", "mg_solve_batch", "mg_profile_solve", "mg_level_write", "mg_level_read",
            "mg_level_info_get", "mg_run_stage", "mg_residual_norms_noalloc", "mg_axpy", "mg_describe_cycle",
-           "mg_fault_inject", "mg_serve_stats_get", "mg_serve_options"]
+           "mg_fault_inject", "mg_serve_stats_get", "mg_serve_options", "mg_tile_set"]
 FAULT_ARENA, FAULT_STAGING = 0, 1
 
 
@@ -157,6 +157,8 @@ def lib() -> ctypes.CDLL:
             L.mg_serve_options.restype = ctypes.c_int
             L.mg_fault_inject.argtypes = [i32, i32]
             L.mg_fault_inject.restype = ctypes.c_int
+            L.mg_tile_set.argtypes = [i32, i32, i32, i32, i32]
+            L.mg_tile_set.restype = ctypes.c_int
             for f in ("mg_create_hierarchy", "mg_solve", "mg_submit", "mg_poll", "mg_destroy",
                       "mg_serve_configure", "mg_solve_batch", "mg_level_write", "mg_level_read",
                       "mg_level_info_get", "mg_run_stage", "mg_profile_solve"):
@@ -407,6 +409,16 @@ def axpy(prec: int, a: float, x, y, stream=None) -> None:
     n = x.numel()
     _check(lib().mg_axpy(int(prec), ctypes.c_int64(n), ctypes.c_double(a), ctypes.c_void_p(_ptr(x)),
                          ctypes.c_void_p(_ptr(y)), ctypes.c_void_p(_stream_handle(stream))), "mg_axpy")
+
+
+TILE_JACOBI, TILE_ZERO2, TILE_RESTRICT = 0, 1, 2
+
+
+def tile_set(kernel: int, prec: int, n: int, rows_per_warp: int, march_len: int = 0) -> None:
+    """mg_tile_set: pin the launch shape of a 3D finite-difference stencil kernel on levels of
+    n points (rows_per_warp -1 forgets it, 0 the direct kernel, 1 or 2 marching; march_len
+    planes, or coarse planes for the restriction, per CTA).  Process-wide."""
+    _check(lib().mg_tile_set(int(kernel), int(prec), int(n), int(rows_per_warp), int(march_len)), "mg_tile_set")
 
 
 def fault_inject(site: int, count: int) -> None:

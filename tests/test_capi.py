@@ -107,6 +107,27 @@ def test_fault_inject_validates_its_arguments_without_gpu():
     assert L.mg_fault_inject(mg.FAULT_STAGING, 0) == 0
 
 
+@pytest.mark.parametrize("bad", [(3, mg.FP16, 95, 1, 1), (0, 9, 95, 1, 1), (0, mg.FP16, 2, 1, 1),
+                                 (0, mg.FP16, 1291, 1, 1), (2, mg.FP16, 95, 2, 1), (0, mg.FP16, 15, 2, 1),
+                                 (0, mg.FP16, 95, 1, 0), (0, mg.FP16, 95, 1, 96), (2, mg.FP16, 95, 1, 48),
+                                 (1, mg.FP16, 95, 3, 1), (1, mg.FP16, 95, -2, 1), (2, mg.FP16, 4, 0, 0)])
+def test_tile_set_validates_its_arguments_without_gpu(bad):
+    """mg_tile_set rejects unknown kernels and precisions, grid sizes outside 3..1290 and shapes
+    the kernels do not have (two rows per warp for the restriction or below 16 rows, march
+    lengths outside 1..n, or 1..(n-1)/2 coarse planes), with MG_ERR_INVALID and no device."""
+    with pytest.raises(mg.MGError) as e:
+        mg.tile_set(*bad)
+    assert e.value.status == 2  # MG_ERR_INVALID
+
+
+def test_tile_set_accepts_and_forgets_shapes_without_gpu():
+    """Valid shapes are recorded and forgotten (rows_per_warp = -1) without a device."""
+    for shape in [(0, mg.FP16, 95, 0, 0), (0, mg.FP64, 95, 1, 95), (1, mg.BF16, 17, 2, 1),
+                  (2, mg.FP32, 95, 1, 47), (2, mg.FP16, 5, 0, 0)]:
+        mg.tile_set(*shape)
+        mg.tile_set(shape[0], shape[1], shape[2], -1)
+
+
 def test_params_struct_matches_the_header():
     """The binding's mg_params mirrors include/mg.h: the C size (compiled with gcc)
     equals ctypes' size, and the defaults of the new fields."""

@@ -144,6 +144,50 @@ def test_residual_restriction(oracle, case):
     check_rounded(oracle, out, ref, mag, pc, "restrict", k=64)
 
 
+TILE_CASES = [(k, n, p) for k in (0, 1, 2) for n in (17, 47, 95) for p in (mg.FP16, mg.FP64)]
+
+
+@pytest.mark.parametrize("case", TILE_CASES,
+                         ids=lambda c: f"{['jacobi', 'zero2', 'restrict'][c[0]]}-n{c[1]}-{['fp64', 'fp32', 'fp16', 'bf16'][c[2]]}")
+def test_tile_shapes_give_the_same_bits(oracle, case):
+    """Every launch shape of a 3D stencil kernel (mg_tile_set) gives the same bits: the direct
+    kernel, one row per warp marching two planes per step (march lengths 1, 2, 3 and whole:
+    single-plane last steps, odd and even plane counts), two rows per warp; and the oracle
+    (Sec. 4.2 smoother, Alg. 1's residual restriction)."""
+    kernel, n, prec = case
+    dim, nc = 3, (n - 1) // 2
+    zmax = nc if kernel == 2 else n
+    shapes = [(0, 0), (1, 1), (1, 2), (1, 3), (1, zmax)]
+    if kernel != 2:
+        shapes += [(2, 1), (2, 2), (2, 5), (2, zmax)]
+    stage = [mg.STAGE_JACOBI, mg.STAGE_JACOBI_ZERO2, mg.STAGE_RESTRICT][kernel]
+    outs = []
+    try:
+        for rpw, z in shapes:
+            mg.tile_set(kernel, prec, n, rpw, z)
+            with hier(dim, n, prec) as h:
+                L = h.nlev - 1
+                c = write(h, L, mg.VEC_C, rnd(dim, n, 21, cscale(dim, n, prec)), prec)
+                g = write(h, L, mg.VEC_G, rnd(dim, n, 22, gscale(dim, n, prec)), prec)
+                h.run_stage(stage, L)
+                outs.append(read(h, L - 1, mg.VEC_G, nc, dim, prec) if kernel == 2 else read(h, L, mg.VEC_C, n, dim, prec))
+    finally:
+        mg.tile_set(kernel, prec, n, -1)
+    for (rpw, z), o in zip(shapes[1:], outs[1:]):
+        assert np.array_equal(o, outs[0]), (rpw, z, np.count_nonzero(o != outs[0]))
+    if kernel == 0:
+        ref = oracle.jacobi(g, c, OMEGA)
+        mag = np.abs(c) + OMEGA * dinv(dim, n) * (np.abs(g) + oracle.apply_A(c, absmode=True))
+    elif kernel == 1:
+        ref = oracle.jacobi(g, oracle.jacobi(g, np.zeros_like(g), OMEGA), OMEGA)
+        c1 = OMEGA * dinv(dim, n) * np.abs(g)
+        mag = c1 + OMEGA * dinv(dim, n) * (np.abs(g) + oracle.apply_A(c1, absmode=True))
+    else:
+        ref = oracle.restrict(oracle.residual(g, c))
+        mag = oracle.restrict(np.abs(g) + oracle.apply_A(c, absmode=True))
+    check_close(outs[0], ref, mag, prec, "tile shapes")
+
+
 @pytest.mark.parametrize("case", [c for c in RCASES if c[0] == 3], ids=rids)
 def test_one_pass_presmoothing_and_restriction(oracle, case):
     """Alg. 1's pre-smoothing and residual restriction in one pass (temporal blocking): c = two sweeps from zero on g,
