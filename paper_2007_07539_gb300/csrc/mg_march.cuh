@@ -318,8 +318,8 @@ __device__ __forceinline__ void march_wait_failed(const KArgs& a) {
 // lane's own row of planes z-1, z, z+1 stays in registers (three arrays that
 // swap roles each plane: the loop body is unrolled three times).
 // Launch bounds: 8 warps (9 for the residual-restriction tiles), 2 CTAs per SM:
-// one row per warp keeps a four-plane window (two planes per step), two rows
-// per warp two three-plane windows, Q1 three in-plane sums per plane.
+// each of a warp's one or two rows keeps a four-plane window (finite
+// differences, two planes per step), Q1 three in-plane sums per plane.
 template <int MODE, int RPW, int OP = 0>
 struct SweepLB {
     static constexpr int kThreads = MODE == M_RESTRICT ? 288 : 256;
@@ -346,8 +346,8 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
     constexpr int VH = V / 2 > 0 ? V / 2 : 1;
     constexpr int S = sweep3_stages(MODE, RPW);  // planes z-1, z, z+1 in use, z+2 .. z+S-2 in flight
     constexpr bool NEED_G = MODE == M_JACOBI || MODE == M_RESTRICT;
-    // finite differences, one row per warp: two planes per step (see step2)
-    constexpr bool TWO = !Q1 && RPW == 1;
+    // finite differences: two planes per step (see step2)
+    constexpr bool TWO = !Q1;
     constexpr int UB = sizeof(T) == 2 ? 4 : 8;  // bytes of one tensor-map unit
     constexpr int RB = kSweepRowBytes;
     if (a.gate && a.st->phase != 0) return;
@@ -587,24 +587,24 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
         so = s1;
     };
     if constexpr (TWO) {
-        // Finite differences, one row per warp, two planes per step: planes z
-        // (t = z - zb even) and z+1 (t odd) from the four-plane window A = z-1,
-        // B = z, C = z+1, D = z+2 of the warp's row, each with the operations of
-        // step -- two independent chains per warp and one barrier per two planes.
+        // Finite differences, two planes per step: planes z (t = z - zb even)
+        // and z+1 (t odd) from the four-plane window A = z-1, B = z, C = z+1,
+        // D = z+2 of each of the warp's rows, each with the operations of step --
+        // twice the independent chains per warp and one barrier per two planes.
         // The leader issues planes z+4 and z+5 into the stages of z-2 and z-1,
         // which no warp uses after the barrier.  Restriction: the z-sum of plane
         // t (even, t >= 2) goes to flush buffer (t / 2) & 1, and its coarse rows
         // are formed after the next step's barrier; the next write into that
         // buffer follows one more barrier.
         // The values of plane z (stage st) of the warp's row.
-        auto row_out = [&](const unsigned char* st, const P2 (&cm)[NP], const P2 (&c0)[NP], const P2 (&cp)[NP],
+        auto row_out = [&](int r, const unsigned char* st, const P2 (&cm)[NP], const P2 (&c0)[NP], const P2 (&cp)[NP],
                            P2 (&out)[NP]) {
             P2 ym[NP], yp[NP], g[NP];
-            lds_pairs<T>(st + own[0] - RB, lane, ym);
-            lds_pairs<T>(st + own[0] + RB, lane, yp);
-            const C left = lds_one<T>(st + own[0], lane * V - 1);
-            const C right = lds_one<T>(st + own[0], lane * V + V);
-            if (NEED_G) lds_pairs<T>(st + gown[0], lane, g);
+            lds_pairs<T>(st + own[r] - RB, lane, ym);
+            lds_pairs<T>(st + own[r] + RB, lane, yp);
+            const C left = lds_one<T>(st + own[r], lane * V - 1);
+            const C right = lds_one<T>(st + own[r], lane * V + V);
+            if (NEED_G) lds_pairs<T>(st + gown[r], lane, g);
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 const P2 xs = xsum(c0, left, right, k);
@@ -618,7 +618,7 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
             }
         };
         // the plane's result: stored (sweeps) or x-restricted (restriction)
-        auto plane_done = [&](int z, const P2 (&out)[NP], C (&q)[VH]) {
+        auto plane_done = [&](int r, int z, const P2 (&out)[NP], C (&q)[VH]) {
             if constexpr (MODE == M_RESTRICT) {
                 C o1[V];
 #pragma unroll
@@ -626,10 +626,10 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
                 fw_x<C, V, VH>(o1, lane, q);
             } else {
                 (void)q;
-                if (do_store[0]) st_pairs<T>(dst_row[0] + (long long)z * a.S, out, wm);
+                if (do_store[r]) st_pairs<T>(dst_row[r] + (long long)z * a.S, out, wm);
             }
         };
-        auto step2 = [&](int z, const P2 (&A)[NP], const P2 (&B)[NP], P2 (&Cn)[NP], P2 (&D)[NP]) {
+        auto step2 = [&](int z, const P2 (&A)[RPW][NP], const P2 (&B)[RPW][NP], P2 (&Cn)[RPW][NP], P2 (&D)[RPW][NP]) {
             __syncthreads();  // every warp is done with the stages of planes z-2 and z-1
             if (leader && !failed) {
                 issue(z + S - 2);
@@ -645,15 +645,22 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
             if (s1 >= S * SB) s1 -= S * SB;
             int s2 = s1 + SB;
             if (s2 >= S * SB) s2 -= S * SB;
-            C q0[VH], q1[VH];
-            P2 o0[NP], o1[NP];
-            lds_pairs<T>(base + s1 + own[0], lane, Cn);
-            row_out(base + so, A, B, Cn, o0);
-            plane_done(z, o0, q0);
+            C q0[VH], q1[VH];  // restriction (one row per warp): the planes' x-restricted residuals
+#pragma unroll
+            for (int r = 0; r < RPW; ++r) {
+                P2 o0[NP];
+                lds_pairs<T>(base + s1 + own[r], lane, Cn[r]);
+                row_out(r, base + so, A[r], B[r], Cn[r], o0);
+                plane_done(r, z, o0, q0);
+            }
             if (two) {
-                lds_pairs<T>(base + s2 + own[0], lane, D);
-                row_out(base + s1, B, Cn, D, o1);
-                plane_done(z + 1, o1, q1);
+#pragma unroll
+                for (int r = 0; r < RPW; ++r) {
+                    P2 o1[NP];
+                    lds_pairs<T>(base + s2 + own[r], lane, D[r]);
+                    row_out(r, base + s1, B[r], Cn[r], D[r], o1);
+                    plane_done(r, z + 1, o1, q1);
+                }
             }
             if constexpr (MODE != M_RESTRICT) {
                 so = s2;
@@ -674,9 +681,9 @@ __device__ __forceinline__ void sweep3_body(const KArgs& a, const SweepMaps& map
             so = s2;
         };
         for (int z = zb; z < ze;) {
-            step2(z, pa[0], pb[0], pc[0], qa[0]);
+            step2(z, pa, pb, pc, qa);
             if ((z += 2) >= ze) break;
-            step2(z, pc[0], qa[0], pa[0], pb[0]);
+            step2(z, pc, qa, pa, pb);
             z += 2;
         }
         if constexpr (MODE == M_RESTRICT) {
