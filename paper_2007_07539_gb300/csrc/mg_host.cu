@@ -705,7 +705,7 @@ static void plan_tail(mgi_hier& h, bool disabled, bool probe) {
 // from zero, residual-restriction, Jacobi on each level above the coarse
 // tail -- time candidate tile shapes (rows per warp 1/2; the model's march
 // length, half and double it; best of five runs; a candidate must beat the
-// model's shape by 3%) on this hierarchy's level
+// model's shape by 8%) on this hierarchy's level
 // arrays (their contents at creation do not matter; pads stay zero) and keep
 // the fastest.
 // The choice is process-wide per (kernel, type, level size): later
@@ -721,19 +721,25 @@ static void autotune(mgi_hier& h) {
     }
     // Inside a solve the finest levels stream from DRAM while the small ones
     // stay in L2: kernels on levels whose arrays exceed a quarter of L2 are
-    // timed after a 256 MB L2 flush, the others warm.
+    // timed after reading 256 MB (an L2 eviction without write-back), the
+    // others warm.
     void* flush = nullptr;
     const size_t kFlush = 256u << 20;
-    if (cudaMalloc(&flush, kFlush) != cudaSuccess) {
+    if (cudaMalloc(&flush, kFlush + 256) != cudaSuccess) {
         cudaGetLastError();
         flush = nullptr;
+    } else if (cudaMemsetAsync(flush, 1, kFlush + 256, s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(flush);
+        flush = nullptr;
     }
+    unsigned* sink = flush ? reinterpret_cast<unsigned*>(static_cast<char*>(flush) + kFlush) : nullptr;
     bool cold = false;
     auto time_op = [&](const Op& op) -> float {
         float best = 1e30f;
         if (mgi_run_op(h, op, s)) return best;  // warm-up (and launch check)
         for (int rep = 0; rep < 5; ++rep) {
-            if (cold && flush) cudaMemsetAsync(flush, rep + 1, kFlush, s);
+            if (cold && flush) launch_l2_evict(flush, kFlush, sink, s);
             cudaEventRecord(ea, s);
             if (mgi_run_op(h, op, s)) return 1e30f;
             cudaEventRecord(eb, s);
@@ -769,9 +775,10 @@ static void autotune(mgi_hier& h) {
             const int zmax = coarse_out ? (n - 1) / 2 : n;
             TileChoice best{base.sh.rpw, z0};
             float tbest = time_op(base);
-            // a candidate replaces the model's shape only when clearly faster
-            // (timing noise of short kernels is a few percent)
-            tbest *= 0.97f;
+            // a candidate replaces the model's shape only when clearly faster:
+            // timed alone, shapes within a few percent of each other order
+            // differently inside a solve
+            tbest *= 0.92f;
             if (h.p.op == 0 && mode != M_PRE && base.sh.rpw != 0 && n <= 255) {  // the direct kernel
                 const TileChoice c{0, 0};
                 tile_choice_set(3, K_SWEEP, kmode, lv.prec, n, &c);

@@ -11,6 +11,9 @@
 
 namespace mgi {
 
+// Evicts L2 by reading `bytes` (> the L2 size) of buf; sink: 4 bytes of device
+// scratch (mg_misc.cu).
+int launch_l2_evict(const void* buf, size_t bytes, unsigned* sink, void* stream);
 // Holds the stream for about ns nanoseconds (bounded; mg_misc.cu), so that work
 // enqueued behind it is queued before the device reaches it (per-kernel profiling).
 int launch_hold(long long ns, void* stream);
