@@ -226,20 +226,22 @@ __device__ void t_prolong(const TailOp& op, const TailSm& x) {
 }
 
 // ---- exact base solve c = A0^-1 g with the dense FP64 inverse (m = n^d)
+// One warp per row: lane l sums the products of columns l, l+32, ... in order,
+// then lane 0 takes the lanes' sums by a fixed shuffle tree (deterministic) --
+// the row's loads are in flight together and the FP64 chain is short, where a
+// thread per row waited on a chain of m/2 dependent FMAs.
 template <int DIM, class T, bool CL>
 __device__ void t_coarse(const TailOp& op, const TailSm& x, const double* minv, int m) {
     int lo, hi;
     owned<CL>(x, m, op.sh, lo, hi);
-    for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p = lo + wid; p < hi; p += nw) {
         const double* row = minv + (long long)p * m;
-        double s0 = 0.0, s1 = 0.0;
-        int q = 0;
-        for (; q + 2 <= m; q += 2) {
-            s0 = fma(__ldg(row + q), (double)dget<T, CL>(x, op.g, op.sh, q), s0);
-            s1 = fma(__ldg(row + q + 1), (double)dget<T, CL>(x, op.g, op.sh, q + 1), s1);
-        }
-        for (; q < m; ++q) s0 = fma(__ldg(row + q), (double)dget<T, CL>(x, op.g, op.sh, q), s0);
-        lput<T>(x, op.dst, p - lo, s0 + s1);
+        double s = 0.0;
+        for (int q = lane; q < m; q += 32) s = fma(__ldg(row + q), (double)dget<T, CL>(x, op.g, op.sh, q), s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
+        if (lane == 0) lput<T>(x, op.dst, p - lo, s);
     }
 }
 
@@ -276,6 +278,7 @@ __device__ void t_copy(const TailOp& op, const TailSm& x, bool load) {
     owned<CL>(x, npoints<DIM>(n), op.sh, lo, hi);
     T* s = reinterpret_cast<T*>(tail_dsm + (load ? op.dst : op.src));
     T* g = reinterpret_cast<T*>(op.gptr);
+#pragma unroll 4
     for (int p = lo + threadIdx.x; p < hi; p += blockDim.x) {
         int i, j, k;
         decode<DIM>(p, n, op.mn, i, j, k);
@@ -332,6 +335,14 @@ __device__ __forceinline__ void tail_body(const TailOp* __restrict__ prog, int n
     // gate: every CTA of the cluster reads the same state (written before the
     // launch), so all of them return here or none
     if (gate && st->phase != 0) return;
+    // the base solve's dense inverse, read row by row by a few threads late in
+    // the program: fetched into this SM's L1 now, while the first stages run
+    // (at most 512 KB; only the matrix's own lines)
+    if (minv && m0 > 0) {
+        const long long lines = ((long long)m0 * m0 * 8 + 127) / 128;
+        for (long long l = threadIdx.x; l < lines && l < 4096; l += blockDim.x)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(minv) + l * 128));
+    }
     unsigned char* sm = tail_dsm;
     __shared__ TailOp chunk[kTailChunk];             // the next stages, staged once per chunk
     __shared__ unsigned char* rbase[kTailMaxCluster];  // every CTA's dynamic shared memory
