@@ -597,7 +597,8 @@ int mgi_run_op(mgi_hier& h, const Op& op, cudaStream_t s) {
             return launch_finalize(op.fin_kind, h.st, h.partials, op.nblocks, s);
         case OP_TAIL:
             return launch_tail(h.dim, h.tail_prec, h.tail_prog + op.prog_off, op.prog_len, h.minv, h.m0, op.a.st,
-                               op.a.gate, h.tail_smem, h.tail_cs, s);
+                               op.a.gate, h.tail_smem, h.tail_cs, s,
+                               op.prog_len > 0 ? &h.tail_host[op.prog_off] : nullptr);
     }
     return (int)cudaErrorInvalidValue;
 }

@@ -60,9 +60,12 @@ int launch_tail_batch(int dim, int uniform_prec, const TailItem* items, int nite
 }
 
 int launch_tail(int dim, int uniform_prec, const TailOp* prog, int nops, const double* minv, int m0,
-                const DevState* st, int gate, size_t smem, int cs, void* stream) {
+                const DevState* st, int gate, size_t smem, int cs, void* stream, const TailOp* first) {
+    TailOp f0{};
+    if (first) f0 = *first;
+    else f0.kind = -1;  // none: the kernel runs every stage from the staged program
     return launch_clustered(pick_tail(dim, uniform_prec, cs), 1, cs, smem, (cudaStream_t)stream, prog, nops, minv,
-                            m0, st, gate, cs);
+                            m0, st, gate, cs, f0);
 }
 
 // Whether a cluster of cs CTAs of the tail kernel with smem bytes of dynamic

@@ -72,7 +72,7 @@ int launch_tail_batch(int dim, int uniform_prec, const TailItem* items, int nite
 // The tail kernels of one dimension, one CTA (CL false) or a cluster (CL
 // true), for a uniform tail storage type or -1 (mixed precisions); each
 // (DIM, CL) is instantiated in its own translation unit.
-using TailFn = void (*)(const TailOp*, int, const double*, int, const DevState*, int, int);
+using TailFn = void (*)(const TailOp*, int, const double*, int, const DevState*, int, int, TailOp);
 using TailBatchFn = void (*)(const TailItem*, int);
 template <int DIM, bool CL>
 TailFn tail_kernel(int uniform_prec);
@@ -82,8 +82,10 @@ TailBatchFn tail_batch_kernel(int uniform_prec);
 // uniform_prec: the storage type of every tail level (selects a kernel
 // specialised for it), or -1 for a mixed-precision tail.
 // cs: CTAs of the thread-block cluster that holds the tail levels (1: one CTA).
+// first: host copy of prog[0] (or nullptr), passed by value so that a one-CTA
+// tail starts its first load without waiting for the program's own fetch.
 int launch_tail(int dim, int uniform_prec, const TailOp* prog, int nops, const double* minv, int m0,
-                const DevState* st, int gate, size_t smem, int cs, void* stream);
+                const DevState* st, int gate, size_t smem, int cs, void* stream, const TailOp* first = nullptr);
 // Active clusters of cs tail CTAs with smem bytes each this device can hold (0: none / no device).
 int tail_cluster_ok(int dim, int uniform_prec, int cs, size_t smem);
 

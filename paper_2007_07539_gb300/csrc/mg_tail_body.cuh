@@ -331,7 +331,7 @@ __device__ void run_tail_op_t(const TailOp& op, const TailSm& sm, const double* 
 
 template <int DIM, class TU, bool CL>
 __device__ __forceinline__ void tail_body(const TailOp* __restrict__ prog, int nops, const double* __restrict__ minv,
-                                          int m0, const DevState* st, int gate, int cs) {
+                                          int m0, const DevState* st, int gate, int cs, const TailOp* first) {
     // gate: every CTA of the cluster reads the same state (written before the
     // launch), so all of them return here or none
     if (gate && st->phase != 0) return;
@@ -360,24 +360,31 @@ __device__ __forceinline__ void tail_body(const TailOp* __restrict__ prog, int n
         rbase[0] = sm;
         __syncthreads();
     }
+    auto run = [&](const TailOp& op) {
+        if constexpr (!std::is_void<TU>::value) {
+            run_tail_op_t<DIM, TU, TU, CL>(op, x, minv, m0);
+        } else {
+            switch (op.prec) {
+                case MG_FP64: run_tail_op_t<DIM, double, void, CL>(op, x, minv, m0); break;
+                case MG_FP32: run_tail_op_t<DIM, float, void, CL>(op, x, minv, m0); break;
+                case MG_FP16: run_tail_op_t<DIM, __half, void, CL>(op, x, minv, m0); break;
+                default: run_tail_op_t<DIM, __nv_bfloat16, void, CL>(op, x, minv, m0); break;
+            }
+        }
+    };
+    // A one-CTA tail runs its first stage (the load of its top level's g) from
+    // the copy passed as a kernel parameter, with the program's staging: both
+    // sets of global loads are in flight together, and one barrier ends both.
+    const bool pre = !CL && first && first->kind == TK_LOAD && nops > 0;
     for (int s0 = 0; s0 < nops; s0 += kTailChunk) {
         const int cnt = min(kTailChunk, nops - s0);
         const unsigned long long* src = reinterpret_cast<const unsigned long long*>(prog + s0);
         unsigned long long* dst = reinterpret_cast<unsigned long long*>(chunk);
         for (int w = threadIdx.x; w < cnt * kTailOpWords; w += blockDim.x) dst[w] = __ldg(src + w);
+        if (s0 == 0 && pre) run(*first);
         __syncthreads();
-        for (int s = 0; s < cnt; ++s) {
-            const TailOp& op = chunk[s];
-            if constexpr (!std::is_void<TU>::value) {
-                run_tail_op_t<DIM, TU, TU, CL>(op, x, minv, m0);
-            } else {
-                switch (op.prec) {
-                    case MG_FP64: run_tail_op_t<DIM, double, void, CL>(op, x, minv, m0); break;
-                    case MG_FP32: run_tail_op_t<DIM, float, void, CL>(op, x, minv, m0); break;
-                    case MG_FP16: run_tail_op_t<DIM, __half, void, CL>(op, x, minv, m0); break;
-                    default: run_tail_op_t<DIM, __nv_bfloat16, void, CL>(op, x, minv, m0); break;
-                }
-            }
+        for (int s = (s0 == 0 && pre) ? 1 : 0; s < cnt; ++s) {
+            run(chunk[s]);
             // the stage's stores are visible to every CTA before the next stage;
             // after the last stage no CTA leaves while another may read its memory
             if constexpr (CL) cgrp::this_cluster().sync();
@@ -389,15 +396,16 @@ __device__ __forceinline__ void tail_body(const TailOp* __restrict__ prog, int n
 template <int DIM, class TU, bool CL>
 __global__ void __launch_bounds__(kTailThreads) k_tail(const TailOp* __restrict__ prog, int nops,
                                                         const double* __restrict__ minv, int m0,
-                                                        const DevState* st, int gate, int cs) {
-    tail_body<DIM, TU, CL>(prog, nops, minv, m0, st, gate, cs);
+                                                        const DevState* st, int gate, int cs,
+                                                        const __grid_constant__ TailOp first) {
+    tail_body<DIM, TU, CL>(prog, nops, minv, m0, st, gate, cs, &first);
 }
 // Batched: one CTA (cluster of cs CTAs) per instance, each with its own
 // program, base inverse and state.
 template <int DIM, class TU, bool CL>
 __global__ void __launch_bounds__(kTailThreads) k_tail_batch(const TailItem* __restrict__ items, int cs) {
     const TailItem& it = items[blockIdx.x / cs];
-    tail_body<DIM, TU, CL>(it.prog, it.nops, it.minv, it.m0, it.st, 1, cs);
+    tail_body<DIM, TU, CL>(it.prog, it.nops, it.minv, it.m0, it.st, 1, cs, nullptr);
 }
 
 // The kernel of one uniform tail storage type (-1: mixed precisions).
