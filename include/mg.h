@@ -135,7 +135,7 @@ typedef struct mg_params {
                            requires fuse_pre = 0 */
     int32_t scale_ahead;/* 1 (default): with scaling = 1 and a non-FP64 finest level, the fused
                            IR update (Alg. 2's solution and residual updates) also writes the next step's g =
-                           cast(r * 2^k) (line 4), with 2^k = 2^sigma_log2 / 2^e and 2^e the
+                           cast(r * 2^k) (Alg. 2's residual scaling), with 2^k = 2^sigma_log2 / 2^e and 2^e the
                            power of two just above the previous ||r||_inf, so the separate
                            scale-and-cast pass over the FP64 residual is skipped; alpha is
                            then 2^-k, a power of two within a factor of two of the previous

@@ -615,9 +615,9 @@ double or_norminf(size_t N, const double *v) {
  *   while the stopping test fails:
  *     alpha = ||r|| (inf-norm, 2-norm, or 1 without scaling)
  *     g = (1/alpha) r                       (Alg. 2's residual scaling)
- *     c = one multigrid cycle for A c = g   (line 5)
- *     u = u + alpha c                       (line 6)
- *     r = r - alpha A c                     (line 7)
+ *     c = one multigrid cycle for A c = g   (Alg. 2's correction by Alg. 1)
+ *     u = u + alpha c                       (Alg. 2's solution update)
+ *     r = r - alpha A c                     (Alg. 2's residual update)
  * When the recursive residual passes the test, b - A u is recomputed; if it
  * fails the test the loop continues from that true residual.
  * history (optional, max_iter+1 entries) receives ||r||_2/||b||_2 before each

@@ -10,7 +10,7 @@ namespace mgi {
 
 // ---------------------------------------------------------------- norms and IR control
 // Reduces per-CTA partials in a fixed order (deterministic), then applies the
-// stopping test of Alg. 2 and sets alpha for the next step (line 4):
+// stopping test of Alg. 2 and sets alpha for the next step's residual scaling:
 // alpha = ||r||_inf / sigma (scaling 1), ||r||_2 / sigma (scaling 2) or 1.
 // kind: FIN_INIT after r = b - A u0, FIN_STEP after an update (partials of
 // stride 2), FIN_GUARD after the true residual, 3 = report only.
